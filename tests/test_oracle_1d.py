@@ -1,0 +1,264 @@
+"""Pins of the one-dimensional CPU oracle against facts the paper and mathematics fix.
+
+Each test below would fail under a plausible mistake in the oracle: a wrong D_h scale or
+sign (eigenvalues), a transposed D_h diag(w) (manufactured-solution order), a dropped
+eps^2 term or a wrong coarse/fine factor (closed forms of Lemma 3.1 / Lemma 3.4), a wrong
+sign or index in the Parareal correction (closed form, finite-step exactness), or a
+non-converged Newton (residual and energy decay).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ch_inputs
+from oracle import oracle1d as o
+
+
+def dense_dh(n):
+    """D_h as a dense matrix, probed column by column through the oracle."""
+    eye = np.eye(n)
+    return np.stack([o.dh_apply(eye[:, j]) for j in range(n)], axis=1)
+
+
+def sine_mode(n, p):
+    x = np.arange(1, n + 1) / (n + 1)
+    return np.sin(p * np.pi * x)
+
+
+def mu(n, p):
+    """-lambda_p, lambda_p = (2/h^2)(cos(p pi/(N_x - 1)) - 1), N_x = n + 2 (below Eq. 3.2)."""
+    h = 1.0 / (n + 1)
+    return -(2.0 / h ** 2) * (math.cos(p * math.pi / (n + 1)) - 1.0)
+
+
+# ------------------------------------------------------------------------- D_h
+
+
+@pytest.mark.parametrize("n", [5, 16, 33])
+def test_dh_eigenvalues_match_paper_formula(n):
+    D = dense_dh(n)
+    assert np.allclose(D, D.T, rtol=0, atol=0)
+    ev = np.sort(np.linalg.eigvalsh(D))
+    lam = np.sort([-mu(n, p) for p in range(1, n + 1)])
+    assert np.max(np.abs(ev - lam) / np.abs(lam)) < 1e-12
+    assert np.all(ev < 0)
+
+
+def test_dh_sine_modes_are_eigenvectors():
+    n = 40
+    for p in (1, 7, 40):
+        v = sine_mode(n, p)
+        assert np.allclose(o.dh_apply(v), -mu(n, p) * v, rtol=0, atol=1e-9 * mu(n, p))
+
+
+# ---------------------------------------------------------------- banded solver
+
+
+def test_band_solve_matches_dense_with_pivoting():
+    rng = np.random.default_rng(3)
+    n, kl, ku = 30, 2, 2
+    A = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - kl), min(n, i + ku + 1)):
+            A[i, j] = rng.standard_normal()
+    A[np.arange(n), np.arange(n)] *= 1e-3  # forces row exchanges
+    b = rng.standard_normal(n)
+    w = 2 * kl + ku + 1
+    ab = np.zeros((n, w))
+    for i in range(n):
+        for j in range(max(0, i - kl), min(n, i + ku + 1)):
+            ab[i, j - i + kl] = A[i, j]
+    x = o.band_solve(ab, b, kl, ku)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------------ single time steps
+
+
+def dense_step(scheme, u, dt, eps):
+    n = u.size
+    D = dense_dh(n)
+    I = np.eye(n)
+    if scheme == "lin1":
+        A = I - dt * D @ np.diag(u ** 2) + eps ** 2 * dt * D @ D
+        return np.linalg.solve(A, u - dt * D @ u)
+    if scheme == "lin2":
+        A = I - 2 * dt * D + eps ** 2 * dt * D @ D
+        return np.linalg.solve(A, u + dt * D @ u ** 3 - 3 * dt * D @ u)
+    raise ValueError(scheme)
+
+
+@pytest.mark.parametrize("scheme", ["lin1", "lin2"])
+def test_linear_steps_match_dense_brute_force(scheme):
+    n, eps, dt = 14, 0.1, 1e-3
+    u = ch_inputs.initial_condition(1, n, 5, amp=0.8)
+    p = o.Params(n=n, eps=eps, T=1, N=1, J=1)
+    out, _ = o.step(p, scheme, dt, u)
+    ref = dense_step(scheme, u, dt, eps)
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
+def test_newton_step_solves_nonlinear_system():
+    """Newton result is a root of H(Y) = Y + eps^2 dt D^2 Y - dt D Y^3 - (I - dt D) u (Eq. 3.17)."""
+    n, eps, dt = 16, 0.1, 5e-3
+    u = ch_inputs.initial_condition(1, n, 6, amp=0.9)
+    p = o.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=1e-13)
+    y, iters = o.step(p, "nl", dt, u)
+    D = dense_dh(n)
+    H = y + eps ** 2 * dt * D @ D @ y - dt * D @ y ** 3 - (u - dt * D @ u)
+    scale = np.max(np.abs(eps ** 2 * dt * D @ D @ y)) + 1
+    assert np.max(np.abs(H)) < 1e-12 * scale
+    assert 2 <= iters <= 8
+
+
+@pytest.mark.parametrize("scheme,i", [("lin1", 1), ("lin2", 2), ("nl", 1)])
+def test_frozen_step_matches_lemma_3_1_factor(scheme, i):
+    """Frozen model (diag(u^2) = I): each sine mode is scaled by g_i(mu_p) of Lemma 3.1."""
+    n, eps, dt = 31, 0.07, 2e-3
+    p = o.Params(n=n, eps=eps, T=1, N=1, J=1, frozen=True)
+    for pm in (1, 5, 31):
+        v = sine_mode(n, pm)
+        out, _ = o.step(p, scheme, dt, v)
+        y = mu(n, pm)
+        g = (1 + i * dt * y) / (1 + i * dt * y + eps ** 2 * dt * y ** 2)
+        assert 0 < g < 1
+        assert np.max(np.abs(out - g * v)) < 1e-13
+
+
+# ------------------------------------------------------- manufactured solutions
+
+
+def mms_forcing(eps):
+    """u = e^{-t} sin(pi x) solves u_t + eps^2 D^2 u = D(u^3 - u) + g with this g."""
+    pi2 = np.pi ** 2
+    return [(-1 + eps ** 2 * pi2 ** 2 - pi2, -1.0, 1), (0.75 * pi2, -3.0, 1), (-2.25 * pi2, -3.0, 3)]
+
+
+def mms_error(scheme, n, nsteps, T, eps=0.1):
+    x = np.arange(1, n + 1) / (n + 1)
+    u0 = np.sin(np.pi * x)
+    p = o.Params(n=n, eps=eps, T=T, N=1, J=nsteps, newton_tol=1e-13)
+    uT = o.propagate(p, scheme, T / nsteps, nsteps, u0, forcing=mms_forcing(eps))
+    return np.max(np.abs(uT - math.exp(-T) * u0))
+
+
+@pytest.mark.parametrize("scheme", ["nl", "lin1", "lin2"])
+def test_mms_first_order_in_time(scheme):
+    errs = [mms_error(scheme, 511, m, 0.2) for m in (40, 80, 160)]
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.8 < r1 < 2.2 and 1.8 < r2 < 2.2, errs
+
+
+@pytest.mark.parametrize("scheme", ["nl", "lin1"])
+def test_mms_second_order_in_space(scheme):
+    errs = [mms_error(scheme, n, 2000, 0.02) for n in (15, 31, 63)]
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.4 < r1 < 4.6 and 3.4 < r2 < 4.6, errs
+
+
+# ----------------------------------------------------------------- energy decay
+
+
+def test_eyre_scheme_energy_non_increasing_at_large_steps():
+    """The nonlinear scheme Eq. 2.3 is unconditionally gradient stable (Section 2.1)."""
+    n, eps = 63, 0.04
+    u = ch_inputs.initial_condition(1, n, 11, amp=0.5)
+    p = o.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=1e-13)
+    E = [o.energy(u, eps)]
+    for dt in [1e-3] * 5 + [2e-2] * 5 + [0.5] * 3:
+        u, _ = o.step(p, "nl", dt, u)
+        E.append(o.energy(u, eps))
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-12 * np.abs(E[:-1])), np.diff(E)
+    assert E[-1] < E[0]
+
+
+def test_energy_matches_definition_on_sine():
+    n, eps = 50, 0.3
+    v = 0.5 * sine_mode(n, 2)
+    h = 1.0 / (n + 1)
+    bulk = h * np.sum((v ** 2 - 1) ** 2 / 4)
+    grad = 0.5 * eps ** 2 * h * mu(n, 2) * np.sum(v ** 2)  # v^T(-D_h)v = mu_p |v|^2
+    assert abs(o.energy(v, eps) - (bulk + grad)) < 1e-12
+
+
+# -------------------------------------------------------------------- Parareal
+
+
+def frozen_parareal_closed_form(n, p_mode, eps, T, N, J, k):
+    """Lemma 3.4 / proof of Theorem 3.7 per DST mode: U_s^k = sum_{j<=k} C(s,j)(b-a)^j a^{s-j} u0."""
+    y = mu(n, p_mode)
+    dT = T / N
+    dt = dT / J
+    a = (1 + dT * y) / (1 + dT * y + eps ** 2 * dT * y ** 2)
+    b = ((1 + dt * y) / (1 + dt * y + eps ** 2 * dt * y ** 2)) ** J
+    coef = np.array([sum(math.comb(s, j) * (b - a) ** j * a ** (s - j) for j in range(min(k, s) + 1))
+                     for s in range(N + 1)])
+    return coef
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 8])
+def test_frozen_parareal_matches_closed_form(k):
+    n, eps, T, N, J = 31, 0.0725, 1.0, 8, 20
+    pm = 3
+    p = o.Params(n=n, eps=eps, T=T, N=N, J=J, fine="lin1", coarse="lin1", frozen=True, max_iters=k)
+    u0 = sine_mode(n, pm)
+    r = o.parareal(p, u0)
+    coef = frozen_parareal_closed_form(n, pm, eps, T, N, J, k)
+    expect = coef[:, None] * u0[None, :]
+    assert r.iterations == k
+    assert np.max(np.abs(r.U - expect)) < 1e-12
+
+
+def test_frozen_parareal_error_within_theorem_3_7_bound():
+    n, eps, T, N, J = 31, 0.0725, 1.0, 10, 20
+    u0 = sum(sine_mode(n, pm) / pm for pm in range(1, n + 1))
+    p = o.Params(n=n, eps=eps, T=T, N=N, J=J, frozen=True)
+    Uf = o.fine_solution(p, u0)
+    dT, dt = T / N, T / N / J
+    ys = np.array([mu(n, pm) for pm in range(1, n + 1)])
+    P1 = (1 + dT * ys) / (1 + dT * ys + eps ** 2 * dT * ys ** 2)
+    PJ = ((1 + dt * ys) / (1 + dt * ys + eps ** 2 * dt * ys ** 2)) ** J
+    alpha, beta = np.max(np.abs(PJ - P1)), np.max(np.abs(P1))  # 2-norms of symmetric operators
+    E0 = None
+    for k in range(0, N):
+        r = o.parareal(o.Params(n=n, eps=eps, T=T, N=N, J=J, frozen=True, max_iters=k), u0)
+        e = max(np.linalg.norm(r.U[j] - Uf[j]) for j in range(1, N + 1))
+        if k == 0:
+            E0 = e
+            continue
+        bound = alpha ** k * min(((1 - beta ** (N - 1)) / (1 - beta)) ** k, math.comb(N - 1, k)) * E0
+        assert e <= bound * (1 + 1e-9) + 1e-14
+
+
+@pytest.mark.parametrize("fine", ["lin1", "nl"])
+def test_parareal_finite_step_exactness(fine):
+    """U_s^k equals the sequential fine solution for s <= k, and everywhere at k = N."""
+    n, N = 32, 6
+    u0 = ch_inputs.initial_condition(1, n, 2, amp=0.3)
+    p = o.Params(n=n, eps=0.08, T=0.2, N=N, J=10, fine=fine, coarse="lin1")
+    Uf = o.fine_solution(p, u0)
+    for k in range(0, N + 1):
+        r = o.parareal(o.Params(**{**p.__dict__, "max_iters": k}), u0, Uf)
+        assert np.array_equal(r.U[: k + 1], Uf[: k + 1])
+    assert r.err_max[-1] == 0.0
+
+
+def test_parareal_stop_rule_on_paper_e1_parameters():
+    """Section 4.1 parameters (T=1, h=1/64, N=20, J=200, eps=0.0725) with a smooth u0.
+
+    The stop rule halts at the first iteration whose increment is below tol; the error
+    against the fine solution there is of the size the paper describes for four to five
+    iterations (O(1e-4)); this part is qualitative, the paper's u0 is not printed.
+    """
+    n = 63
+    x = np.arange(1, n + 1) / (n + 1)
+    u0 = 0.5 * np.sin(np.pi * x) + 0.2 * np.sin(3 * np.pi * x)
+    p = o.Params(n=n, eps=0.0725, T=1.0, N=20, J=200, fine="nl", coarse="lin1", tol=1e-3)
+    Uf = o.fine_solution(p, u0)
+    r = o.parareal(p, u0, Uf)
+    assert r.converged and r.iterations < p.N
+    assert r.inc[-1] < 1e-3 and np.all(r.inc[:-1] >= 1e-3)
+    assert r.err_l2[r.iterations] < 1e-3
+    assert np.all(np.diff(r.err_l2[:5]) < 0)
