@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Parareal path for the Cahn-Hilliard equation.
+
+Workload (default): 1D nonlinear Parareal NPA-I (Newton fine solver, tolerance 1e-12), FP64
+states and residuals, M = 1024 interior nodes, eps = 0.02, T = 1, N = 64 slices, 200 fine steps
+per slice, one plain coarse step per slice, batch of 256 seeded initial conditions
+u0 = 0.1 U(-1,1) (seeds 0..255), all slices of all problems in one persistent launch per
+iteration, each iteration replayed as a CUDA graph.
+
+A step is one pass of the whole path over the batch: the coarse initial sweep, one fine sweep
+over every slice of every problem, and the sequential coarse sweep with the Parareal correction
+and the convergence norms (ch_parareal_run with max_iters = 1). `value` is fine grid-point
+steps per second (one fine time step applied to one interior node), whole job.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Parareal time-to-1e-8 (learned vs plain G) & grid-pt-steps/s; % HBM roofline"
+
+WORKLOADS = {
+    "c2": dict(name="1D nonlinear Parareal NPA-I M=1024 eps=0.02 T=1 N=64 J=200 newton_tol=1e-12 batch=256",
+               n=1024, eps=0.02, T=1.0, N=64, J=200, batch=256, variant="NPA-I", newton_tol=1e-12,
+               amp=0.1, precision=1, ttol=True),
+    "c1": dict(name="1D linear Parareal PA-I M=128 eps=0.05 T=0.1 N=16 dt=1e-5 batch=1",
+               n=128, eps=0.05, T=0.1, N=16, J=625, batch=1, variant="PA-I", newton_tol=1e-12,
+               amp=0.1, precision=0, ttol=True),
+}
+FINE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin2", "NPA-I": "nl", "NPA-II": "nl"}
+COARSE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin1", "NPA-I": "lin1", "NPA-II": "nl"}
+
+# FP64 arithmetic per grid point (FMA = 2 flops) that the nonlinear scheme needs in full
+# precision: the right-hand side (I - dt D_h) u^n once per step, and per Newton iteration the
+# residual H(Y) = Y - Yhat + D_h(eps^2 dt D_h Y - dt Y^3) and the update Y -= dY.
+FP64_FLOPS_RHS = 5
+FP64_FLOPS_NEWTON = 15
+# GB300 FP64: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def u0_batch(w, rank):
+    import ch_inputs
+    import numpy as np
+    base = rank * w["batch"]
+    return np.stack([ch_inputs.initial_condition(1, w["n"], base + b, amp=w["amp"]) for b in range(w["batch"])])
+
+
+# ------------------------------------------------------------------------ clocks sampling
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ CPU oracle leg
+
+
+def _oracle_step(args):
+    """One step of the workload (coarse sweep + one fine sweep + correction) for one problem."""
+    w, u0 = args
+    from oracle import oracle1d as o
+    p = o.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], fine=FINE_OF[w["variant"]],
+                 coarse=COARSE_OF[w["variant"]], newton_tol=w["newton_tol"], max_iters=1)
+    t = time.perf_counter()
+    o.parareal(p, u0)
+    return time.perf_counter() - t
+
+
+def cpu_oracle(w, problems, u0s, steps=1):
+    """Times the oracle on `problems` problems, one process per problem (spawned)."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    pts = w["N"] * w["J"] * w["n"]
+    times = []
+    with ctx.Pool(problems) as pool:
+        for _ in range(steps):
+            t = time.perf_counter()
+            pool.map(_oracle_step, [(w, u0s[b]) for b in range(problems)])
+            times.append(time.perf_counter() - t)
+    return problems * pts, times
+
+
+def cpu_sample_size():
+    cores = os.cpu_count() or 1
+    return max(1, min(4, cores))
+
+
+# ----------------------------------------------------------------------------- our arm
+
+
+def bench_ours(args, w, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2304_14074_gb300 as ch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    u0 = u0_batch(w, rank)
+    B, n, N, J = w["batch"], w["n"], w["N"], w["J"]
+    cfg = ch.Config(n=n, eps=w["eps"], T=w["T"], n_slices=N, fine_steps=J, variant=w["variant"],
+                    newton_tol=w["newton_tol"], max_iters=1, precision=w["precision"])
+    u0_dev = torch.as_tensor(u0, dtype=torch.float64, device=dev).contiguous()
+    pr = ch.Parareal(cfg, batch=B, stream=stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def one_step():
+        pr.set_initial_device(u0_dev)
+        pr.run()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    fine_pts_per_step = B * N * J * n
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fine_ms, newton_total, launches = 0.0, 0, 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            one_step()
+            ev[i][1].record(stream)
+            st = [pr.stats(b) for b in (0,)]
+            fine_ms += st[0]["fine_sweep_ms"]
+            launches += st[0]["kernel_launches"]
+            newton_total += sum(pr.stats(b)["newton_total"] for b in range(B)) if i == 0 else 0
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * fine_pts_per_step / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the fine sweep), timed live inside the graph
+    fine_ms_per_launch = fine_ms / args.steps
+    newton_per_step = newton_total  # Newton iterations (summed over problems) in one step
+    alg_flops = fine_pts_per_step * FP64_FLOPS_RHS + newton_per_step * n * FP64_FLOPS_NEWTON
+    achieved = alg_flops / (fine_ms_per_launch / 1e3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_fine_sweep (FP64 pipe)", "achieved": round(achieved, 2),
+                "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
+                "traffic": None, "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
+                "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
+                "newton_iters_per_step_point": round(newton_per_step / (B * N * J), 3),
+                "algorithmic_fp64_flops_per_launch": alg_flops}
+
+    # end to end through the public API: pinned host inputs in, every slice of the result out
+    u0_pin = torch.from_numpy(u0).pin_memory()
+    out_pin = torch.empty((B, N + 1, n), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(max(1, args.steps // 2)):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr.set_initial_batch(u0_pin)
+        pr.run()
+        pr.get_slices_batch(out_pin)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+    e2e = {"value": world * fine_pts_per_step / (e2e_mean / 1e3), "unit": "grid-pt-steps/s",
+           "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(out_pin.numel() * 8),
+           "ms_per_step": round(e2e_mean, 3)}
+    pr.close()
+
+    ttol = None
+    if w.get("ttol") and not args.no_ttol and rank == 0:
+        ttol = time_to_tolerance(ch, w, u0, stream)
+    return dict(value=value, total_ms=total_ms, step_ms=step_ms, roofline=roofline, e2e=e2e,
+                clocks=clk.summary(), launches=launches, ttol=ttol)
+
+
+def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
+    """Plain-G Parareal until every problem is within err_tol (max_n L2_h) of the sequential fine
+    solution; reports the device time of the Parareal run and of the serial fine solve."""
+    import torch
+    B, N = w["batch"], w["N"]
+    cfg = ch.Config(n=w["n"], eps=w["eps"], T=w["T"], n_slices=N, fine_steps=w["J"], variant=w["variant"],
+                    newton_tol=w["newton_tol"], max_iters=N, precision=w["precision"], err_tol=err_tol)
+    pr = ch.Parareal(cfg, batch=B, stream=stream)
+    pr.set_initial_batch(u0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    pr.compute_reference()
+    b.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = a.elapsed_time(b)
+    status = pr.run()
+    stats = [pr.stats(i) for i in range(B)]
+    iters = max(s["iterations"] for s in stats)
+    t_ms = stats[0]["t_iter_ms"][iters]
+    worst = max(s["err_l2"][s["iterations"]] for s in stats)
+    pr.close()
+    return {"coarse": "plain (one LIN1 step per slice)", "err_tol": err_tol, "seconds": round(t_ms / 1e3, 4),
+            "iterations": int(iters), "converged_all": status == 0, "worst_final_err_l2": worst,
+            "serial_fine_seconds_same_gpu": round(serial_ms / 1e3, 4),
+            "learned_coarse": "not built (no G_theta in this version)"}
+
+
+# ------------------------------------------------------------------------------ main
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--no-ttol", action="store_true", help="skip the time-to-1e-8 run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": w["name"], "global_batch": w["batch"] * world, "slices": w["N"], "fine_steps": w["J"],
+              "grid": w["n"], "parallelism": f"replicas{world}" if world > 1 else "single",
+              "l2": "inputs larger than L2 (U, F, Gold 136 MB each) and a 256 MB L2 flush between steps",
+              "step": "coarse initial sweep + one fine sweep over all slices + coarse sweep/correction/norms"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import ch_inputs  # noqa: F401
+        u0 = u0_batch(w, 0)
+        problems = cpu_sample_size()
+        for _ in range(args.warmup):
+            pass  # the oracle has no warm-up state; each step below is a fresh sample
+        pts, times = cpu_oracle(w, problems, u0, steps=args.steps)
+        total = sum(times)
+        value = args.steps * pts / total
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid-pt-steps/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
+                                 "sample": f"{problems} of {w['batch']} problems per step, one process each "
+                                           "(coarse sweep + full fine sweep + correction)"},
+                "e2e": {"value": value, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    # CPU oracle baseline first (spawned processes, before any GPU work in this process)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        u0 = u0_batch(w, 0)
+        problems = cpu_sample_size()
+        pts, times = cpu_oracle(w, problems, u0, steps=1)
+        cpu = {"value": pts / times[0], "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
+               "sample": f"{problems} of {w['batch']} problems, one step each, one process per problem"}
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    r = bench_ours(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": r["value"], "unit": "grid-pt-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+            "clocks": r["clocks"], "time_to_1e-8": r["ttol"],
+            "precision": "FP64 states, residuals, correction and norms; Newton inner solves FP32 (refined by the FP64 residual)"}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

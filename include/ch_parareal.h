@@ -1,0 +1,180 @@
+/*
+ * ch_parareal.h - C ABI of the GB300 (sm_103a) Parareal library for the Cahn-Hilliard equation
+ *
+ *     u_t + eps^2 Lap^2 u = Lap f(u),  f(u) = u^3 - u,  on (0,1)^d, u = Lap u = 0 on the boundary
+ *
+ * following Garai & Mandal, "Linear and Nonlinear Parareal Methods for the Cahn-Hilliard
+ * Equation" (arXiv 2304.14074): Eq. 1.1 (problem), Section 2.1 (the schemes Eq. 2.3-2.5 on
+ * the discrete Laplacian D_h of Eq. 3.2), Eq. 2.2 (Parareal), Eq. 3.17/3.18 (Newton for the
+ * nonlinear scheme), Section 4 (coarse initial guess, error in L^inf(0,T; L^2)).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns ch_status and never aborts. A handle keeps the first error
+ *    ("sticky") with a message readable through ch_parareal_last_error().
+ *  - Grid: n interior nodes per direction, h = 1/(n+1); boundary values are implicit zeros.
+ *    A state is the interior values, FP64, row-major (y outer, x inner in 2D), n^d entries.
+ *  - Slice layout: slices 0..N of one problem are contiguous, slice 0 = u^0; problems follow
+ *    one another: element (b, s, j) of a [batch][N+1][n^d] array is at (b (N+1) + s) n^d + j.
+ *  - "_host" pointers are host memory; "_dev" pointers are device memory of the current
+ *    device. Caller-owned buffers are never retained past the call.
+ *  - A handle owns its device memory and is bound to one CUDA stream (cudaStream_t passed
+ *    as void*; NULL = the legacy default stream). Work is enqueued on that stream; calls
+ *    that return data to the host synchronise it. A handle is not thread-safe.
+ *  - Only one dimension is implemented by this version (dim = 1); dim = 2 returns
+ *    CH_ERR_INVALID.
+ */
+#ifndef CH_PARAREAL_H
+#define CH_PARAREAL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CH_OK = 0,
+  CH_ERR_INVALID = 1,        /* bad argument, size or configuration                       */
+  CH_ERR_OOM = 2,            /* device or host allocation failed                          */
+  CH_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error)   */
+  CH_ERR_NEWTON = 4,         /* a Newton solve hit newton_max without converging          */
+  CH_ERR_LINSOLVE = 5,       /* a linear solve produced a non-finite value                */
+  CH_ERR_NOT_CONVERGED = 6,  /* Parareal stop rule not met within max_iters               */
+  CH_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up                        */
+  CH_ERR_STATE = 8           /* call out of order (e.g. run before set_initial)           */
+} ch_status;
+
+/* The five Parareal variants of Section 2.1 (fine propagator F / coarse propagator G). */
+typedef enum {
+  CH_PA_I = 0,    /* F = G = linear scheme Eq. 2.4 (LIN1)                    */
+  CH_PA_II = 1,   /* F = G = linear scheme Eq. 2.5 (LIN2)                    */
+  CH_PA_III = 2,  /* F = LIN2, G = LIN1                                      */
+  CH_NPA_I = 3,   /* F = nonlinear scheme Eq. 2.3 (Newton), G = LIN1         */
+  CH_NPA_II = 4   /* F = G = nonlinear scheme Eq. 2.3                        */
+} ch_variant;
+
+/* Time-stepping schemes of Section 2.1, for ch_propagate. */
+typedef enum {
+  CH_SCHEME_LIN1 = 0,  /* Eq. 2.4: (I - dt D diag(u^n)^2 + eps^2 dt D^2) u^{n+1} = (I - dt D) u^n  */
+  CH_SCHEME_NL = 1,    /* Eq. 2.3 solved by Newton (Eq. 3.17/3.18) from Y_0 = u^n               */
+  CH_SCHEME_LIN2 = 2   /* Eq. 2.5 with D on the implicit 2 dt term:
+                          (I - 2 dt D + eps^2 dt D^2) u^{n+1} = u^n + dt D (u^n)^3 - 3 dt D u^n  */
+} ch_scheme;
+
+typedef struct {
+  int dim;             /* 1 (2 reserved)                                                   */
+  int n;               /* interior nodes per direction, h = 1/(n+1)       (Section 2.1)     */
+  double eps;          /* interface parameter epsilon                      (Eq. 1.1)         */
+  double T;            /* final time                                        (Eq. 1.1)         */
+  int n_slices;        /* N; Delta T = T/N                                  (Section 2)       */
+  int fine_steps;      /* J; fine step dt = Delta T / J                     (Section 2)       */
+  int coarse_steps;    /* coarse steps per slice (>= 1), each of Delta T / coarse_steps      */
+  int variant;         /* ch_variant                                                         */
+  double newton_tol;   /* Newton stop: ||Y_{m+1} - Y_m||_inf <= newton_tol, or the FP64
+                          rounding floor (an increment below sqrt(newton_tol) that fails to
+                          halve the previous one)                                            */
+  int newton_max;      /* Newton iteration cap per step                                      */
+  double tol;          /* Parareal stop: max_n ||U_n^k - U_n^{k-1}||_inf < tol; <= 0: never   */
+  int max_iters;       /* Parareal iteration cap, 1 <= max_iters <= N                         */
+  int precision;       /* 0: all solves FP64; 1: Newton's inner linear solves in FP32 against
+                          FP64 residuals (the converged step is the FP64 root)                */
+  int frozen;          /* 1: diag(u^2) replaced by I (analysis model of Section 3); test mode */
+  double err_tol;      /* also stop a problem once max_n ||U_n^k - U_n^fine||_{L2_h} <= err_tol
+                          (the error measure of Section 4; needs ch_parareal_compute_reference);
+                          <= 0: off                                                          */
+} ch_config;
+
+#define CH_MAX_ITERS 1024
+
+typedef struct {
+  int iterations;                 /* completed Parareal iterations k                          */
+  int converged;                  /* stop rule met                                            */
+  double inc[CH_MAX_ITERS];       /* inc[k-1] = max_n ||U_n^k - U_n^{k-1}||_inf               */
+  double err_l2[CH_MAX_ITERS];    /* err_l2[k] = max_n ||U_n^k - U_n^fine||_{L2_h}, L2_h norm
+                                     = sqrt(h^d sum e^2) (Section 4); valid after
+                                     ch_parareal_compute_reference, else -1                   */
+  double err_max[CH_MAX_ITERS];   /* same error, max-abs                                      */
+  double t_iter_ms[CH_MAX_ITERS]; /* t_iter_ms[k] = device time from the start of run to the
+                                     end of iteration k (k = 0: the coarse initial sweep)     */
+  long long newton_total;         /* Newton iterations summed over all fine steps of run      */
+  int newton_max;                 /* most Newton iterations taken by one fine step            */
+  long long fine_point_steps;     /* fine steps x interior points executed by run             */
+  /* Whole-handle figures of the last run (same for every problem): device time of the
+     fine-sweep kernel and of the coarse-sweep kernel summed over iterations, measured with
+     events recorded around them inside the iteration graph, and the number of launches of
+     the library's kernels during run. */
+  double fine_sweep_ms;
+  double coarse_sweep_ms;
+  int fine_sweep_launches;
+  int kernel_launches;
+} ch_stats;
+
+typedef struct ch_parareal ch_parareal;
+
+/* Create a handle for `batch` independent problems sharing `cfg`. Allocates device memory
+ * for the slice states, F(U_n^k), G(U_n^k), the reference solution and the histories.
+ * Errors: CH_ERR_INVALID (cfg out of range: dim != 1, n < 1 or n > 2048, N < 1, J < 1,
+ * eps <= 0, T <= 0, batch < 1, max_iters outside 1..N), CH_ERR_OOM, CH_ERR_CUDA. */
+ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream, ch_parareal** out);
+
+/* u^0 of one problem from host memory, len = n^d values. */
+ch_status ch_parareal_set_initial(ch_parareal* h, int problem, const double* u0_host, size_t len);
+
+/* u^0 of all problems from host memory, [batch][n^d], len = batch n^d values. */
+ch_status ch_parareal_set_initial_batch(ch_parareal* h, const double* u0_host, size_t len);
+
+/* u^0 of all problems from device memory, [batch][n^d], len = batch n^d values. */
+ch_status ch_parareal_set_initial_device(ch_parareal* h, const double* u0_dev, size_t len);
+
+/* The sequential fine solution U^fine_{n+1} = F(U^fine_n) (the serial method Parareal converges
+ * to, Section 2), computed on the device and kept as the reference of err_l2 / err_max. */
+ch_status ch_parareal_compute_reference(ch_parareal* h);
+
+/* Parareal (Eq. 2.2): coarse initial sweep U^0 (Section 4), then iterations of
+ * [fine sweep over all not-yet-exact slices of all active problems in one persistent launch;
+ *  sequential coarse sweep with the correction U_{n+1}^{k+1} = F(U_n^k) + (G(U_n^{k+1}) - G(U_n^k))
+ *  and the increment / error norms], each iteration replayed as one CUDA graph, until every
+ * problem meets a stop rule (tol or err_tol) or max_iters. Returns CH_ERR_NOT_CONVERGED (not
+ * sticky) when a stop rule is set and some problem did not meet it, CH_ERR_NEWTON when a Newton
+ * solve failed. */
+ch_status ch_parareal_run(ch_parareal* h);
+
+/* Final iterate U^k of one problem: (N+1) n^d values to host memory. */
+ch_status ch_parareal_get_slices(ch_parareal* h, int problem, double* out_host, size_t len);
+
+/* Final iterates of all problems to host memory: batch (N+1) n^d values. */
+ch_status ch_parareal_get_slices_batch(ch_parareal* h, double* out_host, size_t len);
+
+/* Final iterates of all problems to device memory: batch (N+1) n^d values. */
+ch_status ch_parareal_get_slices_device(ch_parareal* h, double* out_dev, size_t len);
+
+/* Reference (sequential fine) slices of one problem: (N+1) n^d values to host memory. */
+ch_status ch_parareal_get_reference(ch_parareal* h, int problem, double* out_host, size_t len);
+
+/* Statistics of the last run for one problem. */
+ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out);
+
+/* Releases the handle and its device memory; NULL is accepted. */
+void ch_parareal_destroy(ch_parareal* h);
+
+/* Message of the handle's first error ("" when none). */
+const char* ch_parareal_last_error(const ch_parareal* h);
+
+/* Static name of a status code. */
+const char* ch_status_string(ch_status s);
+
+/* Stateless propagation (the fine or coarse propagator as a batched kernel): applies `nsteps`
+ * steps of `scheme` with step `dt` to each of `batch` problems sharing cfg->n, cfg->eps,
+ * cfg->newton_tol, cfg->newton_max, cfg->precision and cfg->frozen (the other cfg fields are
+ * ignored). u_in_dev / u_out_dev: [batch][n^d] device arrays (may alias). newton_dev: NULL or
+ * a device int array [batch] receiving the Newton iterations summed over the steps.
+ * Enqueued on `cuda_stream`; synchronises it before returning and reports CH_ERR_NEWTON /
+ * CH_ERR_LINSOLVE from the device status. */
+ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, int nsteps,
+                       const double* u_in_dev, double* u_out_dev, int* newton_dev,
+                       void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CH_PARAREAL_H */

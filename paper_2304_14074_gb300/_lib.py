@@ -1,0 +1,259 @@
+"""ctypes binding of the C ABI in ``include/ch_parareal.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/libchparareal.so``. This module
+never computes any part of it: when the library cannot be loaded it raises, it does not
+fall back. Torch is used only for device memory (tensor data pointers) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+CH_MAX_ITERS = 1024
+
+STATUS = {0: "CH_OK", 1: "CH_ERR_INVALID", 2: "CH_ERR_OOM", 3: "CH_ERR_CUDA", 4: "CH_ERR_NEWTON",
+          5: "CH_ERR_LINSOLVE", 6: "CH_ERR_NOT_CONVERGED", 7: "CH_ERR_TIMEOUT", 8: "CH_ERR_STATE"}
+VARIANTS = {"PA-I": 0, "PA-II": 1, "PA-III": 2, "NPA-I": 3, "NPA-II": 4}
+SCHEMES = {"lin1": 0, "nl": 1, "lin2": 2}
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTED_SYMBOLS = [
+    "ch_parareal_create", "ch_parareal_set_initial", "ch_parareal_set_initial_batch",
+    "ch_parareal_set_initial_device", "ch_parareal_get_slices_batch",
+    "ch_parareal_compute_reference", "ch_parareal_run", "ch_parareal_get_slices",
+    "ch_parareal_get_slices_device", "ch_parareal_get_reference", "ch_parareal_get_stats",
+    "ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_propagate",
+]
+
+
+class ChError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, f"status {status}")
+        super().__init__(f"{what}: {self.name}" + (f" ({detail})" if detail else ""))
+
+
+class _Config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int), ("eps", C.c_double), ("T", C.c_double),
+                ("n_slices", C.c_int), ("fine_steps", C.c_int), ("coarse_steps", C.c_int),
+                ("variant", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
+                ("tol", C.c_double), ("max_iters", C.c_int), ("precision", C.c_int), ("frozen", C.c_int),
+                ("err_tol", C.c_double)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("inc", C.c_double * CH_MAX_ITERS),
+                ("err_l2", C.c_double * CH_MAX_ITERS), ("err_max", C.c_double * CH_MAX_ITERS),
+                ("t_iter_ms", C.c_double * CH_MAX_ITERS), ("newton_total", C.c_longlong),
+                ("newton_max", C.c_int), ("fine_point_steps", C.c_longlong), ("fine_sweep_ms", C.c_double),
+                ("coarse_sweep_ms", C.c_double), ("fine_sweep_launches", C.c_int), ("kernel_launches", C.c_int)]
+
+
+@dataclass
+class Config:
+    """Problem and method parameters (Eq. 1.1, Section 2, Section 4); see ch_config."""
+    n: int
+    eps: float
+    T: float
+    n_slices: int
+    fine_steps: int
+    coarse_steps: int = 1
+    variant: str = "NPA-I"
+    newton_tol: float = 1e-12
+    newton_max: int = 50
+    tol: float = 0.0
+    max_iters: int = -1
+    precision: int = 1
+    frozen: bool = False
+    err_tol: float = 0.0
+    dim: int = 1
+
+    def c(self) -> _Config:
+        mi = self.n_slices if self.max_iters < 0 else self.max_iters
+        return _Config(self.dim, self.n, self.eps, self.T, self.n_slices, self.fine_steps, self.coarse_steps,
+                       VARIANTS[self.variant], self.newton_tol, self.newton_max, self.tol, mi, self.precision,
+                       int(self.frozen), self.err_tol)
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Loads the CUDA library; raises when it is missing or cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    vp, d, sz = C.c_void_p, C.POINTER(C.c_double), C.c_size_t
+    lib.ch_parareal_create.argtypes = [C.POINTER(_Config), C.c_int, vp, C.POINTER(vp)]
+    lib.ch_parareal_set_initial.argtypes = [vp, C.c_int, d, sz]
+    lib.ch_parareal_set_initial_device.argtypes = [vp, vp, sz]
+    lib.ch_parareal_set_initial_batch.argtypes = [vp, d, sz]
+    lib.ch_parareal_get_slices_batch.argtypes = [vp, d, sz]
+    lib.ch_parareal_compute_reference.argtypes = [vp]
+    lib.ch_parareal_run.argtypes = [vp]
+    lib.ch_parareal_get_slices.argtypes = [vp, C.c_int, d, sz]
+    lib.ch_parareal_get_slices_device.argtypes = [vp, vp, sz]
+    lib.ch_parareal_get_reference.argtypes = [vp, C.c_int, d, sz]
+    lib.ch_parareal_get_stats.argtypes = [vp, C.c_int, C.POINTER(_Stats)]
+    lib.ch_parareal_destroy.argtypes = [vp]
+    lib.ch_parareal_destroy.restype = None
+    lib.ch_parareal_last_error.argtypes = [vp]
+    lib.ch_parareal_last_error.restype = C.c_char_p
+    lib.ch_status_string.argtypes = [C.c_int]
+    lib.ch_status_string.restype = C.c_char_p
+    lib.ch_propagate.argtypes = [C.POINTER(_Config), C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp]
+    for name in EXPORTED_SYMBOLS:
+        if name not in ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA tensor (validated)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Parareal:
+    """A handle of `batch` problems sharing one configuration (ch_parareal_*)."""
+
+    def __init__(self, cfg: Config, batch: int = 1, stream=None):
+        self.lib = load()
+        self.cfg = cfg
+        self.batch = batch
+        self.pts = cfg.n ** cfg.dim
+        self._h = C.c_void_p()
+        self._cc = cfg.c()
+        s = self.lib.ch_parareal_create(C.byref(self._cc), batch, _stream_ptr(stream), C.byref(self._h))
+        if s != 0:
+            raise ChError(s, "ch_parareal_create")
+
+    def _check(self, s, what, ok=(0,)):
+        if s not in ok:
+            detail = self.lib.ch_parareal_last_error(self._h).decode() if self._h else ""
+            raise ChError(s, what, detail)
+        return s
+
+    def set_initial(self, problem: int, u0) -> None:
+        u = _host(u0)
+        self._check(self.lib.ch_parareal_set_initial(self._h, problem, u.ctypes.data_as(C.POINTER(C.c_double)),
+                                                     u.size), "ch_parareal_set_initial")
+
+    def set_initial_batch(self, u0) -> None:
+        """u0: [batch, n^d] host array (pinned host memory makes the copy asynchronous)."""
+        if isinstance(u0, np.ndarray):
+            u = _host(u0)
+            ptr, size = u.ctypes.data_as(C.POINTER(C.c_double)), u.size
+        else:  # a CPU torch tensor, possibly pinned
+            ptr, size = C.cast(C.c_void_p(u0.data_ptr()), C.POINTER(C.c_double)), u0.numel()
+        self._check(self.lib.ch_parareal_set_initial_batch(self._h, ptr, size), "ch_parareal_set_initial_batch")
+
+    def get_slices_batch(self, out=None):
+        """All problems' final iterates [batch, N+1, n^d] into host memory (numpy or CPU tensor)."""
+        if out is None:
+            out = np.empty((self.batch, self.cfg.n_slices + 1, self.pts))
+        if isinstance(out, np.ndarray):
+            ptr, size = out.ctypes.data_as(C.POINTER(C.c_double)), out.size
+        else:
+            ptr, size = C.cast(C.c_void_p(out.data_ptr()), C.POINTER(C.c_double)), out.numel()
+        self._check(self.lib.ch_parareal_get_slices_batch(self._h, ptr, size), "ch_parareal_get_slices_batch")
+        return out
+
+    def set_initial_device(self, u0_dev) -> None:
+        self._check(self.lib.ch_parareal_set_initial_device(self._h, _dptr(u0_dev), u0_dev.numel()),
+                    "ch_parareal_set_initial_device")
+
+    def compute_reference(self) -> None:
+        self._check(self.lib.ch_parareal_compute_reference(self._h), "ch_parareal_compute_reference")
+
+    def run(self, allow_not_converged: bool = True) -> int:
+        ok = (0, 6) if allow_not_converged else (0,)
+        return self._check(self.lib.ch_parareal_run(self._h), "ch_parareal_run", ok)
+
+    def get_slices(self, problem: int) -> np.ndarray:
+        out = np.empty((self.cfg.n_slices + 1, self.pts))
+        self._check(self.lib.ch_parareal_get_slices(self._h, problem, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                                    out.size), "ch_parareal_get_slices")
+        return out
+
+    def get_slices_device(self, out_dev) -> None:
+        self._check(self.lib.ch_parareal_get_slices_device(self._h, _dptr(out_dev), out_dev.numel()),
+                    "ch_parareal_get_slices_device")
+
+    def get_reference(self, problem: int) -> np.ndarray:
+        out = np.empty((self.cfg.n_slices + 1, self.pts))
+        self._check(self.lib.ch_parareal_get_reference(self._h, problem,
+                                                       out.ctypes.data_as(C.POINTER(C.c_double)), out.size),
+                    "ch_parareal_get_reference")
+        return out
+
+    def stats(self, problem: int) -> dict:
+        st = _Stats()
+        self._check(self.lib.ch_parareal_get_stats(self._h, problem, C.byref(st)), "ch_parareal_get_stats")
+        k = st.iterations
+        return {"iterations": k, "converged": bool(st.converged), "inc": np.array(st.inc[:k]),
+                "err_l2": np.array(st.err_l2[:k + 1]), "err_max": np.array(st.err_max[:k + 1]),
+                "t_iter_ms": np.array(st.t_iter_ms[:self.cfg.c().max_iters + 1]),
+                "newton_total": st.newton_total, "newton_max": st.newton_max,
+                "fine_point_steps": st.fine_point_steps, "fine_sweep_ms": st.fine_sweep_ms,
+                "coarse_sweep_ms": st.coarse_sweep_ms, "fine_sweep_launches": st.fine_sweep_launches,
+                "kernel_launches": st.kernel_launches}
+
+    def close(self) -> None:
+        if self._h:
+            self.lib.ch_parareal_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def propagate(cfg: Config, scheme: str, dt: float, nsteps: int, u_in, u_out=None, newton=None, stream=None):
+    """Batched propagation on the device (ch_propagate). u_in: CUDA float64 tensor [batch, n^d]."""
+    import torch
+    lib = load()
+    if u_out is None:
+        u_out = torch.empty_like(u_in)
+    batch = u_in.shape[0]
+    cc = cfg.c()
+    s = lib.ch_propagate(C.byref(cc), batch, SCHEMES[scheme], dt, nsteps, _dptr(u_in), _dptr(u_out),
+                         _dptr(newton) if newton is not None else None, _stream_ptr(stream))
+    if s != 0:
+        raise ChError(s, "ch_propagate")
+    return u_out

@@ -1,0 +1,643 @@
+// One-dimensional Parareal for the Cahn-Hilliard equation on sm_103a.
+//
+// One CTA owns one state vector (a problem's slice) for the whole propagation: the state
+// lives in registers (thread t holds 2P consecutive rows), so HBM sees only the slice state
+// coming in and F(U) going out. Per time step:
+//   - the nonlinear scheme Eq. 2.3 is solved by Newton (Eq. 3.17/3.18) written as
+//     Y <- Y - J(Y)^{-1} H(Y): the residual H is formed in FP64 (its rounding floor is what
+//     limits attainable accuracy), the Jacobian solve runs in FP32 (precision 1) or FP64;
+//     GB300's FP64 pipe is about 1/58 of its FP32 rate, so FP64 is spent only on H and the
+//     update;
+//   - the linear schemes Eq. 2.4 / Eq. 2.5 are one FP64 pentadiagonal solve.
+// The Jacobian and step matrices are I + eps^2 dt D_h^2 + c dt (-D_h) diag(w) with D_h of
+// Eq. 3.2 (zero boundary values), solved by the partition method of ch_block_solver.cuh.
+#include <cmath>
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "ch1d.cuh"
+#include "ch_block_solver.cuh"
+
+namespace chg {
+
+template <int T>
+union SolverUnion {
+  SolverSmem<float, T> f;
+  SolverSmem<double, T> d;
+};
+
+template <int T>
+struct Smem1D {
+  double fst[T];
+  double lst[T];
+  SolverUnion<T> s;
+  ReduceSmem<T> red;
+  int unit;
+};
+
+template <typename S, int T>
+__device__ __forceinline__ SolverSmem<S, T>& solver_smem(Smem1D<T>& sm);
+template <>
+__device__ __forceinline__ SolverSmem<float, 32>& solver_smem<float, 32>(Smem1D<32>& sm) { return sm.s.f; }
+template <>
+__device__ __forceinline__ SolverSmem<float, 64>& solver_smem<float, 64>(Smem1D<64>& sm) { return sm.s.f; }
+template <>
+__device__ __forceinline__ SolverSmem<float, 128>& solver_smem<float, 128>(Smem1D<128>& sm) { return sm.s.f; }
+template <>
+__device__ __forceinline__ SolverSmem<float, 256>& solver_smem<float, 256>(Smem1D<256>& sm) { return sm.s.f; }
+template <>
+__device__ __forceinline__ SolverSmem<double, 32>& solver_smem<double, 32>(Smem1D<32>& sm) { return sm.s.d; }
+template <>
+__device__ __forceinline__ SolverSmem<double, 64>& solver_smem<double, 64>(Smem1D<64>& sm) { return sm.s.d; }
+template <>
+__device__ __forceinline__ SolverSmem<double, 128>& solver_smem<double, 128>(Smem1D<128>& sm) { return sm.s.d; }
+template <>
+__device__ __forceinline__ SolverSmem<double, 256>& solver_smem<double, 256>(Smem1D<256>& sm) { return sm.s.d; }
+
+// Exchange of chunk-edge values: left = value of row r0-1, right = value of row r0+2P.
+template <int T>
+__device__ __forceinline__ void exchange(Smem1D<T>& sm, double first, double last, double& left,
+                                         double& right) {
+  const int t = threadIdx.x;
+  sm.fst[t] = first;
+  sm.lst[t] = last;
+  __syncthreads();
+  left = (t > 0) ? sm.lst[t - 1] : 0.0;
+  right = (t < T - 1) ? sm.fst[t + 1] : 0.0;
+  __syncthreads();
+}
+
+struct StepCtx {
+  int n;
+  int frozen;
+  int newton_max;
+  double ih2;  // 1/h^2
+  double eps2;
+  double newton_tol;
+  double newton_floor;  // sqrt(newton_tol)
+};
+
+// Blocks of  I + alpha S4 + beta A diag(w)  for the 2P rows r0.. of this thread, where
+// S4 = h^4 D_h^2 rows [1 -4 6 -4 1] (first/last rows [5 -4 1]) and A = -h^2 D_h rows
+// [-1 2 -1]; rows >= n are identity rows with no coupling. w has the neighbours wl (row r0-1)
+// and wr (row r0+2P).
+template <typename S, int P>
+__device__ __forceinline__ void assemble(int r0, int n, S alpha, S beta, const S (&w)[2 * P], S wl,
+                                         S wr, M2<S> (&A)[P], M2<S> (&B)[P], M2<S> (&C)[P]) {
+  constexpr int R = 2 * P;
+  S e[R], a[R], b[R], c[R], f[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = r0 + q;
+    const S wm = (q > 0) ? w[q - 1] : wl;
+    const S wp = (q < R - 1) ? w[q + 1] : wr;
+    const bool in = r < n;
+    e[q] = (in && r >= 2) ? alpha : S(0);
+    a[q] = (in && r >= 1) ? (S(-4) * alpha - beta * wm) : S(0);
+    const S diag4 = S(6) - S(r == 0 ? 1 : 0) - S(r == n - 1 ? 1 : 0);
+    b[q] = in ? (S(1) + diag4 * alpha + S(2) * beta * w[q]) : S(1);
+    c[q] = (r + 1 < n) ? (S(-4) * alpha - beta * wp) : S(0);
+    f[q] = (r + 2 < n) ? alpha : S(0);
+  }
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    const int q0 = 2 * l, q1 = 2 * l + 1;
+    A[l] = {e[q0], a[q0], S(0), e[q1]};
+    B[l] = {b[q0], c[q0], a[q1], b[q1]};
+    C[l] = {f[q0], S(0), c[q1], f[q1]};
+  }
+}
+
+// One step of the nonlinear scheme Eq. 2.3 by Newton from Y_0 = u^n (Eq. 3.17/3.18), with
+// the Jacobian solve in precision S. y holds u^n on entry and u^{n+1} on return.
+// Returns the Newton iterations (negative if newton_max was reached); sets `bad` on a
+// non-finite value.
+template <int T, int P, typename S>
+__device__ int nl_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
+  constexpr int R = 2 * P;
+  const int r0 = threadIdx.x * R;
+  double L, Rt;
+  double yh[R];
+  exchange(sm, y[0], y[R - 1], L, Rt);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const double um = (q > 0) ? y[q - 1] : L;
+    const double up = (q < R - 1) ? y[q + 1] : Rt;
+    yh[q] = (r0 + q < c.n) ? y[q] - dt * c.ih2 * (um - 2.0 * y[q] + up) : 0.0;  // (I - dt D_h) u^n
+  }
+  const double c1 = c.eps2 * dt * c.ih2;
+  const S alpha = S(c.eps2 * dt * c.ih2 * c.ih2);
+  const S beta = S((c.frozen ? 1.0 : 3.0) * dt * c.ih2);
+  double prev = 0.0;
+  int m = 0;
+  bool ok = false;
+  while (m < c.newton_max) {
+    exchange(sm, y[0], y[R - 1], L, Rt);
+    // H(Y) = Y - Yhat + D_h z,  z = eps^2 dt D_h Y - dt Y^3   (Eq. 3.17)
+    double z[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const double um = (q > 0) ? y[q - 1] : L;
+      const double up = (q < R - 1) ? y[q + 1] : Rt;
+      const double cube = c.frozen ? y[q] : y[q] * y[q] * y[q];
+      z[q] = (r0 + q < c.n) ? c1 * (um - 2.0 * y[q] + up) - dt * cube : 0.0;
+    }
+    double zl, zr;
+    exchange(sm, z[0], z[R - 1], zl, zr);
+    S w[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) w[q] = c.frozen ? S(1) : S(y[q]) * S(y[q]);
+    const S wl = c.frozen ? S(1) : S(L) * S(L);
+    const S wr = c.frozen ? S(1) : S(Rt) * S(Rt);
+    M2<S> A[P], B[P], C[P];
+    assemble<S, P>(r0, c.n, alpha, beta, w, wl, wr, A, B, C);
+    V2<S> d[P], x[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+      double hh[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int q = 2 * l + i;
+        const double zm = (q > 0) ? z[q - 1] : zl;
+        const double zp = (q < R - 1) ? z[q + 1] : zr;
+        hh[i] = (r0 + q < c.n) ? (y[q] - yh[q]) + c.ih2 * (zm - 2.0 * z[q] + zp) : 0.0;
+      }
+      d[l] = {S(hh[0]), S(hh[1])};
+    }
+    block_tridiag_solve<S, T, P>(A, B, C, d, x, solver_smem<S, T>(sm));
+    double dm = 0.0;
+    bool nf = false;
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+      const double dx = double(x[l].x), dy = double(x[l].y);
+      nf |= !isfinite(dx) || !isfinite(dy);
+      y[2 * l] = (r0 + 2 * l < c.n) ? y[2 * l] - dx : 0.0;
+      y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? y[2 * l + 1] - dy : 0.0;
+      dm = fmax(dm, fmax(fabs(dx), fabs(dy)));
+    }
+    if (__syncthreads_or(nf)) {
+      bad = true;
+      return -(m + 1);
+    }
+    dm = cta_max<T>(dm, sm.red);
+    ++m;
+    if (dm <= c.newton_tol) { ok = true; break; }
+    // FP64 rounding floor of the residual reached (see the header comment of ch_parareal.h)
+    if (m >= 2 && dm <= c.newton_floor && dm > 0.5 * prev) { ok = true; break; }
+    prev = dm;
+  }
+  return ok ? m : -m;
+}
+
+// One step of the linear scheme Eq. 2.4 (LIN1), FP64 solve.
+template <int T, int P>
+__device__ void lin1_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
+  constexpr int R = 2 * P;
+  const int r0 = threadIdx.x * R;
+  double L, Rt;
+  exchange(sm, y[0], y[R - 1], L, Rt);
+  double w[R];
+  V2<double> d[P], x[P];
+#pragma unroll
+  for (int q = 0; q < R; ++q) w[q] = c.frozen ? 1.0 : y[q] * y[q];
+  const double wl = c.frozen ? 1.0 : L * L, wr = c.frozen ? 1.0 : Rt * Rt;
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    double rr[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = 2 * l + i;
+      const double um = (q > 0) ? y[q - 1] : L;
+      const double up = (q < R - 1) ? y[q + 1] : Rt;
+      rr[i] = (r0 + q < c.n) ? y[q] - dt * c.ih2 * (um - 2.0 * y[q] + up) : 0.0;  // (I - dt D_h) u^n
+    }
+    d[l] = {rr[0], rr[1]};
+  }
+  M2<double> A[P], B[P], C[P];
+  assemble<double, P>(r0, c.n, c.eps2 * dt * c.ih2 * c.ih2, dt * c.ih2, w, wl, wr, A, B, C);
+  block_tridiag_solve<double, T, P>(A, B, C, d, x, solver_smem<double, T>(sm));
+  bool nf = false;
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    nf |= !isfinite(x[l].x) || !isfinite(x[l].y);
+    y[2 * l] = (r0 + 2 * l < c.n) ? x[l].x : 0.0;
+    y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? x[l].y : 0.0;
+  }
+  if (__syncthreads_or(nf)) bad = true;
+}
+
+// One step of the linear scheme Eq. 2.5 (LIN2, Laplacian on the implicit 2 dt term), FP64 solve.
+template <int T, int P>
+__device__ void lin2_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
+  constexpr int R = 2 * P;
+  const int r0 = threadIdx.x * R;
+  double L, Rt;
+  exchange(sm, y[0], y[R - 1], L, Rt);
+  // rhs = u + dt D_h (u^3 - 3u)   (frozen: u + dt D_h (-2u))
+  auto vfun = [&](double u) { return c.frozen ? -2.0 * u : u * u * u - 3.0 * u; };
+  double v[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = vfun(y[q]);
+  const double vl = vfun(L), vr = vfun(Rt);
+  double w[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) w[q] = 1.0;
+  V2<double> d[P], x[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    double rr[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = 2 * l + i;
+      const double vm = (q > 0) ? v[q - 1] : vl;
+      const double vp = (q < R - 1) ? v[q + 1] : vr;
+      rr[i] = (r0 + q < c.n) ? y[q] + dt * c.ih2 * (vm - 2.0 * v[q] + vp) : 0.0;
+    }
+    d[l] = {rr[0], rr[1]};
+  }
+  M2<double> A[P], B[P], C[P];
+  assemble<double, P>(r0, c.n, c.eps2 * dt * c.ih2 * c.ih2, 2.0 * dt * c.ih2, w, 1.0, 1.0, A, B, C);
+  block_tridiag_solve<double, T, P>(A, B, C, d, x, solver_smem<double, T>(sm));
+  bool nf = false;
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    nf |= !isfinite(x[l].x) || !isfinite(x[l].y);
+    y[2 * l] = (r0 + 2 * l < c.n) ? x[l].x : 0.0;
+    y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? x[l].y : 0.0;
+  }
+  if (__syncthreads_or(nf)) bad = true;
+}
+
+// Dispatch one step. Returns Newton iterations (0 for the linear schemes; negative on failure).
+template <int T, int P>
+__device__ __forceinline__ int do_step(Smem1D<T>& sm, const StepCtx& c, int scheme, int fp32_newton,
+                                       double (&y)[2 * P], double dt, bool& bad) {
+  if (scheme == SCHEME_NL) {
+    return fp32_newton ? nl_step<T, P, float>(sm, c, y, dt, bad) : nl_step<T, P, double>(sm, c, y, dt, bad);
+  }
+  if (scheme == SCHEME_LIN2) {
+    lin2_step<T, P>(sm, c, y, dt, bad);
+  } else {
+    lin1_step<T, P>(sm, c, y, dt, bad);
+  }
+  return 0;
+}
+
+__device__ __forceinline__ StepCtx make_ctx(const Params1D& p) {
+  StepCtx c;
+  c.n = p.n;
+  c.frozen = p.frozen;
+  c.newton_max = p.newton_max;
+  c.ih2 = 1.0 / (p.h * p.h);
+  c.eps2 = p.eps2;
+  c.newton_tol = p.newton_tol;
+  c.newton_floor = sqrt(p.newton_tol);
+  return c;
+}
+
+template <int P>
+__device__ __forceinline__ void load_state(const double* __restrict__ src, int n, double (&y)[2 * P]) {
+  const int r0 = threadIdx.x * 2 * P;
+#pragma unroll
+  for (int q = 0; q < 2 * P; ++q) y[q] = (r0 + q < n) ? src[r0 + q] : 0.0;
+}
+template <int P>
+__device__ __forceinline__ void store_state(double* __restrict__ dst, int n, const double (&y)[2 * P]) {
+  const int r0 = threadIdx.x * 2 * P;
+#pragma unroll
+  for (int q = 0; q < 2 * P; ++q)
+    if (r0 + q < n) dst[r0 + q] = y[q];
+}
+
+// Runs `nsteps` steps; accumulates Newton statistics; returns false on failure.
+template <int T, int P>
+__device__ bool run_steps(Smem1D<T>& sm, const StepCtx& c, int scheme, int fp32_newton, double (&y)[2 * P],
+                          double dt, int nsteps, unsigned long long& newton_sum, int& newton_peak,
+                          unsigned& status) {
+  bool bad = false;
+  for (int j = 0; j < nsteps; ++j) {
+    const int m = do_step<T, P>(sm, c, scheme, fp32_newton, y, dt, bad);
+    if (m < 0) {
+      status |= ST_NEWTON;
+      newton_sum += (unsigned long long)(-m);
+      newton_peak = max(newton_peak, -m);
+    } else {
+      newton_sum += (unsigned long long)m;
+      newton_peak = max(newton_peak, m);
+    }
+    if (bad) {
+      status |= ST_NONFINITE;
+      return false;
+    }
+  }
+  return status == 0;
+}
+
+// ----------------------------------------------------------------------------- kernels
+
+// Fine sweep of one Parareal iteration: F(U_s^k) for every active problem b and slice s >= k,
+// as one persistent launch; CTAs take (problem, slice) units from a device counter.
+template <int T, int P>
+__global__ void __launch_bounds__(T) k_fine_sweep(Params1D p, const double* __restrict__ U,
+                                                  double* __restrict__ F, Ctrl* ctrl, ProblemState ps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
+  const int k = ctrl->k;
+  const int per = p.N - k;
+  if (per <= 0) return;
+  const int total = p.B * per;
+  const StepCtx c = make_ctx(p);
+  for (;;) {
+    if (threadIdx.x == 0) sm.unit = atomicAdd(&ctrl->next_unit, 1);
+    __syncthreads();
+    const int u = sm.unit;
+    __syncthreads();
+    if (u >= total) break;
+    const int b = u / per;
+    const int s = k + u % per;
+    if (!ps.active[b]) continue;
+    double y[2 * P];
+    load_state<P>(U + ((size_t)b * (p.N + 1) + s) * p.n, p.n, y);
+    unsigned long long nsum = 0;
+    int npeak = 0;
+    unsigned status = 0;
+    run_steps<T, P>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
+    store_state<P>(F + ((size_t)b * p.N + s) * p.n, p.n, y);
+    if (threadIdx.x == 0) {
+      atomicAdd(&ps.newton_total[b], nsum);
+      atomicMax(&ps.newton_max[b], npeak);
+      if (status) atomicOr(&ctrl->status, status);
+    }
+  }
+}
+
+// L2_h and max-abs error of one slice against the reference (Section 4 norm).
+template <int T, int P>
+__device__ __forceinline__ void slice_error(Smem1D<T>& sm, const double (&y)[2 * P], const double* ref,
+                                            int n, double h, double& el2, double& emx) {
+  const int r0 = threadIdx.x * 2 * P;
+  double s = 0.0, m = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2 * P; ++q) {
+    if (r0 + q < n) {
+      const double e = y[q] - ref[r0 + q];
+      s += e * e;
+      m = fmax(m, fabs(e));
+    }
+  }
+  cta_sum_max<T>(s, m, sm.red);
+  el2 = fmax(el2, sqrt(h * s));
+  emx = fmax(emx, m);
+}
+
+// Coarse sweep, sequential over slices, one CTA per problem.
+// init = 1: U_{s+1}^0 = G(U_s^0), Gold_s = U_{s+1}^0 (Section 4 initial guess).
+// init = 0: U_{s+1}^{k+1} = F_s + (G(U_s^{k+1}) - Gold_s), Gold_s = G(U_s^{k+1}) (Eq. 2.2), for
+//           s >= k, with the increment max_s |U^{k+1} - U^k| and the error against Uref.
+template <int T, int P>
+__global__ void __launch_bounds__(T) k_coarse_sweep(Params1D p, double* __restrict__ U,
+                                                    const double* __restrict__ F, double* __restrict__ Gold,
+                                                    const double* __restrict__ Uref, Ctrl* ctrl,
+                                                    ProblemState ps, int init) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
+  const int b = blockIdx.x;
+  if (!init && !ps.active[b]) return;
+  const int k = init ? 0 : ctrl->k;
+  const int n = p.n;
+  const StepCtx c = make_ctx(p);
+  double* Ub = U + (size_t)b * (p.N + 1) * n;
+  const double* Rb = Uref ? Uref + (size_t)b * (p.N + 1) * n : nullptr;
+  const int r0 = threadIdx.x * 2 * P;
+  double cur[2 * P];
+  load_state<P>(Ub + (size_t)k * n, n, cur);
+  double el2 = 0.0, emx = 0.0, inc = 0.0;
+  if (Rb) {
+    for (int s = 0; s <= k; ++s) {
+      double y[2 * P];
+      load_state<P>(Ub + (size_t)s * n, n, y);
+      slice_error<T, P>(sm, y, Rb + (size_t)s * n, n, p.h, el2, emx);
+    }
+  }
+  unsigned long long nsum = 0;
+  int npeak = 0;
+  unsigned status = 0;
+  for (int s = k; s < p.N; ++s) {
+    double g[2 * P];
+#pragma unroll
+    for (int q = 0; q < 2 * P; ++q) g[q] = cur[q];
+    run_steps<T, P>(sm, c, p.coarse_scheme, 0, g, p.dtc, p.coarse_steps, nsum, npeak, status);
+    double* Gs = Gold + ((size_t)b * p.N + s) * n;
+    double* Un = Ub + (size_t)(s + 1) * n;
+    if (init) {
+#pragma unroll
+      for (int q = 0; q < 2 * P; ++q) cur[q] = g[q];
+    } else {
+      const double* Fs = F + ((size_t)b * p.N + s) * n;
+#pragma unroll
+      for (int q = 0; q < 2 * P; ++q) {
+        if (r0 + q < n) {
+          const double nw = Fs[r0 + q] + (g[q] - Gs[r0 + q]);
+          inc = fmax(inc, fabs(nw - Un[r0 + q]));
+          cur[q] = nw;
+        } else {
+          cur[q] = 0.0;
+        }
+      }
+    }
+    store_state<P>(Un, n, cur);
+    store_state<P>(Gs, n, g);
+    if (Rb) slice_error<T, P>(sm, cur, Rb + (size_t)(s + 1) * n, n, p.h, el2, emx);
+  }
+  inc = cta_max<T>(inc, sm.red);
+  if (threadIdx.x == 0) {
+    const size_t eo = (size_t)b * (p.maxit + 1);
+    if (init) {
+      ps.err_l2[eo] = Rb ? el2 : -1.0;
+      ps.err_max[eo] = Rb ? emx : -1.0;
+    } else {
+      ps.inc[(size_t)b * p.maxit + k] = inc;
+      ps.err_l2[eo + k + 1] = Rb ? el2 : -1.0;
+      ps.err_max[eo + k + 1] = Rb ? emx : -1.0;
+      ps.iterations[b] = k + 1;
+      if ((p.tol > 0.0 && inc < p.tol) || (Rb && p.err_tol > 0.0 && el2 <= p.err_tol)) {
+        ps.converged[b] = 1;
+        ps.active[b] = 0;
+      }
+    }
+    if (status) atomicOr(&ctrl->status, status);
+  }
+}
+
+// End of an iteration: count active problems, advance k, reset the work counter.
+__global__ void k_tally(int B, Ctrl* ctrl, ProblemState ps, int* host_active) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int local = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) local += ps.active[b] ? 1 : 0;
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctrl->n_active = cnt;
+    ctrl->k += 1;
+    ctrl->next_unit = 0;
+    if (host_active) *host_active = cnt;
+  }
+}
+
+// Sequential fine solution U^fine_{s+1} = F(U^fine_s), one CTA per problem (serial in time).
+template <int T, int P>
+__global__ void __launch_bounds__(T) k_reference(Params1D p, double* __restrict__ Uref, Ctrl* ctrl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
+  const int b = blockIdx.x;
+  const StepCtx c = make_ctx(p);
+  double* Rb = Uref + (size_t)b * (p.N + 1) * p.n;
+  double y[2 * P];
+  load_state<P>(Rb, p.n, y);
+  unsigned long long nsum = 0;
+  int npeak = 0;
+  unsigned status = 0;
+  for (int s = 0; s < p.N; ++s) {
+    run_steps<T, P>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
+    store_state<P>(Rb + (size_t)(s + 1) * p.n, p.n, y);
+  }
+  if (threadIdx.x == 0 && status) atomicOr(&ctrl->status, status);
+}
+
+// Stateless propagation: nsteps steps of `scheme` for each problem (one CTA each).
+template <int T, int P>
+__global__ void __launch_bounds__(T) k_propagate(Params1D p, int scheme, double dt, int nsteps,
+                                                 const double* uin, double* uout, int* newton, Ctrl* ctrl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
+  const int b = blockIdx.x;
+  const StepCtx c = make_ctx(p);
+  double y[2 * P];
+  load_state<P>(uin + (size_t)b * p.n, p.n, y);
+  __syncthreads();  // uin and uout may alias: every thread has read its rows before any write
+  unsigned long long nsum = 0;
+  int npeak = 0;
+  unsigned status = 0;
+  run_steps<T, P>(sm, c, scheme, p.precision, y, dt, nsteps, nsum, npeak, status);
+  store_state<P>(uout + (size_t)b * p.n, p.n, y);
+  if (threadIdx.x == 0) {
+    if (newton) newton[b] = (int)nsum;
+    if (status) atomicOr(&ctrl->status, status);
+  }
+}
+
+// ------------------------------------------------------------------------- host dispatch
+
+// (T, P) by problem size: T threads, 2P rows per thread, n <= 2 T P.
+#define CH_DISPATCH_TP(n, ...)            \
+  do {                                    \
+    if ((n) <= 128) {                     \
+      constexpr int T_ = 32, P_ = 2;      \
+      __VA_ARGS__;                        \
+    } else if ((n) <= 256) {              \
+      constexpr int T_ = 64, P_ = 2;      \
+      __VA_ARGS__;                        \
+    } else if ((n) <= 512) {              \
+      constexpr int T_ = 128, P_ = 2;     \
+      __VA_ARGS__;                        \
+    } else if ((n) <= 1024) {             \
+      constexpr int T_ = 128, P_ = 4;     \
+      __VA_ARGS__;                        \
+    } else {                              \
+      constexpr int T_ = 256, P_ = 4;     \
+      __VA_ARGS__;                        \
+    }                                     \
+  } while (0)
+
+// Opt a kernel into its dynamic shared memory once per device (not during graph capture).
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  if (done.count(key)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
+
+int fine_sweep_max_grid(const Params1D& p) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  CH_DISPATCH_TP(p.n, {
+    const size_t smem = sizeof(Smem1D<T_>);
+    prep(k_fine_sweep<T_, P_>, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_>, T_, smem);
+  });
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps,
+                              int grid, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  CH_DISPATCH_TP(p.n, {
+    const size_t smem = sizeof(Smem1D<T_>);
+    e = prep(k_fine_sweep<T_, P_>, smem);
+    if (e == cudaSuccess) {
+      k_fine_sweep<T_, P_><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
+      e = cudaGetLastError();
+    }
+  });
+  return e;
+}
+
+cudaError_t launch_coarse_sweep(const Params1D& p, double* U, const double* F, double* Gold,
+                                const double* Uref, Ctrl* ctrl, ProblemState ps, int init, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  CH_DISPATCH_TP(p.n, {
+    const size_t smem = sizeof(Smem1D<T_>);
+    e = prep(k_coarse_sweep<T_, P_>, smem);
+    if (e == cudaSuccess) {
+      k_coarse_sweep<T_, P_><<<p.B, T_, smem, st>>>(p, U, F, Gold, Uref, ctrl, ps, init);
+      e = cudaGetLastError();
+    }
+  });
+  return e;
+}
+
+cudaError_t launch_tally(const Params1D& p, Ctrl* ctrl, ProblemState ps, int* host_active, cudaStream_t st) {
+  k_tally<<<1, 256, 0, st>>>(p.B, ctrl, ps, host_active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  CH_DISPATCH_TP(p.n, {
+    const size_t smem = sizeof(Smem1D<T_>);
+    e = prep(k_reference<T_, P_>, smem);
+    if (e == cudaSuccess) {
+      k_reference<T_, P_><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
+      e = cudaGetLastError();
+    }
+  });
+  return e;
+}
+
+cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nsteps, const double* uin,
+                             double* uout, int* newton, Ctrl* ctrl, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  CH_DISPATCH_TP(p.n, {
+    const size_t smem = sizeof(Smem1D<T_>);
+    e = prep(k_propagate<T_, P_>, smem);
+    if (e == cudaSuccess) {
+      k_propagate<T_, P_><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
+      e = cudaGetLastError();
+    }
+  });
+  return e;
+}
+
+}  // namespace chg

@@ -1,0 +1,446 @@
+// C ABI of the Parareal library (declared in include/ch_parareal.h): handle lifetime, device
+// memory, the iteration driver (one CUDA graph per Parareal iteration) and statistics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ch1d.cuh"
+#include "ch_parareal.h"
+
+using chg::Ctrl;
+using chg::Params1D;
+using chg::ProblemState;
+
+struct ch_parareal {
+  ch_config cfg{};
+  int B = 0;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  Params1D p{};
+  size_t pts = 0;
+  double* U = nullptr;     // [B][N+1][pts]
+  double* F = nullptr;     // [B][N][pts]
+  double* Gold = nullptr;  // [B][N][pts]
+  double* Uref = nullptr;  // [B][N+1][pts]
+  Ctrl* ctrl = nullptr;
+  ProblemState ps{};
+  void* ps_block = nullptr;
+  int* host_active = nullptr;  // mapped pinned
+  int* host_active_dev = nullptr;
+  std::vector<int> initial_set;
+  bool ref_valid = false;
+  bool ran = false;
+  int grid = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_ref = -1;  // whether the captured graph reads the reference solution
+  std::vector<cudaEvent_t> ev;  // ev[0] = start, ev[k+1] = end of iteration k (k = 0: coarse sweep)
+  cudaEvent_t ph[3] = {nullptr, nullptr, nullptr};  // inside the graph: before fine, after fine, after coarse
+  double fine_ms = 0.0, coarse_ms = 0.0;
+  int kernel_launches = 0;
+  std::vector<int> active_before;  // active problems entering each iteration
+  int iters_done = 0;
+  ch_status sticky = CH_OK;
+  std::string msg;
+};
+
+namespace {
+
+ch_status fail(ch_parareal* h, ch_status s, const std::string& m) {
+  if (h && h->sticky == CH_OK) {
+    h->sticky = s;
+    h->msg = m;
+  }
+  return s;
+}
+
+ch_status cuda_fail(ch_parareal* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return fail(h, CH_ERR_OOM, m);
+  return fail(h, CH_ERR_CUDA, m);
+}
+
+#define CH_CUDA(h, call)                                  \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+int fine_of(int v) { return (v == CH_PA_I) ? chg::SCHEME_LIN1 : (v == CH_NPA_I || v == CH_NPA_II) ? chg::SCHEME_NL : chg::SCHEME_LIN2; }
+int coarse_of(int v) { return (v == CH_PA_II) ? chg::SCHEME_LIN2 : (v == CH_NPA_II) ? chg::SCHEME_NL : chg::SCHEME_LIN1; }
+
+bool valid_common(const ch_config* c, std::string& why) {
+  if (!c) { why = "cfg is NULL"; return false; }
+  if (c->dim != 1) { why = "only dim = 1 is implemented"; return false; }
+  if (c->n < 1 || c->n > 2048) { why = "n must be in 1..2048"; return false; }
+  if (!(c->eps > 0.0) || !std::isfinite(c->eps)) { why = "eps must be > 0"; return false; }
+  if (c->newton_max < 1 || c->newton_max > 1000) { why = "newton_max must be in 1..1000"; return false; }
+  if (!(c->newton_tol > 0.0)) { why = "newton_tol must be > 0"; return false; }
+  if (c->precision != 0 && c->precision != 1) { why = "precision must be 0 or 1"; return false; }
+  return true;
+}
+
+Params1D make_params(const ch_config* c, int B) {
+  Params1D p{};
+  p.n = c->n;
+  p.B = B;
+  p.N = c->n_slices;
+  p.J = c->fine_steps;
+  p.coarse_steps = c->coarse_steps;
+  p.fine_scheme = fine_of(c->variant);
+  p.coarse_scheme = coarse_of(c->variant);
+  p.precision = c->precision;
+  p.frozen = c->frozen ? 1 : 0;
+  p.newton_max = c->newton_max;
+  p.maxit = c->max_iters;
+  p.eps2 = c->eps * c->eps;
+  p.h = 1.0 / (c->n + 1);
+  const double dT = (c->n_slices > 0) ? c->T / c->n_slices : 0.0;
+  p.dt = (c->fine_steps > 0) ? dT / c->fine_steps : 0.0;
+  p.dtc = (c->coarse_steps > 0) ? dT / c->coarse_steps : 0.0;
+  p.newton_tol = c->newton_tol;
+  p.tol = c->tol;
+  p.err_tol = c->err_tol;
+  return p;
+}
+
+ch_status device_status(ch_parareal* h, unsigned status) {
+  if (status & chg::ST_NONFINITE) return fail(h, CH_ERR_LINSOLVE, "a solve produced a non-finite value");
+  if (status & chg::ST_NEWTON) return fail(h, CH_ERR_NEWTON, "a Newton solve reached newton_max");
+  return CH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ch_status_string(ch_status s) {
+  switch (s) {
+    case CH_OK: return "CH_OK";
+    case CH_ERR_INVALID: return "CH_ERR_INVALID";
+    case CH_ERR_OOM: return "CH_ERR_OOM";
+    case CH_ERR_CUDA: return "CH_ERR_CUDA";
+    case CH_ERR_NEWTON: return "CH_ERR_NEWTON";
+    case CH_ERR_LINSOLVE: return "CH_ERR_LINSOLVE";
+    case CH_ERR_NOT_CONVERGED: return "CH_ERR_NOT_CONVERGED";
+    case CH_ERR_TIMEOUT: return "CH_ERR_TIMEOUT";
+    case CH_ERR_STATE: return "CH_ERR_STATE";
+  }
+  return "CH_ERR_UNKNOWN";
+}
+
+const char* ch_parareal_last_error(const ch_parareal* h) { return h ? h->msg.c_str() : "NULL handle"; }
+
+void ch_parareal_destroy(ch_parareal* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (auto e : h->ev) cudaEventDestroy(e);
+  for (auto e : h->ph)
+    if (e) cudaEventDestroy(e);
+  cudaFree(h->U);
+  cudaFree(h->F);
+  cudaFree(h->Gold);
+  cudaFree(h->Uref);
+  cudaFree(h->ctrl);
+  cudaFree(h->ps_block);
+  if (h->host_active) cudaFreeHost(h->host_active);
+  delete h;
+}
+
+ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream, ch_parareal** out) {
+  if (!out) return CH_ERR_INVALID;
+  *out = nullptr;
+  std::string why;
+  if (!valid_common(cfg, why)) return CH_ERR_INVALID;
+  if (batch < 1 || cfg->n_slices < 1 || cfg->n_slices > CH_MAX_ITERS - 1 || cfg->fine_steps < 1 ||
+      cfg->coarse_steps < 1 || !(cfg->T > 0.0) || cfg->variant < CH_PA_I || cfg->variant > CH_NPA_II ||
+      cfg->max_iters < 1 || cfg->max_iters > cfg->n_slices)
+    return CH_ERR_INVALID;
+  ch_parareal* h = new (std::nothrow) ch_parareal();
+  if (!h) return CH_ERR_OOM;
+  h->cfg = *cfg;
+  h->B = batch;
+  h->st = static_cast<cudaStream_t>(cuda_stream);
+  h->p = make_params(cfg, batch);
+  h->pts = (size_t)cfg->n;
+  h->initial_set.assign(batch, 0);
+  cudaGetDevice(&h->device);
+  const size_t N = cfg->n_slices, B = batch, pts = h->pts;
+  const size_t maxit = cfg->max_iters;
+  cudaError_t e;
+  auto bail = [&](cudaError_t err, const char* w) {
+    ch_status s = cuda_fail(h, err, w);
+    ch_parareal_destroy(h);
+    return s;
+  };
+  if ((e = cudaMalloc(&h->U, B * (N + 1) * pts * sizeof(double)))) return bail(e, "cudaMalloc(U)");
+  if ((e = cudaMalloc(&h->F, B * N * pts * sizeof(double)))) return bail(e, "cudaMalloc(F)");
+  if ((e = cudaMalloc(&h->Gold, B * N * pts * sizeof(double)))) return bail(e, "cudaMalloc(Gold)");
+  if ((e = cudaMalloc(&h->Uref, B * (N + 1) * pts * sizeof(double)))) return bail(e, "cudaMalloc(Uref)");
+  if ((e = cudaMalloc(&h->ctrl, sizeof(Ctrl)))) return bail(e, "cudaMalloc(ctrl)");
+  // per-problem arrays in one block: doubles first (8-byte aligned), then ints
+  const size_t nd = B * maxit + 2 * B * (maxit + 1);
+  const size_t bytes = nd * sizeof(double) + B * sizeof(unsigned long long) + 4 * B * sizeof(int);
+  if ((e = cudaMalloc(&h->ps_block, bytes))) return bail(e, "cudaMalloc(problem state)");
+  char* q = static_cast<char*>(h->ps_block);
+  h->ps.inc = reinterpret_cast<double*>(q);
+  h->ps.err_l2 = h->ps.inc + B * maxit;
+  h->ps.err_max = h->ps.err_l2 + B * (maxit + 1);
+  h->ps.newton_total = reinterpret_cast<unsigned long long*>(h->ps.err_max + B * (maxit + 1));
+  h->ps.active = reinterpret_cast<int*>(h->ps.newton_total + B);
+  h->ps.iterations = h->ps.active + B;
+  h->ps.converged = h->ps.iterations + B;
+  h->ps.newton_max = h->ps.converged + B;
+  if ((e = cudaHostAlloc(&h->host_active, sizeof(int), cudaHostAllocMapped))) return bail(e, "cudaHostAlloc");
+  if ((e = cudaHostGetDevicePointer(&h->host_active_dev, h->host_active, 0))) return bail(e, "cudaHostGetDevicePointer");
+  if ((e = cudaMemsetAsync(h->U, 0, B * (N + 1) * pts * sizeof(double), h->st))) return bail(e, "cudaMemsetAsync");
+  h->ev.resize(maxit + 2);
+  for (auto& ev : h->ev)
+    if ((e = cudaEventCreate(&ev))) return bail(e, "cudaEventCreate");
+  for (auto& ev : h->ph)
+    if ((e = cudaEventCreate(&ev))) return bail(e, "cudaEventCreate");
+  h->grid = chg::fine_sweep_max_grid(h->p);
+  if ((e = cudaGetLastError())) return bail(e, "fine_sweep_max_grid");
+  *out = h;
+  return CH_OK;
+}
+
+ch_status ch_parareal_set_initial(ch_parareal* h, int problem, const double* u0_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  if (problem < 0 || problem >= h->B || !u0_host || len != h->pts)
+    return fail(h, CH_ERR_INVALID, "set_initial: bad problem index, pointer or length");
+  CH_CUDA(h, cudaMemcpyAsync(h->U + (size_t)problem * (h->p.N + 1) * h->pts, u0_host, h->pts * sizeof(double),
+                             cudaMemcpyHostToDevice, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  h->initial_set[problem] = 1;
+  h->ref_valid = false;
+  return CH_OK;
+}
+
+ch_status ch_parareal_set_initial_device(ch_parareal* h, const double* u0_dev, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  if (!u0_dev || len != (size_t)h->B * h->pts) return fail(h, CH_ERR_INVALID, "set_initial_device: bad pointer or length");
+  CH_CUDA(h, cudaMemcpy2DAsync(h->U, (h->p.N + 1) * h->pts * sizeof(double), u0_dev, h->pts * sizeof(double),
+                               h->pts * sizeof(double), h->B, cudaMemcpyDeviceToDevice, h->st));
+  for (auto& v : h->initial_set) v = 1;
+  h->ref_valid = false;
+  return CH_OK;
+}
+
+ch_status ch_parareal_set_initial_batch(ch_parareal* h, const double* u0_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  if (!u0_host || len != (size_t)h->B * h->pts) return fail(h, CH_ERR_INVALID, "set_initial_batch: bad pointer or length");
+  CH_CUDA(h, cudaMemcpy2DAsync(h->U, (h->p.N + 1) * h->pts * sizeof(double), u0_host, h->pts * sizeof(double),
+                               h->pts * sizeof(double), h->B, cudaMemcpyHostToDevice, h->st));
+  for (auto& v : h->initial_set) v = 1;
+  h->ref_valid = false;
+  return CH_OK;
+}
+
+static bool all_initial(const ch_parareal* h) {
+  for (int v : h->initial_set)
+    if (!v) return false;
+  return true;
+}
+
+ch_status ch_parareal_compute_reference(ch_parareal* h) {
+  if (!h) return CH_ERR_INVALID;
+  if (h->sticky != CH_OK) return h->sticky;
+  if (!all_initial(h)) return fail(h, CH_ERR_STATE, "compute_reference before set_initial");
+  const size_t N = h->p.N, pts = h->pts;
+  CH_CUDA(h, cudaMemcpy2DAsync(h->Uref, (N + 1) * pts * sizeof(double), h->U, (N + 1) * pts * sizeof(double),
+                               pts * sizeof(double), h->B, cudaMemcpyDeviceToDevice, h->st));
+  CH_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->st));
+  CH_CUDA(h, chg::launch_reference(h->p, h->Uref, h->ctrl, h->st));
+  Ctrl c;
+  CH_CUDA(h, cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  ch_status s = device_status(h, c.status);
+  if (s != CH_OK) return s;
+  h->ref_valid = true;
+  return CH_OK;
+}
+
+static ch_status enqueue_iteration(ch_parareal* h) {
+  const double* ref = h->ref_valid ? h->Uref : nullptr;
+  CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
+  CH_CUDA(h, chg::launch_fine_sweep(h->p, h->U, h->F, h->ctrl, h->ps, h->grid, h->st));
+  CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
+  CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 0, h->st));
+  CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
+  CH_CUDA(h, chg::launch_tally(h->p, h->ctrl, h->ps, h->host_active_dev, h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_run(ch_parareal* h) {
+  if (!h) return CH_ERR_INVALID;
+  if (h->sticky != CH_OK) return h->sticky;
+  if (!all_initial(h)) return fail(h, CH_ERR_STATE, "run before set_initial");
+  const int B = h->B, maxit = h->p.maxit;
+  // reset control and per-problem state
+  std::vector<int> ones(B, 1);
+  CH_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->st));
+  CH_CUDA(h, cudaMemsetAsync(h->ps_block, 0,
+                             (size_t)B * maxit * sizeof(double) + 2 * (size_t)B * (maxit + 1) * sizeof(double) +
+                                 B * sizeof(unsigned long long) + 4 * (size_t)B * sizeof(int),
+                             h->st));
+  CH_CUDA(h, cudaMemcpyAsync(h->ps.active, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  const double* ref = h->ref_valid ? h->Uref : nullptr;
+  CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
+  CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 1, h->st));
+  CH_CUDA(h, cudaEventRecord(h->ev[1], h->st));
+  // one CUDA graph per iteration: fine sweep, coarse sweep with correction and norms, tally.
+  // The graph reads k and the active set from device memory, so one capture serves all k.
+  if (!h->gexec || h->graph_ref != (h->ref_valid ? 1 : 0)) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    cudaStream_t cs = nullptr;
+    CH_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CH_CUDA(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t keep = h->st;
+    h->st = cs;
+    ch_status s = enqueue_iteration(h);
+    h->st = keep;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (s != CH_OK) return s;
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+    h->graph = g;
+    CH_CUDA(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->graph_ref = h->ref_valid ? 1 : 0;
+  }
+  h->active_before.clear();
+  h->fine_ms = h->coarse_ms = 0.0;
+  h->kernel_launches = 1;
+  int active = B;
+  int k = 0;
+  for (; k < maxit && active > 0; ++k) {
+    h->active_before.push_back(active);
+    CH_CUDA(h, cudaGraphLaunch(h->gexec, h->st));
+    CH_CUDA(h, cudaEventRecord(h->ev[k + 2], h->st));
+    CH_CUDA(h, cudaStreamSynchronize(h->st));
+    h->kernel_launches += 3;
+    float fm = 0.f, cm = 0.f;
+    CH_CUDA(h, cudaEventElapsedTime(&fm, h->ph[0], h->ph[1]));
+    CH_CUDA(h, cudaEventElapsedTime(&cm, h->ph[1], h->ph[2]));
+    h->fine_ms += fm;
+    h->coarse_ms += cm;
+    active = *(volatile int*)h->host_active;
+  }
+  h->iters_done = k;
+  h->ran = true;
+  Ctrl c;
+  CH_CUDA(h, cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  ch_status s = device_status(h, c.status);
+  if (s != CH_OK) return s;
+  if ((h->p.tol > 0.0 || (h->p.err_tol > 0.0 && h->ref_valid)) && active > 0) return CH_ERR_NOT_CONVERGED;
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_slices(ch_parareal* h, int problem, double* out_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  const size_t want = (size_t)(h->p.N + 1) * h->pts;
+  if (problem < 0 || problem >= h->B || !out_host || len != want)
+    return fail(h, CH_ERR_INVALID, "get_slices: bad problem index, pointer or length");
+  CH_CUDA(h, cudaMemcpyAsync(out_host, h->U + (size_t)problem * want, want * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_slices_batch(ch_parareal* h, double* out_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  const size_t want = (size_t)h->B * (h->p.N + 1) * h->pts;
+  if (!out_host || len != want) return fail(h, CH_ERR_INVALID, "get_slices_batch: bad pointer or length");
+  CH_CUDA(h, cudaMemcpyAsync(out_host, h->U, want * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_slices_device(ch_parareal* h, double* out_dev, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  const size_t want = (size_t)h->B * (h->p.N + 1) * h->pts;
+  if (!out_dev || len != want) return fail(h, CH_ERR_INVALID, "get_slices_device: bad pointer or length");
+  CH_CUDA(h, cudaMemcpyAsync(out_dev, h->U, want * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_reference(ch_parareal* h, int problem, double* out_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  const size_t want = (size_t)(h->p.N + 1) * h->pts;
+  if (!h->ref_valid) return fail(h, CH_ERR_STATE, "get_reference before compute_reference");
+  if (problem < 0 || problem >= h->B || !out_host || len != want)
+    return fail(h, CH_ERR_INVALID, "get_reference: bad problem index, pointer or length");
+  CH_CUDA(h, cudaMemcpyAsync(out_host, h->Uref + (size_t)problem * want, want * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
+  if (!h) return CH_ERR_INVALID;
+  if (!out || problem < 0 || problem >= h->B) return fail(h, CH_ERR_INVALID, "get_stats: bad problem index or pointer");
+  if (!h->ran) return fail(h, CH_ERR_STATE, "get_stats before run");
+  std::memset(out, 0, sizeof(*out));
+  const int maxit = h->p.maxit;
+  int it = 0, conv = 0, nmax = 0;
+  unsigned long long ntot = 0;
+  CH_CUDA(h, cudaMemcpyAsync(&it, h->ps.iterations + problem, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(&conv, h->ps.converged + problem, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(&nmax, h->ps.newton_max + problem, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(&ntot, h->ps.newton_total + problem, sizeof(ntot), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(out->inc, h->ps.inc + (size_t)problem * maxit, maxit * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(out->err_l2, h->ps.err_l2 + (size_t)problem * (maxit + 1), (maxit + 1) * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(out->err_max, h->ps.err_max + (size_t)problem * (maxit + 1), (maxit + 1) * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->st));
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  out->iterations = it;
+  out->converged = conv;
+  out->newton_total = (long long)ntot;
+  out->newton_max = nmax;
+  for (int k = 0; k <= h->iters_done; ++k) {
+    float ms = 0.f;
+    CH_CUDA(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[k + 1]));
+    out->t_iter_ms[k] = ms;
+  }
+  long long fps = 0;
+  for (int k = 0; k < it; ++k) fps += (long long)(h->p.N - k) * h->p.J * (long long)h->pts;
+  out->fine_point_steps = fps;
+  out->fine_sweep_ms = h->fine_ms;
+  out->coarse_sweep_ms = h->coarse_ms;
+  out->fine_sweep_launches = h->iters_done;
+  out->kernel_launches = h->kernel_launches;
+  return CH_OK;
+}
+
+ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, int nsteps, const double* u_in_dev,
+                       double* u_out_dev, int* newton_dev, void* cuda_stream) {
+  std::string why;
+  if (!valid_common(cfg, why) || batch < 1 || nsteps < 0 || !(dt > 0.0) || !u_in_dev || !u_out_dev ||
+      scheme < CH_SCHEME_LIN1 || scheme > CH_SCHEME_LIN2)
+    return CH_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  Params1D p = make_params(cfg, batch);
+  Ctrl* ctrl = nullptr;
+  if (cudaMalloc(&ctrl, sizeof(Ctrl)) != cudaSuccess) return CH_ERR_OOM;
+  ch_status s = CH_OK;
+  cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+  if (e == cudaSuccess) e = chg::launch_propagate(p, scheme, dt, nsteps, u_in_dev, u_out_dev, newton_dev, ctrl, st);
+  Ctrl c{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) s = CH_ERR_CUDA;
+  else if (c.status & chg::ST_NONFINITE) s = CH_ERR_LINSOLVE;
+  else if (c.status & chg::ST_NEWTON) s = CH_ERR_NEWTON;
+  cudaFree(ctrl);
+  return s;
+}
+
+}  // extern "C"

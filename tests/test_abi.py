@@ -1,0 +1,87 @@
+"""C ABI checks that need no GPU: the library loads, exports every declared symbol, and
+rejects invalid configurations before touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2304_14074_gb300 as ch
+from paper_2304_14074_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ch_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ch.load()
+    decl = declared_functions()
+    assert len(decl) >= 15
+    missing = [n for n in decl if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(decl) == set(ch.EXPORTED_SYMBOLS)
+
+
+def test_status_strings():
+    lib = ch.load()
+    for code, name in ch.STATUS.items():
+        assert lib.ch_status_string(code).decode() == name
+
+
+def _cfg(**kw):
+    base = dict(n=64, eps=0.05, T=0.1, n_slices=4, fine_steps=10)
+    base.update(kw)
+    return ch.Config(**base).c()
+
+
+@pytest.mark.parametrize("bad", [dict(dim=2), dict(n=0), dict(n=5000), dict(eps=0.0), dict(T=-1.0),
+                                 dict(n_slices=0), dict(fine_steps=0), dict(coarse_steps=0),
+                                 dict(max_iters=9), dict(precision=3), dict(newton_tol=0.0),
+                                 dict(variant="PA-I", newton_max=0)])
+def test_create_rejects_invalid_config_without_device(bad):
+    lib = ch.load()
+    cc = _cfg(**bad)
+    h = C.c_void_p()
+    assert lib.ch_parareal_create(C.byref(cc), 1, None, C.byref(h)) == 1
+    assert not h.value
+
+
+def test_create_rejects_bad_batch_and_null_out():
+    lib = ch.load()
+    cc = _cfg()
+    h = C.c_void_p()
+    assert lib.ch_parareal_create(C.byref(cc), 0, None, C.byref(h)) == 1
+    assert lib.ch_parareal_create(C.byref(cc), 1, None, None) == 1
+    assert lib.ch_parareal_create(None, 1, None, C.byref(h)) == 1
+
+
+def test_propagate_rejects_invalid_arguments_without_device():
+    lib = ch.load()
+    cc = _cfg()
+    assert lib.ch_propagate(C.byref(cc), 0, 0, 1e-3, 1, C.c_void_p(8), C.c_void_p(8), None, None) == 1
+    assert lib.ch_propagate(C.byref(cc), 1, 7, 1e-3, 1, C.c_void_p(8), C.c_void_p(8), None, None) == 1
+    assert lib.ch_propagate(C.byref(cc), 1, 0, 0.0, 1, C.c_void_p(8), C.c_void_p(8), None, None) == 1
+    assert lib.ch_propagate(C.byref(cc), 1, 0, 1e-3, 1, None, C.c_void_p(8), None, None) == 1
+
+
+def test_destroy_accepts_null_and_last_error_on_null():
+    lib = ch.load()
+    lib.ch_parareal_destroy(None)
+    assert lib.ch_parareal_last_error(None).decode() == "NULL handle"
+
+
+def test_binding_struct_layout_matches_header():
+    # ch_config: 2 ints, 2 doubles, 4 ints, double, int, double, 3 ints, double -> 88 bytes with padding
+    assert C.sizeof(_lib._Config) == 88
+    assert C.sizeof(_lib._Stats) == 8 + 4 * 8 * ch.CH_MAX_ITERS + 8 + 8 + 8 + 8 + 8 + 4 + 4
