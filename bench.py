@@ -37,6 +37,10 @@ WORKLOADS = {
     "c2": dict(name="1D nonlinear Parareal NPA-I M=1024 eps=0.02 T=1 N=64 J=200 newton_tol=1e-12 batch=256",
                n=1024, eps=0.02, T=1.0, N=64, J=200, batch=256, variant="NPA-I", newton_tol=1e-12,
                amp=0.1, precision=1, ttol=True),
+    # profiling case of the same kernels: c2's batch, grid and slices, 10 fine steps per slice
+    "c2-profile": dict(name="1D NPA-I M=1024 eps=0.02 N=64 J=10 (dt as c2) batch=256, profiling case",
+                       n=1024, eps=0.02, T=0.05, N=64, J=10, batch=256, variant="NPA-I", newton_tol=1e-12,
+                       amp=0.1, precision=1, ttol=False),
     "c1": dict(name="1D linear Parareal PA-I M=128 eps=0.05 T=0.1 N=16 dt=1e-5 batch=1",
                n=128, eps=0.05, T=0.1, N=16, J=625, batch=1, variant="PA-I", newton_tol=1e-12,
                amp=0.1, precision=0, ttol=True),

@@ -172,7 +172,24 @@ int orc1d_step(const orc_params* p, int scheme, double dt, double t_next, const 
       } else {
         assemble(n, 3.0 * dt, e2 * dt, w, a);
       }
-      rc = orc_band_solve(n, 2, 2, a, nxt);
+      if (p->newton_form == 1 && !p->frozen) {
+        /* H(Y) = Y + eps^2 dt D_h (D_h Y) - dt D_h Y^3 - Yhat (Eq. 3.17); Y_{m+1} = Y_m - J^{-1} H */
+        double* dy = (double*)malloc(sizeof(double) * n);
+        double* d2y = (double*)malloc(sizeof(double) * n);
+        double* y3 = (double*)malloc(sizeof(double) * n);
+        double* dy3 = (double*)malloc(sizeof(double) * n);
+        if (!dy || !d2y || !y3 || !dy3) { free(dy); free(d2y); free(y3); free(dy3); rc = 1; break; }
+        orc1d_dh_apply(n, y, dy);
+        orc1d_dh_apply(n, dy, d2y);
+        for (int j = 0; j < n; ++j) y3[j] = y[j] * y[j] * y[j];
+        orc1d_dh_apply(n, y3, dy3);
+        for (int j = 0; j < n; ++j) nxt[j] = y[j] + e2 * dt * d2y[j] - dt * dy3[j] - yhat[j];
+        rc = orc_band_solve(n, 2, 2, a, nxt);
+        for (int j = 0; j < n; ++j) nxt[j] = y[j] - nxt[j];
+        free(dy); free(d2y); free(y3); free(dy3);
+      } else {
+        rc = orc_band_solve(n, 2, 2, a, nxt);
+      }
       if (rc) break;
       double diff = 0.0;
       for (int j = 0; j < n; ++j) {

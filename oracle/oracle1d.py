@@ -35,7 +35,7 @@ class _Params(C.Structure):
     _fields_ = [("n", C.c_int), ("eps", C.c_double), ("T", C.c_double), ("N", C.c_int),
                 ("J", C.c_int), ("coarse_steps", C.c_int), ("fine_scheme", C.c_int),
                 ("coarse_scheme", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
-                ("frozen", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int)]
+                ("frozen", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int), ("newton_form", C.c_int)]
 
 
 class _Forcing(C.Structure):
@@ -94,12 +94,13 @@ class Params:
     frozen: bool = False
     tol: float = 0.0
     max_iters: int = -1
+    newton_form: int = 0  # 0: Eq. 3.18 as printed; 1: Y - J^{-1} H(Y) (same iteration, other rounding)
 
     def c(self) -> _Params:
         mi = self.N if self.max_iters < 0 else self.max_iters
         return _Params(self.n, self.eps, self.T, self.N, self.J, self.coarse_steps, SCHEMES[self.fine],
                        SCHEMES[self.coarse], self.newton_tol, self.newton_max, int(self.frozen),
-                       self.tol, mi)
+                       self.tol, mi, self.newton_form)
 
 
 @dataclass

@@ -4,10 +4,12 @@ Tolerances. Two correct FP64 solvers of the implicit steps differ by the roundin
 step matrix: its entries are up to 16 alpha with alpha = eps^2 dt / h^4 while the smooth
 solution components see eigenvalues near 1, so one solve is accurate to about
 u * (1 + 16 alpha + 4 beta max w), u = 2^-53, beta = c dt / h^2 (the same bound sets the
-Newton rounding floor). Single-step tests allow 64 times that bound. Whole-run tests use
-1e-11 where the problem's own sensitivity to a 1e-15 relative perturbation of u^0 is below
-it (c1), and ten times that measured sensitivity otherwise (c2's full horizon, where
-spinodal growth amplifies rounding by about 1e6).
+Newton rounding floor). Single-step tests allow 64 times that bound. Whole-run tests require
+1e-11 or, where that is below what FP64 can resolve, four times the measured floor: the
+difference between two correct FP64 oracles that run the same Newton iteration with
+different rounding (Eq. 3.18 as printed, and the unsimplified step Y - J^-1 H(Y)). Spinodal
+growth amplifies the per-step rounding, so at c2's size that floor is about 4e-7 after two
+iterations.
 """
 import math
 
@@ -34,6 +36,21 @@ def step_bound(n, eps, dt, c=3.0, wmax=1.0):
     alpha = eps ** 2 * dt / h ** 4
     beta = c * dt / h ** 2
     return U_ROUND * (1 + 16 * alpha + 4 * beta * wmax)
+
+
+def oracle_and_floor(p, u0, Ufine=None):
+    """Oracle Parareal and its rounding floor (Eq. 3.18 form vs the unsimplified Newton form)."""
+    r = o.parareal(p, u0, Ufine)
+    if FINE_OF_SCHEME_NL(p):
+        q = o.Params(**{**p.__dict__, "newton_form": 1})
+        floor = float(np.max(np.abs(o.parareal(q, u0).U - r.U)))
+    else:
+        floor = 0.0
+    return r, max(1e-11, 4 * floor)
+
+
+def FINE_OF_SCHEME_NL(p):
+    return p.fine == "nl" or p.coarse == "nl"
 
 
 def oracle_params(cfg, **kw):
@@ -101,7 +118,7 @@ def test_frozen_steps_match_lemma_3_1_on_gpu(gpu_lib):
         for k, p in enumerate(modes):
             y = (2.0 * (n + 1) ** 2) * (1.0 - math.cos(p * math.pi / (n + 1)))
             g = (1 + i * dt * y) / (1 + i * dt * y + eps ** 2 * dt * y ** 2)
-            assert np.max(np.abs(out[k] - g * u[k])) < 1e-12, (scheme, p)
+            assert np.max(np.abs(out[k] - g * u[k])) < 64 * step_bound(n, eps, dt), (scheme, p)
 
 
 # ------------------------------------------------------------------------- Parareal
@@ -175,10 +192,10 @@ def test_intermediate_iterates_match_oracle(gpu_lib, k):
     assert np.array_equal(U[: k + 1], Uref[: k + 1])  # slices n <= k are exact (bitwise, same F)
     p = oracle_params(cfg)
     Uf = o.fine_solution(p, u0)
-    r = o.parareal(p, u0, Uf)
-    assert np.max(np.abs(U - r.U)) <= 1e-11
+    r, tol = oracle_and_floor(p, u0, Uf)
+    assert np.max(np.abs(U - r.U)) <= tol
     st = pr.stats(0)
-    assert np.allclose(st["err_max"], r.err_max, rtol=1e-6, atol=1e-11)
+    assert np.allclose(st["err_max"], r.err_max, rtol=1e-6, atol=tol)
     pr.close()
 
 
@@ -199,14 +216,14 @@ def test_frozen_parareal_matches_closed_form_on_gpu(gpu_lib):
         U = pr.get_slices(0)
         coef = np.array([sum(math.comb(s, j) * (bb - a) ** j * a ** (s - j) for j in range(min(k, s) + 1))
                          for s in range(N + 1)])
-        assert np.max(np.abs(U - coef[:, None] * u0[None, :])) < 1e-12
+        assert np.max(np.abs(U - coef[:, None] * u0[None, :])) < 64 * step_bound(n, eps, dt, c=1.0)
         pr.close()
 
 
 def test_c2_full_size_sampled_problems(gpu_lib):
     """1D NPA-I, M=1024, eps=0.02, T=1, N=64, J=200, Newton tol 1e-12, batch 256, u0 = 0.1 U(-1,1)
     seeds 0..255, the launch configuration of the benchmark; two iterations; sampled problems are
-    compared with the oracle within ten times the oracle's own sensitivity to rounding."""
+    compared with the oracle within four times the oracle's own rounding floor."""
     ch = gpu_lib
     B = 256
     cfg = ch.Config(n=1024, eps=0.02, T=1.0, n_slices=64, fine_steps=200, variant="NPA-I", newton_tol=1e-12,
@@ -216,12 +233,11 @@ def test_c2_full_size_sampled_problems(gpu_lib):
     p = oracle_params(cfg)
     for b in (0, 255):
         U = pr.get_slices(b)
-        r = o.parareal(p, u0s[b])
-        pert = u0s[b] * (1 + 1e-15 * ch_inputs.normal(777 + b, 1024, 1.0))
-        r2 = o.parareal(p, pert)
-        floor = np.max(np.abs(r2.U - r.U))
+        r, tol = oracle_and_floor(p, u0s[b])
         err = np.max(np.abs(U - r.U))
-        assert err <= max(1e-11, 10 * floor), (b, err, floor)
+        assert err <= tol, (b, err, tol)
+        # slice 1 after two iterations is exact: F(u0), far from the amplified tail
+        assert np.max(np.abs(U[1] - r.U[1])) <= 64 * step_bound(1024, 0.02, 1.0 / 64 / 200) * 200
         assert pr.stats(b)["iterations"] == 2
     pr.close()
 
@@ -267,7 +283,10 @@ def test_precisions_agree_and_runs_are_deterministic(gpu_lib):
             pr.close()
         assert np.array_equal(runs[0], runs[1])
         out[prec] = runs[0]
-    assert np.max(np.abs(out[0] - out[1])) <= 1e-11
+    r, tol = oracle_and_floor(o.Params(n=n, eps=0.03, T=0.02, N=5, J=20, fine="nl", coarse="lin1",
+                                       newton_tol=1e-12, max_iters=3), u0)
+    assert np.max(np.abs(out[0] - out[1])) <= tol
+    assert np.max(np.abs(out[1] - r.U)) <= tol
 
 
 def test_errors_are_reported_not_faulted(gpu_lib):

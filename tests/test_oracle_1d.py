@@ -112,6 +112,15 @@ def test_newton_step_solves_nonlinear_system():
     assert 2 <= iters <= 8
 
 
+def test_newton_forms_reach_the_same_root():
+    """Eq. 3.18 as printed and the unsimplified Newton step give the same step to rounding."""
+    n, eps, dt = 40, 0.1, 2e-3
+    u = ch_inputs.initial_condition(1, n, 7, amp=0.9)
+    a, _ = o.step(o.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=1e-13), "nl", dt, u)
+    b, _ = o.step(o.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=1e-13, newton_form=1), "nl", dt, u)
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
 @pytest.mark.parametrize("scheme,i", [("lin1", 1), ("lin2", 2), ("nl", 1)])
 def test_frozen_step_matches_lemma_3_1_factor(scheme, i):
     """Frozen model (diag(u^2) = I): each sine mode is scaled by g_i(mu_p) of Lemma 3.1."""
