@@ -567,17 +567,20 @@ static cudaError_t prep(K kernel, size_t smem) {
   return e;
 }
 
-int fine_sweep_max_grid(const Params1D& p) {
+cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   CH_DISPATCH_TP(p.n, {
     const size_t smem = sizeof(Smem1D<T_>);
-    prep(k_fine_sweep<T_, P_>, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_>, T_, smem);
+    e = prep(k_fine_sweep<T_, P_>, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_>, T_, smem);
+    if (e == cudaSuccess) e = prep(k_coarse_sweep<T_, P_>, smem);
   });
   if (per_sm < 1) per_sm = 1;
-  return sms * per_sm;
+  *grid = sms * per_sm;
+  return e;
 }
 
 cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps,

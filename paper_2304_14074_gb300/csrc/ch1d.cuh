@@ -65,7 +65,7 @@ cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaSt
 cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nsteps, const double* uin,
                              double* uout, int* newton, Ctrl* ctrl, cudaStream_t st);
 // CTAs of the fine sweep that fit on the device at once (for the persistent grid).
-int fine_sweep_max_grid(const Params1D& p);
+cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid);
 // Largest n the kernels support.
 constexpr int kMaxN1D = 4096;
 

@@ -1,5 +1,5 @@
 // C ABI of the Parareal library (declared in include/ch_parareal.h): handle lifetime, device
-// memory, the iteration driver (one CUDA graph per Parareal iteration) and statistics.
+// memory, the iteration driver (CUDA graphs replayed per Parareal iteration) and statistics.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,11 +35,13 @@ struct ch_parareal {
   bool ref_valid = false;
   bool ran = false;
   int grid = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_ref = -1;  // whether the captured graph reads the reference solution
+  // Each iteration replays two graphs, [fine sweep] then [coarse sweep + correction, tally];
+  // timing events are recorded on the stream between them (events inside a graph cannot time).
+  cudaGraphExec_t gfine = nullptr;
+  cudaGraphExec_t gcoarse = nullptr;
+  int graph_ref = -1;  // whether the captured coarse graph reads the reference solution
   std::vector<cudaEvent_t> ev;  // ev[0] = start, ev[k+1] = end of iteration k (k = 0: coarse sweep)
-  cudaEvent_t ph[3] = {nullptr, nullptr, nullptr};  // inside the graph: before fine, after fine, after coarse
+  cudaEvent_t ph[3] = {nullptr, nullptr, nullptr};  // before fine, after fine, after coarse
   double fine_ms = 0.0, coarse_ms = 0.0;
   int kernel_launches = 0;
   std::vector<int> active_before;  // active problems entering each iteration
@@ -138,8 +140,8 @@ const char* ch_parareal_last_error(const ch_parareal* h) { return h ? h->msg.c_s
 void ch_parareal_destroy(ch_parareal* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->gfine) cudaGraphExecDestroy(h->gfine);
+  if (h->gcoarse) cudaGraphExecDestroy(h->gcoarse);
   for (auto e : h->ev) cudaEventDestroy(e);
   for (auto e : h->ph)
     if (e) cudaEventDestroy(e);
@@ -164,6 +166,7 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
     return CH_ERR_INVALID;
   ch_parareal* h = new (std::nothrow) ch_parareal();
   if (!h) return CH_ERR_OOM;
+  (void)cudaGetLastError();  // a stale non-sticky error of an earlier call must not fail this one
   h->cfg = *cfg;
   h->B = batch;
   h->st = static_cast<cudaStream_t>(cuda_stream);
@@ -205,8 +208,7 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
     if ((e = cudaEventCreate(&ev))) return bail(e, "cudaEventCreate");
   for (auto& ev : h->ph)
     if ((e = cudaEventCreate(&ev))) return bail(e, "cudaEventCreate");
-  h->grid = chg::fine_sweep_max_grid(h->p);
-  if ((e = cudaGetLastError())) return bail(e, "fine_sweep_max_grid");
+  if ((e = chg::fine_sweep_max_grid(h->p, &h->grid))) return bail(e, "fine_sweep_max_grid");
   *out = h;
   return CH_OK;
 }
@@ -267,16 +269,34 @@ ch_status ch_parareal_compute_reference(ch_parareal* h) {
   return CH_OK;
 }
 
-static ch_status enqueue_iteration(ch_parareal* h) {
-  const double* ref = h->ref_valid ? h->Uref : nullptr;
-  CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
-  CH_CUDA(h, chg::launch_fine_sweep(h->p, h->U, h->F, h->ctrl, h->ps, h->grid, h->st));
-  CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
-  CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 0, h->st));
-  CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
-  CH_CUDA(h, chg::launch_tally(h->p, h->ctrl, h->ps, h->host_active_dev, h->st));
+}  // extern "C"
+
+// Captures the work enqueued by `enqueue` on a private stream into an executable graph.
+template <typename F>
+static ch_status capture(ch_parareal* h, F enqueue, cudaGraphExec_t* out) {
+  cudaStream_t cs = nullptr;
+  CH_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(h, e, "cudaStreamBeginCapture");
+  }
+  cudaError_t le = enqueue(cs);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, le, "kernel launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
   return CH_OK;
 }
+
+extern "C" {
 
 ch_status ch_parareal_run(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
@@ -295,25 +315,22 @@ ch_status ch_parareal_run(ch_parareal* h) {
   CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
   CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 1, h->st));
   CH_CUDA(h, cudaEventRecord(h->ev[1], h->st));
-  // one CUDA graph per iteration: fine sweep, coarse sweep with correction and norms, tally.
-  // The graph reads k and the active set from device memory, so one capture serves all k.
-  if (!h->gexec || h->graph_ref != (h->ref_valid ? 1 : 0)) {
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
-    cudaStream_t cs = nullptr;
-    CH_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    CH_CUDA(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaStream_t keep = h->st;
-    h->st = cs;
-    ch_status s = enqueue_iteration(h);
-    h->st = keep;
-    cudaGraph_t g = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(cs, &g);
-    cudaStreamDestroy(cs);
+  // The iteration graphs read k and the active set from device memory, so one capture
+  // serves every iteration.
+  if (!h->gfine) {
+    ch_status s = capture(h, [&](cudaStream_t cs) {
+      return chg::launch_fine_sweep(h->p, h->U, h->F, h->ctrl, h->ps, h->grid, cs);
+    }, &h->gfine);
     if (s != CH_OK) return s;
-    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
-    h->graph = g;
-    CH_CUDA(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
+  }
+  if (!h->gcoarse || h->graph_ref != (h->ref_valid ? 1 : 0)) {
+    if (h->gcoarse) { cudaGraphExecDestroy(h->gcoarse); h->gcoarse = nullptr; }
+    ch_status s = capture(h, [&](cudaStream_t cs) {
+      cudaError_t e = chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 0, cs);
+      if (e == cudaSuccess) e = chg::launch_tally(h->p, h->ctrl, h->ps, h->host_active_dev, cs);
+      return e;
+    }, &h->gcoarse);
+    if (s != CH_OK) return s;
     h->graph_ref = h->ref_valid ? 1 : 0;
   }
   h->active_before.clear();
@@ -323,7 +340,11 @@ ch_status ch_parareal_run(ch_parareal* h) {
   int k = 0;
   for (; k < maxit && active > 0; ++k) {
     h->active_before.push_back(active);
-    CH_CUDA(h, cudaGraphLaunch(h->gexec, h->st));
+    CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
+    CH_CUDA(h, cudaGraphLaunch(h->gfine, h->st));
+    CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
+    CH_CUDA(h, cudaGraphLaunch(h->gcoarse, h->st));
+    CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
     CH_CUDA(h, cudaEventRecord(h->ev[k + 2], h->st));
     CH_CUDA(h, cudaStreamSynchronize(h->st));
     h->kernel_launches += 3;
