@@ -174,6 +174,47 @@ ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, i
                        const double* u_in_dev, double* u_out_dev, int* newton_dev,
                        void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free solve. The paper has no counterpart: this is a library-level service.
+ *
+ * For callers that cannot call cudaMalloc: applications whose device memory belongs to
+ * another allocator (a framework's caching pool that must not be bypassed, or a memory budget
+ * fixed at start-up), and latency-critical loops where cudaMalloc/cudaFree would synchronise
+ * the device. It runs the same Parareal kernels as ch_parareal_run, but every scratch buffer
+ * (control block, per-problem histories, F(U_n^k), G(U_n^k)) lives in one file-scope device
+ * array of CH_NOALLOC_SCRATCH_BYTES (16 MiB) that each GPU loading the library holds until the
+ * process exits. It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *  cfg, batch   as for ch_parareal_create (dim = 1); err_tol is ignored (there is no
+ *               reference solution here), tol and max_iters apply.
+ *  u0_dev       device, [batch][n] initial states.
+ *  U_dev        device, [batch][N+1][n] output: the final iterate (slice 0 = u^0);
+ *               len must equal batch (N+1) n.
+ *  iterations_host  NULL or host int receiving the completed Parareal iterations.
+ *  cuda_stream  stream the work is enqueued on; the call synchronises it before returning.
+ *
+ * Returns CH_ERR_INVALID for a bad argument and when the problem needs more scratch than the
+ * array holds, i.e. CH_NOALLOC_SCRATCH_NEEDED(batch, N, n, max_iters) > CH_NOALLOC_SCRATCH_BYTES;
+ * otherwise the codes of ch_parareal_run (CH_ERR_NEWTON, CH_ERR_LINSOLVE, CH_ERR_NOT_CONVERGED,
+ * CH_ERR_CUDA).
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture begins. Every call
+ * shares the one array and overwrites it (the parts that must start at zero are cleared by
+ * each call), so calls whose work overlaps on the GPU, from several threads or streams, race
+ * and must be serialised by the caller.
+ */
+#define CH_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+#define CH_NOALLOC_ALIGN256(x) ((((size_t)(x)) + 255) & ~(size_t)255)
+#define CH_NOALLOC_SCRATCH_NEEDED(B, N, n, maxit)                                                  \
+  ((size_t)256 +                                                                                     \
+   CH_NOALLOC_ALIGN256(((size_t)(B) * (maxit) + 2 * (size_t)(B) * ((maxit) + 1)) * 8 + (size_t)(B) * 8 + \
+                       (size_t)(B) * 16) +                                                         \
+   2 * CH_NOALLOC_ALIGN256((size_t)(B) * (N) * (n) * 8))
+
+ch_status ch_parareal_solve_noalloc(const ch_config* cfg, int batch, const double* u0_dev, double* U_dev,
+                                    size_t len, int* iterations_host, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

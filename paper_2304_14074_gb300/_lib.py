@@ -28,6 +28,7 @@ EXPORTED_SYMBOLS = [
     "ch_parareal_compute_reference", "ch_parareal_run", "ch_parareal_get_slices",
     "ch_parareal_get_slices_device", "ch_parareal_get_reference", "ch_parareal_get_stats",
     "ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_propagate",
+    "ch_parareal_solve_noalloc",
 ]
 
 
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True):
     lib.ch_status_string.argtypes = [C.c_int]
     lib.ch_status_string.restype = C.c_char_p
     lib.ch_propagate.argtypes = [C.POINTER(_Config), C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp]
+    lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     for name in EXPORTED_SYMBOLS:
         if name not in ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string"):
             getattr(lib, name).restype = C.c_int
