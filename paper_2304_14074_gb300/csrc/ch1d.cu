@@ -190,6 +190,99 @@ __device__ int nl_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], doub
   return ok ? m : -m;
 }
 
+// One step of the nonlinear scheme Eq. 2.3 by Newton (Eq. 3.17/3.18) with the Jacobian solve in
+// FP32 through a balanced mixed form. The correction d of J d = H, J = I + eps^2 dt A^2 + c dt A W
+// (A = -D_h, W = diag(w), c = 3, w = Y^2), is found from the pair (d, v) with
+//     d + s A v = H,      v - (eps^2 dt A d + c dt W d) / s = 0,      s = eps sqrt(dt),
+// which eliminates to J d = H. With this s both couplings have size sigma = eps sqrt(dt) / h^2,
+// about the square root of the 16 eps^2 dt / h^4 of the pentadiagonal form, so the FP32 solve is
+// accurate to ~3e-6 instead of ~3e-3 and Newton keeps its quadratic rate down to the FP64
+// rounding floor. Unknowns (d_i, v_i) form the 2x2 blocks
+//     B_i = [[1, 2 sigma], [-2 sigma - c dt w_i / s, 1]],  A_i = C_i = [[0, -sigma], [sigma, 0]].
+// FP64 is spent on the residual H and the update only; w comes from a float shadow of Y, and the
+// stop test uses the float correction. The iteration starts from the linear extrapolation
+// 2 u^n - u^{n-1} when the previous state of the same propagation is known (u^n otherwise);
+// the root it converges to is the same (the step is the unique minimiser of a strictly convex
+// functional), only the number of iterations changes.
+template <int T, int P>
+__device__ int nl_step_mixed(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double (&yp)[2 * P],
+                             bool have_prev, float (&y32)[2 * P], double dt, bool& bad) {
+  constexpr int R = 2 * P;
+  const int r0 = threadIdx.x * R;
+  double L, Rt;
+  double yh[R];
+  exchange(sm, y[0], y[R - 1], L, Rt);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const double um = (q > 0) ? y[q - 1] : L;
+    const double up = (q < R - 1) ? y[q + 1] : Rt;
+    yh[q] = (r0 + q < c.n) ? y[q] - dt * c.ih2 * (um - 2.0 * y[q] + up) : 0.0;  // (I - dt D_h) u^n
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const double g = have_prev ? 2.0 * y[q] - yp[q] : y[q];
+    yp[q] = y[q];
+    y[q] = (r0 + q < c.n) ? g : 0.0;
+    y32[q] = float(y[q]);
+  }
+  const double c1 = c.eps2 * dt * c.ih2;
+  const float sigma = float(sqrt(c.eps2 * dt) * c.ih2);
+  const float cs = float((c.frozen ? 1.0 : 3.0) * sqrt(dt / c.eps2));  // c dt / s
+  const float tol = float(c.newton_tol), floor_ = float(c.newton_floor);
+  float prev = 0.f;
+  int m = 0;
+  bool ok = false;
+  while (m < c.newton_max) {
+    exchange(sm, y[0], y[R - 1], L, Rt);
+    double z[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const double um = (q > 0) ? y[q - 1] : L;
+      const double up = (q < R - 1) ? y[q + 1] : Rt;
+      const double cube = c.frozen ? y[q] : y[q] * y[q] * y[q];
+      z[q] = (r0 + q < c.n) ? c1 * (um - 2.0 * y[q] + up) - dt * cube : 0.0;
+    }
+    double zl, zr;
+    exchange(sm, z[0], z[R - 1], zl, zr);
+    M2<float> A[R], B[R], C[R];
+    V2<float> d[R], x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = r0 + q;
+      const double zm = (q > 0) ? z[q - 1] : zl;
+      const double zp = (q < R - 1) ? z[q + 1] : zr;
+      const float hq = (i < c.n) ? float((y[q] - yh[q]) + c.ih2 * (zm - 2.0 * z[q] + zp)) : 0.f;
+      const float w = c.frozen ? 1.f : y32[q] * y32[q];
+      A[q] = (i >= 1 && i < c.n) ? M2<float>{0.f, -sigma, sigma, 0.f} : mzero<float>();
+      C[q] = (i + 1 < c.n) ? M2<float>{0.f, -sigma, sigma, 0.f} : mzero<float>();
+      B[q] = (i < c.n) ? M2<float>{1.f, 2.f * sigma, -2.f * sigma - cs * w, 1.f} : M2<float>{1.f, 0.f, 0.f, 1.f};
+      d[q] = {hq, 0.f};
+    }
+    block_tridiag_solve<float, T, R>(A, B, C, d, x, solver_smem<float, T>(sm));
+    float dm = 0.f;
+    bool nf = false;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const float dx = (r0 + q < c.n) ? x[q].x : 0.f;
+      nf |= !isfinite(dx);
+      y[q] -= double(dx);
+      y32[q] -= dx;
+      dm = fmaxf(dm, fabsf(dx));
+    }
+    if (__syncthreads_or(nf)) {
+      bad = true;
+      return -(m + 1);
+    }
+    dm = cta_max_f<T>(dm, sm.red);
+    ++m;
+    if (dm <= tol) { ok = true; break; }
+    // FP64 rounding floor of the residual reached (an increment below sqrt(tol) not halving)
+    if (m >= 2 && dm <= floor_ && dm > 0.5f * prev) { ok = true; break; }
+    prev = dm;
+  }
+  return ok ? m : -m;
+}
+
 // One step of the linear scheme Eq. 2.4 (LIN1), FP64 solve.
 template <int T, int P>
 __device__ void lin1_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
@@ -334,11 +427,45 @@ __device__ bool run_steps(Smem1D<T>& sm, const StepCtx& c, int scheme, int fp32_
   return status == 0;
 }
 
+// `nsteps` nonlinear steps with FP32 mixed-form Jacobian solves (nl_step_mixed); keeps the
+// previous state for the Newton predictor and the float shadow of Y across steps.
+template <int T, int P>
+__device__ bool run_steps_nl32(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, int nsteps,
+                               unsigned long long& newton_sum, int& newton_peak, unsigned& status) {
+  double yp[2 * P];
+  float y32[2 * P];
+  bool bad = false;
+  for (int j = 0; j < nsteps; ++j) {
+    const int m = nl_step_mixed<T, P>(sm, c, y, yp, j > 0, y32, dt, bad);
+    const int a = (m < 0) ? -m : m;
+    if (m < 0) status |= ST_NEWTON;
+    newton_sum += (unsigned long long)a;
+    newton_peak = max(newton_peak, a);
+    if (bad) {
+      status |= ST_NONFINITE;
+      return false;
+    }
+  }
+  return status == 0;
+}
+
+// Dispatch of a propagation: FAST = nonlinear scheme with FP32 mixed-form Jacobian solves.
+template <int T, int P, bool FAST>
+__device__ __forceinline__ bool propagate_state(Smem1D<T>& sm, const StepCtx& c, int scheme, int precision,
+                                                double (&y)[2 * P], double dt, int nsteps,
+                                                unsigned long long& nsum, int& npeak, unsigned& status) {
+  if constexpr (FAST) {
+    return run_steps_nl32<T, P>(sm, c, y, dt, nsteps, nsum, npeak, status);
+  } else {
+    return run_steps<T, P>(sm, c, scheme, precision, y, dt, nsteps, nsum, npeak, status);
+  }
+}
+
 // ----------------------------------------------------------------------------- kernels
 
 // Fine sweep of one Parareal iteration: F(U_s^k) for every active problem b and slice s >= k,
 // as one persistent launch; CTAs take (problem, slice) units from a device counter.
-template <int T, int P>
+template <int T, int P, bool FAST>
 __global__ void __launch_bounds__(T) k_fine_sweep(Params1D p, const double* __restrict__ U,
                                                   double* __restrict__ F, Ctrl* ctrl, ProblemState ps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,7 +489,7 @@ __global__ void __launch_bounds__(T) k_fine_sweep(Params1D p, const double* __re
     unsigned long long nsum = 0;
     int npeak = 0;
     unsigned status = 0;
-    run_steps<T, P>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
+    propagate_state<T, P, FAST>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
     store_state<P>(F + ((size_t)b * p.N + s) * p.n, p.n, y);
     if (threadIdx.x == 0) {
       atomicAdd(&ps.newton_total[b], nsum);
@@ -488,7 +615,7 @@ __global__ void k_tally(int B, Ctrl* ctrl, ProblemState ps, int* host_active) {
 }
 
 // Sequential fine solution U^fine_{s+1} = F(U^fine_s), one CTA per problem (serial in time).
-template <int T, int P>
+template <int T, int P, bool FAST>
 __global__ void __launch_bounds__(T) k_reference(Params1D p, double* __restrict__ Uref, Ctrl* ctrl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
@@ -501,14 +628,14 @@ __global__ void __launch_bounds__(T) k_reference(Params1D p, double* __restrict_
   int npeak = 0;
   unsigned status = 0;
   for (int s = 0; s < p.N; ++s) {
-    run_steps<T, P>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
+    propagate_state<T, P, FAST>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
     store_state<P>(Rb + (size_t)(s + 1) * p.n, p.n, y);
   }
   if (threadIdx.x == 0 && status) atomicOr(&ctrl->status, status);
 }
 
 // Stateless propagation: nsteps steps of `scheme` for each problem (one CTA each).
-template <int T, int P>
+template <int T, int P, bool FAST>
 __global__ void __launch_bounds__(T) k_propagate(Params1D p, int scheme, double dt, int nsteps,
                                                  const double* uin, double* uout, int* newton, Ctrl* ctrl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -521,7 +648,7 @@ __global__ void __launch_bounds__(T) k_propagate(Params1D p, int scheme, double 
   unsigned long long nsum = 0;
   int npeak = 0;
   unsigned status = 0;
-  run_steps<T, P>(sm, c, scheme, p.precision, y, dt, nsteps, nsum, npeak, status);
+  propagate_state<T, P, FAST>(sm, c, scheme, p.precision, y, dt, nsteps, nsum, npeak, status);
   store_state<P>(uout + (size_t)b * p.n, p.n, y);
   if (threadIdx.x == 0) {
     if (newton) newton[b] = (int)nsum;
@@ -567,6 +694,9 @@ static cudaError_t prep(K kernel, size_t smem) {
   return e;
 }
 
+// The fine propagator is the nonlinear scheme with FP32 Jacobian solves: use the mixed-form path.
+static bool fast_fine(const Params1D& p) { return p.fine_scheme == SCHEME_NL && p.precision == 1; }
+
 cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -574,8 +704,15 @@ cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   if (e != cudaSuccess) return e;
   CH_DISPATCH_TP(p.n, {
     const size_t smem = sizeof(Smem1D<T_>);
-    e = prep(k_fine_sweep<T_, P_>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_>, T_, smem);
+    if (fast_fine(p)) {
+      e = prep(k_fine_sweep<T_, P_, true>, smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, true>, T_, smem);
+    } else {
+      e = prep(k_fine_sweep<T_, P_, false>, smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, false>, T_, smem);
+    }
     if (e == cudaSuccess) e = prep(k_coarse_sweep<T_, P_>, smem);
   });
   if (per_sm < 1) per_sm = 1;
@@ -588,11 +725,14 @@ cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctr
   cudaError_t e = cudaSuccess;
   CH_DISPATCH_TP(p.n, {
     const size_t smem = sizeof(Smem1D<T_>);
-    e = prep(k_fine_sweep<T_, P_>, smem);
-    if (e == cudaSuccess) {
-      k_fine_sweep<T_, P_><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
-      e = cudaGetLastError();
+    if (fast_fine(p)) {
+      e = prep(k_fine_sweep<T_, P_, true>, smem);
+      if (e == cudaSuccess) k_fine_sweep<T_, P_, true><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
+    } else {
+      e = prep(k_fine_sweep<T_, P_, false>, smem);
+      if (e == cudaSuccess) k_fine_sweep<T_, P_, false><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
     }
+    if (e == cudaSuccess) e = cudaGetLastError();
   });
   return e;
 }
@@ -620,11 +760,14 @@ cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaSt
   cudaError_t e = cudaSuccess;
   CH_DISPATCH_TP(p.n, {
     const size_t smem = sizeof(Smem1D<T_>);
-    e = prep(k_reference<T_, P_>, smem);
-    if (e == cudaSuccess) {
-      k_reference<T_, P_><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
-      e = cudaGetLastError();
+    if (fast_fine(p)) {
+      e = prep(k_reference<T_, P_, true>, smem);
+      if (e == cudaSuccess) k_reference<T_, P_, true><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
+    } else {
+      e = prep(k_reference<T_, P_, false>, smem);
+      if (e == cudaSuccess) k_reference<T_, P_, false><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
     }
+    if (e == cudaSuccess) e = cudaGetLastError();
   });
   return e;
 }
@@ -634,11 +777,14 @@ cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nstep
   cudaError_t e = cudaSuccess;
   CH_DISPATCH_TP(p.n, {
     const size_t smem = sizeof(Smem1D<T_>);
-    e = prep(k_propagate<T_, P_>, smem);
-    if (e == cudaSuccess) {
-      k_propagate<T_, P_><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
-      e = cudaGetLastError();
+    if (scheme == SCHEME_NL && p.precision == 1) {
+      e = prep(k_propagate<T_, P_, true>, smem);
+      if (e == cudaSuccess) k_propagate<T_, P_, true><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
+    } else {
+      e = prep(k_propagate<T_, P_, false>, smem);
+      if (e == cudaSuccess) k_propagate<T_, P_, false><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
     }
+    if (e == cudaSuccess) e = cudaGetLastError();
   });
   return e;
 }

@@ -217,6 +217,19 @@ __device__ __forceinline__ double cta_max(double v, ReduceSmem<T>& sm) {
   return r;
 }
 
+template <int T>
+__device__ __forceinline__ float cta_max_f(float v, ReduceSmem<T>& sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sm.v[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = float(sm.v[0]);
+#pragma unroll
+  for (int i = 1; i < T / 32; ++i) r = fmaxf(r, float(sm.v[i]));
+  __syncthreads();
+  return r;
+}
+
 // Sum and max in one pass; the sum uses a fixed reduction tree (deterministic).
 template <int T>
 __device__ __forceinline__ void cta_sum_max(double& s, double& m, ReduceSmem<T>& sm) {
