@@ -234,13 +234,14 @@ __device__ int nl_step_mixed(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P]
   bool ok = false;
   while (m < c.newton_max) {
     exchange(sm, y[0], y[R - 1], L, Rt);
+    // z = eps^2 dt D_h Y - dt Y^3 = c1 (Y_{i-1} + Y_{i+1}) + Y (-2 c1 - dt Y^2)
     double z[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const double um = (q > 0) ? y[q - 1] : L;
       const double up = (q < R - 1) ? y[q + 1] : Rt;
-      const double cube = c.frozen ? y[q] : y[q] * y[q] * y[q];
-      z[q] = (r0 + q < c.n) ? c1 * (um - 2.0 * y[q] + up) - dt * cube : 0.0;
+      const double y2 = c.frozen ? 1.0 : y[q] * y[q];
+      z[q] = (r0 + q < c.n) ? fma(y[q], fma(-dt, y2, -2.0 * c1), c1 * (um + up)) : 0.0;
     }
     double zl, zr;
     exchange(sm, z[0], z[R - 1], zl, zr);
@@ -680,6 +681,28 @@ __global__ void __launch_bounds__(T) k_propagate(Params1D p, int scheme, double 
   } while (0)
 
 // Opt a kernel into its dynamic shared memory once per device (not during graph capture).
+// (T, P) for the nonlinear FP32-Newton path: at most 4 rows per thread up to n = 1024, which
+// halves the registers per thread and doubles the resident warps of the FP64-bound sweep.
+#define CH_DISPATCH_TP_FAST(n, ...)       \
+  do {                                    \
+    if ((n) <= 128) {                     \
+      constexpr int T_ = 32, P_ = 2;      \
+      __VA_ARGS__;                        \
+    } else if ((n) <= 256) {              \
+      constexpr int T_ = 64, P_ = 2;      \
+      __VA_ARGS__;                        \
+    } else if ((n) <= 512) {              \
+      constexpr int T_ = 128, P_ = 2;     \
+      __VA_ARGS__;                        \
+    } else if ((n) <= 1024) {             \
+      constexpr int T_ = 256, P_ = 2;     \
+      __VA_ARGS__;                        \
+    } else {                              \
+      constexpr int T_ = 256, P_ = 4;     \
+      __VA_ARGS__;                        \
+    }                                     \
+  } while (0)
+
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
   static std::mutex mu;
@@ -702,18 +725,23 @@ cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  CH_DISPATCH_TP(p.n, {
-    const size_t smem = sizeof(Smem1D<T_>);
-    if (fast_fine(p)) {
+  if (fast_fine(p)) {
+    CH_DISPATCH_TP_FAST(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_fine_sweep<T_, P_, true>, smem);
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, true>, T_, smem);
-    } else {
+    });
+  } else {
+    CH_DISPATCH_TP(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_fine_sweep<T_, P_, false>, smem);
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, false>, T_, smem);
-    }
-    if (e == cudaSuccess) e = prep(k_coarse_sweep<T_, P_>, smem);
+    });
+  }
+  CH_DISPATCH_TP(p.n, {
+    if (e == cudaSuccess) e = prep(k_coarse_sweep<T_, P_>, sizeof(Smem1D<T_>));
   });
   if (per_sm < 1) per_sm = 1;
   *grid = sms * per_sm;
@@ -723,17 +751,20 @@ cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
 cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps,
                               int grid, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  CH_DISPATCH_TP(p.n, {
-    const size_t smem = sizeof(Smem1D<T_>);
-    if (fast_fine(p)) {
+  if (fast_fine(p)) {
+    CH_DISPATCH_TP_FAST(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_fine_sweep<T_, P_, true>, smem);
       if (e == cudaSuccess) k_fine_sweep<T_, P_, true><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
-    } else {
+    });
+  } else {
+    CH_DISPATCH_TP(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_fine_sweep<T_, P_, false>, smem);
       if (e == cudaSuccess) k_fine_sweep<T_, P_, false><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
-  });
+    });
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }
 
@@ -758,34 +789,42 @@ cudaError_t launch_tally(const Params1D& p, Ctrl* ctrl, ProblemState ps, int* ho
 
 cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  CH_DISPATCH_TP(p.n, {
-    const size_t smem = sizeof(Smem1D<T_>);
-    if (fast_fine(p)) {
+  if (fast_fine(p)) {
+    CH_DISPATCH_TP_FAST(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_reference<T_, P_, true>, smem);
       if (e == cudaSuccess) k_reference<T_, P_, true><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
-    } else {
+    });
+  } else {
+    CH_DISPATCH_TP(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_reference<T_, P_, false>, smem);
       if (e == cudaSuccess) k_reference<T_, P_, false><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
-  });
+    });
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }
 
 cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nsteps, const double* uin,
                              double* uout, int* newton, Ctrl* ctrl, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  CH_DISPATCH_TP(p.n, {
-    const size_t smem = sizeof(Smem1D<T_>);
-    if (scheme == SCHEME_NL && p.precision == 1) {
+  if (scheme == SCHEME_NL && p.precision == 1) {
+    CH_DISPATCH_TP_FAST(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_propagate<T_, P_, true>, smem);
-      if (e == cudaSuccess) k_propagate<T_, P_, true><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
-    } else {
+      if (e == cudaSuccess)
+        k_propagate<T_, P_, true><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
+    });
+  } else {
+    CH_DISPATCH_TP(p.n, {
+      const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_propagate<T_, P_, false>, smem);
-      if (e == cudaSuccess) k_propagate<T_, P_, false><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
-  });
+      if (e == cudaSuccess)
+        k_propagate<T_, P_, false><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
+    });
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }
 
