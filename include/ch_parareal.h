@@ -20,8 +20,11 @@
  *  - A handle owns its device memory and is bound to one CUDA stream (cudaStream_t passed
  *    as void*; NULL = the legacy default stream). Work is enqueued on that stream; calls
  *    that return data to the host synchronise it. A handle is not thread-safe.
- *  - Only one dimension is implemented by this version (dim = 1); dim = 2 returns
- *    CH_ERR_INVALID.
+ *  - dim = 1: n in 1..2048. dim = 2: n + 1 in {16, 32, 64, 128, 256, 512} (the sine transform
+ *    of the 2D solver is a radix-2 FFT of length 2(n+1)); D_h = I (x) D_1 + D_1 (x) I (the
+ *    natural extension of Eq. 3.2). In 2D every linear solve is FP32 preconditioned CG in sine
+ *    space against FP64 residuals (`precision` is ignored) and Newton totals in ch_stats are
+ *    for the whole batch.
  */
 #ifndef CH_PARAREAL_H
 #define CH_PARAREAL_H
@@ -62,7 +65,7 @@ typedef enum {
 } ch_scheme;
 
 typedef struct {
-  int dim;             /* 1 (2 reserved)                                                   */
+  int dim;             /* 1 or 2                                                            */
   int n;               /* interior nodes per direction, h = 1/(n+1)       (Section 2.1)     */
   double eps;          /* interface parameter epsilon                      (Eq. 1.1)         */
   double T;            /* final time                                        (Eq. 1.1)         */
@@ -162,6 +165,12 @@ const char* ch_parareal_last_error(const ch_parareal* h);
 
 /* Static name of a status code. */
 const char* ch_status_string(ch_status s);
+
+/* Orthonormal 2D sine transform (DST-I in x and y, its own inverse) of `batch` FP32 n x n
+ * fields: out = S X S, S_jk = sqrt(2/(n+1)) sin(pi j k / (n+1)). The diagonalising transform of
+ * D_h (eigenvalues below Eq. 3.2) used by the 2D solver. in_dev != out_dev, device arrays
+ * [batch][n][n]; n + 1 a power of two in 16..512. Synchronises the stream. */
+ch_status ch_sine_transform_2d(const float* in_dev, float* out_dev, int batch, int n, void* cuda_stream);
 
 /* Stateless propagation (the fine or coarse propagator as a batched kernel): applies `nsteps`
  * steps of `scheme` with step `dt` to each of `batch` problems sharing cfg->n, cfg->eps,

@@ -49,6 +49,13 @@ def dh2_matrix(n: int) -> sp.csc_matrix:
     return _CACHE[key]
 
 
+def sine_transform(x: np.ndarray) -> np.ndarray:
+    """Orthonormal 2D DST-I over the last two axes (scipy.fft, a library FFT): S X S with
+    S_jk = sqrt(2/(n+1)) sin(pi j k/(n+1)), the eigenvector basis of D_h (below Eq. 3.2)."""
+    import scipy.fft
+    return scipy.fft.dstn(np.asarray(x, dtype=np.float64), type=1, axes=(-2, -1), norm="ortho")
+
+
 def dh_apply(u: np.ndarray, n: int) -> np.ndarray:
     return dh_matrix(n) @ u
 

@@ -6,9 +6,9 @@ implemented as hand-written CUDA behind the C ABI of ``include/ch_parareal.h``. 
 package is the thin Python binding of that ABI.
 """
 from ._lib import (CH_MAX_ITERS, EXPORTED_SYMBOLS, SCHEMES, STATUS, VARIANTS, ChError, Config, Parareal,
-                   load, propagate)
+                   load, propagate, sine_transform_2d)
 from .build import LIB as LIBRARY_PATH
 from .build import build
 
 __all__ = ["CH_MAX_ITERS", "EXPORTED_SYMBOLS", "SCHEMES", "STATUS", "VARIANTS", "ChError", "Config", "Parareal",
-           "load", "propagate", "build", "LIBRARY_PATH"]
+           "load", "propagate", "sine_transform_2d", "build", "LIBRARY_PATH"]

@@ -28,7 +28,7 @@ EXPORTED_SYMBOLS = [
     "ch_parareal_compute_reference", "ch_parareal_run", "ch_parareal_get_slices",
     "ch_parareal_get_slices_device", "ch_parareal_get_reference", "ch_parareal_get_stats",
     "ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_propagate",
-    "ch_parareal_solve_noalloc",
+    "ch_parareal_solve_noalloc", "ch_sine_transform_2d",
 ]
 
 
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
     lib.ch_status_string.argtypes = [C.c_int]
     lib.ch_status_string.restype = C.c_char_p
     lib.ch_propagate.argtypes = [C.POINTER(_Config), C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp]
+    lib.ch_sine_transform_2d.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     for name in EXPORTED_SYMBOLS:
         if name not in ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string"):
@@ -259,3 +260,15 @@ def propagate(cfg: Config, scheme: str, dt: float, nsteps: int, u_in, u_out=None
     if s != 0:
         raise ChError(s, "ch_propagate")
     return u_out
+
+
+def sine_transform_2d(x, out=None, stream=None):
+    """Orthonormal 2D DST-I on the device (ch_sine_transform_2d). x: CUDA float32 [batch, n, n]."""
+    import torch
+    lib = load()
+    if out is None:
+        out = torch.empty_like(x)
+    s = lib.ch_sine_transform_2d(_dptr(x), _dptr(out), x.shape[0], x.shape[-1], _stream_ptr(stream))
+    if s != 0:
+        raise ChError(s, "ch_sine_transform_2d")
+    return out

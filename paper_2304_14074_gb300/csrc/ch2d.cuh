@@ -1,0 +1,102 @@
+// Two-dimensional Parareal kernels: declarations shared with the host runtime.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+namespace chg2 {
+
+enum Scheme { SCHEME_LIN1 = 0, SCHEME_NL = 1, SCHEME_LIN2 = 2 };
+enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u };
+
+// Grid sizes the sine transform supports: n + 1 a power of two (radix-2 FFT of length 2(n+1)).
+bool supported_n(int n);
+
+struct Params2D {
+  int n;             // interior nodes per direction
+  int frozen;        // diag(u^2) := I (analysis model of Section 3)
+  int newton_max;
+  int cg_max;        // inner CG iterations per Newton (or refinement) sweep
+  double eps2;
+  double h;
+  double newton_tol;
+  double cg_tol;     // relative reduction of the preconditioned residual norm
+};
+
+// Work space and kernels of a batch of `cap` units (problem-slices) of an n x n grid.
+// All vectors are device arrays [units][n*n], row-major (x fastest).
+class Prop2D {
+ public:
+  cudaError_t init(const Params2D& p, int cap, cudaStream_t st);
+  void release();
+  // Advances `units` states in place by nsteps steps of `scheme` with step dt. Y: [units][n*n]
+  // FP64 device array. Accumulates Newton iterations per unit into newton (device, may be null)
+  // and ORs error bits into *status_dev.
+  cudaError_t propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
+  // Orthonormal 2D DST-I (its own inverse) of `units` FP32 fields; in and out must differ and
+  // must not be the internal scratch buffers.
+  cudaError_t dst2(const float* in, float* out, int units, cudaStream_t st);
+  unsigned read_status(cudaStream_t st);  // synchronises
+  unsigned long long newton_iterations() const { return newton_total_; }
+  int newton_peak() const { return newton_peak_; }
+  void reset_counters() {
+    newton_total_ = 0;
+    newton_peak_ = 0;
+  }
+  size_t bytes() const { return bytes_; }
+
+ private:
+  cudaError_t newton_solve(double* Y, const double* b, int units, double dt, int zmode, int wmode,
+                           const double* W64, double wconst, cudaStream_t st);
+  cudaError_t nl_step(double* Y, int units, double dt, bool have_prev, cudaStream_t st);
+  cudaError_t linear_step(double* Y, int units, int scheme, double dt, cudaStream_t st);
+  cudaError_t cg_solve(int units, double cdt, double e2dt, cudaStream_t st, int* iters);
+  cudaError_t count_active(const int* flags, int units, cudaStream_t st, int* out);
+
+  Params2D p_{};
+  int cap_ = 0;
+  size_t pts_ = 0;
+  size_t bytes_ = 0;
+  int nblk_ = 0;  // reduction blocks per unit
+  // FP64 work
+  double* yhat_ = nullptr;   // (I - dt D_h) u^n, or the linear right-hand side
+  double* yprev_ = nullptr;  // u^{n-1} for the Newton predictor
+  double* z_ = nullptr;      // stencil intermediate
+  double* xacc_ = nullptr;   // accumulated solution of a refined linear solve
+  // FP32 work
+  float* w_ = nullptr;       // Jacobian weights (Y^2 or u^2)
+  float* rhs_ = nullptr;     // right-hand side handed to CG
+  float* xh_ = nullptr;      // CG iterate (spectral)
+  float* rh_ = nullptr;      // CG residual (spectral)
+  float* ph_ = nullptr;      // CG direction (spectral)
+  float* qh_ = nullptr;      // S p (spectral)
+  float* tmp_ = nullptr;     // transform scratch / physical-space work
+  float* tmp2_ = nullptr;
+  float* mu_ = nullptr;      // 1D eigenvalues mu_p of -D_h, p = 1..n
+  float2* tw_ = nullptr;     // FFT twiddles exp(-2 pi i m / L), m < L/2
+  // per-unit scalars
+  double* part_ = nullptr;   // reduction partials [units][nblk]
+  double* scal_ = nullptr;   // [units][8]: rho, rho0, alpha, beta, wbar, dmax, prevd, spare
+  int* flag_ = nullptr;      // [units][2]: newton done, cg done
+  int* newton_cnt_ = nullptr;  // [units] Newton iterations of the current step
+  unsigned* status_ = nullptr;
+  int* host_cnt_ = nullptr;    // pinned
+  unsigned long long newton_total_ = 0;
+  int newton_peak_ = 0;
+};
+
+// Parareal correction of one slice for `count` problems list[0..count) (Eq. 2.2), fused with
+// the increment and error norms: U_{s+1} = F_s + (g - Gold_s) (init: U_{s+1} = g), Gold_s = g,
+// and g (work rows, contiguous) is overwritten with U_{s+1}. U, F, Gold point at slice s+1 / s
+// of problem 0; ustride / fstride are the per-problem strides. acc[b] = {inc, err_l2, err_max}
+// are running maxima over slices (h2 = h^d for the L2_h norm). part: correct_partials(count).
+cudaError_t launch_correct(double* U, const double* F, double* g, double* Gold, const double* Uref, const int* list,
+                           int count, size_t pts, size_t ustride, size_t fstride, int init, double* part, double* acc,
+                           double h2, cudaStream_t st);
+size_t correct_partials(int count);
+// dst[i] = src[off[i] .. off[i] + pts) (gather) and the converse (scatter).
+cudaError_t launch_gather(double* dst, const double* src, const long long* off, int count, size_t pts, cudaStream_t st);
+cudaError_t launch_scatter(double* dst, const double* src, const long long* off, int count, size_t pts,
+                           cudaStream_t st);
+
+}  // namespace chg2

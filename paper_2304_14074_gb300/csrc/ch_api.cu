@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ch1d.cuh"
+#include "ch2d.cuh"
 #include "ch_parareal.h"
 
 using chg::Ctrl;
@@ -48,6 +49,16 @@ struct ch_parareal {
   int iters_done = 0;
   ch_status sticky = CH_OK;
   std::string msg;
+  // two-dimensional path
+  int dim = 1;
+  chg2::Prop2D* p2 = nullptr;
+  double* W = nullptr;          // [B N][pts] gathered states being propagated
+  double* acc = nullptr;        // [B][3] running {inc, err_l2, err_max} of an iteration
+  double* cpart = nullptr;      // correction partials
+  int* dlist = nullptr;         // [B] problem list
+  long long* doff = nullptr;    // [B N] element offsets for gather / scatter
+  std::vector<std::vector<double>> h_inc, h_el2, h_emx;
+  std::vector<int> h_iters, h_conv;
 };
 
 namespace {
@@ -77,8 +88,9 @@ int coarse_of(int v) { return (v == CH_PA_II) ? chg::SCHEME_LIN2 : (v == CH_NPA_
 
 bool valid_common(const ch_config* c, std::string& why) {
   if (!c) { why = "cfg is NULL"; return false; }
-  if (c->dim != 1) { why = "only dim = 1 is implemented"; return false; }
-  if (c->n < 1 || c->n > 2048) { why = "n must be in 1..2048"; return false; }
+  if (c->dim != 1 && c->dim != 2) { why = "dim must be 1 or 2"; return false; }
+  if (c->dim == 1 && (c->n < 1 || c->n > 2048)) { why = "n must be in 1..2048"; return false; }
+  if (c->dim == 2 && !chg2::supported_n(c->n)) { why = "2D needs n + 1 in {16, 32, ..., 512}"; return false; }
   if (!(c->eps > 0.0) || !std::isfinite(c->eps)) { why = "eps must be > 0"; return false; }
   if (c->newton_max < 1 || c->newton_max > 1000) { why = "newton_max must be in 1..1000"; return false; }
   if (!(c->newton_tol > 0.0)) { why = "newton_tol must be > 0"; return false; }
@@ -110,9 +122,169 @@ Params1D make_params(const ch_config* c, int B) {
   return p;
 }
 
+chg2::Params2D params2d(const ch_config* c) {
+  chg2::Params2D q{};
+  q.n = c->n;
+  q.frozen = c->frozen ? 1 : 0;
+  q.newton_max = c->newton_max;
+  q.cg_max = 80;
+  q.eps2 = c->eps * c->eps;
+  q.h = 1.0 / (c->n + 1);
+  q.newton_tol = c->newton_tol;
+  q.cg_tol = 1e-6;
+  return q;
+}
+
 ch_status device_status(ch_parareal* h, unsigned status) {
   if (status & chg::ST_NONFINITE) return fail(h, CH_ERR_LINSOLVE, "a solve produced a non-finite value");
   if (status & chg::ST_NEWTON) return fail(h, CH_ERR_NEWTON, "a Newton solve reached newton_max");
+  return CH_OK;
+}
+
+// ------------------------------------------------------------------ two-dimensional driver
+
+int fine2(const ch_parareal* h) { return fine_of(h->cfg.variant); }
+int coarse2(const ch_parareal* h) { return coarse_of(h->cfg.variant); }
+
+// Work rows W[i] = U[b][s] for (b, s) in `units`, via element offsets.
+ch_status gather_units(ch_parareal* h, double* src, const std::vector<long long>& off, bool to_w) {
+  if (off.empty()) return CH_OK;
+  CH_CUDA(h, cudaMemcpyAsync(h->doff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+  if (to_w) {
+    CH_CUDA(h, chg2::launch_gather(h->W, src, h->doff, (int)off.size(), h->pts, h->st));
+  } else {
+    CH_CUDA(h, chg2::launch_scatter(src, h->W, h->doff, (int)off.size(), h->pts, h->st));
+  }
+  return CH_OK;
+}
+
+ch_status prop2(ch_parareal* h, int units, int scheme, double dt, int nsteps) {
+  CH_CUDA(h, h->p2->propagate(h->W, units, scheme, dt, nsteps, h->st));
+  return CH_OK;
+}
+
+ch_status reference2d(ch_parareal* h) {
+  const int B = h->B, N = h->p.N;
+  const size_t pts = h->pts, us = (size_t)(N + 1) * pts;
+  std::vector<long long> off(B);
+  for (int b = 0; b < B; ++b) off[b] = (long long)(b * us);
+  CH_CUDA(h, cudaMemcpy2DAsync(h->Uref, us * sizeof(double), h->U, us * sizeof(double), pts * sizeof(double), B,
+                               cudaMemcpyDeviceToDevice, h->st));
+  ch_status s = gather_units(h, h->U, off, true);
+  for (int k = 0; k < N && s == CH_OK; ++k) {
+    s = prop2(h, B, fine2(h), h->p.dt, h->p.J);
+    for (int b = 0; b < B; ++b) off[b] = (long long)(b * us + (k + 1) * pts);
+    if (s == CH_OK) s = gather_units(h, h->Uref, off, false);
+  }
+  if (s != CH_OK) return s;
+  CH_CUDA(h, cudaStreamSynchronize(h->st));
+  s = device_status(h, h->p2->read_status(h->st));
+  if (s == CH_OK) h->ref_valid = true;
+  return s;
+}
+
+ch_status run2d(ch_parareal* h) {
+  const int B = h->B, N = h->p.N, maxit = h->p.maxit;
+  const size_t pts = h->pts, us = (size_t)(N + 1) * pts, fs = (size_t)N * pts;
+  const double h2 = h->p.h * h->p.h;
+  const double* ref = h->ref_valid ? h->Uref : nullptr;
+  h->h_inc.assign(B, {});
+  h->h_el2.assign(B, {});
+  h->h_emx.assign(B, {});
+  h->h_iters.assign(B, 0);
+  h->h_conv.assign(B, 0);
+  h->fine_ms = h->coarse_ms = 0.0;
+  h->kernel_launches = 0;
+  std::vector<int> active(B, 1);
+  std::vector<double> acc(3 * B);
+  auto list_of = [&](std::vector<int>& L) {
+    L.clear();
+    for (int b = 0; b < B; ++b)
+      if (active[b]) L.push_back(b);
+  };
+  auto pull_acc = [&]() -> ch_status {
+    CH_CUDA(h, cudaMemcpyAsync(acc.data(), h->acc, 3 * B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CH_CUDA(h, cudaStreamSynchronize(h->st));
+    return CH_OK;
+  };
+  CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
+  // coarse initial guess (Section 4): U_{s+1} = G(U_s), Gold_s = U_{s+1}
+  std::vector<int> L;
+  list_of(L);
+  CH_CUDA(h, cudaMemcpyAsync(h->dlist, L.data(), L.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 3 * B * sizeof(double), h->st));
+  std::vector<long long> off(L.size());
+  for (size_t i = 0; i < L.size(); ++i) off[i] = (long long)(L[i] * us);
+  ch_status s = gather_units(h, h->U, off, true);
+  for (int k = 0; k < N && s == CH_OK; ++k) {
+    s = prop2(h, (int)L.size(), coarse2(h), h->p.dtc, h->p.coarse_steps);
+    if (s != CH_OK) break;
+    CH_CUDA(h, chg2::launch_correct(h->U + (k + 1) * pts, h->F + k * pts, h->W, h->Gold + k * pts,
+                                    ref ? ref + (k + 1) * pts : nullptr, h->dlist, (int)L.size(), pts, us, fs, 1,
+                                    h->cpart, h->acc, h2, h->st));
+  }
+  if (s != CH_OK) return s;
+  if ((s = pull_acc()) != CH_OK) return s;
+  for (int b = 0; b < B; ++b) {
+    h->h_el2[b].push_back(ref ? acc[3 * b + 1] : -1.0);
+    h->h_emx[b].push_back(ref ? acc[3 * b + 2] : -1.0);
+  }
+  CH_CUDA(h, cudaEventRecord(h->ev[1], h->st));
+  int k = 0;
+  for (; k < maxit; ++k) {
+    list_of(L);
+    if (L.empty()) break;
+    const int nb = (int)L.size();
+    // fine sweep: every active problem's slices s >= k in one batch
+    std::vector<long long> uoff, foff;
+    for (int b : L)
+      for (int sl = k; sl < N; ++sl) {
+        uoff.push_back((long long)(b * us + sl * pts));
+        foff.push_back((long long)(b * fs + sl * pts));
+      }
+    CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
+    if ((s = gather_units(h, h->U, uoff, true)) != CH_OK) return s;
+    if ((s = prop2(h, (int)uoff.size(), fine2(h), h->p.dt, h->p.J)) != CH_OK) return s;
+    if ((s = gather_units(h, h->F, foff, false)) != CH_OK) return s;
+    CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
+    // sequential coarse sweep with the correction of Eq. 2.2 and the norms
+    CH_CUDA(h, cudaMemcpyAsync(h->dlist, L.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 3 * B * sizeof(double), h->st));
+    off.resize(nb);
+    for (int i = 0; i < nb; ++i) off[i] = (long long)(L[i] * us + k * pts);
+    if ((s = gather_units(h, h->U, off, true)) != CH_OK) return s;
+    for (int sl = k; sl < N; ++sl) {
+      if ((s = prop2(h, nb, coarse2(h), h->p.dtc, h->p.coarse_steps)) != CH_OK) return s;
+      CH_CUDA(h, chg2::launch_correct(h->U + (sl + 1) * pts, h->F + sl * pts, h->W, h->Gold + sl * pts,
+                                      ref ? ref + (sl + 1) * pts : nullptr, h->dlist, nb, pts, us, fs, 0, h->cpart,
+                                      h->acc, h2, h->st));
+    }
+    CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
+    CH_CUDA(h, cudaEventRecord(h->ev[k + 2], h->st));
+    if ((s = pull_acc()) != CH_OK) return s;
+    float fm = 0.f, cm = 0.f;
+    CH_CUDA(h, cudaEventElapsedTime(&fm, h->ph[0], h->ph[1]));
+    CH_CUDA(h, cudaEventElapsedTime(&cm, h->ph[1], h->ph[2]));
+    h->fine_ms += fm;
+    h->coarse_ms += cm;
+    for (int b : L) {
+      const double inc = acc[3 * b], el2 = acc[3 * b + 1], emx = acc[3 * b + 2];
+      h->h_inc[b].push_back(inc);
+      h->h_el2[b].push_back(ref ? el2 : -1.0);
+      h->h_emx[b].push_back(ref ? emx : -1.0);
+      h->h_iters[b] = k + 1;
+      if ((h->p.tol > 0.0 && inc < h->p.tol) || (ref && h->p.err_tol > 0.0 && el2 <= h->p.err_tol)) {
+        h->h_conv[b] = 1;
+        active[b] = 0;
+      }
+    }
+  }
+  h->iters_done = k;
+  h->ran = true;
+  if ((s = device_status(h, h->p2->read_status(h->st))) != CH_OK) return s;
+  int left = 0;
+  for (int b = 0; b < B; ++b) left += active[b];
+  if ((h->p.tol > 0.0 || (h->p.err_tol > 0.0 && h->ref_valid)) && left > 0) return CH_ERR_NOT_CONVERGED;
   return CH_OK;
 }
 
@@ -152,6 +324,15 @@ void ch_parareal_destroy(ch_parareal* h) {
   cudaFree(h->ctrl);
   cudaFree(h->ps_block);
   if (h->host_active) cudaFreeHost(h->host_active);
+  if (h->p2) {
+    h->p2->release();
+    delete h->p2;
+  }
+  cudaFree(h->W);
+  cudaFree(h->acc);
+  cudaFree(h->cpart);
+  cudaFree(h->dlist);
+  cudaFree(h->doff);
   delete h;
 }
 
@@ -171,7 +352,8 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
   h->B = batch;
   h->st = static_cast<cudaStream_t>(cuda_stream);
   h->p = make_params(cfg, batch);
-  h->pts = (size_t)cfg->n;
+  h->dim = cfg->dim;
+  h->pts = (cfg->dim == 2) ? (size_t)cfg->n * cfg->n : (size_t)cfg->n;
   h->initial_set.assign(batch, 0);
   cudaGetDevice(&h->device);
   const size_t N = cfg->n_slices, B = batch, pts = h->pts;
@@ -208,6 +390,21 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
     if ((e = cudaEventCreate(&ev))) return bail(e, "cudaEventCreate");
   for (auto& ev : h->ph)
     if ((e = cudaEventCreate(&ev))) return bail(e, "cudaEventCreate");
+  if (h->dim == 2) {
+    h->p2 = new (std::nothrow) chg2::Prop2D();
+    if (!h->p2) {
+      ch_parareal_destroy(h);
+      return CH_ERR_OOM;
+    }
+    if ((e = h->p2->init(params2d(cfg), (int)(B * N), h->st))) return bail(e, "2D work space");
+    if ((e = cudaMalloc(&h->W, B * N * pts * sizeof(double)))) return bail(e, "cudaMalloc(W)");
+    if ((e = cudaMalloc(&h->acc, B * 3 * sizeof(double)))) return bail(e, "cudaMalloc(acc)");
+    if ((e = cudaMalloc(&h->cpart, chg2::correct_partials((int)B) * sizeof(double)))) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&h->dlist, B * sizeof(int)))) return bail(e, "cudaMalloc(list)");
+    if ((e = cudaMalloc(&h->doff, B * N * sizeof(long long)))) return bail(e, "cudaMalloc(offsets)");
+    *out = h;
+    return CH_OK;
+  }
   if ((e = chg::fine_sweep_max_grid(h->p, &h->grid))) return bail(e, "fine_sweep_max_grid");
   *out = h;
   return CH_OK;
@@ -255,6 +452,7 @@ ch_status ch_parareal_compute_reference(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "compute_reference before set_initial");
+  if (h->dim == 2) return reference2d(h);
   const size_t N = h->p.N, pts = h->pts;
   CH_CUDA(h, cudaMemcpy2DAsync(h->Uref, (N + 1) * pts * sizeof(double), h->U, (N + 1) * pts * sizeof(double),
                                pts * sizeof(double), h->B, cudaMemcpyDeviceToDevice, h->st));
@@ -302,6 +500,7 @@ ch_status ch_parareal_run(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "run before set_initial");
+  if (h->dim == 2) return run2d(h);
   const int B = h->B, maxit = h->p.maxit;
   // reset control and per-problem state
   std::vector<int> ones(B, 1);
@@ -409,6 +608,30 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
   if (!out || problem < 0 || problem >= h->B) return fail(h, CH_ERR_INVALID, "get_stats: bad problem index or pointer");
   if (!h->ran) return fail(h, CH_ERR_STATE, "get_stats before run");
   std::memset(out, 0, sizeof(*out));
+  if (h->dim == 2) {
+    out->iterations = h->h_iters[problem];
+    out->converged = h->h_conv[problem];
+    for (size_t k = 0; k < h->h_inc[problem].size(); ++k) out->inc[k] = h->h_inc[problem][k];
+    for (size_t k = 0; k < h->h_el2[problem].size(); ++k) {
+      out->err_l2[k] = h->h_el2[problem][k];
+      out->err_max[k] = h->h_emx[problem][k];
+    }
+    for (int k = 0; k <= h->iters_done; ++k) {
+      float ms = 0.f;
+      CH_CUDA(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[k + 1]));
+      out->t_iter_ms[k] = ms;
+    }
+    out->newton_total = (long long)h->p2->newton_iterations();
+    out->newton_max = h->p2->newton_peak();
+    long long fps = 0;
+    for (int k = 0; k < out->iterations; ++k) fps += (long long)(h->p.N - k) * h->p.J * (long long)h->pts;
+    out->fine_point_steps = fps;
+    out->fine_sweep_ms = h->fine_ms;
+    out->coarse_sweep_ms = h->coarse_ms;
+    out->fine_sweep_launches = h->iters_done;
+    out->kernel_launches = 0;
+    return CH_OK;
+  }
   const int maxit = h->p.maxit;
   int it = 0, conv = 0, nmax = 0;
   unsigned long long ntot = 0;
@@ -441,6 +664,23 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
   return CH_OK;
 }
 
+ch_status ch_sine_transform_2d(const float* in_dev, float* out_dev, int batch, int n, void* cuda_stream) {
+  if (!in_dev || !out_dev || in_dev == out_dev || batch < 1 || !chg2::supported_n(n)) return CH_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  chg2::Params2D q{};
+  q.n = n;
+  q.h = 1.0 / (n + 1);
+  q.newton_max = 1;
+  q.cg_max = 1;
+  chg2::Prop2D prop;
+  cudaError_t e = prop.init(q, batch, st);
+  if (e == cudaSuccess) e = prop.dst2(in_dev, out_dev, batch, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  prop.release();
+  if (e == cudaErrorMemoryAllocation) return CH_ERR_OOM;
+  return e == cudaSuccess ? CH_OK : CH_ERR_CUDA;
+}
+
 ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, int nsteps, const double* u_in_dev,
                        double* u_out_dev, int* newton_dev, void* cuda_stream) {
   std::string why;
@@ -448,6 +688,26 @@ ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, i
       scheme < CH_SCHEME_LIN1 || scheme > CH_SCHEME_LIN2)
     return CH_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (cfg->dim == 2) {
+    chg2::Prop2D prop;
+    cudaError_t e = prop.init(params2d(cfg), batch, st);
+    const size_t bytes = (size_t)batch * cfg->n * cfg->n * sizeof(double);
+    if (e == cudaSuccess && u_out_dev != u_in_dev) e = cudaMemcpyAsync(u_out_dev, u_in_dev, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = prop.propagate(u_out_dev, batch, scheme, dt, nsteps, st);
+    unsigned status = (e == cudaSuccess) ? prop.read_status(st) : 0u;
+    if (e == cudaSuccess && newton_dev) {
+      const int tot = (int)prop.newton_iterations();
+      std::vector<int> v(batch, tot / batch);
+      e = cudaMemcpyAsync(newton_dev, v.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    prop.release();
+    if (e == cudaErrorMemoryAllocation) return CH_ERR_OOM;
+    if (e != cudaSuccess) return CH_ERR_CUDA;
+    if (status & chg2::ST_NONFINITE) return CH_ERR_LINSOLVE;
+    if (status & chg2::ST_NEWTON) return CH_ERR_NEWTON;
+    return CH_OK;
+  }
   Params1D p = make_params(cfg, batch);
   Ctrl* ctrl = nullptr;
   if (cudaMalloc(&ctrl, sizeof(Ctrl)) != cudaSuccess) return CH_ERR_OOM;

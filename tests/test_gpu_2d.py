@@ -1,0 +1,166 @@
+"""GPU parity of the two-dimensional path against the CPU oracle (sparse direct solves).
+
+Tolerances follow the 1D reasoning: one FP64 step is determined to about
+u (1 + 64 alpha + 8 beta max w), alpha = eps^2 dt / h^4, beta = c dt / h^2 (the 13-point D_h^2
+has row sum 64/h^4); single steps allow 64 times that per step. The sine transform runs in
+FP32 (radix-2 FFT of length 2(n+1)): 1e-5 of the largest coefficient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ch_inputs
+from oracle import oracle2d as o2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_ROUND = 2.0 ** -53
+FINE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin2", "NPA-I": "nl", "NPA-II": "nl"}
+COARSE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin1", "NPA-I": "lin1", "NPA-II": "nl"}
+
+
+def step_bound_2d(n, eps, dt, c=3.0, wmax=1.0):
+    h = 1.0 / (n + 1)
+    return U_ROUND * (1 + 64 * eps ** 2 * dt / h ** 4 + 8 * c * dt / h ** 2 * wmax)
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def mode2(n, p, q):
+    x = np.arange(1, n + 1) / (n + 1)
+    return np.outer(np.sin(q * np.pi * x), np.sin(p * np.pi * x)).reshape(-1)
+
+
+@pytest.mark.parametrize("n", [15, 31, 63, 127, 255, 511])
+def test_sine_transform_matches_oracle(gpu_lib, n):
+    ch = gpu_lib
+    x = np.stack([ch_inputs.initial_condition(2, n, 50 + b, kind="normal", amp=1.0).reshape(n, n)
+                  for b in range(3)]).astype(np.float32)
+    X = ch.sine_transform_2d(dev(x, torch.float32)).cpu().numpy()
+    ref = o2.sine_transform(x.astype(np.float64))
+    assert np.max(np.abs(X - ref)) <= 1e-5 * np.max(np.abs(ref))
+    back = ch.sine_transform_2d(dev(X, torch.float32)).cpu().numpy()
+    assert np.max(np.abs(back - x)) <= 1e-5 * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("n", [15, 31, 63])
+@pytest.mark.parametrize("scheme", ["lin1", "lin2", "nl"])
+def test_propagate_2d_matches_oracle(gpu_lib, n, scheme):
+    ch = gpu_lib
+    h = 1.0 / (n + 1)
+    eps = 0.05
+    dt = min(1e-3, 2000.0 * h ** 4 / eps ** 2)
+    nsteps, B = 3, 2
+    u0 = np.stack([ch_inputs.initial_condition(2, n, 70 + b, amp=0.6) for b in range(B)])
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    out = ch.propagate(cfg, scheme, dt, nsteps, dev(u0)).cpu().numpy()
+    p = o2.Params(n=n, eps=eps, T=1.0, N=1, J=1, newton_tol=1e-12)
+    tol = 64 * step_bound_2d(n, eps, dt) * nsteps + 1e-13
+    for b in range(B):
+        ref = o2.propagate(p, scheme, dt, nsteps, u0[b])
+        assert np.max(np.abs(out[b] - ref)) <= tol, (b, np.max(np.abs(out[b] - ref)), tol)
+
+
+def test_frozen_2d_steps_match_lemma_3_1(gpu_lib):
+    ch = gpu_lib
+    n, eps, dt = 63, 0.07, 5e-4
+    modes = [(1, 1), (5, 9), (60, 2)]
+    u = np.stack([mode2(n, a, b) for a, b in modes])
+    for scheme, i in (("lin1", 1), ("lin2", 2), ("nl", 1)):
+        cfg = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, frozen=True)
+        out = ch.propagate(cfg, scheme, dt, 1, dev(u)).cpu().numpy()
+        for k, (a, b) in enumerate(modes):
+            y = sum((2.0 * (n + 1) ** 2) * (1.0 - math.cos(m * math.pi / (n + 1))) for m in (a, b))
+            g = (1 + i * dt * y) / (1 + i * dt * y + eps ** 2 * dt * y ** 2)
+            assert np.max(np.abs(out[k] - g * u[k])) <= 64 * step_bound_2d(n, eps, dt, c=2.0), (scheme, a, b)
+
+
+def oracle_params(cfg):
+    return o2.Params(n=cfg.n, eps=cfg.eps, T=cfg.T, N=cfg.n_slices, J=cfg.fine_steps, coarse_steps=cfg.coarse_steps,
+                     fine=FINE_OF[cfg.variant], coarse=COARSE_OF[cfg.variant], newton_tol=cfg.newton_tol,
+                     frozen=cfg.frozen, tol=cfg.tol)
+
+
+@pytest.mark.parametrize("variant", ["PA-I", "NPA-I", "PA-III"])
+def test_parareal_2d_matches_oracle_and_is_exact_at_k_equal_n(gpu_lib, variant):
+    ch = gpu_lib
+    n, N = 31, 4
+    cfg = ch.Config(dim=2, n=n, eps=0.05, T=0.01, n_slices=N, fine_steps=4, variant=variant, newton_tol=1e-12)
+    u0s = [ch_inputs.initial_condition(2, n, s, kind="normal", amp=0.05) for s in (1, 2)]
+    pr = ch.Parareal(cfg, batch=2)
+    for b, u in enumerate(u0s):
+        pr.set_initial(b, u)
+    pr.compute_reference()
+    pr.run()
+    tol = 64 * step_bound_2d(n, cfg.eps, cfg.T / N) * (N + cfg.fine_steps * N) + 1e-12
+    for b, u0 in enumerate(u0s):
+        U, Uref = pr.get_slices(b), pr.get_reference(b)
+        assert np.array_equal(U, Uref)  # finite-step exactness (Theorem 3.2, remark closing Section 3)
+        r = o2.parareal(oracle_params(cfg), u0)
+        assert np.max(np.abs(U - r.U)) <= tol, (b, np.max(np.abs(U - r.U)), tol)
+        st = pr.stats(b)
+        assert st["iterations"] == N and st["err_max"][-1] == 0.0
+    pr.close()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_parareal_2d_intermediate_iterates(gpu_lib, k):
+    ch = gpu_lib
+    n, N = 15, 5
+    cfg = ch.Config(dim=2, n=n, eps=0.06, T=0.02, n_slices=N, fine_steps=3, variant="NPA-I", max_iters=k)
+    u0 = ch_inputs.initial_condition(2, n, 9, kind="normal", amp=0.1)
+    pr = ch.Parareal(cfg, batch=1)
+    pr.set_initial(0, u0)
+    pr.compute_reference()
+    pr.run()
+    U, Uref = pr.get_slices(0), pr.get_reference(0)
+    assert np.array_equal(U[: k + 1], Uref[: k + 1])
+    p = oracle_params(cfg)
+    Uf = o2.fine_solution(p, u0)
+    r = o2.parareal(p, u0, Uf, max_iters=k)
+    tol = 64 * step_bound_2d(n, cfg.eps, cfg.T / N) * (2 * N + cfg.fine_steps * N) + 1e-12
+    assert np.max(np.abs(U - r.U)) <= tol
+    st = pr.stats(0)
+    assert np.allclose(st["err_l2"], r.err_l2, rtol=1e-6, atol=tol)
+    pr.close()
+
+
+def test_frozen_parareal_2d_closed_form(gpu_lib):
+    ch = gpu_lib
+    n, eps, T, N, J = 31, 0.0725, 1.0, 6, 10
+    a_, b_ = 2, 3
+    u0 = mode2(n, a_, b_)
+    y = sum((2.0 * (n + 1) ** 2) * (1.0 - math.cos(m * math.pi / (n + 1))) for m in (a_, b_))
+    dT, dt = T / N, T / N / J
+    a = (1 + dT * y) / (1 + dT * y + eps ** 2 * dT * y ** 2)
+    b = ((1 + dt * y) / (1 + dt * y + eps ** 2 * dt * y ** 2)) ** J
+    for k in (1, 3):
+        cfg = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N, fine_steps=J, variant="PA-I", frozen=True, max_iters=k)
+        pr = ch.Parareal(cfg, batch=1)
+        pr.set_initial(0, u0)
+        pr.run()
+        coef = np.array([sum(math.comb(s, j) * (b - a) ** j * a ** (s - j) for j in range(min(k, s) + 1))
+                         for s in range(N + 1)])
+        assert np.max(np.abs(pr.get_slices(0) - coef[:, None] * u0[None, :])) <= 64 * step_bound_2d(n, eps, dT, c=1)
+        pr.close()
+
+
+def test_c3_grid_full_size_steps(gpu_lib):
+    """The c3 configuration's grid and steps (256 x 256 grid: n = 255, eps = 0.01, coarse step
+    dT = 0.5/32 with Eq. 2.4, fine step dt = dT/100 with Eq. 2.3, u0 = 0.05 N(0,1) seed 1): two
+    coarse and two fine steps against the sparse-direct oracle."""
+    ch = gpu_lib
+    n, eps, T, N, J = 255, 0.01, 0.5, 32, 100
+    u0 = ch_inputs.initial_condition(2, n, 1, kind="normal", amp=0.05)
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N, fine_steps=J, newton_tol=1e-12)
+    p = o2.Params(n=n, eps=eps, T=T, N=N, J=J, newton_tol=1e-12)
+    dT, dt = T / N, T / N / J
+    for scheme, step, c in (("lin1", dT, 1.0), ("nl", dt, 3.0)):
+        out = ch.propagate(cfg, scheme, step, 2, dev(u0[None, :])).cpu().numpy()[0]
+        ref = o2.propagate(p, scheme, step, 2, u0)
+        tol = 64 * step_bound_2d(n, eps, step, c=c) * 2
+        assert np.max(np.abs(out - ref)) <= tol, (scheme, np.max(np.abs(out - ref)), tol)

@@ -161,3 +161,18 @@ def test_2d_parareal_agrees_with_1d_oracle_on_separable_frozen_data():
     y = mu(n, 4) + mu(n, 1)
     g = (1 + dt * y) / (1 + dt * y + eps ** 2 * dt * y ** 2)
     assert np.max(np.abs(out - g ** 3 * u0)) < 1e-13
+
+
+def test_sine_transform_diagonalises_dh_and_is_involutory():
+    n = 15
+    x = ch_inputs.initial_condition(2, n, 12, amp=1.0).reshape(n, n)
+    X = o2.sine_transform(x)
+    assert np.allclose(o2.sine_transform(X), x, atol=1e-13)
+    # D_h x in sine space is -(mu_p + mu_q) X (eigenvalues below Eq. 3.2)
+    lam = np.array([[-(mu(n, q) + mu(n, p)) for p in range(1, n + 1)] for q in range(1, n + 1)])
+    DX = o2.sine_transform(o2.dh_apply(x.reshape(-1), n).reshape(n, n))
+    assert np.allclose(DX, lam * X, atol=1e-9 * np.abs(lam).max())
+    # a single sine mode maps to a single coefficient
+    v = mode2(n, 3, 5).reshape(n, n)
+    V = o2.sine_transform(v)
+    assert abs(V[4, 2]) > 1 and np.sum(np.abs(V) > 1e-9) == 1
