@@ -110,6 +110,7 @@ typedef struct {
   double coarse_sweep_ms;
   int fine_sweep_launches;
   int kernel_launches;
+  long long inner_iterations;     /* 2D: CG iterations summed over all linear solves of run  */
 } ch_stats;
 
 typedef struct ch_parareal ch_parareal;

@@ -52,7 +52,8 @@ class _Stats(C.Structure):
                 ("err_l2", C.c_double * CH_MAX_ITERS), ("err_max", C.c_double * CH_MAX_ITERS),
                 ("t_iter_ms", C.c_double * CH_MAX_ITERS), ("newton_total", C.c_longlong),
                 ("newton_max", C.c_int), ("fine_point_steps", C.c_longlong), ("fine_sweep_ms", C.c_double),
-                ("coarse_sweep_ms", C.c_double), ("fine_sweep_launches", C.c_int), ("kernel_launches", C.c_int)]
+                ("coarse_sweep_ms", C.c_double), ("fine_sweep_launches", C.c_int), ("kernel_launches", C.c_int),
+                ("inner_iterations", C.c_longlong)]
 
 
 @dataclass
@@ -227,7 +228,7 @@ class Parareal:
                 "newton_total": st.newton_total, "newton_max": st.newton_max,
                 "fine_point_steps": st.fine_point_steps, "fine_sweep_ms": st.fine_sweep_ms,
                 "coarse_sweep_ms": st.coarse_sweep_ms, "fine_sweep_launches": st.fine_sweep_launches,
-                "kernel_launches": st.kernel_launches}
+                "kernel_launches": st.kernel_launches, "inner_iterations": st.inner_iterations}
 
     def close(self) -> None:
         if self._h:

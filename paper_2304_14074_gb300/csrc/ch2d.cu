@@ -20,7 +20,8 @@
 // attainable accuracy of each step.
 //
 // DST-I: the sine transform of length n is computed from the complex FFT of length L = 2(n+1)
-// of the odd extension of a row (Stockham radix-2 in shared memory), two real rows packed as
+// of the odd extension of a row (mixed radix-8 Stockham, butterflies in registers, one shared
+// memory buffer; the first stage reads the row from global memory), two real rows packed as
 // the real and imaginary parts of one complex FFT; each pass transforms rows and writes them
 // transposed, so two passes give S X S (S the orthonormal DST-I matrix, S^2 = I).
 #include <cuda_runtime.h>
@@ -50,64 +51,151 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Radix-R DFT in registers, R in {2, 4, 8}: V_s = sum_r v_r exp(-2 pi i r s / R).
+template <int R>
+__device__ __forceinline__ void dft_small(float2 (&v)[R]);
+template <>
+__device__ __forceinline__ void dft_small<2>(float2 (&v)[2]) {
+  const float2 a = v[0], b = v[1];
+  v[0] = make_float2(a.x + b.x, a.y + b.y);
+  v[1] = make_float2(a.x - b.x, a.y - b.y);
+}
+template <>
+__device__ __forceinline__ void dft_small<4>(float2 (&v)[4]) {
+  const float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+  const float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+  const float2 a2 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+  const float2 a3 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);  // -i (v1 - v3)
+  v[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
+  v[2] = make_float2(a0.x - a2.x, a0.y - a2.y);
+  v[1] = make_float2(a1.x + a3.x, a1.y + a3.y);
+  v[3] = make_float2(a1.x - a3.x, a1.y - a3.y);
+}
+template <>
+__device__ __forceinline__ void dft_small<8>(float2 (&v)[8]) {
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft_small<4>(e);
+  dft_small<4>(o);
+  const float r2 = 0.70710678118654752f;
+  // o_s *= W8^s, W8 = exp(-2 pi i / 8)
+  const float2 o1 = make_float2((o[1].x + o[1].y) * r2, (o[1].y - o[1].x) * r2);
+  const float2 o2 = make_float2(o[2].y, -o[2].x);
+  const float2 o3 = make_float2((o[3].y - o[3].x) * r2, -(o[3].x + o[3].y) * r2);
+  v[0] = make_float2(e[0].x + o[0].x, e[0].y + o[0].y);
+  v[4] = make_float2(e[0].x - o[0].x, e[0].y - o[0].y);
+  v[1] = make_float2(e[1].x + o1.x, e[1].y + o1.y);
+  v[5] = make_float2(e[1].x - o1.x, e[1].y - o1.y);
+  v[2] = make_float2(e[2].x + o2.x, e[2].y + o2.y);
+  v[6] = make_float2(e[2].x - o2.x, e[2].y - o2.y);
+  v[3] = make_float2(e[3].x + o3.x, e[3].y + o3.y);
+  v[7] = make_float2(e[3].x - o3.x, e[3].y - o3.y);
+}
+
+// Odd extension of a row pair: y_m = (x0[m-1], x1[m-1]) for 0 < m < N, 0 at m = 0 and m = N,
+// y_{L-m} = -y_m.
+template <int N>
+__device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const float* __restrict__ r1, int m) {
+  constexpr int L = 2 * N;
+  if (m == 0 || m == N) return make_float2(0.f, 0.f);
+  const bool neg = m > N;
+  const int q = neg ? L - m - 1 : m - 1;
+  const float a = r0 ? r0[q] : 0.f, b = r1 ? r1[q] : 0.f;
+  return neg ? make_float2(-a, -b) : make_float2(a, b);
+}
+
+// One Stockham stage of radix R on the F complex FFTs of length L held in buf (in place: all
+// items are loaded to registers, then the block synchronises, then results are stored).
+// Stage 0 reads the odd extension of the input rows straight from global memory.
+template <int N, int R, int F, bool FIRST>
+__device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns, const float* src, int a0) {
+  constexpr int L = 2 * N, LR = L / R, ITEMS = F * LR;
+  constexpr int IPT = (ITEMS + kThreads - 1) / kThreads;
+  constexpr int n = N - 1;
+  float2 v[IPT][R];
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int it = threadIdx.x + q * kThreads;
+    if (it < ITEMS) {
+      const int f = it / LR, j = it - f * LR;
+      if (FIRST) {
+        const int ra = a0 + 2 * f, rb = ra + 1;
+        const float* r0 = (ra < n) ? src + (size_t)ra * n : nullptr;
+        const float* r1 = (rb < n) ? src + (size_t)rb * n : nullptr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = odd_ext<N>(r0, r1, j + r * LR);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = buf[f * L + j + r * LR];
+      }
+    }
+  }
+  if (!FIRST) __syncthreads();
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int it = threadIdx.x + q * kThreads;
+    if (it < ITEMS) {
+      const int f = it / LR, j = it - f * LR;
+      const int k = j & (Ns - 1);
+      const int step = k * (L / (R * Ns));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], twd[r * step]);
+      dft_small<R>(v[q]);
+      const int o = f * L + (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[o + r * Ns] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Complex FFT of length L = 2N of F rows: radix-8 stages, then one radix-2 or radix-4 stage.
+template <int N, int F>
+__device__ __forceinline__ void fft_rows(float2* buf, const float2* twd, const float* src, int a0) {
+  constexpr int L = 2 * N;
+  constexpr int lg = (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7 : (L == 256) ? 8 : (L == 512) ? 9 : 10;
+  constexpr int n8 = lg / 3, rem = lg - 3 * n8;
+  static_assert(n8 >= 1, "transform length too short");
+  fft_stage<N, 8, F, true>(buf, twd, 1, src, a0);
+  int Ns = 8;
+#pragma unroll
+  for (int s = 1; s < n8; ++s) {
+    fft_stage<N, 8, F, false>(buf, twd, Ns, nullptr, 0);
+    Ns *= 8;
+  }
+  if constexpr (rem == 1) fft_stage<N, 2, F, false>(buf, twd, Ns, nullptr, 0);
+  if constexpr (rem == 2) fft_stage<N, 4, F, false>(buf, twd, Ns, nullptr, 0);
+}
+
 // One transform pass: rows of `in` ([units][n][n]) -> orthonormal DST-I -> written transposed.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__ in, float* __restrict__ out,
                                                         const float2* __restrict__ tw) {
-  constexpr int n = N - 1, L = 2 * N, F = kDstRows / 2, HL = L / 2;
+  constexpr int n = N - 1, L = 2 * N, F = kDstRows / 2;
   extern __shared__ float2 smem2[];
-  float2* x = smem2;
-  float2* y = smem2 + F * L;
-  float2* twd = smem2 + 2 * F * L;
+  float2* buf = smem2;
+  float2* twd = smem2 + F * L;
   const int u = blockIdx.y;
   const int a0 = blockIdx.x * kDstRows;
   const float* src = in + (size_t)u * n * n;
-  for (int m = threadIdx.x; m < HL; m += kThreads) twd[m] = tw[m];
-  for (int idx = threadIdx.x; idx < F * N; idx += kThreads) {
-    const int f = idx / N, j = idx - f * N;
-    const int r0 = a0 + 2 * f, r1 = r0 + 1;
-    float v0 = 0.f, v1 = 0.f;
-    if (j >= 1) {
-      if (r0 < n) v0 = src[(size_t)r0 * n + j - 1];
-      if (r1 < n) v1 = src[(size_t)r1 * n + j - 1];
-      x[f * L + j] = make_float2(v0, v1);
-      x[f * L + L - j] = make_float2(-v0, -v1);
-    } else {
-      x[f * L] = make_float2(0.f, 0.f);
-      x[f * L + N] = make_float2(0.f, 0.f);
-    }
-  }
+  for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = tw[m];
   __syncthreads();
-#pragma unroll 1
-  for (int Ns = 1; Ns < L; Ns <<= 1) {
-    for (int idx = threadIdx.x; idx < F * HL; idx += kThreads) {
-      const int f = idx / HL, j = idx - f * HL;
-      const int k = j & (Ns - 1);
-      const float2 a = x[f * L + j];
-      const float2 b = cmul(x[f * L + j + HL], twd[k * (HL / Ns)]);
-      const int o = f * L + (j - k) * 2 + k;
-      y[o] = make_float2(a.x + b.x, a.y + b.y);
-      y[o + Ns] = make_float2(a.x - b.x, a.y - b.y);
-    }
-    __syncthreads();
-    float2* t = x;
-    x = y;
-    y = t;
-  }
+  fft_rows<N, F>(buf, twd, src, a0);
+  // row pair (2f, 2f+1) packed as real + i imag: S x_{2f} = -Im Y / 2, S x_{2f+1} = Re Y / 2
   const float sc = 0.5f * sqrtf(2.0f / N);
   float* dst = out + (size_t)u * n * n;
   for (int idx = threadIdx.x; idx < n * kDstRows; idx += kThreads) {
     const int k = idx / kDstRows, r = idx - k * kDstRows;
     const int a = a0 + r;
     if (a >= n) continue;
-    const float2 v = x[(r >> 1) * L + k + 1];
+    const float2 v = buf[(r >> 1) * L + k + 1];
     dst[(size_t)k * n + a] = (r & 1) ? v.x * sc : -v.y * sc;
   }
 }
 
 template <int N>
 size_t dst_smem() {
-  return (size_t)(2 * (kDstRows / 2) * 2 * N + N) * sizeof(float2);
+  return (size_t)((kDstRows / 2) * 2 * N + 2 * N) * sizeof(float2);
 }
 
 // ------------------------------------------------------------------ FP64 stencils
@@ -402,9 +490,12 @@ __global__ void k2_update(double* __restrict__ X, const float* __restrict__ d, s
 
 // Newton bookkeeping per unit: stop on max|d| <= tol or at the FP64 rounding floor (an
 // increment below sqrt(tol) that fails to halve the previous one); count iterations.
+// ctr[0] is the 0-based Newton iteration of the batch; the last allowed one flags failure.
 __global__ void k2_newton_end(double* __restrict__ scal, const double* __restrict__ part, int* __restrict__ flag,
-                              int* __restrict__ cnt, int units, double tol, double floor_, int last, unsigned* status) {
+                              int* __restrict__ cnt, int units, double tol, double floor_, const int* __restrict__ ctr,
+                              int newton_max, unsigned* status) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int last = (ctr[0] >= newton_max - 1);
   if (u >= units || flag[2 * u]) return;
   double dm = 0.0;
   for (int b = 0; b < kBlk; ++b) dm = fmax(dm, part[(size_t)u * kBlk + b]);
@@ -419,27 +510,34 @@ __global__ void k2_newton_end(double* __restrict__ scal, const double* __restric
   if (done) flag[2 * u] = 1;
 }
 
-__global__ void k2_count(const int* __restrict__ flag, int units, int* __restrict__ out) {
+// Loop control of the device-driven Newton and CG loops (single block). which = 0: Newton
+// (continue while a unit is not converged and fewer than lim iterations ran); 1: CG.
+__global__ void k2_loop_cond(cudaGraphConditionalHandle hnd, const int* __restrict__ flag, int units,
+                             int* __restrict__ ctr, int which, int lim, unsigned long long* __restrict__ total) {
   __shared__ int c;
   if (threadIdx.x == 0) c = 0;
   __syncthreads();
   int local = 0;
-  for (int u = threadIdx.x; u < units; u += blockDim.x) local += (flag[2 * u] == 0 && flag[2 * u + 1] == 0) ? 1 : 0;
-  atomicAdd(&c, local);
+  for (int u = threadIdx.x; u < units; u += blockDim.x)
+    local += (which == 0) ? (flag[2 * u] == 0) : (flag[2 * u] == 0 && flag[2 * u + 1] == 0);
+  if (local) atomicAdd(&c, local);
   __syncthreads();
-  if (threadIdx.x == 0) *out = c;
+  if (threadIdx.x == 0) {
+    const int it = ++ctr[which];
+    if (total) *total += 1ull;
+    cudaGraphSetConditional(hnd, (c > 0 && it < lim) ? 1u : 0u);
+  }
 }
 
-__global__ void k2_count_newton(const int* __restrict__ flag, int units, int* __restrict__ out) {
-  __shared__ int c;
-  if (threadIdx.x == 0) c = 0;
-  __syncthreads();
-  int local = 0;
-  for (int u = threadIdx.x; u < units; u += blockDim.x) local += flag[2 * u] == 0 ? 1 : 0;
-  atomicAdd(&c, local);
-  __syncthreads();
-  if (threadIdx.x == 0) *out = c;
+// Start of a loop: counter = 0 and, for a nested loop, its condition = 1.
+__global__ void k2_loop_start(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, int which, int set_cond) {
+  if (threadIdx.x == 0) {
+    ctr[which] = 0;
+    if (set_cond) cudaGraphSetConditional(hnd, 1u);
+  }
 }
+
+
 
 __global__ void k2_reset_flags(int* __restrict__ flag, int* __restrict__ cnt, double* __restrict__ scal, int units) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -486,6 +584,18 @@ cudaError_t dst_pass_n(const float* in, float* out, int units, const float2* tw,
   dim3 grid((N - 1 + kDstRows - 1) / kDstRows, units);
   k_dst_pass<N><<<grid, kThreads, smem, st>>>(in, out, tw);
   return cudaGetLastError();
+}
+
+cudaError_t dst_prepare(int n) {
+  switch (n + 1) {
+    case 16: return prep(k_dst_pass<16>, dst_smem<16>());
+    case 32: return prep(k_dst_pass<32>, dst_smem<32>());
+    case 64: return prep(k_dst_pass<64>, dst_smem<64>());
+    case 128: return prep(k_dst_pass<128>, dst_smem<128>());
+    case 256: return prep(k_dst_pass<256>, dst_smem<256>());
+    case 512: return prep(k_dst_pass<512>, dst_smem<512>());
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t dst_pass(int n, const float* in, float* out, int units, const float2* tw, cudaStream_t st) {
@@ -628,15 +738,18 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   al((void**)&tmp_, v32);
   al((void**)&tmp2_, v32);
   al((void**)&mu_, p.n * sizeof(float));
-  al((void**)&tw_, (size_t)(p.n + 1) * sizeof(float2));
+  al((void**)&tw_, (size_t)2 * (p.n + 1) * sizeof(float2));
   al((void**)&part_, (size_t)cap * 2 * kBlk * sizeof(double));
   al((void**)&scal_, (size_t)cap * 8 * sizeof(double));
   al((void**)&flag_, (size_t)cap * 2 * sizeof(int));
   al((void**)&newton_cnt_, (size_t)cap * sizeof(int));
   al((void**)&status_, 4 * sizeof(unsigned) + sizeof(unsigned long long));
+  al((void**)&ctr_, 4 * sizeof(int));
+  al((void**)&cg_dev_, sizeof(unsigned long long));
   if (e != cudaSuccess) return e;
   e = cudaHostAlloc((void**)&host_cnt_, 4 * sizeof(int), 0);
   if (e != cudaSuccess) return e;
+  if ((e = dst_prepare(p.n)) != cudaSuccess) return e;  // kernel attributes, before any capture
   // eigenvalues of A = -D_1: mu_p = (4/h^2) sin^2(p pi / (2(n+1))), p = 1..n (host libm)
   std::vector<float> mu(p.n);
   for (int q = 1; q <= p.n; ++q) {
@@ -644,18 +757,21 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
     mu[q - 1] = float(4.0 / (p.h * p.h) * s * s);
   }
   const int L = 2 * (p.n + 1);
-  std::vector<float2> tw(L / 2);
-  for (int m = 0; m < L / 2; ++m) tw[m] = make_float2(float(std::cos(-2.0 * M_PI * m / L)), float(std::sin(-2.0 * M_PI * m / L)));
+  std::vector<float2> tw(L);
+  for (int m = 0; m < L; ++m) tw[m] = make_float2(float(std::cos(-2.0 * M_PI * m / L)), float(std::sin(-2.0 * M_PI * m / L)));
   e = cudaMemcpyAsync(mu_, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
 
 void Prop2D::release() {
+  for (auto& c : graphs_) cudaGraphExecDestroy(c.second);
+  graphs_.clear();
   void* ptrs[] = {yhat_, yprev_, z_, xacc_, w_, rhs_, xh_, rh_, ph_, qh_, tmp_, tmp2_, mu_, tw_, part_, scal_, flag_,
-                  newton_cnt_, status_};
+                  newton_cnt_, status_, ctr_, cg_dev_};
   for (void* q : ptrs) cudaFree(q);
   if (host_cnt_) cudaFreeHost(host_cnt_);
   host_cnt_ = nullptr;
@@ -663,8 +779,9 @@ void Prop2D::release() {
   w_ = rhs_ = xh_ = rh_ = ph_ = qh_ = tmp_ = tmp2_ = mu_ = nullptr;
   tw_ = nullptr;
   part_ = scal_ = nullptr;
-  flag_ = newton_cnt_ = nullptr;
+  flag_ = newton_cnt_ = ctr_ = nullptr;
   status_ = nullptr;
+  cg_dev_ = nullptr;
 }
 
 cudaError_t Prop2D::dst2(const float* in, float* out, int units, cudaStream_t st) {
@@ -673,127 +790,207 @@ cudaError_t Prop2D::dst2(const float* in, float* out, int units, cudaStream_t st
   return e;
 }
 
-cudaError_t Prop2D::count_active(const int* flags, int units, cudaStream_t st, int* out) {
-  k2_count<<<1, 256, 0, st>>>(flags, units, host_cnt_ ? (int*)status_ + 2 : nullptr);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host_cnt_, (int*)status_ + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) *out = host_cnt_[0];
-  return e;
-}
 
-// Preconditioned CG in sine space on S d = A^{-1} H for all units with Newton not done;
-// rhs_ holds H (physical, FP32); the correction d ends up in tmp_ (physical).
-cudaError_t Prop2D::cg_solve(int units, double dt, double e2dt, cudaStream_t st, int* iters) {
+// One CG iteration in sine space (enqueued on st; the body of the CG loop).
+cudaError_t Prop2D::enqueue_cg_iteration(int units, double dt, cudaStream_t st) {
   const dim3 grid(kBlk, units);
-  const float fe2dt = float(e2dt), fdt = float(dt);
-  cudaError_t e = dst2(rhs_, qh_, units, st);  // Hhat
+  const float fe2dt = float(p_.eps2 * dt), fdt = float(dt);
+  cudaError_t e = dst2(ph_, tmp_, units, st);  // p (physical)
   if (e != cudaSuccess) return e;
-  k2_cg_reopen<<<(units + 255) / 256, 256, 0, st>>>(flag_, units);
-  k2_cg_init<<<grid, kThreads, 0, st>>>(qh_, xh_, rh_, ph_, mu_, p_.n, fe2dt, fdt, scal_, part_, flag_);
-  k2_cg_start<<<(units + 255) / 256, 256, 0, st>>>(part_, scal_, flag_, units);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const double tol2 = p_.cg_tol * p_.cg_tol;
-  int it = 0;
-  for (; it < p_.cg_max; ++it) {
-    e = dst2(ph_, tmp_, units, st);  // p (physical)
-    if (e != cudaSuccess) return e;
-    k2_cg_wprod<<<grid, kThreads, 0, st>>>(tmp_, w_, tmp_, pts_, fdt, scal_, flag_);
-    e = dst2(tmp_, qh_, units, st);  // That
-    if (e != cudaSuccess) return e;
-    k2_cg_q<<<grid, kThreads, 0, st>>>(ph_, qh_, mu_, p_.n, fe2dt, fdt, scal_, part_, flag_);
-    k2_cg_step<<<grid, kThreads, 0, st>>>(xh_, rh_, ph_, qh_, mu_, p_.n, fe2dt, fdt, scal_, part_,
-                                          part_ + (size_t)cap_ * kBlk, flag_);
-    k2_cg_dir<<<grid, kThreads, 0, st>>>(ph_, rh_, mu_, p_.n, fe2dt, fdt, scal_, part_ + (size_t)cap_ * kBlk, flag_,
-                                         tol2);
-    k2_cg_end<<<(units + 255) / 256, 256, 0, st>>>(scal_, part_ + (size_t)cap_ * kBlk, flag_, units, tol2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((it & 3) == 3) {
-      int act = 0;
-      if ((e = count_active(flag_, units, st, &act)) != cudaSuccess) return e;
-      if (act == 0) {
-        ++it;
-        break;
-      }
-    }
-  }
-  if (iters) *iters = it;
-  return dst2(xh_, tmp_, units, st);  // d (physical)
-}
-
-// Newton on the step residual H(X) = X - b + D_h z(X) for all units, starting from X = Y:
-//   zmode 0: z = c1 lap X - dt X^3 (Eq. 3.17), 1: frozen (X^3 -> X), 2: z = c1 lap X - dt W64^2 X
-//   (Eq. 2.4 with W64 = u^n), 3: z = c1 lap X - dt wconst X (Eq. 2.5: wconst = 2).
-//   wmode selects the Jacobian weights the same way (0: 3X^2, 1: 1, 2: W64^2, 3: wconst).
-cudaError_t Prop2D::newton_solve(double* Y, const double* b, int units, double dt, int zmode, int wmode,
-                                 const double* W64, double wconst, cudaStream_t st) {
-  const dim3 grid(kBlk, units);
-  const double ih2 = 1.0 / (p_.h * p_.h);
-  const double c1 = p_.eps2 * dt * ih2;
-  k2_reset_flags<<<(units + 255) / 256, 256, 0, st>>>(flag_, newton_cnt_, scal_, units);
-  cudaError_t e = cudaGetLastError();
+  k2_cg_wprod<<<grid, kThreads, 0, st>>>(tmp_, w_, tmp_, pts_, fdt, scal_, flag_);
+  e = dst2(tmp_, qh_, units, st);  // That
   if (e != cudaSuccess) return e;
-  for (int m = 0; m < p_.newton_max; ++m) {
-    k2_z<<<grid, kThreads, 0, st>>>(Y, z_, p_.n, c1, dt, zmode, W64, wconst, flag_);
-    k2_resid<<<grid, kThreads, 0, st>>>(Y, b, z_, rhs_, p_.n, ih2, flag_);
-    k2_weights<<<grid, kThreads, 0, st>>>(Y, W64, w_, wmode, wconst, pts_, part_, flag_);
-    k2_wbar<<<(units + 255) / 256, 256, 0, st>>>(part_, scal_, units, flag_);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cg_solve(units, dt, p_.eps2 * dt, st, nullptr)) != cudaSuccess) return e;
-    k2_update<<<grid, kThreads, 0, st>>>(Y, tmp_, pts_, part_, flag_, status_);
-    k2_newton_end<<<(units + 255) / 256, 256, 0, st>>>(scal_, part_, flag_, newton_cnt_, units, p_.newton_tol,
-                                                        std::sqrt(p_.newton_tol), m == p_.newton_max - 1, status_);
-    k2_count_newton<<<1, 256, 0, st>>>(flag_, units, (int*)status_ + 2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(host_cnt_, (int*)status_ + 2, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    if (host_cnt_[0] == 0) break;
-  }
-  k2_newton_stats<<<(units + 255) / 256, 256, 0, st>>>(newton_cnt_, units,
-                                                        reinterpret_cast<unsigned long long*>((int*)status_ + 4),
-                                                        (int*)status_ + 3);
+  k2_cg_q<<<grid, kThreads, 0, st>>>(ph_, qh_, mu_, p_.n, fe2dt, fdt, scal_, part_, flag_);
+  k2_cg_step<<<grid, kThreads, 0, st>>>(xh_, rh_, ph_, qh_, mu_, p_.n, fe2dt, fdt, scal_, part_,
+                                        part_ + (size_t)cap_ * kBlk, flag_);
+  k2_cg_dir<<<grid, kThreads, 0, st>>>(ph_, rh_, mu_, p_.n, fe2dt, fdt, scal_, part_ + (size_t)cap_ * kBlk, flag_,
+                                       p_.cg_tol * p_.cg_tol);
+  k2_cg_end<<<(units + 255) / 256, 256, 0, st>>>(scal_, part_ + (size_t)cap_ * kBlk, flag_, units,
+                                                  p_.cg_tol * p_.cg_tol);
   return cudaGetLastError();
 }
 
-// One step of the nonlinear scheme Eq. 2.3: b = (I - dt D_h) u^n (Eq. 3.17); Newton from the
-// linear extrapolation 2u^n - u^{n-1} inside a propagation (u^n at its first step).
-cudaError_t Prop2D::nl_step(double* Y, int units, double dt, bool have_prev, cudaStream_t st) {
-  const dim3 grid(kBlk, units);
-  const size_t total = (size_t)units * pts_;
-  const double ih2 = 1.0 / (p_.h * p_.h);
-  k2_yhat<<<grid, kThreads, 0, st>>>(Y, yhat_, p_.n, dt * ih2);
-  k2_predict<<<(unsigned)((total + 1023) / 1024), 1024, 0, st>>>(Y, yprev_, total, have_prev ? 1 : 0);
-  cudaError_t e = cudaGetLastError();
+namespace {
+
+// Adds a WHILE node at the current capture position of `st` and returns its body graph.
+cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle* hnd, unsigned dflt, unsigned flags,
+                      cudaGraph_t* body) {
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &stt, nullptr, &g, &deps, nullptr, &nd);
   if (e != cudaSuccess) return e;
-  return newton_solve(Y, yhat_, units, dt, p_.frozen ? 1 : 0, p_.frozen ? 1 : 0, nullptr, 0.0, st);
+  if (hnd && !*hnd) {
+    e = cudaGraphConditionalHandleCreate(hnd, g, dflt, flags);
+    if (e != cudaSuccess) return e;
+  }
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *hnd;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
-// One step of a linear scheme (Eq. 2.4 or Eq. 2.5) from X = u^n: FP32 CG corrections against
-// FP64 residuals of J X = b (iterative refinement) until newton_tol or the rounding floor.
-cudaError_t Prop2D::linear_step(double* Y, int units, int scheme, double dt, cudaStream_t st) {
+// Current capture graph of a stream (to create a handle before the node that uses it).
+cudaError_t capture_graph(cudaStream_t st, cudaGraph_t* g) {
+  cudaStreamCaptureStatus stt;
+  return cudaStreamGetCaptureInfo(st, &stt, nullptr, g, nullptr, nullptr, nullptr);
+}
+
+}  // namespace
+
+// Captures one implicit step of the batch as a graph: the right-hand side kernels, then a
+// device-driven Newton loop whose body forms the FP64 residual, runs a device-driven CG loop
+// in sine space and applies the correction. Nothing returns to the host inside the step.
+cudaError_t Prop2D::build_step(const StepKey& k, cudaGraphExec_t* out) {
+  const int units = k.units;
   const dim3 grid(kBlk, units);
-  const double ih2 = 1.0 / (p_.h * p_.h);
-  cudaError_t e = cudaMemcpyAsync(yprev_, Y, (size_t)units * pts_ * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
-  if (scheme == SCHEME_LIN1) {
-    k2_yhat<<<grid, kThreads, 0, st>>>(yprev_, yhat_, p_.n, dt * ih2);  // (I - dt D_h) u^n
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return p_.frozen ? newton_solve(Y, yhat_, units, dt, 3, 3, nullptr, 1.0, st)
-                     : newton_solve(Y, yhat_, units, dt, 2, 2, yprev_, 0.0, st);
+  const double dt = k.dt, ih2 = 1.0 / (p_.h * p_.h), c1 = p_.eps2 * dt * ih2;
+  double* Y = k.Y;
+  const size_t total = (size_t)units * pts_;
+  int zmode, wmode;
+  const double* W64 = nullptr;
+  double wconst = 0.0;
+  if (k.scheme == SCHEME_NL) {
+    zmode = wmode = p_.frozen ? 1 : 0;
+  } else if (k.scheme == SCHEME_LIN1) {
+    zmode = wmode = p_.frozen ? 3 : 2;
+    W64 = yprev_;
+    wconst = 1.0;
+  } else {
+    zmode = wmode = 3;
+    wconst = 2.0;
   }
-  k2_lin2_rhs<<<grid, kThreads, 0, st>>>(yprev_, yhat_, p_.n, dt * ih2, p_.frozen);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return newton_solve(Y, yhat_, units, dt, 3, 3, nullptr, 2.0, st);
+  cudaStream_t cs = nullptr, bs = nullptr, bs2 = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  cudaGraphConditionalHandle hN = 0, hC = 0;
+  if (e == cudaSuccess) {
+    // right-hand side b (in yhat_) and starting point
+    if (k.scheme == SCHEME_NL) {
+      k2_yhat<<<grid, kThreads, 0, cs>>>(Y, yhat_, p_.n, dt * ih2);
+      k2_predict<<<(unsigned)((total + 1023) / 1024), 1024, 0, cs>>>(Y, yprev_, total, k.have_prev);
+    } else {
+      cudaMemcpyAsync(yprev_, Y, total * sizeof(double), cudaMemcpyDeviceToDevice, cs);
+      if (k.scheme == SCHEME_LIN1) k2_yhat<<<grid, kThreads, 0, cs>>>(yprev_, yhat_, p_.n, dt * ih2);
+      else k2_lin2_rhs<<<grid, kThreads, 0, cs>>>(yprev_, yhat_, p_.n, dt * ih2, p_.frozen);
+    }
+    k2_reset_flags<<<(units + 255) / 256, 256, 0, cs>>>(flag_, newton_cnt_, scal_, units);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = capture_graph(cs, &g);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hN, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    k2_loop_start<<<1, 32, 0, cs>>>(hN, ctr_, 0, 0);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t bodyN = nullptr;
+  if (e == cudaSuccess) e = add_while(cs, &hN, 1, cudaGraphCondAssignDefault, &bodyN);
+  // ---- Newton body
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    k2_z<<<grid, kThreads, 0, bs>>>(Y, z_, p_.n, c1, dt, zmode, W64, wconst, flag_);
+    k2_resid<<<grid, kThreads, 0, bs>>>(Y, yhat_, z_, rhs_, p_.n, ih2, flag_);
+    k2_weights<<<grid, kThreads, 0, bs>>>(Y, W64, w_, wmode, wconst, pts_, part_, flag_);
+    k2_wbar<<<(units + 255) / 256, 256, 0, bs>>>(part_, scal_, units, flag_);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = dst2(rhs_, qh_, units, bs);  // H in sine space
+  if (e == cudaSuccess) {
+    const float fe2dt = float(p_.eps2 * dt), fdt = float(dt);
+    k2_cg_reopen<<<(units + 255) / 256, 256, 0, bs>>>(flag_, units);
+    k2_cg_init<<<grid, kThreads, 0, bs>>>(qh_, xh_, rh_, ph_, mu_, p_.n, fe2dt, fdt, scal_, part_, flag_);
+    k2_cg_start<<<(units + 255) / 256, 256, 0, bs>>>(part_, scal_, flag_, units);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t gN = nullptr;
+  if (e == cudaSuccess) e = capture_graph(bs, &gN);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hC, gN, 0, 0);
+  if (e == cudaSuccess) {
+    k2_loop_start<<<1, 32, 0, bs>>>(hC, ctr_, 1, 1);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t bodyC = nullptr;
+  if (e == cudaSuccess) e = add_while(bs, &hC, 0, 0, &bodyC);
+  // ---- CG body
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs2, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = enqueue_cg_iteration(units, dt, bs2);
+  if (e == cudaSuccess) {
+    k2_loop_cond<<<1, 256, 0, bs2>>>(hC, flag_, units, ctr_, 1, p_.cg_max, cg_dev_);
+    e = cudaGetLastError();
+  }
+  {
+    cudaGraph_t dummy = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bs2, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  // ---- back in the Newton body: correction d = S^{-1} ... in physical space, update, stop test
+  if (e == cudaSuccess) e = dst2(xh_, tmp_, units, bs);
+  if (e == cudaSuccess) {
+    k2_update<<<grid, kThreads, 0, bs>>>(Y, tmp_, pts_, part_, flag_, status_);
+    k2_newton_end<<<(units + 255) / 256, 256, 0, bs>>>(scal_, part_, flag_, newton_cnt_, units, p_.newton_tol,
+                                                        std::sqrt(p_.newton_tol), ctr_, p_.newton_max, status_);
+    k2_loop_cond<<<1, 256, 0, bs>>>(hN, flag_, units, ctr_, 0, p_.newton_max, nullptr);
+    e = cudaGetLastError();
+  }
+  {
+    cudaGraph_t dummy = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bs, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) {
+    k2_newton_stats<<<(units + 255) / 256, 256, 0, cs>>>(newton_cnt_, units,
+                                                          reinterpret_cast<unsigned long long*>((int*)status_ + 4),
+                                                          (int*)status_ + 3);
+    e = cudaGetLastError();
+  }
+  {
+    cudaGraph_t dummy = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (bs) cudaStreamDestroy(bs);
+  if (bs2) cudaStreamDestroy(bs2);
+  return e;
 }
 
 cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
   if (units > cap_ || units < 1) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  for (int j = 0; j < nsteps && e == cudaSuccess; ++j) {
-    if (scheme == SCHEME_NL) e = nl_step(Y, units, dt, j > 0, st);
-    else e = linear_step(Y, units, scheme, dt, st);
+  for (int j = 0; j < nsteps; ++j) {
+    StepKey k{Y, units, scheme, dt, (scheme == SCHEME_NL && j > 0) ? 1 : 0};
+    cudaGraphExec_t ex = nullptr;
+    for (auto& c : graphs_)
+      if (c.first == k) ex = c.second;
+    if (!ex) {
+      const cudaError_t e = build_step(k, &ex);
+      if (e != cudaSuccess) return e;
+      graphs_.push_back({k, ex});
+    }
+    const cudaError_t e = cudaGraphLaunch(ex, st);
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t Prop2D::reset_counters(cudaStream_t st) {
+  newton_total_ = 0;
+  newton_peak_ = 0;
+  cg_total_ = 0;
+  cudaError_t e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, sizeof(unsigned long long), st);
   return e;
 }
 
@@ -802,7 +999,10 @@ unsigned Prop2D::read_status(cudaStream_t st) {
   unsigned long long tot = 0;
   cudaMemcpyAsync(s, status_, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&tot, (int*)status_ + 4, sizeof(tot), cudaMemcpyDeviceToHost, st);
+  unsigned long long cgt = 0;
+  cudaMemcpyAsync(&cgt, cg_dev_, sizeof(cgt), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
+  cg_total_ = (long long)cgt;
   newton_total_ = tot;
   newton_peak_ = (int)s[3];
   return s[0];

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
 #include <vector>
 
 namespace chg2 {
@@ -38,20 +39,26 @@ class Prop2D {
   cudaError_t dst2(const float* in, float* out, int units, cudaStream_t st);
   unsigned read_status(cudaStream_t st);  // synchronises
   unsigned long long newton_iterations() const { return newton_total_; }
+  long long cg_iterations() const { return cg_total_; }
   int newton_peak() const { return newton_peak_; }
-  void reset_counters() {
-    newton_total_ = 0;
-    newton_peak_ = 0;
-  }
+  // Zeroes the device status bits and the Newton / CG counters (enqueued on st).
+  cudaError_t reset_counters(cudaStream_t st);
   size_t bytes() const { return bytes_; }
 
  private:
-  cudaError_t newton_solve(double* Y, const double* b, int units, double dt, int zmode, int wmode,
-                           const double* W64, double wconst, cudaStream_t st);
-  cudaError_t nl_step(double* Y, int units, double dt, bool have_prev, cudaStream_t st);
-  cudaError_t linear_step(double* Y, int units, int scheme, double dt, cudaStream_t st);
-  cudaError_t cg_solve(int units, double cdt, double e2dt, cudaStream_t st, int* iters);
-  cudaError_t count_active(const int* flags, int units, cudaStream_t st, int* out);
+  struct StepKey {
+    double* Y;
+    int units;
+    int scheme;
+    double dt;
+    int have_prev;
+    bool operator==(const StepKey& o) const {
+      return Y == o.Y && units == o.units && scheme == o.scheme && dt == o.dt && have_prev == o.have_prev;
+    }
+  };
+  cudaError_t build_step(const StepKey& k, cudaGraphExec_t* out);
+  cudaError_t enqueue_cg_iteration(int units, double dt, cudaStream_t st);
+  std::vector<std::pair<StepKey, cudaGraphExec_t>> graphs_;
 
   Params2D p_{};
   int cap_ = 0;
@@ -73,16 +80,19 @@ class Prop2D {
   float* tmp_ = nullptr;     // transform scratch / physical-space work
   float* tmp2_ = nullptr;
   float* mu_ = nullptr;      // 1D eigenvalues mu_p of -D_h, p = 1..n
-  float2* tw_ = nullptr;     // FFT twiddles exp(-2 pi i m / L), m < L/2
+  float2* tw_ = nullptr;     // FFT twiddles exp(-2 pi i m / L), m < L
   // per-unit scalars
   double* part_ = nullptr;   // reduction partials [units][nblk]
   double* scal_ = nullptr;   // [units][8]: rho, rho0, alpha, beta, wbar, dmax, prevd, spare
   int* flag_ = nullptr;      // [units][2]: newton done, cg done
   int* newton_cnt_ = nullptr;  // [units] Newton iterations of the current step
   unsigned* status_ = nullptr;
+  int* ctr_ = nullptr;         // device loop counters: [0] Newton, [1] CG
+  unsigned long long* cg_dev_ = nullptr;  // CG iterations (batched) since the last reset
   int* host_cnt_ = nullptr;    // pinned
   unsigned long long newton_total_ = 0;
   int newton_peak_ = 0;
+  long long cg_total_ = 0;
 };
 
 // Parareal correction of one slice for `count` problems list[0..count) (Eq. 2.2), fused with

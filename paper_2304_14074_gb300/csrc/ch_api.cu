@@ -185,6 +185,7 @@ ch_status reference2d(ch_parareal* h) {
 
 ch_status run2d(ch_parareal* h) {
   const int B = h->B, N = h->p.N, maxit = h->p.maxit;
+  CH_CUDA(h, h->p2->reset_counters(h->st));
   const size_t pts = h->pts, us = (size_t)(N + 1) * pts, fs = (size_t)N * pts;
   const double h2 = h->p.h * h->p.h;
   const double* ref = h->ref_valid ? h->Uref : nullptr;
@@ -630,6 +631,7 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
     out->coarse_sweep_ms = h->coarse_ms;
     out->fine_sweep_launches = h->iters_done;
     out->kernel_launches = 0;
+    out->inner_iterations = h->p2->cg_iterations();
     return CH_OK;
   }
   const int maxit = h->p.maxit;

@@ -84,4 +84,4 @@ def test_destroy_accepts_null_and_last_error_on_null():
 def test_binding_struct_layout_matches_header():
     # ch_config: 2 ints, 2 doubles, 4 ints, double, int, double, 3 ints, double -> 88 bytes with padding
     assert C.sizeof(_lib._Config) == 88
-    assert C.sizeof(_lib._Stats) == 8 + 4 * 8 * ch.CH_MAX_ITERS + 8 + 8 + 8 + 8 + 8 + 4 + 4
+    assert C.sizeof(_lib._Stats) == 8 + 4 * 8 * ch.CH_MAX_ITERS + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8
