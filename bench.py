@@ -41,6 +41,9 @@ WORKLOADS = {
     "c2-profile": dict(name="1D NPA-I M=1024 eps=0.02 N=64 J=10 (dt as c2) batch=256, profiling case",
                        n=1024, eps=0.02, T=0.05, N=64, J=10, batch=256, variant="NPA-I", newton_tol=1e-12,
                        amp=0.1, precision=1, ttol=False),
+    "c3": dict(name="2D nonlinear Parareal NPA-I 256x256 grid (n=255) eps=0.01 T=0.5 N=32 J=100 u0=0.05*N(0,1) seed 1",
+               dim=2, n=255, eps=0.01, T=0.5, N=32, J=100, batch=1, variant="NPA-I", newton_tol=1e-12,
+               amp=0.05, kind="normal", seed0=1, precision=1, ttol=True),
     "c1": dict(name="1D linear Parareal PA-I M=128 eps=0.05 T=0.1 N=16 dt=1e-5 batch=1",
                n=128, eps=0.05, T=0.1, N=16, J=625, batch=1, variant="PA-I", newton_tol=1e-12,
                amp=0.1, precision=0, ttol=True),
@@ -57,11 +60,22 @@ FP64_FLOPS_NEWTON = 15
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
+# 2D fine sweep, algorithmic HBM bytes per grid point: a sine-transform pass reads and writes an
+# FP32 field (8 B); a CG iteration = 4 passes + the pointwise sweeps (t = dt (wc - wbar) p: 12 B,
+# q = m p + That: 12 B, x/r update: 24 B, p update: 12 B); a Newton iteration adds the FP64
+# residual (z: 16 B, H: 28 B), weights (12 B), 4 passes for H and the correction, and the FP64
+# update (20 B).
+BYTES_CG_2D = 4 * 8 + 12 + 12 + 24 + 12
+BYTES_NEWTON_2D = 16 + 28 + 12 + 4 * 8 + 20
+
+
 def u0_batch(w, rank):
     import ch_inputs
     import numpy as np
-    base = rank * w["batch"]
-    return np.stack([ch_inputs.initial_condition(1, w["n"], base + b, amp=w["amp"]) for b in range(w["batch"])])
+    base = rank * w["batch"] + w.get("seed0", 0)
+    dim = w.get("dim", 1)
+    return np.stack([ch_inputs.initial_condition(dim, w["n"], base + b, kind=w.get("kind", "uniform"), amp=w["amp"])
+                     for b in range(w["batch"])])
 
 
 # ------------------------------------------------------------------------ clocks sampling
@@ -123,14 +137,23 @@ class ClockSampler:
 # ------------------------------------------------------------------------ CPU oracle leg
 
 
+ORACLE_2D_STEPS = 2  # 2D sample: this many fine steps of one slice per process (sparse LU per step)
+
+
 def _oracle_step(args):
-    """One step of the workload (coarse sweep + one fine sweep + correction) for one problem."""
+    """1D: one step of the workload (coarse sweep + one fine sweep + correction) for one problem.
+    2D: ORACLE_2D_STEPS fine steps of one slice (a full 2D step takes hours with sparse LU)."""
     w, u0 = args
-    from oracle import oracle1d as o
-    p = o.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], fine=FINE_OF[w["variant"]],
-                 coarse=COARSE_OF[w["variant"]], newton_tol=w["newton_tol"], max_iters=1)
     t = time.perf_counter()
-    o.parareal(p, u0)
+    if w.get("dim", 1) == 2:
+        from oracle import oracle2d as o2
+        p = o2.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], newton_tol=w["newton_tol"])
+        o2.propagate(p, FINE_OF[w["variant"]], w["T"] / w["N"] / w["J"], ORACLE_2D_STEPS, u0)
+    else:
+        from oracle import oracle1d as o
+        p = o.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], fine=FINE_OF[w["variant"]],
+                     coarse=COARSE_OF[w["variant"]], newton_tol=w["newton_tol"], max_iters=1)
+        o.parareal(p, u0)
     return time.perf_counter() - t
 
 
@@ -139,7 +162,11 @@ def cpu_oracle(w, problems, u0s, steps=1):
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
-    pts = w["N"] * w["J"] * w["n"]
+    if w.get("dim", 1) == 2:
+        pts = ORACLE_2D_STEPS * w["n"] ** 2
+        u0s = [u0s[b % len(u0s)] for b in range(problems)]
+    else:
+        pts = w["N"] * w["J"] * w["n"]
     times = []
     with ctx.Pool(problems) as pool:
         for _ in range(steps):
@@ -171,7 +198,9 @@ def bench_ours(args, w, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     u0 = u0_batch(w, rank)
     B, n, N, J = w["batch"], w["n"], w["N"], w["J"]
-    cfg = ch.Config(n=n, eps=w["eps"], T=w["T"], n_slices=N, fine_steps=J, variant=w["variant"],
+    dim = w.get("dim", 1)
+    pts = n ** dim
+    cfg = ch.Config(dim=dim, n=n, eps=w["eps"], T=w["T"], n_slices=N, fine_steps=J, variant=w["variant"],
                     newton_tol=w["newton_tol"], max_iters=1, precision=w["precision"])
     u0_dev = torch.as_tensor(u0, dtype=torch.float64, device=dev).contiguous()
     pr = ch.Parareal(cfg, batch=B, stream=stream)
@@ -184,9 +213,9 @@ def bench_ours(args, w, rank, world, local_rank):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
-    fine_pts_per_step = B * N * J * n
+    fine_pts_per_step = B * N * J * pts
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    fine_ms, newton_total, launches = 0.0, 0, 0
+    fine_ms, newton_total, launches, cg_per_step = 0.0, 0, 0, 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -199,7 +228,12 @@ def bench_ours(args, w, rank, world, local_rank):
             st = [pr.stats(b) for b in (0,)]
             fine_ms += st[0]["fine_sweep_ms"]
             launches += st[0]["kernel_launches"]
-            newton_total += sum(pr.stats(b)["newton_total"] for b in range(B)) if i == 0 else 0
+            if i == 0:
+                if dim == 1:
+                    newton_total = sum(pr.stats(b)["newton_total"] for b in range(B))
+                else:
+                    newton_total = st[0]["newton_total"]
+                    cg_per_step = st[0]["inner_iterations"]
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -211,22 +245,39 @@ def bench_ours(args, w, rank, world, local_rank):
         total_ms = float(t.item())
     value = world * args.steps * fine_pts_per_step / (total_ms / 1e3)
 
-    # roofline of the dominant kernel (the fine sweep), timed live inside the graph
+    # roofline of the dominant kernel (the fine sweep), timed live between the iteration graphs
     fine_ms_per_launch = fine_ms / args.steps
     newton_per_step = newton_total  # Newton iterations (summed over problems) in one step
-    alg_flops = fine_pts_per_step * FP64_FLOPS_RHS + newton_per_step * n * FP64_FLOPS_NEWTON
-    achieved = alg_flops / (fine_ms_per_launch / 1e3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_fine_sweep (FP64 pipe)", "achieved": round(achieved, 2),
-                "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
-                "traffic": None, "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
-                "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
-                "newton_iters_per_step_point": round(newton_per_step / (B * N * J), 3),
-                "algorithmic_fp64_flops_per_launch": alg_flops}
+    if dim == 1:
+        alg_flops = fine_pts_per_step * FP64_FLOPS_RHS + newton_per_step * n * FP64_FLOPS_NEWTON
+        achieved = alg_flops / (fine_ms_per_launch / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_fine_sweep (FP64 pipe)", "achieved": round(achieved, 2),
+                    "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                    "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
+                    "traffic": None, "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
+                    "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
+                    "newton_iters_per_step_point": round(newton_per_step / (B * N * J), 3),
+                    "algorithmic_fp64_flops_per_launch": alg_flops}
+    else:
+        # 2D: Newton and CG counts are batched over the units of the sweep (one count per batch)
+        units = B * N
+        alg_bytes = units * pts * (newton_per_step * BYTES_NEWTON_2D + cg_per_step * BYTES_CG_2D)
+        achieved = alg_bytes / (fine_ms_per_launch / 1e3) / 1e9
+        peak = measured_peaks().get("hbm_gbs", 6800.0)
+        roofline = {"bound": "hbm", "kernel": "2D fine sweep (sine-transform passes + pointwise sweeps)",
+                    "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)", "traffic": None,
+                    "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
+                    "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
+                    "newton_iterations_per_step": round(newton_per_step / J, 3),
+                    "cg_iterations_per_newton": round(cg_per_step / max(newton_per_step, 1), 3),
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "note": "working set per field 8.3 MB: L2-resident, so HBM bandwidth is a bound, not the limit"}
 
     # end to end through the public API: pinned host inputs in, every slice of the result out
     u0_pin = torch.from_numpy(u0).pin_memory()
-    out_pin = torch.empty((B, N + 1, n), dtype=torch.float64).pin_memory()
+    out_pin = torch.empty((B, N + 1, pts), dtype=torch.float64).pin_memory()
     e2e_ms = []
     for i in range(max(1, args.steps // 2)):
         flush.fill_(float(i))
@@ -254,13 +305,22 @@ def bench_ours(args, w, rank, world, local_rank):
                 clocks=clk.summary(), launches=launches, ttol=ttol)
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
     """Plain-G Parareal until every problem is within err_tol (max_n L2_h) of the sequential fine
     solution; reports the device time of the Parareal run and of the serial fine solve."""
     import torch
     B, N = w["batch"], w["N"]
-    cfg = ch.Config(n=w["n"], eps=w["eps"], T=w["T"], n_slices=N, fine_steps=w["J"], variant=w["variant"],
-                    newton_tol=w["newton_tol"], max_iters=N, precision=w["precision"], err_tol=err_tol)
+    cfg = ch.Config(dim=w.get("dim", 1), n=w["n"], eps=w["eps"], T=w["T"], n_slices=N, fine_steps=w["J"],
+                    variant=w["variant"], newton_tol=w["newton_tol"], max_iters=N, precision=w["precision"],
+                    err_tol=err_tol)
     pr = ch.Parareal(cfg, batch=B, stream=stream)
     pr.set_initial_batch(u0)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -321,8 +381,10 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": value, "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
-                                 "sample": f"{problems} of {w['batch']} problems per step, one process each "
-                                           "(coarse sweep + full fine sweep + correction)"},
+                                 "sample": (f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice per step"
+                                            if w.get("dim", 1) == 2 else
+                                            f"{problems} of {w['batch']} problems per step, one process each "
+                                            "(coarse sweep + full fine sweep + correction)")},
                 "e2e": {"value": value, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -333,8 +395,9 @@ def main():
         u0 = u0_batch(w, 0)
         problems = cpu_sample_size()
         pts, times = cpu_oracle(w, problems, u0, steps=1)
-        cpu = {"value": pts / times[0], "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
-               "sample": f"{problems} of {w['batch']} problems, one step each, one process per problem"}
+        what = (f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice (sparse LU)"
+                if w.get("dim", 1) == 2 else f"{problems} of {w['batch']} problems, one step each, one process per problem")
+        cpu = {"value": pts / times[0], "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle", "sample": what}
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -104,6 +104,11 @@ __device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const fl
   return neg ? make_float2(-a, -b) : make_float2(a, b);
 }
 
+// Shared-memory index with one padding element every 8 complex values: the radix-8 stores of
+// the early stages write with strides of 8 and 64 elements, which would otherwise hit the same
+// banks (16-way conflicts at stride 8).
+__device__ __forceinline__ int pad8(int x) { return x + (x >> 3); }
+
 // One Stockham stage of radix R on the F complex FFTs of length L held in buf (in place: all
 // items are loaded to registers, then the block synchronises, then results are stored).
 // Stage 0 reads the odd extension of the input rows straight from global memory.
@@ -126,7 +131,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns
         for (int r = 0; r < R; ++r) v[q][r] = odd_ext<N>(r0, r1, j + r * LR);
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = buf[f * L + j + r * LR];
+        for (int r = 0; r < R; ++r) v[q][r] = buf[pad8(f * L + j + r * LR)];
       }
     }
   }
@@ -143,7 +148,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns
       dft_small<R>(v[q]);
       const int o = f * L + (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[o + r * Ns] = v[q][r];
+      for (int r = 0; r < R; ++r) buf[pad8(o + r * Ns)] = v[q][r];
     }
   }
   __syncthreads();
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__
   constexpr int n = N - 1, L = 2 * N, F = kDstRows / 2;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
-  float2* twd = smem2 + F * L;
+  float2* twd = smem2 + F * L + F * L / 8;
   const int u = blockIdx.y;
   const int a0 = blockIdx.x * kDstRows;
   const float* src = in + (size_t)u * n * n;
@@ -188,14 +193,15 @@ __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__
     const int k = idx / kDstRows, r = idx - k * kDstRows;
     const int a = a0 + r;
     if (a >= n) continue;
-    const float2 v = buf[(r >> 1) * L + k + 1];
+    const float2 v = buf[pad8((r >> 1) * L + k + 1)];
     dst[(size_t)k * n + a] = (r & 1) ? v.x * sc : -v.y * sc;
   }
 }
 
 template <int N>
 size_t dst_smem() {
-  return (size_t)((kDstRows / 2) * 2 * N + 2 * N) * sizeof(float2);
+  constexpr int FL = (kDstRows / 2) * 2 * N;
+  return (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2);
 }
 
 // ------------------------------------------------------------------ FP64 stencils
@@ -349,6 +355,9 @@ __device__ __forceinline__ double sum_partials(const double* part, int u) {
 // m(p,q) = 1/mu + e2dt mu + cdt wbar (diagonal of the preconditioner M in sine space)
 __device__ __forceinline__ float mdiag(float mu, float e2dt, float cwb) { return 1.f / mu + e2dt * mu + cwb; }
 
+// Sine-space pointwise kernels: block b of unit u walks rows i = b, b + kBlk, ..., threads walk
+// columns; per-thread partial sums are FP32 (tens of terms), the block reduction is FP64.
+
 // CG start: bh = Hh / mu; x = 0; r = bh; p = r / m; rho partial = (r, r/m).
 __global__ void k2_cg_init(const float* __restrict__ Hh, float* __restrict__ xh, float* __restrict__ rh,
                            float* __restrict__ ph, const float* __restrict__ mu1, int n, float e2dt, float cdt,
@@ -358,18 +367,21 @@ __global__ void k2_cg_init(const float* __restrict__ Hh, float* __restrict__ xh,
   if (skip && skip[2 * u]) return;
   const size_t pts = (size_t)n * n;
   const float cwb = cdt * float(scal[u * 8 + 4]);
-  double acc = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    const float mu = mu1[i] + mu1[j];
-    const float r = Hh[u * pts + k] / mu;
-    const float z = r / mdiag(mu, e2dt, cwb);
-    xh[u * pts + k] = 0.f;
-    rh[u * pts + k] = r;
-    ph[u * pts + k] = z;
-    acc += (double)r * (double)z;
+  float acc = 0.f;
+  for (int i = blockIdx.x; i < n; i += kBlk) {
+    const float mi = mu1[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const size_t k = u * pts + (size_t)i * n + j;
+      const float mu = mi + mu1[j];
+      const float r = Hh[k] / mu;
+      const float z = r * __frcp_rn(mdiag(mu, e2dt, cwb));
+      xh[k] = 0.f;
+      rh[k] = r;
+      ph[k] = z;
+      acc += r * z;
+    }
   }
-  const double s = block_reduce<0>(acc, sh);
+  const double s = block_reduce<0>((double)acc, sh);
   if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = s;
 }
 
@@ -403,16 +415,18 @@ __global__ void k2_cg_q(const float* __restrict__ ph, float* __restrict__ qh, co
   if (flag[2 * u] || flag[2 * u + 1]) return;
   const size_t pts = (size_t)n * n;
   const float cwb = cdt * float(scal[u * 8 + 4]);
-  double acc = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    const float mu = mu1[i] + mu1[j];
-    const float p = ph[u * pts + k];
-    const float q = mdiag(mu, e2dt, cwb) * p + qh[u * pts + k];
-    qh[u * pts + k] = q;
-    acc += (double)p * (double)q;
+  float acc = 0.f;
+  for (int i = blockIdx.x; i < n; i += kBlk) {
+    const float mi = mu1[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const size_t k = u * pts + (size_t)i * n + j;
+      const float p = ph[k];
+      const float q = mdiag(mi + mu1[j], e2dt, cwb) * p + qh[k];
+      qh[k] = q;
+      acc += p * q;
+    }
   }
-  const double s = block_reduce<0>(acc, sh);
+  const double s = block_reduce<0>((double)acc, sh);
   if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = s;
 }
 
@@ -428,16 +442,18 @@ __global__ void k2_cg_step(float* __restrict__ xh, float* __restrict__ rh, const
   const double sig = sum_partials(part_sig, u);
   const float alpha = (sig > 0.0) ? float(scal[u * 8 + 0] / sig) : 0.f;
   const float cwb = cdt * float(scal[u * 8 + 4]);
-  double acc = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    const float mu = mu1[i] + mu1[j];
-    xh[u * pts + k] += alpha * ph[u * pts + k];
-    const float r = rh[u * pts + k] - alpha * qh[u * pts + k];
-    rh[u * pts + k] = r;
-    acc += (double)r * (double)(r / mdiag(mu, e2dt, cwb));
+  float acc = 0.f;
+  for (int i = blockIdx.x; i < n; i += kBlk) {
+    const float mi = mu1[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const size_t k = u * pts + (size_t)i * n + j;
+      xh[k] += alpha * ph[k];
+      const float r = rh[k] - alpha * qh[k];
+      rh[k] = r;
+      acc += r * r * __frcp_rn(mdiag(mi + mu1[j], e2dt, cwb));
+    }
   }
-  const double s = block_reduce<0>(acc, sh);
+  const double s = block_reduce<0>((double)acc, sh);
   if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = s;
 }
 
@@ -452,10 +468,12 @@ __global__ void k2_cg_dir(float* __restrict__ ph, const float* __restrict__ rh, 
   const double rho = scal[u * 8 + 0];
   const float beta = (rho > 0.0) ? float(rho_new / rho) : 0.f;
   const float cwb = cdt * float(scal[u * 8 + 4]);
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    const float mu = mu1[i] + mu1[j];
-    ph[u * pts + k] = rh[u * pts + k] / mdiag(mu, e2dt, cwb) + beta * ph[u * pts + k];
+  for (int i = blockIdx.x; i < n; i += kBlk) {
+    const float mi = mu1[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const size_t k = u * pts + (size_t)i * n + j;
+      ph[k] = rh[k] * __frcp_rn(mdiag(mi + mu1[j], e2dt, cwb)) + beta * ph[k];
+    }
   }
 }
 
