@@ -58,6 +58,9 @@ FP64_FLOPS_RHS = 5
 FP64_FLOPS_NEWTON = 15
 # GB300 FP64: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# DRAM bytes (read + write) of one 1D fine-sweep launch at c2's batch and slices, from the ncu
+# capture summarised in profiles/k_fine_sweep_c2.md (independent of the fine steps per slice).
+FINE_SWEEP_1D_TRAFFIC = 223.7e6
 
 
 # 2D fine sweep, algorithmic HBM bytes per grid point: a sine-transform pass reads and writes an
@@ -255,14 +258,16 @@ def bench_ours(args, w, rank, world, local_rank):
                     "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
                     "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
                     "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
-                    "traffic": None, "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
+                    "traffic": FINE_SWEEP_1D_TRAFFIC if (n, B, N) == (1024, 256, 64) else None,
+                    "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
                     "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
                     "newton_iters_per_step_point": round(newton_per_step / (B * N * J), 3),
                     "algorithmic_fp64_flops_per_launch": alg_flops}
     else:
-        # 2D: Newton and CG counts are batched over the units of the sweep (one count per batch)
+        # 2D: newton_total sums Newton iterations over units; CG iterations are counted per batched
+        # iteration of all B N units
         units = B * N
-        alg_bytes = units * pts * (newton_per_step * BYTES_NEWTON_2D + cg_per_step * BYTES_CG_2D)
+        alg_bytes = pts * (newton_per_step * BYTES_NEWTON_2D + units * cg_per_step * BYTES_CG_2D)
         achieved = alg_bytes / (fine_ms_per_launch / 1e3) / 1e9
         peak = measured_peaks().get("hbm_gbs", 6800.0)
         roofline = {"bound": "hbm", "kernel": "2D fine sweep (sine-transform passes + pointwise sweeps)",
@@ -270,8 +275,8 @@ def bench_ours(args, w, rank, world, local_rank):
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)", "traffic": None,
                     "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
                     "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
-                    "newton_iterations_per_step": round(newton_per_step / J, 3),
-                    "cg_iterations_per_newton": round(cg_per_step / max(newton_per_step, 1), 3),
+                    "newton_iterations_per_unit_step": round(newton_per_step / (units * J), 3),
+                    "batched_cg_iterations_per_step": round(cg_per_step / J, 3),
                     "algorithmic_bytes_per_launch": alg_bytes,
                     "note": "working set per field 8.3 MB: L2-resident, so HBM bandwidth is a bound, not the limit"}
 

@@ -99,7 +99,8 @@ typedef struct {
   double err_max[CH_MAX_ITERS];   /* same error, max-abs                                      */
   double t_iter_ms[CH_MAX_ITERS]; /* t_iter_ms[k] = device time from the start of run to the
                                      end of iteration k (k = 0: the coarse initial sweep)     */
-  long long newton_total;         /* Newton iterations summed over all fine steps of run      */
+  long long newton_total;         /* Newton iterations of the fine sweeps of run, summed over
+                                     fine steps (2D: and over the batch's units)               */
   int newton_max;                 /* most Newton iterations taken by one fine step            */
   long long fine_point_steps;     /* fine steps x interior points executed by run             */
   /* Whole-handle figures of the last run (same for every problem): device time of the
@@ -110,7 +111,8 @@ typedef struct {
   double coarse_sweep_ms;
   int fine_sweep_launches;
   int kernel_launches;
-  long long inner_iterations;     /* 2D: CG iterations summed over all linear solves of run  */
+  long long inner_iterations;     /* 2D: CG iterations of the fine sweeps (one count per batched
+                                     iteration of all units)                                  */
 } ch_stats;
 
 typedef struct ch_parareal ch_parareal;

@@ -59,6 +59,8 @@ struct ch_parareal {
   long long* doff = nullptr;    // [B N] element offsets for gather / scatter
   std::vector<std::vector<double>> h_inc, h_el2, h_emx;
   std::vector<int> h_iters, h_conv;
+  unsigned long long fine_newton = 0;  // Newton iterations (summed over units) of the fine sweeps
+  long long fine_cg = 0;               // CG iterations (batched) of the fine sweeps
 };
 
 namespace {
@@ -188,6 +190,8 @@ ch_status reference2d(ch_parareal* h) {
 ch_status run2d(ch_parareal* h) {
   const int B = h->B, N = h->p.N, maxit = h->p.maxit;
   CH_CUDA(h, h->p2->reset_counters(h->st));
+  h->fine_newton = 0;
+  h->fine_cg = 0;
   const size_t pts = h->pts, us = (size_t)(N + 1) * pts, fs = (size_t)N * pts;
   const double h2 = h->p.h * h->p.h;
   const double* ref = h->ref_valid ? h->Uref : nullptr;
@@ -245,11 +249,17 @@ ch_status run2d(ch_parareal* h) {
         uoff.push_back((long long)(b * us + sl * pts));
         foff.push_back((long long)(b * fs + sl * pts));
       }
+    h->p2->read_status(h->st);
+    const unsigned long long n0 = h->p2->newton_iterations();
+    const long long c0 = h->p2->cg_iterations();
     CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
     if ((s = gather_units(h, h->U, uoff, true)) != CH_OK) return s;
     if ((s = prop2(h, (int)uoff.size(), fine2(h), h->p.dt, h->p.J)) != CH_OK) return s;
     if ((s = gather_units(h, h->F, foff, false)) != CH_OK) return s;
     CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
+    h->p2->read_status(h->st);
+    h->fine_newton += h->p2->newton_iterations() - n0;
+    h->fine_cg += h->p2->cg_iterations() - c0;
     // sequential coarse sweep with the correction of Eq. 2.2 and the norms
     CH_CUDA(h, cudaMemcpyAsync(h->dlist, L.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
     CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 3 * B * sizeof(double), h->st));
@@ -624,7 +634,7 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
       CH_CUDA(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[k + 1]));
       out->t_iter_ms[k] = ms;
     }
-    out->newton_total = (long long)h->p2->newton_iterations();
+    out->newton_total = (long long)h->fine_newton;
     out->newton_max = h->p2->newton_peak();
     long long fps = 0;
     for (int k = 0; k < out->iterations; ++k) fps += (long long)(h->p.N - k) * h->p.J * (long long)h->pts;
@@ -633,7 +643,7 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
     out->coarse_sweep_ms = h->coarse_ms;
     out->fine_sweep_launches = h->iters_done;
     out->kernel_launches = 0;
-    out->inner_iterations = h->p2->cg_iterations();
+    out->inner_iterations = h->fine_cg;
     return CH_OK;
   }
   const int maxit = h->p.maxit;
