@@ -13,6 +13,13 @@ scalar loss through all layers), ``mse_crop_loss`` (mean squared error over a ce
 ``adam_step`` (Kingma and Ba, 2015, with bias correction). Pinned in tests/test_oracle_gtheta.py
 by central finite differences of the loss in every layer, by the convolution of a delta image,
 and by the shift structure of zero padding.
+
+Storage precision. The network is specified with BF16 weights and activations and FP32
+accumulation. ``forward(..., bf16=True)`` / ``backward(..., bf16=True)`` evaluate that storage
+model in FP64 arithmetic: the hidden activations a1..a5, the weights of the four 32 -> 32 layers
+and the hidden-layer gradients are rounded to BF16 (round to nearest, ties to even) where they
+are stored; the input, the first and last layers' weights, R and dLoss/dR stay unrounded.
+``bf16_round`` is pinned against torch's own float32 -> bfloat16 conversion.
 """
 from __future__ import annotations
 
@@ -63,23 +70,45 @@ def conv3_backward(x: np.ndarray, w: np.ndarray, gy: np.ndarray):
     return gxp[1:-1, 1:-1], gw, gy.sum(axis=(0, 1))
 
 
-def forward(u: np.ndarray, W, b):
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Nearest BF16 value (ties to even) of each entry, returned as float64. BF16 keeps the top
+    16 bits of the IEEE float32 pattern; the input is first rounded to float32."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    bits = f.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    rounded = ((bits + 0x7FFF + lsb) >> 16) << 16
+    return rounded.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)
+
+
+def _stored_weights(W, bf16: bool):
+    return [bf16_round(w) if (bf16 and 0 < l < 5) else w for l, w in enumerate(W)]
+
+
+def forward(u: np.ndarray, W, b, bf16: bool = False):
     """Returns (G(U), [a0, a1, ..., a6]) with a0 = U[..., None] and a6 = R(U)."""
+    Ws = _stored_weights(W, bf16)
     a = [u[..., None].astype(np.float64)]
     for l in range(6):
-        z = conv3(a[-1], W[l], b[l])
-        a.append(np.maximum(z, 0.0) if l < 5 else z)
+        z = conv3(a[-1], Ws[l], b[l])
+        if l < 5:
+            z = np.maximum(z, 0.0)
+            if bf16:
+                z = bf16_round(z)
+        a.append(z)
     return u + a[-1][..., 0], a
 
 
-def backward(acts, W, grad_r: np.ndarray):
+def backward(acts, W, grad_r: np.ndarray, bf16: bool = False):
     """Gradients of a loss with dLoss/dR = grad_r ([H][W]) through the six layers."""
+    Ws = _stored_weights(W, bf16)
     gW, gb = [None] * 6, [None] * 6
     g = grad_r[..., None]
     for l in range(5, -1, -1):
-        gx, gW[l], gb[l] = conv3_backward(acts[l], W[l], g)
+        gx, gW[l], gb[l] = conv3_backward(acts[l], Ws[l], g)
         if l > 0:
             g = gx * (acts[l] > 0)  # ReLU of layer l (activation a_l = relu(z_l))
+            if bf16:
+                g = bf16_round(g)
     return gW, gb
 
 

@@ -91,3 +91,45 @@ def test_adam_step_matches_definition_on_a_scalar():
     g.adam_step(p, np.array([0.5]), m, v, t=1, lr=0.1)
     # first step: mh = g, vh = g^2 -> p -= lr * g / (|g| + eps)
     assert abs(p[0] - (1.0 - 0.1 * 0.5 / (0.5 + 1e-8))) < 1e-15
+
+
+def test_bf16_round_matches_torch_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-8, 8, 4000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.0078125, 3.0e38, -1.5e-40]])
+    # values exactly halfway between two BF16 neighbours: ties go to the even pattern
+    half = (np.arange(1, 200, dtype=np.uint32) << 16 | 0x8000).view(np.float32).astype(np.float64)
+    x = np.concatenate([x, half, -half])
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(g.bf16_round(x), want)
+
+
+def test_bf16_storage_model_is_close_to_fp64():
+    W, b = small_net(5)
+    rng = np.random.default_rng(2)
+    u = 0.5 * rng.standard_normal((12, 12))
+    gu, acts = g.forward(u, W, b)
+    gq, aq = g.forward(u, W, b, bf16=True)
+    r, rq = acts[-1][..., 0], aq[-1][..., 0]
+    assert np.abs(rq - r).max() <= 3e-2 * np.abs(r).max()
+    assert np.abs(rq - r).max() > 0.0
+    # every stored hidden activation is a BF16 value
+    for a in aq[1:6]:
+        assert np.array_equal(g.bf16_round(a), a)
+
+
+def test_bf16_backward_matches_fp64_backward_to_bf16_accuracy():
+    W, b = small_net(9)
+    rng = np.random.default_rng(4)
+    u = 0.6 * rng.standard_normal((10, 10))
+    t = 0.05 * rng.standard_normal((10, 10))
+    _, a = g.forward(u, W, b)
+    _, dr = g.mse_crop_loss(a[-1][..., 0], t, 2)
+    gW, gb = g.backward(a, W, dr)
+    _, aq = g.forward(u, W, b, bf16=True)
+    _, drq = g.mse_crop_loss(aq[-1][..., 0], t, 2)
+    gWq, gbq = g.backward(aq, W, drq, bf16=True)
+    for l in range(6):
+        rel = np.linalg.norm(gWq[l] - gW[l]) / np.linalg.norm(gW[l])
+        assert rel < 5e-2, (l, rel)
