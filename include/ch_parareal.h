@@ -113,6 +113,10 @@ typedef struct {
   int kernel_launches;
   long long inner_iterations;     /* 2D: CG iterations of the fine sweeps (one count per batched
                                      iteration of all units)                                  */
+  int coarse_model;               /* 1: this problem's coarse sweeps started with the learned
+                                     propagator G_theta (ch_parareal_set_coarse_model)          */
+  int coarse_fallback_iter;       /* iteration after which G_theta was replaced by the plain
+                                     coarse step, -1 if it never was                          */
 } ch_stats;
 
 typedef struct ch_parareal ch_parareal;
@@ -185,6 +189,64 @@ ch_status ch_sine_transform_2d(const float* in_dev, float* out_dev, int batch, i
 ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, int nsteps,
                        const double* u_in_dev, double* u_out_dev, int* newton_dev,
                        void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned coarse propagator G_theta(U) = U + R(U). The paper has none: it replaces the plain
+ * coarse step G of Eq. 2.2 (one LIN1 step of Delta T), and Parareal still reaches the fine
+ * solution (slice n is exact after n iterations for any G), so G_theta changes iteration
+ * counts and wall time only.
+ *
+ * R: six 3x3 convolutions with zero padding (u = 0 outside the interior grid), channels
+ * 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU after the first five; hidden activations BF16, the
+ * four 32 -> 32 layers on the tensor cores (BF16 x BF16 -> FP32), first and last layers FP32.
+ * Parameters: CH_GTHETA_PARAMS FP32 values, for layer l = 0..5 the weights W_l[3][3][Cout][Cin]
+ * (tap (dy, dx) applies to u[y + dy - 1][x + dx - 1]) followed by the biases b_l[Cout].
+ * A ch_gtheta handle owns an FP32 master copy with Adam moments and its device work space; it
+ * is bound to one stream and is not thread-safe. Errors as for ch_parareal.
+ */
+#define CH_GTHETA_PARAMS 37601
+
+typedef struct ch_gtheta ch_gtheta;
+
+/* New network with He-normal weights from `seed` (last layer scaled by 0.1), zero biases. */
+ch_status ch_gtheta_create(unsigned long long seed, void* cuda_stream, ch_gtheta** out);
+void ch_gtheta_destroy(ch_gtheta* g);
+const char* ch_gtheta_last_error(const ch_gtheta* g);
+
+/* Parameters from / to host memory, len = CH_GTHETA_PARAMS. set_params resets Adam. */
+ch_status ch_gtheta_set_params(ch_gtheta* g, const float* params_host, size_t len);
+ch_status ch_gtheta_get_params(ch_gtheta* g, float* params_host, size_t len);
+
+/* out = U + R(U) for `batch` FP64 n x n fields (device, [batch][n][n]; out may alias in);
+ * n >= 1. Enqueued on the handle's stream. */
+ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, double* out_dev, int batch, int n);
+
+/* Loss and gradients for one minibatch: in_dev, target_dev FP32 [batch][S][S] (device); loss =
+ * mean over the batch and the window [margin, S - margin)^2 of (R(in) - target)^2.
+ * grad_host: CH_GTHETA_PARAMS FP32 values in the parameter layout (len must match);
+ * loss_host: NULL or one float. Synchronises. */
+ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* target_dev, int batch, int S,
+                              int margin, float* grad_host, size_t len, float* loss_host);
+
+/* Trains R on pairs of snapshots of the fine solver: states_dev FP64 [ntraj][nsnap][n][n]
+ * (device; e.g. the reference slices of a ch_parareal handle), pair (s, s + stride) for
+ * s < nsnap - stride. Each of `steps` Adam steps (learning rate lr, betas 0.9 / 0.999,
+ * eps 1e-8) draws `batch` crops (trajectory, snapshot, position from SplitMix64(seed)) of
+ * min(76, n + 12) pixels and fits R(crop of U_s) to the crop of U_{s+stride} - U_s on the
+ * crop's interior (6 pixels in from each side). losses_host: NULL or `steps` floats receiving
+ * the minibatch losses. Synchronises. */
+ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, int ntraj, int nsnap, int n, int stride,
+                          int steps, int batch, double lr, unsigned long long seed, float* losses_host);
+
+/* Uses G_theta with these parameters (CH_GTHETA_PARAMS values, host) as the coarse propagator
+ * of the next runs of a 2D handle; params_host = NULL (len 0) restores the plain coarse step.
+ * The plain step stays as judge: when a problem's Parareal increment grows from one iteration
+ * to the next, its remaining iterations use the plain step (G(U_n^k) recomputed with it).
+ * CH_ERR_INVALID for dim = 1. */
+ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len);
+
+/* Reference slices of all problems to device memory: batch (N+1) n^d values. */
+ch_status ch_parareal_get_reference_device(ch_parareal* h, double* out_dev, size_t len);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free solve. The paper has no counterpart: this is a library-level service.

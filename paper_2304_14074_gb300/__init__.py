@@ -5,10 +5,11 @@ propagator over all time slices at once, the coarse sweep and the correction of 
 implemented as hand-written CUDA behind the C ABI of ``include/ch_parareal.h``. This
 package is the thin Python binding of that ABI.
 """
-from ._lib import (CH_MAX_ITERS, EXPORTED_SYMBOLS, SCHEMES, STATUS, VARIANTS, ChError, Config, Parareal,
-                   load, propagate, sine_transform_2d)
+from ._lib import (CH_GTHETA_PARAMS, CH_MAX_ITERS, EXPORTED_SYMBOLS, SCHEMES, STATUS, VARIANTS, ChError, Config,
+                   GTheta, Parareal, gtheta_flatten, gtheta_unflatten, load, propagate, sine_transform_2d)
 from .build import LIB as LIBRARY_PATH
 from .build import build
 
-__all__ = ["CH_MAX_ITERS", "EXPORTED_SYMBOLS", "SCHEMES", "STATUS", "VARIANTS", "ChError", "Config", "Parareal",
-           "load", "propagate", "sine_transform_2d", "build", "LIBRARY_PATH"]
+__all__ = ["CH_GTHETA_PARAMS", "CH_MAX_ITERS", "EXPORTED_SYMBOLS", "SCHEMES", "STATUS", "VARIANTS", "ChError",
+           "Config", "GTheta", "Parareal", "gtheta_flatten", "gtheta_unflatten", "load", "propagate",
+           "sine_transform_2d", "build", "LIBRARY_PATH"]

@@ -28,8 +28,17 @@ EXPORTED_SYMBOLS = [
     "ch_parareal_compute_reference", "ch_parareal_run", "ch_parareal_get_slices",
     "ch_parareal_get_slices_device", "ch_parareal_get_reference", "ch_parareal_get_stats",
     "ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_propagate",
-    "ch_parareal_solve_noalloc", "ch_sine_transform_2d",
+    "ch_parareal_solve_noalloc", "ch_sine_transform_2d", "ch_parareal_set_coarse_model",
+    "ch_parareal_get_reference_device", "ch_gtheta_create", "ch_gtheta_destroy", "ch_gtheta_last_error",
+    "ch_gtheta_set_params", "ch_gtheta_get_params", "ch_gtheta_forward", "ch_gtheta_gradients",
+    "ch_gtheta_train",
 ]
+_NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
+              "ch_gtheta_last_error")
+
+CH_GTHETA_PARAMS = 37601
+# Flat parameter layout of G_theta: layer l has W_l [3][3][Cout][Cin] then b_l [Cout].
+GTHETA_CHANNELS = [1, 32, 32, 32, 32, 32, 1]
 
 
 class ChError(RuntimeError):
@@ -53,7 +62,7 @@ class _Stats(C.Structure):
                 ("t_iter_ms", C.c_double * CH_MAX_ITERS), ("newton_total", C.c_longlong),
                 ("newton_max", C.c_int), ("fine_point_steps", C.c_longlong), ("fine_sweep_ms", C.c_double),
                 ("coarse_sweep_ms", C.c_double), ("fine_sweep_launches", C.c_int), ("kernel_launches", C.c_int),
-                ("inner_iterations", C.c_longlong)]
+                ("inner_iterations", C.c_longlong), ("coarse_model", C.c_int), ("coarse_fallback_iter", C.c_int)]
 
 
 @dataclass
@@ -117,8 +126,22 @@ def load(build_if_missing: bool = True):
     lib.ch_propagate.argtypes = [C.POINTER(_Config), C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp]
     lib.ch_sine_transform_2d.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
+    f = C.POINTER(C.c_float)
+    lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz]
+    lib.ch_parareal_get_reference_device.argtypes = [vp, vp, sz]
+    lib.ch_gtheta_create.argtypes = [C.c_ulonglong, vp, C.POINTER(vp)]
+    lib.ch_gtheta_destroy.argtypes = [vp]
+    lib.ch_gtheta_destroy.restype = None
+    lib.ch_gtheta_last_error.argtypes = [vp]
+    lib.ch_gtheta_last_error.restype = C.c_char_p
+    lib.ch_gtheta_set_params.argtypes = [vp, f, sz]
+    lib.ch_gtheta_get_params.argtypes = [vp, f, sz]
+    lib.ch_gtheta_forward.argtypes = [vp, vp, vp, C.c_int, C.c_int]
+    lib.ch_gtheta_gradients.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, f, sz, f]
+    lib.ch_gtheta_train.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                    C.c_ulonglong, f]
     for name in EXPORTED_SYMBOLS:
-        if name not in ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string"):
+        if name not in _NO_STATUS:
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -228,7 +251,21 @@ class Parareal:
                 "newton_total": st.newton_total, "newton_max": st.newton_max,
                 "fine_point_steps": st.fine_point_steps, "fine_sweep_ms": st.fine_sweep_ms,
                 "coarse_sweep_ms": st.coarse_sweep_ms, "fine_sweep_launches": st.fine_sweep_launches,
-                "kernel_launches": st.kernel_launches, "inner_iterations": st.inner_iterations}
+                "kernel_launches": st.kernel_launches, "inner_iterations": st.inner_iterations,
+                "coarse_model": st.coarse_model, "coarse_fallback_iter": st.coarse_fallback_iter}
+
+    def set_coarse_model(self, params) -> None:
+        """Learned coarse propagator G_theta with these FP32 parameters (None: plain coarse step)."""
+        if params is None:
+            self._check(self.lib.ch_parareal_set_coarse_model(self._h, None, 0), "ch_parareal_set_coarse_model")
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.lib.ch_parareal_set_coarse_model(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+                    "ch_parareal_set_coarse_model")
+
+    def get_reference_device(self, out_dev) -> None:
+        self._check(self.lib.ch_parareal_get_reference_device(self._h, _dptr(out_dev), out_dev.numel()),
+                    "ch_parareal_get_reference_device")
 
     def close(self) -> None:
         if self._h:
@@ -273,3 +310,89 @@ def sine_transform_2d(x, out=None, stream=None):
     if s != 0:
         raise ChError(s, "ch_sine_transform_2d")
     return out
+
+
+class GTheta:
+    """Learned coarse propagator G_theta(U) = U + R(U) (ch_gtheta_*)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        self.lib = load()
+        self._h = C.c_void_p()
+        s = self.lib.ch_gtheta_create(seed, _stream_ptr(stream), C.byref(self._h))
+        if s != 0:
+            raise ChError(s, "ch_gtheta_create")
+
+    def _check(self, s, what):
+        if s != 0:
+            detail = self.lib.ch_gtheta_last_error(self._h).decode() if self._h else ""
+            raise ChError(s, what, detail)
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.lib.ch_gtheta_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+                    "ch_gtheta_set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(CH_GTHETA_PARAMS, dtype=np.float32)
+        self._check(self.lib.ch_gtheta_get_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+                    "ch_gtheta_get_params")
+        return p
+
+    def forward(self, u_dev, out=None):
+        """G_theta(U) of a CUDA float64 tensor [batch, n, n]."""
+        import torch
+        if out is None:
+            out = torch.empty_like(u_dev)
+        self._check(self.lib.ch_gtheta_forward(self._h, _dptr(u_dev), _dptr(out), u_dev.shape[0], u_dev.shape[-1]),
+                    "ch_gtheta_forward")
+        return out
+
+    def gradients(self, x_dev, target_dev, margin: int):
+        """(loss, flat FP32 gradient) of one minibatch: CUDA float32 tensors [batch, S, S]."""
+        g = np.empty(CH_GTHETA_PARAMS, dtype=np.float32)
+        loss = C.c_float()
+        self._check(self.lib.ch_gtheta_gradients(self._h, _dptr(x_dev), _dptr(target_dev), x_dev.shape[0],
+                                                 x_dev.shape[-1], margin, g.ctypes.data_as(C.POINTER(C.c_float)),
+                                                 g.size, C.byref(loss)), "ch_gtheta_gradients")
+        return float(loss.value), g
+
+    def train(self, states_dev, stride: int, steps: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
+        """Adam on crops of snapshot pairs; states_dev: CUDA float64 [ntraj, nsnap, n, n] (or
+        [ntraj, nsnap, n*n] with square n). Returns the per-step minibatch losses."""
+        ntraj, nsnap = states_dev.shape[0], states_dev.shape[1]
+        n = int(round((states_dev[0, 0].numel()) ** 0.5))
+        losses = np.empty(steps, dtype=np.float32)
+        self._check(self.lib.ch_gtheta_train(self._h, _dptr(states_dev), ntraj, nsnap, n, stride, steps, batch, lr,
+                                             seed, losses.ctypes.data_as(C.POINTER(C.c_float))), "ch_gtheta_train")
+        return losses
+
+    def close(self) -> None:
+        if self._h:
+            self.lib.ch_gtheta_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gtheta_unflatten(p):
+    """Flat parameter vector -> ([W_l [3][3][Cout][Cin]], [b_l [Cout]]) as float64 arrays."""
+    p = np.asarray(p, dtype=np.float64)
+    W, b, o = [], [], 0
+    for l in range(6):
+        ci, co = GTHETA_CHANNELS[l], GTHETA_CHANNELS[l + 1]
+        W.append(p[o:o + 9 * co * ci].reshape(3, 3, co, ci))
+        o += 9 * co * ci
+        b.append(p[o:o + co].copy())
+        o += co
+    assert o == CH_GTHETA_PARAMS
+    return W, b
+
+
+def gtheta_flatten(W, b) -> np.ndarray:
+    """Inverse of gtheta_unflatten (FP32)."""
+    return np.concatenate([np.concatenate([np.asarray(w).ravel(), np.asarray(bb).ravel()])
+                           for w, bb in zip(W, b)]).astype(np.float32)

@@ -763,7 +763,7 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   al((void**)&newton_cnt_, (size_t)cap * sizeof(int));
   al((void**)&status_, 4 * sizeof(unsigned) + sizeof(unsigned long long));
   al((void**)&ctr_, 4 * sizeof(int));
-  al((void**)&cg_dev_, sizeof(unsigned long long));
+  al((void**)&cg_dev_, 2 * sizeof(unsigned long long));  // [0] CG, [1] Newton loop passes (batched)
   if (e != cudaSuccess) return e;
   e = cudaHostAlloc((void**)&host_cnt_, 4 * sizeof(int), 0);
   if (e != cudaSuccess) return e;
@@ -780,7 +780,7 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   e = cudaMemcpyAsync(mu_, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 2 * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
@@ -958,7 +958,7 @@ cudaError_t Prop2D::build_step(const StepKey& k, cudaGraphExec_t* out) {
     k2_update<<<grid, kThreads, 0, bs>>>(Y, tmp_, pts_, part_, flag_, status_);
     k2_newton_end<<<(units + 255) / 256, 256, 0, bs>>>(scal_, part_, flag_, newton_cnt_, units, p_.newton_tol,
                                                         std::sqrt(p_.newton_tol), ctr_, p_.newton_max, status_);
-    k2_loop_cond<<<1, 256, 0, bs>>>(hN, flag_, units, ctr_, 0, p_.newton_max, nullptr);
+    k2_loop_cond<<<1, 256, 0, bs>>>(hN, flag_, units, ctr_, 0, p_.newton_max, cg_dev_ + 1);
     e = cudaGetLastError();
   }
   {
@@ -999,6 +999,7 @@ cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int n
     }
     const cudaError_t e = cudaGraphLaunch(ex, st);
     if (e != cudaSuccess) return e;
+    step_kernels_ += (scheme == SCHEME_NL) ? kStepKernelsNL : kStepKernelsLin;
   }
   return cudaSuccess;
 }
@@ -1008,7 +1009,7 @@ cudaError_t Prop2D::reset_counters(cudaStream_t st) {
   newton_peak_ = 0;
   cg_total_ = 0;
   cudaError_t e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 2 * sizeof(unsigned long long), st);
   return e;
 }
 
@@ -1017,10 +1018,11 @@ unsigned Prop2D::read_status(cudaStream_t st) {
   unsigned long long tot = 0;
   cudaMemcpyAsync(s, status_, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&tot, (int*)status_ + 4, sizeof(tot), cudaMemcpyDeviceToHost, st);
-  unsigned long long cgt = 0;
-  cudaMemcpyAsync(&cgt, cg_dev_, sizeof(cgt), cudaMemcpyDeviceToHost, st);
+  unsigned long long cgt[2] = {0, 0};
+  cudaMemcpyAsync(cgt, cg_dev_, sizeof(cgt), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
-  cg_total_ = (long long)cgt;
+  cg_total_ = (long long)cgt[0];
+  newton_passes_ = (long long)cgt[1];
   newton_total_ = tot;
   newton_peak_ = (int)s[3];
   return s[0];

@@ -41,6 +41,17 @@ class Prop2D {
   unsigned long long newton_iterations() const { return newton_total_; }
   long long cg_iterations() const { return cg_total_; }
   int newton_peak() const { return newton_peak_; }
+  // Kernels launched by the step graphs since the last reset (as of the last read_status): each
+  // step runs a fixed prologue and epilogue, each batched Newton pass kNewtonKernels and each
+  // batched CG iteration kCgKernels.
+  long long kernel_launches() const {
+    return step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
+  }
+  static constexpr int kStepKernelsNL = 5;   // yhat, predict, reset_flags, loop_start, newton_stats
+  static constexpr int kStepKernelsLin = 4;  // right-hand side, reset_flags, loop_start, newton_stats
+  static constexpr int kNewtonKernels = 15;  // z, resid, weights, wbar, 2 DST, reopen, init, start,
+                                             // loop_start, 2 DST, update, newton_end, loop_cond
+  static constexpr int kCgKernels = 10;      // 4 DST, wprod, q, step, dir, end, loop_cond
   // Zeroes the device status bits and the Newton / CG counters (enqueued on st).
   cudaError_t reset_counters(cudaStream_t st);
   size_t bytes() const { return bytes_; }
@@ -93,6 +104,8 @@ class Prop2D {
   unsigned long long newton_total_ = 0;
   int newton_peak_ = 0;
   long long cg_total_ = 0;
+  long long newton_passes_ = 0;
+  long long step_kernels_ = 0;
 };
 
 // Parareal correction of one slice for `count` problems list[0..count) (Eq. 2.2), fused with

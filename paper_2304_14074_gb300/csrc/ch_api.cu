@@ -2,7 +2,9 @@
 // memory, the iteration driver (CUDA graphs replayed per Parareal iteration) and statistics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <new>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -11,6 +13,7 @@
 #include "ch1d.cuh"
 #include "ch2d.cuh"
 #include "ch_parareal.h"
+#include "gtheta.cuh"
 
 using chg::Ctrl;
 using chg::Params1D;
@@ -61,6 +64,11 @@ struct ch_parareal {
   std::vector<int> h_iters, h_conv;
   unsigned long long fine_newton = 0;  // Newton iterations (summed over units) of the fine sweeps
   long long fine_cg = 0;               // CG iterations (batched) of the fine sweeps
+  // learned coarse propagator (2D): null = plain coarse step
+  chg3::GTheta* gt = nullptr;
+  std::vector<int> h_learned, h_fallback;
+  long long gt_launches = 0;
+  long long aux_launches = 0;  // gather / scatter / correction kernels of the 2D driver
 };
 
 namespace {
@@ -154,6 +162,7 @@ int coarse2(const ch_parareal* h) { return coarse_of(h->cfg.variant); }
 ch_status gather_units(ch_parareal* h, double* src, const std::vector<long long>& off, bool to_w) {
   if (off.empty()) return CH_OK;
   CH_CUDA(h, cudaMemcpyAsync(h->doff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, h->st));
+  h->aux_launches += 1;
   if (to_w) {
     CH_CUDA(h, chg2::launch_gather(h->W, src, h->doff, (int)off.size(), h->pts, h->st));
   } else {
@@ -162,8 +171,19 @@ ch_status gather_units(ch_parareal* h, double* src, const std::vector<long long>
   return CH_OK;
 }
 
-ch_status prop2(ch_parareal* h, int units, int scheme, double dt, int nsteps) {
-  CH_CUDA(h, h->p2->propagate(h->W, units, scheme, dt, nsteps, h->st));
+ch_status prop2(ch_parareal* h, int units, int scheme, double dt, int nsteps, size_t row0 = 0) {
+  CH_CUDA(h, h->p2->propagate(h->W + row0 * h->pts, units, scheme, dt, nsteps, h->st));
+  return CH_OK;
+}
+
+// One coarse step of the work rows W[0, nb): rows [0, nl) with G_theta, the rest with the plain
+// coarse scheme.
+ch_status coarse_rows(ch_parareal* h, int nb, int nl) {
+  if (nl > 0) {
+    CH_CUDA(h, h->gt->forward64(h->W, h->W, nl, h->cfg.n, h->st));
+    h->gt_launches += chg3::GTheta::kForwardKernels;
+  }
+  if (nb > nl) return prop2(h, nb - nl, coarse_of(h->cfg.variant), h->p.dtc, h->p.coarse_steps, (size_t)nl);
   return CH_OK;
 }
 
@@ -202,12 +222,21 @@ ch_status run2d(ch_parareal* h) {
   h->h_conv.assign(B, 0);
   h->fine_ms = h->coarse_ms = 0.0;
   h->kernel_launches = 0;
+  h->gt_launches = 0;
+  h->aux_launches = 0;
+  h->h_learned.assign(B, h->gt ? 1 : 0);
+  h->h_fallback.assign(B, -1);
   std::vector<int> active(B, 1);
+  std::vector<int>& learned = h->h_learned;
   std::vector<double> acc(3 * B);
+  int nl = 0;  // active problems still on G_theta: listed first
   auto list_of = [&](std::vector<int>& L) {
     L.clear();
-    for (int b = 0; b < B; ++b)
-      if (active[b]) L.push_back(b);
+    for (int pass = 1; pass >= 0; --pass)
+      for (int b = 0; b < B; ++b)
+        if (active[b] && learned[b] == pass) L.push_back(b);
+    nl = 0;
+    for (int b : L) nl += learned[b];
   };
   auto pull_acc = [&]() -> ch_status {
     CH_CUDA(h, cudaMemcpyAsync(acc.data(), h->acc, 3 * B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -224,11 +253,12 @@ ch_status run2d(ch_parareal* h) {
   for (size_t i = 0; i < L.size(); ++i) off[i] = (long long)(L[i] * us);
   ch_status s = gather_units(h, h->U, off, true);
   for (int k = 0; k < N && s == CH_OK; ++k) {
-    s = prop2(h, (int)L.size(), coarse2(h), h->p.dtc, h->p.coarse_steps);
+    s = coarse_rows(h, (int)L.size(), nl);
     if (s != CH_OK) break;
     CH_CUDA(h, chg2::launch_correct(h->U + (k + 1) * pts, h->F + k * pts, h->W, h->Gold + k * pts,
                                     ref ? ref + (k + 1) * pts : nullptr, h->dlist, (int)L.size(), pts, us, fs, 1,
                                     h->cpart, h->acc, h2, h->st));
+    h->aux_launches += 2;
   }
   if (s != CH_OK) return s;
   if ((s = pull_acc()) != CH_OK) return s;
@@ -267,10 +297,11 @@ ch_status run2d(ch_parareal* h) {
     for (int i = 0; i < nb; ++i) off[i] = (long long)(L[i] * us + k * pts);
     if ((s = gather_units(h, h->U, off, true)) != CH_OK) return s;
     for (int sl = k; sl < N; ++sl) {
-      if ((s = prop2(h, nb, coarse2(h), h->p.dtc, h->p.coarse_steps)) != CH_OK) return s;
+      if ((s = coarse_rows(h, nb, nl)) != CH_OK) return s;
       CH_CUDA(h, chg2::launch_correct(h->U + (sl + 1) * pts, h->F + sl * pts, h->W, h->Gold + sl * pts,
                                       ref ? ref + (sl + 1) * pts : nullptr, h->dlist, nb, pts, us, fs, 0, h->cpart,
                                       h->acc, h2, h->st));
+      h->aux_launches += 2;
     }
     CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
     CH_CUDA(h, cudaEventRecord(h->ev[k + 2], h->st));
@@ -280,6 +311,7 @@ ch_status run2d(ch_parareal* h) {
     CH_CUDA(h, cudaEventElapsedTime(&cm, h->ph[1], h->ph[2]));
     h->fine_ms += fm;
     h->coarse_ms += cm;
+    std::vector<long long> goff, uoff2;  // G(U_n^k) of problems leaving G_theta, slices > k
     for (int b : L) {
       const double inc = acc[3 * b], el2 = acc[3 * b + 1], emx = acc[3 * b + 2];
       h->h_inc[b].push_back(inc);
@@ -290,11 +322,30 @@ ch_status run2d(ch_parareal* h) {
         h->h_conv[b] = 1;
         active[b] = 0;
       }
+      // the plain step judges G_theta: a growing increment sends the problem back to it
+      const size_t nk = h->h_inc[b].size();
+      if (learned[b] && nk >= 2 && !(h->h_inc[b][nk - 1] <= h->h_inc[b][nk - 2])) {
+        learned[b] = 0;
+        h->h_fallback[b] = k + 1;
+        if (active[b])
+          for (int sl = k + 1; sl < N; ++sl) {
+            uoff2.push_back((long long)(b * us + sl * pts));
+            goff.push_back((long long)(b * fs + sl * pts));
+          }
+      }
+    }
+    if (!goff.empty()) {
+      // Gold_s = G(U_s^{k+1}) with the plain step, so the next correction differences one G
+      if ((s = gather_units(h, h->U, uoff2, true)) != CH_OK) return s;
+      if ((s = prop2(h, (int)uoff2.size(), coarse2(h), h->p.dtc, h->p.coarse_steps)) != CH_OK) return s;
+      if ((s = gather_units(h, h->Gold, goff, false)) != CH_OK) return s;
     }
   }
   h->iters_done = k;
   h->ran = true;
   if ((s = device_status(h, h->p2->read_status(h->st))) != CH_OK) return s;
+  h->kernel_launches = (int)std::min<long long>(h->p2->kernel_launches() + h->gt_launches + h->aux_launches,
+                                                 2147483647LL);
   int left = 0;
   for (int b = 0; b < B; ++b) left += active[b];
   if ((h->p.tol > 0.0 || (h->p.err_tol > 0.0 && h->ref_valid)) && left > 0) return CH_ERR_NOT_CONVERGED;
@@ -346,6 +397,10 @@ void ch_parareal_destroy(ch_parareal* h) {
   cudaFree(h->cpart);
   cudaFree(h->dlist);
   cudaFree(h->doff);
+  if (h->gt) {
+    h->gt->release();
+    delete h->gt;
+  }
   delete h;
 }
 
@@ -642,8 +697,10 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
     out->fine_sweep_ms = h->fine_ms;
     out->coarse_sweep_ms = h->coarse_ms;
     out->fine_sweep_launches = h->iters_done;
-    out->kernel_launches = 0;
+    out->kernel_launches = h->kernel_launches;
     out->inner_iterations = h->fine_cg;
+    out->coarse_model = h->h_learned.empty() ? 0 : (h->h_learned[problem] || h->h_fallback[problem] >= 0);
+    out->coarse_fallback_iter = h->h_fallback.empty() ? -1 : h->h_fallback[problem];
     return CH_OK;
   }
   const int maxit = h->p.maxit;
@@ -675,6 +732,40 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
   out->coarse_sweep_ms = h->coarse_ms;
   out->fine_sweep_launches = h->iters_done;
   out->kernel_launches = h->kernel_launches;
+  out->coarse_model = 0;
+  out->coarse_fallback_iter = -1;
+  return CH_OK;
+}
+
+ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  if (h->dim != 2) return fail(h, CH_ERR_INVALID, "set_coarse_model: the learned coarse propagator is 2D only");
+  if (!params_host) {
+    if (len != 0) return fail(h, CH_ERR_INVALID, "set_coarse_model: NULL parameters need len = 0");
+    if (h->gt) {
+      CH_CUDA(h, cudaStreamSynchronize(h->st));
+      h->gt->release();
+      delete h->gt;
+      h->gt = nullptr;
+    }
+    return CH_OK;
+  }
+  if (len != (size_t)CH_GTHETA_PARAMS) return fail(h, CH_ERR_INVALID, "set_coarse_model: len != CH_GTHETA_PARAMS");
+  if (!h->gt) {
+    h->gt = new (std::nothrow) chg3::GTheta();
+    if (!h->gt) return fail(h, CH_ERR_OOM, "set_coarse_model: host allocation");
+    CH_CUDA(h, h->gt->init(0, h->st));
+  }
+  CH_CUDA(h, h->gt->set_params(params_host, h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_reference_device(ch_parareal* h, double* out_dev, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  const size_t want = (size_t)h->B * (h->p.N + 1) * h->pts;
+  if (!h->ref_valid) return fail(h, CH_ERR_STATE, "get_reference_device before compute_reference");
+  if (!out_dev || len != want) return fail(h, CH_ERR_INVALID, "get_reference_device: bad pointer or length");
+  CH_CUDA(h, cudaMemcpyAsync(out_dev, h->Uref, want * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   return CH_OK;
 }
 

@@ -1,0 +1,654 @@
+// Learned coarse propagator G_theta(U) = U + R(U) on sm_103a: inference and training kernels.
+//
+// R is six 3x3 convolutions with zero padding (u = 0 outside the interior grid, Section 2.1),
+// channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU after the first five. Activations are BF16,
+// channels last ([B][S][S][32]); accumulation is FP32.
+//
+// The four 32 -> 32 layers carry almost all of the arithmetic (2 x 32 x 288 flops per pixel each)
+// and run as an implicit GEMM on the tensor cores: M = 16 output pixels of a row, N = 8 output
+// channels, K = 16 input channels of one tap, 18 K-steps (9 taps x 2 channel halves) per tile,
+// mma.sync m16n8k16 BF16 x BF16 -> FP32. A CTA computes a 16 x 16 pixel tile from an 18 x 18 halo
+// tile in shared memory (pixel stride 80 B so the eight ldmatrix rows of a phase fall on
+// distinct banks). The backward pass through a 32 -> 32 layer is the same kernel with taps
+// flipped and channels swapped, its epilogue multiplying by the ReLU mask of the layer below.
+// The 1 -> 32 and 32 -> 1 layers, the weight gradients (per-tile partials reduced in a fixed
+// order), the loss and Adam (Kingma and Ba, 2015) run on the CUDA cores.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "gtheta.cuh"
+
+namespace chg3 {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kTile = 16;        // output tile edge
+constexpr int kHalo = kTile + 2;
+constexpr int kPix = 40;         // BF16 elements per pixel in shared tiles (80 B)
+constexpr int kThreads = 256;
+// scalar copies of the layout offsets for device code
+constexpr int kW1 = kOffW[0], kW2 = kOffW[1], kW6 = kOffW[5], kMidStride = kOffW[2] - kOffW[1];
+static_assert(kOffW[3] - kOffW[2] == kMidStride && kOffW[4] - kOffW[3] == kMidStride, "layout");
+static_assert(kOffB[0] == kW1 + 9 * kC && kOffB[5] == kW6 + 9 * kC, "layout");
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Loads the 18 x 18 halo tile of a [S][S][32] BF16 field into shared memory (zeros outside).
+__device__ __forceinline__ void load_halo(bf16* tile, const bf16* __restrict__ x, int S, int ty0, int tx0) {
+  for (int c = threadIdx.x; c < kHalo * kHalo * 4; c += kThreads) {
+    const int pix = c >> 2, part = c & 3;
+    const int yy = pix / kHalo, xx = pix - yy * kHalo;
+    const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (gy >= 0 && gy < S && gx >= 0 && gx < S)
+      v = *reinterpret_cast<const uint4*>(x + ((size_t)gy * S + gx) * kC + part * 8);
+    *reinterpret_cast<uint4*>(tile + pix * kPix + part * 8) = v;
+  }
+}
+
+// 32 -> 32 convolution on the tensor cores.
+// mode 0 (forward): y = relu(conv(x, W) + b); mode 1 (backward data): y = conv(x, W) * (mask > 0).
+__global__ void __launch_bounds__(kThreads) k_conv_mid(const bf16* __restrict__ x, bf16* __restrict__ y,
+                                                       const bf16* __restrict__ W, const float* __restrict__ bias,
+                                                       const bf16* __restrict__ mask, int S, int mode) {
+  __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
+  __shared__ __align__(16) bf16 ws[9 * kC * kPix];
+  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+  const size_t off = (size_t)img * S * S * kC;
+  load_halo(tile, x + off, S, ty0, tx0);
+  for (int c = threadIdx.x; c < 9 * kC * 4; c += kThreads) {
+    const int row = c >> 2, part = c & 3;  // row = tap * 32 + output channel
+    *reinterpret_cast<uint4*>(ws + row * kPix + part * 8) = *reinterpret_cast<const uint4*>(W + row * kC + part * 8);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
+  const int akof = (lane >> 4) * 8;
+  float acc[2][4][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.f;
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap - 3 * dy;
+#pragma unroll
+    for (int kh = 0; kh < 2; ++kh) {
+      const int c0 = kh * 16;
+      unsigned a[2][4];
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int oy = warp * 2 + m;
+        ldsm_x4(a[m][0], a[m][1], a[m][2], a[m][3], tile + ((oy + dy) * kHalo + arow + dx) * kPix + c0 + akof);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bf16* wb = ws + (tap * kC + j * 8 + g) * kPix + c0 + 2 * t;
+        const unsigned b0 = *reinterpret_cast<const unsigned*>(wb);
+        const unsigned b1 = *reinterpret_cast<const unsigned*>(wb + 8);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) mma16816(acc[m][j], a[m], b0, b1);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int Y = ty0 + warp * 2 + m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int co = j * 8 + 2 * t;
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int X = tx0 + g + 8 * hf;
+        if (Y >= S || X >= S) continue;
+        const size_t o = off + ((size_t)Y * S + X) * kC + co;
+        float v0 = acc[m][j][2 * hf], v1 = acc[m][j][2 * hf + 1];
+        if (mode == 0) {
+          v0 = fmaxf(v0 + bias[co], 0.f);
+          v1 = fmaxf(v1 + bias[co + 1], 0.f);
+        } else {
+          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + o);
+          v0 = (__bfloat162float(mk.x) > 0.f) ? v0 : 0.f;
+          v1 = (__bfloat162float(mk.y) > 0.f) ? v1 : 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat162*>(y + o) = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+// First layer 1 -> 32: a1 = relu(conv(U, W1) + b1); U FP64 (inference) or FP32 (training).
+template <typename TIn>
+__global__ void __launch_bounds__(kThreads) k_conv_first(const TIn* __restrict__ u, bf16* __restrict__ y,
+                                                         const float* __restrict__ P, int S, float* __restrict__ a0) {
+  __shared__ float tile[kHalo * kHalo];
+  __shared__ float w[9 * kC + kC];
+  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+  const TIn* ui = u + (size_t)img * S * S;
+  for (int c = threadIdx.x; c < kHalo * kHalo; c += kThreads) {
+    const int yy = c / kHalo, xx = c - yy * kHalo;
+    const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+    tile[c] = (gy >= 0 && gy < S && gx >= 0 && gx < S) ? float(ui[(size_t)gy * S + gx]) : 0.f;
+  }
+  for (int c = threadIdx.x; c < 9 * kC + kC; c += kThreads) w[c] = P[kW1 + c];  // W1 then b1 (contiguous)
+  __syncthreads();
+  const int oy = threadIdx.x / kTile, ox = threadIdx.x - oy * kTile;
+  const int Y = ty0 + oy, X = tx0 + ox;
+  if (Y >= S || X >= S) return;
+  if (a0) a0[((size_t)img * S + Y) * S + X] = tile[(oy + 1) * kHalo + ox + 1];
+  float nb[9];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) nb[tap] = tile[(oy + tap / 3) * kHalo + ox + tap % 3];
+  bf16* yo = y + (((size_t)img * S + Y) * S + X) * kC;
+#pragma unroll
+  for (int co = 0; co < kC; co += 2) {
+    float s0 = w[9 * kC + co], s1 = w[9 * kC + co + 1];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      s0 += w[tap * kC + co] * nb[tap];
+      s1 += w[tap * kC + co + 1] * nb[tap];
+    }
+    *reinterpret_cast<__nv_bfloat162*>(yo + co) = __floats2bfloat162_rn(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+  }
+}
+
+// Last layer 32 -> 1: r = conv(a5, W6) + b6 (FP32); inference variant writes out = in + r (FP64).
+__global__ void __launch_bounds__(kThreads) k_conv_last(const bf16* __restrict__ x, float* __restrict__ r,
+                                                        const float* __restrict__ P, int S, const double* __restrict__ in,
+                                                        double* __restrict__ out) {
+  __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
+  __shared__ float w[9 * kC + 1];
+  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+  load_halo(tile, x + (size_t)img * S * S * kC, S, ty0, tx0);
+  for (int c = threadIdx.x; c < 9 * kC + 1; c += kThreads) w[c] = P[kW6 + c];  // W6 then b6
+  __syncthreads();
+  const int oy = threadIdx.x / kTile, ox = threadIdx.x - oy * kTile;
+  const int Y = ty0 + oy, X = tx0 + ox;
+  if (Y >= S || X >= S) return;
+  float s = w[9 * kC];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const bf16* p = tile + ((oy + tap / 3) * kHalo + ox + tap % 3) * kPix;
+#pragma unroll
+    for (int ci = 0; ci < kC; ci += 2) {
+      const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + ci));
+      s += w[tap * kC + ci] * v.x + w[tap * kC + ci + 1] * v.y;
+    }
+  }
+  const size_t o = ((size_t)img * S + Y) * S + X;
+  if (r) r[o] = s;
+  if (out) out[o] = in[o] + (double)s;
+}
+
+// Loss on the window [margin, S - margin)^2: dr = 2 (r - t) / count there, 0 elsewhere;
+// per-block partial sums of (r - t)^2.
+__global__ void k_loss(const float* __restrict__ r, const float* __restrict__ t, float* __restrict__ dr, int B, int S,
+                       int margin, double* __restrict__ part) {
+  __shared__ double sh[kThreads / 32];
+  const size_t total = (size_t)B * S * S;
+  const int inner = S - 2 * margin;
+  const double inv = 1.0 / ((double)B * inner * inner);
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)kThreads + threadIdx.x; k < total; k += (size_t)gridDim.x * kThreads) {
+    const int X = (int)(k % S), Y = (int)((k / S) % S);
+    const bool in = Y >= margin && Y < S - margin && X >= margin && X < S - margin;
+    const float d = in ? r[k] - t[k] : 0.f;
+    dr[k] = (float)(2.0 * d * inv);
+    acc += (double)d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) s += sh[i];
+    part[blockIdx.x] = s * inv;
+  }
+}
+
+__global__ void k_loss_sum(const double* __restrict__ part, int n, float* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = (float)s;
+  }
+}
+
+// Gradient into the last hidden layer: g5[p][ci] = sum_tap W6[tap][ci] dr[p - (tap - 1)], times
+// the ReLU mask of a5.
+__global__ void __launch_bounds__(kThreads) k_last_bwd(const float* __restrict__ dr, const bf16* __restrict__ a5,
+                                                       bf16* __restrict__ g5, const float* __restrict__ P, int S) {
+  __shared__ float tile[kHalo * kHalo];
+  __shared__ float w[9 * kC];
+  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+  const float* di = dr + (size_t)img * S * S;
+  for (int c = threadIdx.x; c < kHalo * kHalo; c += kThreads) {
+    const int yy = c / kHalo, xx = c - yy * kHalo;
+    const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+    tile[c] = (gy >= 0 && gy < S && gx >= 0 && gx < S) ? di[(size_t)gy * S + gx] : 0.f;
+  }
+  for (int c = threadIdx.x; c < 9 * kC; c += kThreads) w[c] = P[kW6 + c];
+  __syncthreads();
+  const int oy = threadIdx.x / kTile, ox = threadIdx.x - oy * kTile;
+  const int Y = ty0 + oy, X = tx0 + ox;
+  if (Y >= S || X >= S) return;
+  // dr at p - (tap - 1) = tile position (oy + 1 - (dy - 1), ox + 1 - (dx - 1)) = (oy + 2 - dy, ox + 2 - dx)
+  float nb[9];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) nb[tap] = tile[(oy + 2 - tap / 3) * kHalo + ox + 2 - tap % 3];
+  const size_t o = (((size_t)img * S + Y) * S + X) * kC;
+#pragma unroll
+  for (int ci = 0; ci < kC; ci += 2) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      s0 += w[tap * kC + ci] * nb[tap];
+      s1 += w[tap * kC + ci + 1] * nb[tap];
+    }
+    const float2 m = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(a5 + o + ci));
+    *reinterpret_cast<__nv_bfloat162*>(g5 + o + ci) =
+        __floats2bfloat162_rn(m.x > 0.f ? s0 : 0.f, m.y > 0.f ? s1 : 0.f);
+  }
+}
+
+// Weight gradient of a 32 -> 32 layer over one 16 x 16 tile: partial[tile][tap][co][ci] =
+// sum_p g[p][co] x[p + tap - 1][ci]; partial bias sum_p g[p][co] after the 9216 weights.
+__global__ void __launch_bounds__(kThreads) k_wgrad_mid(const bf16* __restrict__ g, const bf16* __restrict__ x,
+                                                        float* __restrict__ part, int S) {
+  __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
+  __shared__ __align__(16) bf16 gt[kTile * kTile * kPix];
+  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+  const size_t off = (size_t)img * S * S * kC;
+  load_halo(tile, x + off, S, ty0, tx0);
+  for (int c = threadIdx.x; c < kTile * kTile * 4; c += kThreads) {
+    const int pix = c >> 2, part4 = c & 3;
+    const int Y = ty0 + pix / kTile, X = tx0 + pix % kTile;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (Y < S && X < S) v = *reinterpret_cast<const uint4*>(g + off + ((size_t)Y * S + X) * kC + part4 * 8);
+    *reinterpret_cast<uint4*>(gt + pix * kPix + part4 * 8) = v;
+  }
+  __syncthreads();
+  const int co = threadIdx.x >> 3, ci0 = (threadIdx.x & 7) * 4;
+  float acc[9][4];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[tap][q] = 0.f;
+  float bsum = 0.f;
+  for (int pix = 0; pix < kTile * kTile; ++pix) {
+    const float gv = __bfloat162float(gt[pix * kPix + co]);
+    bsum += gv;
+    const int oy = pix / kTile, ox = pix - oy * kTile;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const bf16* p = tile + ((oy + tap / 3) * kHalo + ox + tap % 3) * kPix + ci0;
+      const float2 v0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+      const float2 v1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + 2));
+      acc[tap][0] += gv * v0.x;
+      acc[tap][1] += gv * v0.y;
+      acc[tap][2] += gv * v1.x;
+      acc[tap][3] += gv * v1.y;
+    }
+  }
+  const size_t tileid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  float* pp = part + tileid * (9 * kC * kC + kC);
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pp[(tap * kC + co) * kC + ci0 + q] = acc[tap][q];
+  if ((threadIdx.x & 7) == 0) pp[9 * kC * kC + co] = bsum;
+}
+
+// Weight gradients of the first layer (x = a0 scalar, g = gz1 [32]) or the last (x = a5 [32],
+// g = dr scalar) over one tile: 288 weights + bias per tile.
+__global__ void __launch_bounds__(kThreads) k_wgrad_edge(const float* __restrict__ a0, const bf16* __restrict__ g1,
+                                                         const float* __restrict__ dr, const bf16* __restrict__ a5,
+                                                         float* __restrict__ part, int S, int first) {
+  __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
+  __shared__ float ft[kHalo * kHalo];
+  __shared__ __align__(16) bf16 gt[kTile * kTile * kPix];
+  __shared__ float fg[kTile * kTile];
+  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+  const size_t s2 = (size_t)S * S;
+  if (first) {
+    for (int c = threadIdx.x; c < kHalo * kHalo; c += kThreads) {
+      const int yy = c / kHalo, xx = c - yy * kHalo;
+      const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+      ft[c] = (gy >= 0 && gy < S && gx >= 0 && gx < S) ? a0[img * s2 + (size_t)gy * S + gx] : 0.f;
+    }
+    for (int c = threadIdx.x; c < kTile * kTile * 4; c += kThreads) {
+      const int pix = c >> 2, part4 = c & 3;
+      const int Y = ty0 + pix / kTile, X = tx0 + pix % kTile;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (Y < S && X < S) v = *reinterpret_cast<const uint4*>(g1 + (img * s2 + (size_t)Y * S + X) * kC + part4 * 8);
+      *reinterpret_cast<uint4*>(gt + pix * kPix + part4 * 8) = v;
+    }
+  } else {
+    load_halo(tile, a5 + img * s2 * kC, S, ty0, tx0);
+    for (int c = threadIdx.x; c < kTile * kTile; c += kThreads) {
+      const int Y = ty0 + c / kTile, X = tx0 + c % kTile;
+      fg[c] = (Y < S && X < S) ? dr[img * s2 + (size_t)Y * S + X] : 0.f;
+    }
+  }
+  __syncthreads();
+  const size_t tileid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  float* pp = part + tileid * (9 * kC + kC);
+  for (int o = threadIdx.x; o < 9 * kC + kC; o += kThreads) {
+    float acc = 0.f;
+    if (o < 9 * kC) {
+      const int tap = o / kC, c = o - tap * kC;  // first: c = output channel; last: c = input channel
+      for (int pix = 0; pix < kTile * kTile; ++pix) {
+        const int oy = pix / kTile, ox = pix - oy * kTile;
+        const int hp = (oy + tap / 3) * kHalo + ox + tap % 3;
+        if (first) acc += __bfloat162float(gt[pix * kPix + c]) * ft[hp];
+        else acc += fg[pix] * __bfloat162float(tile[hp * kPix + c]);
+      }
+    } else {
+      const int c = o - 9 * kC;
+      for (int pix = 0; pix < kTile * kTile; ++pix)
+        acc += first ? __bfloat162float(gt[pix * kPix + c]) : (c == 0 ? fg[pix] : 0.f);
+    }
+    pp[o] = acc;
+  }
+}
+
+// Sum over tiles (in tile order) of part[tile * stride + j], j < len: the weights (j < wlen) go
+// to grad[dst_w + j], the biases to grad[dst_b + j - wlen].
+__global__ void k_reduce(const float* __restrict__ part, int tiles, int stride, int len, float* __restrict__ grad,
+                         int dst_w, int wlen, int dst_b) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  double s = 0.0;
+  for (int tl = 0; tl < tiles; ++tl) s += part[(size_t)tl * stride + j];
+  if (j < wlen) grad[dst_w + j] = (float)s;
+  else grad[dst_b + (j - wlen)] = (float)s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// BF16 weights of the 32 -> 32 layers: forward [tap][co][ci]; backward data [tap'][ci][co] with
+// tap' = 8 - tap (flipped taps, swapped channels).
+__global__ void k_pack(const float* __restrict__ P, bf16* __restrict__ wf, bf16* __restrict__ wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * 9 * kC * kC) return;
+  const int l = i / (9 * kC * kC), r = i - l * 9 * kC * kC;
+  const int tap = r / (kC * kC), co = (r / kC) % kC, ci = r % kC;
+  const float w = P[kW2 + l * kMidStride + r];
+  wf[i] = __float2bfloat16_rn(w);
+  wb[(size_t)l * 9 * kC * kC + ((8 - tap) * kC + ci) * kC + co] = __float2bfloat16_rn(w);
+}
+
+// Random crops of pairs: in = states[t][s] on [y0, y0+S) x [x0, x0+S) (0 outside the grid),
+// target = states[t][s + stride] - in there.
+__global__ void k_crops(const double* __restrict__ states, const int4* __restrict__ crops, int nsnap, int n,
+                        int stride, int S, float* __restrict__ in, float* __restrict__ tgt) {
+  const int b = blockIdx.y;
+  const int4 c = crops[b];  // (traj, snap, y0, x0)
+  const size_t base = ((size_t)c.x * nsnap + c.y) * n * n;
+  const size_t base2 = ((size_t)c.x * nsnap + c.y + stride) * n * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S * S; k += gridDim.x * blockDim.x) {
+    const int yy = k / S, xx = k - yy * S;
+    const int Y = c.z + yy, X = c.w + xx;
+    double a = 0.0, t = 0.0;
+    if (Y >= 0 && Y < n && X >= 0 && X < n) {
+      a = states[base + (size_t)Y * n + X];
+      t = states[base2 + (size_t)Y * n + X] - a;
+    }
+    in[(size_t)b * S * S + k] = (float)a;
+    tgt[(size_t)b * S * S + k] = (float)t;
+  }
+}
+
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------- GTheta
+
+cudaError_t GTheta::init(unsigned long long seed, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  al((void**)&master_, kParams * sizeof(float));
+  al((void**)&grad_, kParams * sizeof(float));
+  al((void**)&m_, kParams * sizeof(float));
+  al((void**)&v_, kParams * sizeof(float));
+  al((void**)&wmid_, 4 * 9 * kC * kC * sizeof(bf16));
+  al((void**)&wbwd_, 4 * 9 * kC * kC * sizeof(bf16));
+  al((void**)&lpart_, 1024 * sizeof(double));
+  if (e != cudaSuccess) return e;
+  // He-normal initial weights (Box-Muller on SplitMix64), zero biases; the last layer scaled 0.1
+  std::vector<float> p(kParams, 0.f);
+  const int cin[6] = {1, 32, 32, 32, 32, 32}, cout[6] = {32, 32, 32, 32, 32, 1};
+  uint64_t s = seed;
+  for (int l = 0; l < 6; ++l) {
+    const double sd = std::sqrt(2.0 / (9.0 * cin[l])) * (l == 5 ? 0.1 : 1.0);
+    for (int i = 0; i < 9 * cout[l] * cin[l]; ++i) {
+      const double u1 = ((splitmix(s) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+      const double u2 = (splitmix(s) >> 11) * (1.0 / 9007199254740992.0);
+      p[kOffW[l] + i] = float(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2));
+    }
+  }
+  return set_params(p.data(), st);
+}
+
+void GTheta::release() {
+  void* ptrs[] = {master_, grad_, m_, v_, wmid_, wbwd_, loss_dev_, a0_, r_, dr_, part_, tgt_, crops_, lpart_,
+                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1]};
+  for (void* q : ptrs) cudaFree(q);
+  master_ = grad_ = m_ = v_ = nullptr;
+  wmid_ = wbwd_ = nullptr;
+  loss_dev_ = a0_ = r_ = dr_ = part_ = tgt_ = nullptr;
+  crops_ = nullptr;
+  lpart_ = nullptr;
+  for (auto& a : act_) a = nullptr;
+  for (auto& gg : g_) gg = nullptr;
+  cap_batch_ = cap_S_ = 0;
+}
+
+cudaError_t GTheta::refresh_bf16(cudaStream_t st) {
+  k_pack<<<(4 * 9 * kC * kC + 255) / 256, 256, 0, st>>>(master_, wmid_, wbwd_);
+  return cudaGetLastError();
+}
+
+cudaError_t GTheta::set_params(const float* host, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(master_, host, kParams * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m_, 0, kParams * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v_, 0, kParams * sizeof(float), st);
+  adam_t_ = 0;
+  if (e == cudaSuccess) e = refresh_bf16(st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t GTheta::get_params(float* host, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(host, master_, kParams * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t GTheta::ensure(int batch, int S) {
+  if (batch <= cap_batch_ && S <= cap_S_) return cudaSuccess;
+  const int B = std::max(batch, cap_batch_), SS = std::max(S, cap_S_);
+  void* old[] = {a0_, r_, dr_, tgt_, act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part_, crops_};
+  for (void* q : old) cudaFree(q);
+  const size_t f = (size_t)B * SS * SS;
+  const size_t tiles = (size_t)B * ((SS + kTile - 1) / kTile) * ((SS + kTile - 1) / kTile);
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  al((void**)&a0_, f * sizeof(float));
+  al((void**)&r_, f * sizeof(float));
+  al((void**)&dr_, f * sizeof(float));
+  al((void**)&tgt_, f * sizeof(float));
+  for (auto& a : act_) al((void**)&a, f * kC * sizeof(bf16));
+  for (auto& gg : g_) al((void**)&gg, f * kC * sizeof(bf16));
+  part_cap_ = tiles * (9 * kC * kC + kC);
+  al((void**)&part_, part_cap_ * sizeof(float));
+  al((void**)&crops_, (size_t)B * sizeof(int4));
+  if (e == cudaSuccess) {
+    cap_batch_ = B;
+    cap_S_ = SS;
+  }
+  return e;
+}
+
+cudaError_t GTheta::ensure_losses(int count, cudaStream_t st) {
+  if (count <= loss_cap_) return cudaSuccess;
+  const int cap = std::max(count, 2 * loss_cap_);
+  float* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, cap * sizeof(float));
+  if (e == cudaSuccess && loss_cap_ > 0)
+    e = cudaMemcpyAsync(p, loss_dev_, loss_cap_ * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return e;
+  }
+  cudaFree(loss_dev_);
+  loss_dev_ = p;
+  loss_cap_ = cap;
+  return cudaSuccess;
+}
+
+cudaError_t GTheta::forward_acts(const void* in, bool in64, int batch, int S, cudaStream_t st) {
+  const dim3 grid((S + kTile - 1) / kTile, (S + kTile - 1) / kTile, batch);
+  if (in64) k_conv_first<double><<<grid, kThreads, 0, st>>>((const double*)in, act_[0], master_, S, nullptr);
+  else  // keep a copy of the input for the first layer's weight gradient (unless it already is a0_)
+    k_conv_first<float><<<grid, kThreads, 0, st>>>((const float*)in, act_[0], master_, S,
+                                                   in == a0_ ? nullptr : a0_);
+  for (int l = 0; l < 4; ++l)
+    k_conv_mid<<<grid, kThreads, 0, st>>>(act_[l], act_[l + 1], wmid_ + (size_t)l * 9 * kC * kC,
+                                          master_ + kOffB[l + 1], nullptr, S, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t GTheta::forward64(const double* in, double* out, int batch, int S, cudaStream_t st) {
+  cudaError_t e = ensure(batch, S);
+  if (e != cudaSuccess) return e;
+  e = forward_acts(in, true, batch, S, st);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((S + kTile - 1) / kTile, (S + kTile - 1) / kTile, batch);
+  k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], nullptr, master_, S, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, int S, int margin, int slot,
+                              cudaStream_t st) {
+  cudaError_t e = ensure(batch, S);
+  if (e != cudaSuccess) return e;
+  if ((e = ensure_losses(slot + 1, st)) != cudaSuccess) return e;
+  const dim3 grid((S + kTile - 1) / kTile, (S + kTile - 1) / kTile, batch);
+  const int tiles = grid.x * grid.y * grid.z;
+  e = forward_acts(in, false, batch, S, st);
+  if (e != cudaSuccess) return e;
+  k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], r_, master_, S, nullptr, nullptr);
+  const int lb = 256;
+  k_loss<<<lb, kThreads, 0, st>>>(r_, target, dr_, batch, S, margin, lpart_);
+  k_loss_sum<<<1, 32, 0, st>>>(lpart_, lb, loss_dev_ + slot);
+  // last layer: weights from (dr, a5), gradient into a5
+  const int le = 9 * kC + kC;
+  k_wgrad_edge<<<grid, kThreads, 0, st>>>(nullptr, nullptr, dr_, act_[4], part_, S, 0);
+  k_reduce<<<(le + 255) / 256, 256, 0, st>>>(part_, tiles, le, 9 * kC + 1, grad_, kOffW[5], 9 * kC, kOffB[5]);
+  k_last_bwd<<<grid, kThreads, 0, st>>>(dr_, act_[4], g_[0], master_, S);
+  // 32 -> 32 layers 5, 4, 3, 2 (indices l + 1 = 4..1): weights from (g, input activation), then
+  // gradient through the layer into the activation below (masked by its ReLU)
+  int cur = 0;
+  const int lm = 9 * kC * kC + kC;
+  for (int l = 3; l >= 0; --l) {
+    k_wgrad_mid<<<grid, kThreads, 0, st>>>(g_[cur], act_[l], part_, S);
+    k_reduce<<<(lm + 255) / 256, 256, 0, st>>>(part_, tiles, lm, lm, grad_, kOffW[l + 1], 9 * kC * kC,
+                                               kOffB[l + 1]);
+    k_conv_mid<<<grid, kThreads, 0, st>>>(g_[cur], g_[cur ^ 1], wbwd_ + (size_t)l * 9 * kC * kC, nullptr, act_[l], S, 1);
+    cur ^= 1;
+  }
+  // first layer: weights from (g1, a0)
+  k_wgrad_edge<<<grid, kThreads, 0, st>>>(a0_, g_[cur], nullptr, nullptr, part_, S, 1);
+  k_reduce<<<(le + 255) / 256, 256, 0, st>>>(part_, tiles, le, le, grad_, kOffW[0], 9 * kC, kOffB[0]);
+  return cudaGetLastError();
+}
+
+cudaError_t GTheta::train(const double* states, int ntraj, int nsnap, int n, int stride, int steps, int batch,
+                          double lr, unsigned long long seed, cudaStream_t st) {
+  // Crops of 76 x 76 with the loss on the central 64 x 64: the 13 x 13 receptive field of the
+  // window stays inside the crop. A grid smaller than the window is taken whole (S = n + 12).
+  const int margin = kTrainMargin, S = train_crop(n);
+  if (nsnap <= stride || ntraj < 1 || steps < 1 || batch < 1) return cudaErrorInvalidValue;
+  cudaError_t e = ensure(batch, S);
+  if (e == cudaSuccess) e = ensure_losses(steps, st);
+  if (e != cudaSuccess) return e;
+  std::vector<int4> crops(batch);
+  uint64_t s = seed;
+  const int span = n + 2 * margin - S + 1;  // crop origins in [-margin, n + margin - S]
+  for (int it = 0; it < steps && e == cudaSuccess; ++it) {
+    for (int b = 0; b < batch; ++b) {
+      crops[b].x = (int)(splitmix(s) % (uint64_t)ntraj);
+      crops[b].y = (int)(splitmix(s) % (uint64_t)(nsnap - stride));
+      crops[b].z = (int)(splitmix(s) % (uint64_t)std::max(span, 1)) - margin;
+      crops[b].w = (int)(splitmix(s) % (uint64_t)std::max(span, 1)) - margin;
+    }
+    e = cudaMemcpyAsync(crops_, crops.data(), batch * sizeof(int4), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) break;
+    k_crops<<<dim3((S * S + 255) / 256, batch), 256, 0, st>>>(states, crops_, nsnap, n, stride, S, a0_, tgt_);
+    // a0_ doubles as the crop input buffer: k_conv_first re-writes the same values into it
+    e = grad_step(a0_, tgt_, batch, S, margin, it, st);
+    if (e != cudaSuccess) break;
+    ++adam_t_;
+    const float c1 = 1.f - std::pow(0.9f, (float)adam_t_), c2 = 1.f - std::pow(0.999f, (float)adam_t_);
+    k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(master_, grad_, m_, v_, kParams, (float)lr, c1, c2);
+    e = refresh_bf16(st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t GTheta::read_losses(float* host, int count, cudaStream_t st) {
+  if (count > loss_cap_) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(host, loss_dev_, count * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+}  // namespace chg3

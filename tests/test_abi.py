@@ -84,4 +84,32 @@ def test_destroy_accepts_null_and_last_error_on_null():
 def test_binding_struct_layout_matches_header():
     # ch_config: 2 ints, 2 doubles, 4 ints, double, int, double, 3 ints, double -> 88 bytes with padding
     assert C.sizeof(_lib._Config) == 88
-    assert C.sizeof(_lib._Stats) == 8 + 4 * 8 * ch.CH_MAX_ITERS + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8
+    assert C.sizeof(_lib._Stats) == 8 + 4 * 8 * ch.CH_MAX_ITERS + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 4 + 4
+
+
+def test_gtheta_entry_points_reject_invalid_arguments_without_device():
+    lib = ch.load()
+    assert lib.ch_gtheta_create(0, None, None) == 1
+    lib.ch_gtheta_destroy(None)
+    assert lib.ch_gtheta_last_error(None).decode() == "NULL handle"
+    assert lib.ch_gtheta_set_params(None, None, 0) == 1
+    assert lib.ch_gtheta_get_params(None, None, 0) == 1
+    assert lib.ch_gtheta_forward(None, None, None, 1, 8) == 1
+    assert lib.ch_gtheta_gradients(None, None, None, 1, 8, 1, None, 0, None) == 1
+    assert lib.ch_gtheta_train(None, None, 1, 2, 8, 1, 1, 1, 1e-3, 0, None) == 1
+    assert lib.ch_parareal_set_coarse_model(None, None, 0) == 1
+    assert lib.ch_parareal_get_reference_device(None, None, 0) == 1
+
+
+def test_gtheta_parameter_layout_matches_header():
+    src = open(os.path.join(ROOT, "include", "ch_parareal.h")).read()
+    m = re.search(r"#define\s+CH_GTHETA_PARAMS\s+(\d+)", src)
+    assert m and int(m.group(1)) == ch.CH_GTHETA_PARAMS
+    c = _lib.GTHETA_CHANNELS
+    assert sum(9 * c[l] * c[l + 1] + c[l + 1] for l in range(6)) == ch.CH_GTHETA_PARAMS
+    import numpy as np
+    p = np.arange(ch.CH_GTHETA_PARAMS, dtype=np.float32)
+    W, b = ch.gtheta_unflatten(p)
+    assert W[0].shape == (3, 3, 32, 1) and W[5].shape == (3, 3, 1, 32) and b[5].shape == (1,)
+    assert W[1][0, 0, 0, 1] == 320 + 1 and b[0][0] == 288  # W_l[dy][dx][co][ci] then b_l
+    assert np.array_equal(ch.gtheta_flatten(W, b), p)

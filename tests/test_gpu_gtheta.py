@@ -1,0 +1,233 @@
+"""GPU parity of the learned coarse propagator G_theta against its CPU oracle, its training
+plumbing, and its use as the coarse step of 2D Parareal.
+
+Tolerances. The kernels store hidden activations, mid-layer weights and hidden gradients in
+BF16 and accumulate in FP32; the oracle's BF16 storage model rounds at the same places in
+FP64. What remains is FP32 against FP64 accumulation (about 1e-7 relative per layer) and the
+BF16 rounding decisions it flips: an activation within ~1e-7 of a rounding boundary (a
+fraction ~1e-7 / 2^-9 of them, a handful per field) moves by one BF16 ulp (2^-8 relative) and
+that change spreads through the later layers to the pixels around it. So the bulk of the
+output agrees to ~1e-6 of its scale (99th percentile <= 1e-5), and the largest deviation, from
+the flips, stays below 1e-2 of it. Against the unrounded FP64 network the difference is the BF16
+storage itself: a few 1e-3 relative per layer, 3e-2 over six layers.
+"""
+import numpy as np
+import pytest
+
+import ch_inputs
+from oracle import gtheta_oracle as go
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def scaling_net(ch, alpha):
+    """R(U) = alpha U exactly: layer 1 splits u into relu(u) and relu(-u), the hidden layers pass
+    both channels through their centre taps, the last layer returns alpha (relu(u) - relu(-u))."""
+    W = [np.zeros((3, 3, 32, 1))] + [np.zeros((3, 3, 32, 32)) for _ in range(4)] + [np.zeros((3, 3, 1, 32))]
+    b = [np.zeros(32) for _ in range(5)] + [np.zeros(1)]
+    W[0][1, 1, 0, 0], W[0][1, 1, 1, 0] = 1.0, -1.0
+    for l in range(1, 5):
+        W[l][1, 1, 0, 0] = W[l][1, 1, 1, 1] = 1.0
+    W[5][1, 1, 0, 0], W[5][1, 1, 0, 1] = alpha, -alpha
+    return ch.gtheta_flatten(W, b)
+
+
+def test_scaling_network_closed_form(gpu_lib):
+    """G(U) = (1 + alpha) U for the scaling network; the only error is the BF16 storage of
+    relu(+-u) (2^-9 relative)."""
+    ch = gpu_lib
+    net = ch.GTheta()
+    net.set_params(scaling_net(ch, 0.5))
+    n = 37
+    u = np.stack([ch_inputs.initial_condition(2, n, 60 + i, kind="normal", amp=0.5).reshape(n, n) for i in range(2)])
+    out = net.forward(dev(u)).cpu().numpy()
+    assert np.all(np.abs(out - 1.5 * u) <= 0.5 * 2.0 ** -8 * np.abs(u) + 1e-12)
+
+
+def random_net(seed, bias=0.1, scale_last=1.0):
+    W, b = go.init_params(seed, scale_last=scale_last)
+    rng = np.random.default_rng(seed + 100)
+    b = [bias * rng.standard_normal(x.shape) for x in b]
+    return W, b
+
+
+def fp32_net(ch, W, b):
+    """The oracle's parameters as the FP32 values the library holds."""
+    p = ch.gtheta_flatten(W, b)
+    return p, ch.gtheta_unflatten(p)
+
+
+@pytest.mark.parametrize("n", [16, 40, 63])
+def test_forward_matches_oracle(gpu_lib, n):
+    ch = gpu_lib
+    p, (W, b) = fp32_net(ch, *random_net(3))
+    net = ch.GTheta()
+    net.set_params(p)
+    B = 2
+    u = np.stack([ch_inputs.initial_condition(2, n, 10 + i, kind="normal", amp=0.5).reshape(n, n) for i in range(B)])
+    out = net.forward(dev(u)).cpu().numpy()
+    for i in range(B):
+        gq, aq = go.forward(u[i], W, b, bf16=True)
+        g64, a64 = go.forward(u[i], W, b)
+        r = out[i] - u[i]
+        scale = np.abs(aq[-1]).max()
+        dq = np.abs(r - aq[-1][..., 0])
+        assert np.quantile(dq, 0.99) <= 1e-5 * scale
+        assert dq.max() <= 1e-2 * scale
+        assert np.abs(r - a64[-1][..., 0]).max() <= 3e-2 * scale
+    # out may alias in
+    x = dev(u)
+    net.forward(x, out=x)
+    assert np.array_equal(x.cpu().numpy(), out)
+
+
+def test_forward_is_deterministic_and_batch_independent(gpu_lib):
+    ch = gpu_lib
+    p, _ = fp32_net(ch, *random_net(4))
+    net = ch.GTheta()
+    net.set_params(p)
+    n = 33
+    u = np.stack([ch_inputs.initial_condition(2, n, 20 + i, kind="normal", amp=0.5).reshape(n, n) for i in range(3)])
+    a = net.forward(dev(u)).cpu().numpy()
+    b = net.forward(dev(u)).cpu().numpy()
+    c = net.forward(dev(u[1:2])).cpu().numpy()
+    assert np.array_equal(a, b)
+    assert np.array_equal(a[1:2], c)
+
+
+@pytest.mark.parametrize("S,margin", [(24, 3), (43, 6)])
+def test_gradients_match_oracle(gpu_lib, S, margin):
+    ch = gpu_lib
+    p, (W, b) = fp32_net(ch, *random_net(5))
+    net = ch.GTheta()
+    net.set_params(p)
+    B = 2
+    rng = np.random.default_rng(S)
+    x = (0.6 * rng.standard_normal((B, S, S))).astype(np.float32)
+    t = (0.05 * rng.standard_normal((B, S, S))).astype(np.float32)
+    loss, grad = net.gradients(dev(x, torch.float32), dev(t, torch.float32), margin)
+    gW = [np.zeros_like(w) for w in W]
+    gb = [np.zeros_like(v) for v in b]
+    want_loss = 0.0
+    for i in range(B):
+        _, aq = go.forward(x[i].astype(np.float64), W, b, bf16=True)
+        li, dr = go.mse_crop_loss(aq[-1][..., 0], t[i].astype(np.float64), margin)
+        want_loss += li / B
+        gWi, gbi = go.backward(aq, W, dr / B, bf16=True)
+        for l in range(6):
+            gW[l] += gWi[l]
+            gb[l] += gbi[l]
+    assert abs(loss - want_loss) <= 1e-5 * want_loss
+    Wg, bg = ch.gtheta_unflatten(grad)
+    for l in range(6):
+        for got, want in ((Wg[l], gW[l]), (bg[l], gb[l])):
+            err = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert err <= 1e-3, (l, err)
+
+
+def test_first_adam_step_of_training(gpu_lib):
+    """One training step on a single snapshot pair: the crop is the whole (zero-padded) grid,
+    so the step's gradient is the gradient of that pair, and Adam's first step is
+    p - lr g / (|g| + 1e-8)."""
+    ch = gpu_lib
+    n, lr = 20, 1e-3
+    p0, _ = fp32_net(ch, *random_net(6))
+    net = ch.GTheta()
+    net.set_params(p0)
+    u0 = ch_inputs.initial_condition(2, n, 30, kind="normal", amp=0.5).reshape(n, n)
+    u1 = 0.8 * u0 + 0.05 * np.roll(u0, 1, axis=0)
+    states = dev(np.stack([u0, u1])[None])
+    S, m = n + 12, 6
+    x = np.zeros((1, S, S), np.float32)
+    t = np.zeros((1, S, S), np.float32)
+    x[0, m:m + n, m:m + n] = u0
+    t[0, m:m + n, m:m + n] = u1 - u0
+    loss, g = net.gradients(dev(x, torch.float32), dev(t, torch.float32), m)
+    losses = net.train(states, stride=1, steps=1, batch=2, lr=lr, seed=1)
+    assert abs(losses[0] - loss) <= 1e-6 * loss
+    p1 = net.get_params()
+    g64 = g.astype(np.float64)
+    want = p0 - lr * g64 / (np.abs(g64) + 1e-8)
+    assert np.abs(p1 - want).max() <= 1e-3 * lr + 1e-7
+
+
+def fine_states(ch, n, eps, T, nsnap, J, seeds, amp=0.05):
+    """Sequential fine solutions at nsnap - 1 equal intervals (the reference of a handle)."""
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=nsnap - 1, fine_steps=J, variant="NPA-I",
+                    newton_tol=1e-12)
+    with ch.Parareal(cfg, batch=len(seeds)) as pr:
+        pr.set_initial_batch(np.stack([ch_inputs.initial_condition(2, n, s, kind="normal", amp=amp)
+                                       for s in seeds]))
+        pr.compute_reference()
+        out = torch.empty((len(seeds), nsnap, n * n), dtype=torch.float64, device="cuda")
+        pr.get_reference_device(out)
+    return out
+
+
+def test_training_reduces_the_loss(gpu_lib):
+    ch = gpu_lib
+    n = 31
+    states = fine_states(ch, n, 0.05, 0.08, 17, 5, seeds=range(200, 208))
+    net = ch.GTheta(seed=3)
+    losses = net.train(states, stride=4, steps=300, batch=8, lr=2e-3, seed=9)
+    assert np.all(np.isfinite(losses))
+    assert losses[-30:].mean() < 0.2 * losses[:10].mean()
+
+
+def run_parareal(ch, cfg, u0, params=None, reference=True):
+    pr = ch.Parareal(cfg, batch=u0.shape[0])
+    pr.set_initial_batch(u0)
+    if reference:
+        pr.compute_reference()
+    if params is not None:
+        pr.set_coarse_model(params)
+    pr.run()
+    return pr
+
+
+@pytest.mark.parametrize("model", ["random", "sign-flip"])
+def test_parareal_with_gtheta_is_exact_after_n_iterations(gpu_lib, model):
+    """Any coarse propagator gives the sequential fine solution at k = N (slice n is exact after
+    n iterations). G(U) = -U (a network far from the dynamics) makes the increment grow at the
+    second iteration and trips the plain-step judge."""
+    ch = gpu_lib
+    n, N = 31, 6
+    cfg = ch.Config(dim=2, n=n, eps=0.05, T=0.03, n_slices=N, fine_steps=4, variant="NPA-I", newton_tol=1e-12)
+    if model == "random":
+        p, _ = fp32_net(ch, *random_net(7, bias=0.0, scale_last=0.1))
+    else:
+        p = scaling_net(ch, -2.0)
+    u0 = np.stack([ch_inputs.initial_condition(2, n, 40 + i, kind="normal", amp=0.05) for i in range(2)])
+    pr = run_parareal(ch, cfg, u0, params=p)
+    for b in range(2):
+        st = pr.stats(b)
+        assert st["iterations"] == N and st["coarse_model"] == 1
+        assert np.array_equal(pr.get_slices(b), pr.get_reference(b))
+        if model == "sign-flip":
+            assert st["coarse_fallback_iter"] == 2
+            assert st["inc"][1] > st["inc"][0]
+    pr.close()
+
+
+def test_plain_coarse_model_can_be_restored(gpu_lib):
+    ch = gpu_lib
+    n, N = 15, 4
+    cfg = ch.Config(dim=2, n=n, eps=0.05, T=0.02, n_slices=N, fine_steps=3, variant="NPA-I", newton_tol=1e-12,
+                    max_iters=2)
+    u0 = ch_inputs.initial_condition(2, n, 50, kind="normal", amp=0.05)[None]
+    plain = run_parareal(ch, cfg, u0, reference=False)
+    pr = ch.Parareal(cfg, batch=1)
+    pr.set_initial_batch(u0)
+    p, _ = fp32_net(ch, *random_net(8))
+    pr.set_coarse_model(p)
+    pr.set_coarse_model(None)
+    pr.run()
+    assert np.array_equal(pr.get_slices(0), plain.get_slices(0))
+    assert pr.stats(0)["coarse_model"] == 0
+    plain.close()
+    pr.close()
