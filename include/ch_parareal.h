@@ -217,9 +217,11 @@ const char* ch_gtheta_last_error(const ch_gtheta* g);
 ch_status ch_gtheta_set_params(ch_gtheta* g, const float* params_host, size_t len);
 ch_status ch_gtheta_get_params(ch_gtheta* g, float* params_host, size_t len);
 
-/* out = U + R(U) for `batch` FP64 n x n fields (device, [batch][n][n]; out may alias in);
- * n >= 1. Enqueued on the handle's stream. */
-ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, double* out_dev, int batch, int n);
+/* out = base + R(U) for `batch` FP64 n x n fields U = in_dev (device, [batch][n][n]); base_dev
+ * NULL means base = U (the residual form U + R(U)). out may alias in or base; n >= 1. Enqueued
+ * on the handle's stream. */
+ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, const double* base_dev, double* out_dev, int batch,
+                            int n);
 
 /* Loss and gradients for one minibatch: in_dev, target_dev FP32 [batch][S][S] (device); loss =
  * mean over the batch and the window [margin, S - margin)^2 of (R(in) - target)^2.
@@ -232,18 +234,29 @@ ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* ta
  * (device; e.g. the reference slices of a ch_parareal handle), pair (s, s + stride) for
  * s < nsnap - stride. Each of `steps` Adam steps (learning rate lr, betas 0.9 / 0.999,
  * eps 1e-8) draws `batch` crops (trajectory, snapshot, position from SplitMix64(seed)) of
- * min(76, n + 12) pixels and fits R(crop of U_s) to the crop of U_{s+stride} - U_s on the
- * crop's interior (6 pixels in from each side). losses_host: NULL or `steps` floats receiving
- * the minibatch losses. Synchronises. */
-ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, int ntraj, int nsnap, int n, int stride,
-                          int steps, int batch, double lr, unsigned long long seed, float* losses_host);
+ * min(76, n + 12) pixels and fits R(crop of U_s) to the crop of U_{s+stride} - base_s on the
+ * crop's interior (6 pixels in from each side). base_dev: NULL (base_s = U_s, the residual
+ * form) or FP64 [ntraj][nsnap][n][n] with base_s = G(U_s), the plain coarse step over the pair's
+ * interval (the correction form). Adam's moments carry over between calls (a learning-rate
+ * schedule is a sequence of calls). losses_host: NULL or `steps` floats receiving the
+ * minibatch losses. Synchronises. */
+ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, const double* base_dev, int ntraj, int nsnap,
+                          int n, int stride, int steps, int batch, double lr, unsigned long long seed,
+                          float* losses_host);
 
-/* Uses G_theta with these parameters (CH_GTHETA_PARAMS values, host) as the coarse propagator
- * of the next runs of a 2D handle; params_host = NULL (len 0) restores the plain coarse step.
- * The plain step stays as judge: when a problem's Parareal increment grows from one iteration
- * to the next, its remaining iterations use the plain step (G(U_n^k) recomputed with it).
- * CH_ERR_INVALID for dim = 1. */
-ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len);
+/* Forms of the learned coarse step. */
+typedef enum {
+  CH_GTHETA_RESIDUAL = 0,   /* G_theta(U) = U + R(U)                                         */
+  CH_GTHETA_CORRECTION = 1  /* G_theta(U) = G(U) + R(U), G the plain coarse step (R trained on
+                               F(U) - G(U), base_dev of ch_gtheta_train)                      */
+} ch_gtheta_form;
+
+/* Uses G_theta with these parameters (CH_GTHETA_PARAMS values, host) in form `form`
+ * (ch_gtheta_form) as the coarse propagator of the next runs of a 2D handle; params_host =
+ * NULL (len 0) restores the plain coarse step. The plain step stays as judge: when a problem's
+ * Parareal increment grows from one iteration to the next, its remaining iterations use the
+ * plain step (G(U_n^k) recomputed with it). CH_ERR_INVALID for dim = 1. */
+ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len, int form);
 
 /* Reference slices of all problems to device memory: batch (N+1) n^d values. */
 ch_status ch_parareal_get_reference_device(ch_parareal* h, double* out_dev, size_t len);

@@ -37,6 +37,7 @@ _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string
               "ch_gtheta_last_error")
 
 CH_GTHETA_PARAMS = 37601
+GTHETA_FORMS = {"residual": 0, "correction": 1}
 # Flat parameter layout of G_theta: layer l has W_l [3][3][Cout][Cin] then b_l [Cout].
 GTHETA_CHANNELS = [1, 32, 32, 32, 32, 32, 1]
 
@@ -127,7 +128,7 @@ def load(build_if_missing: bool = True):
     lib.ch_sine_transform_2d.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     f = C.POINTER(C.c_float)
-    lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz]
+    lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz, C.c_int]
     lib.ch_parareal_get_reference_device.argtypes = [vp, vp, sz]
     lib.ch_gtheta_create.argtypes = [C.c_ulonglong, vp, C.POINTER(vp)]
     lib.ch_gtheta_destroy.argtypes = [vp]
@@ -136,9 +137,9 @@ def load(build_if_missing: bool = True):
     lib.ch_gtheta_last_error.restype = C.c_char_p
     lib.ch_gtheta_set_params.argtypes = [vp, f, sz]
     lib.ch_gtheta_get_params.argtypes = [vp, f, sz]
-    lib.ch_gtheta_forward.argtypes = [vp, vp, vp, C.c_int, C.c_int]
+    lib.ch_gtheta_forward.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int]
     lib.ch_gtheta_gradients.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, f, sz, f]
-    lib.ch_gtheta_train.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+    lib.ch_gtheta_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                     C.c_ulonglong, f]
     for name in EXPORTED_SYMBOLS:
         if name not in _NO_STATUS:
@@ -254,14 +255,16 @@ class Parareal:
                 "kernel_launches": st.kernel_launches, "inner_iterations": st.inner_iterations,
                 "coarse_model": st.coarse_model, "coarse_fallback_iter": st.coarse_fallback_iter}
 
-    def set_coarse_model(self, params) -> None:
-        """Learned coarse propagator G_theta with these FP32 parameters (None: plain coarse step)."""
+    def set_coarse_model(self, params, form: str = "correction") -> None:
+        """Learned coarse propagator G_theta with these FP32 parameters (None: plain coarse step);
+        form "residual" (U + R(U)) or "correction" (G(U) + R(U))."""
+        f = GTHETA_FORMS[form]
         if params is None:
-            self._check(self.lib.ch_parareal_set_coarse_model(self._h, None, 0), "ch_parareal_set_coarse_model")
+            self._check(self.lib.ch_parareal_set_coarse_model(self._h, None, 0, f), "ch_parareal_set_coarse_model")
             return
         p = np.ascontiguousarray(params, dtype=np.float32)
-        self._check(self.lib.ch_parareal_set_coarse_model(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
-                    "ch_parareal_set_coarse_model")
+        self._check(self.lib.ch_parareal_set_coarse_model(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size,
+                                                          f), "ch_parareal_set_coarse_model")
 
     def get_reference_device(self, out_dev) -> None:
         self._check(self.lib.ch_parareal_get_reference_device(self._h, _dptr(out_dev), out_dev.numel()),
@@ -338,13 +341,13 @@ class GTheta:
                     "ch_gtheta_get_params")
         return p
 
-    def forward(self, u_dev, out=None):
-        """G_theta(U) of a CUDA float64 tensor [batch, n, n]."""
+    def forward(self, u_dev, out=None, base=None):
+        """base + R(U) (base = U when None) of a CUDA float64 tensor [batch, n, n]."""
         import torch
         if out is None:
             out = torch.empty_like(u_dev)
-        self._check(self.lib.ch_gtheta_forward(self._h, _dptr(u_dev), _dptr(out), u_dev.shape[0], u_dev.shape[-1]),
-                    "ch_gtheta_forward")
+        self._check(self.lib.ch_gtheta_forward(self._h, _dptr(u_dev), _dptr(base) if base is not None else None,
+                                               _dptr(out), u_dev.shape[0], u_dev.shape[-1]), "ch_gtheta_forward")
         return out
 
     def gradients(self, x_dev, target_dev, margin: int):
@@ -356,14 +359,19 @@ class GTheta:
                                                  g.size, C.byref(loss)), "ch_gtheta_gradients")
         return float(loss.value), g
 
-    def train(self, states_dev, stride: int, steps: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
-        """Adam on crops of snapshot pairs; states_dev: CUDA float64 [ntraj, nsnap, n, n] (or
-        [ntraj, nsnap, n*n] with square n). Returns the per-step minibatch losses."""
+    def train(self, states_dev, stride: int, steps: int, batch: int, lr: float, seed: int = 0,
+              base=None) -> np.ndarray:
+        """Adam on crops of snapshot pairs; states_dev (and base, the plain coarse step of each
+        snapshot for the correction form): CUDA float64 [ntraj, nsnap, n, n] (or [ntraj, nsnap,
+        n*n] with square n). Returns the per-step minibatch losses."""
         ntraj, nsnap = states_dev.shape[0], states_dev.shape[1]
         n = int(round((states_dev[0, 0].numel()) ** 0.5))
+        if base is not None and base.shape != states_dev.shape:
+            raise ValueError("base must have the shape of states")
         losses = np.empty(steps, dtype=np.float32)
-        self._check(self.lib.ch_gtheta_train(self._h, _dptr(states_dev), ntraj, nsnap, n, stride, steps, batch, lr,
-                                             seed, losses.ctypes.data_as(C.POINTER(C.c_float))), "ch_gtheta_train")
+        self._check(self.lib.ch_gtheta_train(self._h, _dptr(states_dev), _dptr(base) if base is not None else None,
+                                             ntraj, nsnap, n, stride, steps, batch, lr, seed,
+                                             losses.ctypes.data_as(C.POINTER(C.c_float))), "ch_gtheta_train")
         return losses
 
     def close(self) -> None:

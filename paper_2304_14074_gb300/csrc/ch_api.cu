@@ -66,6 +66,8 @@ struct ch_parareal {
   long long fine_cg = 0;               // CG iterations (batched) of the fine sweeps
   // learned coarse propagator (2D): null = plain coarse step
   chg3::GTheta* gt = nullptr;
+  int gt_form = CH_GTHETA_RESIDUAL;
+  double* Wtmp = nullptr;  // [B][pts] G_theta inputs of the correction form
   std::vector<int> h_learned, h_fallback;
   long long gt_launches = 0;
   long long aux_launches = 0;  // gather / scatter / correction kernels of the 2D driver
@@ -177,13 +179,23 @@ ch_status prop2(ch_parareal* h, int units, int scheme, double dt, int nsteps, si
 }
 
 // One coarse step of the work rows W[0, nb): rows [0, nl) with G_theta, the rest with the plain
-// coarse scheme.
+// coarse scheme. The correction form runs the plain step on every row and adds R of the row's
+// input to the first nl.
 ch_status coarse_rows(ch_parareal* h, int nb, int nl) {
+  const int scheme = coarse_of(h->cfg.variant);
+  if (nl > 0 && h->gt_form == CH_GTHETA_CORRECTION) {
+    CH_CUDA(h, cudaMemcpyAsync(h->Wtmp, h->W, (size_t)nl * h->pts * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    ch_status s = prop2(h, nb, scheme, h->p.dtc, h->p.coarse_steps);
+    if (s != CH_OK) return s;
+    CH_CUDA(h, h->gt->forward64(h->Wtmp, h->W, h->W, nl, h->cfg.n, h->st));
+    h->gt_launches += chg3::GTheta::kForwardKernels;
+    return CH_OK;
+  }
   if (nl > 0) {
-    CH_CUDA(h, h->gt->forward64(h->W, h->W, nl, h->cfg.n, h->st));
+    CH_CUDA(h, h->gt->forward64(h->W, nullptr, h->W, nl, h->cfg.n, h->st));
     h->gt_launches += chg3::GTheta::kForwardKernels;
   }
-  if (nb > nl) return prop2(h, nb - nl, coarse_of(h->cfg.variant), h->p.dtc, h->p.coarse_steps, (size_t)nl);
+  if (nb > nl) return prop2(h, nb - nl, scheme, h->p.dtc, h->p.coarse_steps, (size_t)nl);
   return CH_OK;
 }
 
@@ -401,6 +413,7 @@ void ch_parareal_destroy(ch_parareal* h) {
     h->gt->release();
     delete h->gt;
   }
+  cudaFree(h->Wtmp);
   delete h;
 }
 
@@ -737,9 +750,11 @@ ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out) {
   return CH_OK;
 }
 
-ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len) {
+ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len, int form) {
   if (!h) return CH_ERR_INVALID;
   if (h->dim != 2) return fail(h, CH_ERR_INVALID, "set_coarse_model: the learned coarse propagator is 2D only");
+  if (form != CH_GTHETA_RESIDUAL && form != CH_GTHETA_CORRECTION)
+    return fail(h, CH_ERR_INVALID, "set_coarse_model: unknown form");
   if (!params_host) {
     if (len != 0) return fail(h, CH_ERR_INVALID, "set_coarse_model: NULL parameters need len = 0");
     if (h->gt) {
@@ -756,7 +771,10 @@ ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host,
     if (!h->gt) return fail(h, CH_ERR_OOM, "set_coarse_model: host allocation");
     CH_CUDA(h, h->gt->init(0, h->st));
   }
+  if (form == CH_GTHETA_CORRECTION && !h->Wtmp)
+    CH_CUDA(h, cudaMalloc(&h->Wtmp, (size_t)h->B * h->pts * sizeof(double)));
   CH_CUDA(h, h->gt->set_params(params_host, h->st));
+  h->gt_form = form;
   return CH_OK;
 }
 

@@ -74,11 +74,13 @@ ch_status ch_gtheta_get_params(ch_gtheta* g, float* params_host, size_t len) {
   return gcuda(g, g->net.get_params(params_host, g->st), "get_params");
 }
 
-ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, double* out_dev, int batch, int n) {
+ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, const double* base_dev, double* out_dev, int batch,
+                            int n) {
   if (!g) return CH_ERR_INVALID;
   if (g->sticky != CH_OK) return g->sticky;
-  if (!in_dev || !out_dev || batch < 1 || n < 1 || n > 65535) return gfail(g, CH_ERR_INVALID, "forward: bad arguments");
-  return gcuda(g, g->net.forward64(in_dev, out_dev, batch, n, g->st), "forward");
+  if (!in_dev || !out_dev || batch < 1 || batch > 65535 || n < 1 || n > 65535)
+    return gfail(g, CH_ERR_INVALID, "forward: bad arguments");
+  return gcuda(g, g->net.forward64(in_dev, base_dev, out_dev, batch, n, g->st), "forward");
 }
 
 ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* target_dev, int batch, int S,
@@ -99,14 +101,16 @@ ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* ta
   return s;
 }
 
-ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, int ntraj, int nsnap, int n, int stride, int steps,
-                          int batch, double lr, unsigned long long seed, float* losses_host) {
+ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, const double* base_dev, int ntraj, int nsnap,
+                          int n, int stride, int steps, int batch, double lr, unsigned long long seed,
+                          float* losses_host) {
   if (!g) return CH_ERR_INVALID;
   if (g->sticky != CH_OK) return g->sticky;
   if (!states_dev || ntraj < 1 || stride < 1 || nsnap <= stride || n < 1 || n > 65535 || steps < 1 || batch < 1 ||
       batch > 65535 || !(lr > 0.0))
     return gfail(g, CH_ERR_INVALID, "train: bad arguments");
-  ch_status s = gcuda(g, g->net.train(states_dev, ntraj, nsnap, n, stride, steps, batch, lr, seed, g->st), "train");
+  ch_status s =
+      gcuda(g, g->net.train(states_dev, base_dev, ntraj, nsnap, n, stride, steps, batch, lr, seed, g->st), "train");
   if (s == CH_OK && losses_host) s = gcuda(g, g->net.read_losses(losses_host, steps, g->st), "train: losses");
   return s;
 }

@@ -176,10 +176,10 @@ __global__ void __launch_bounds__(kThreads) k_conv_first(const TIn* __restrict__
   }
 }
 
-// Last layer 32 -> 1: r = conv(a5, W6) + b6 (FP32); inference variant writes out = in + r (FP64).
+// Last layer 32 -> 1: r = conv(a5, W6) + b6 (FP32); inference variant writes out = base + r (FP64).
 __global__ void __launch_bounds__(kThreads) k_conv_last(const bf16* __restrict__ x, float* __restrict__ r,
-                                                        const float* __restrict__ P, int S, const double* __restrict__ in,
-                                                        double* __restrict__ out) {
+                                                        const float* __restrict__ P, int S,
+                                                        const double* __restrict__ base, double* __restrict__ out) {
   __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
   __shared__ float w[9 * kC + 1];
   const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_last(const bf16* __restrict__
   }
   const size_t o = ((size_t)img * S + Y) * S + X;
   if (r) r[o] = s;
-  if (out) out[o] = in[o] + (double)s;
+  if (out) out[o] = base[o] + (double)s;
 }
 
 // Loss on the window [margin, S - margin)^2: dr = 2 (r - t) / count there, 0 elsewhere;
@@ -414,20 +414,21 @@ __global__ void k_pack(const float* __restrict__ P, bf16* __restrict__ wf, bf16*
 }
 
 // Random crops of pairs: in = states[t][s] on [y0, y0+S) x [x0, x0+S) (0 outside the grid),
-// target = states[t][s + stride] - in there.
-__global__ void k_crops(const double* __restrict__ states, const int4* __restrict__ crops, int nsnap, int n,
-                        int stride, int S, float* __restrict__ in, float* __restrict__ tgt) {
+// target = states[t][s + stride] - base[t][s] there (base = states when null).
+__global__ void k_crops(const double* __restrict__ states, const double* __restrict__ base,
+                        const int4* __restrict__ crops, int nsnap, int n, int stride, int S, float* __restrict__ in,
+                        float* __restrict__ tgt) {
   const int b = blockIdx.y;
   const int4 c = crops[b];  // (traj, snap, y0, x0)
-  const size_t base = ((size_t)c.x * nsnap + c.y) * n * n;
-  const size_t base2 = ((size_t)c.x * nsnap + c.y + stride) * n * n;
+  const size_t off = ((size_t)c.x * nsnap + c.y) * n * n;
+  const size_t off2 = ((size_t)c.x * nsnap + c.y + stride) * n * n;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S * S; k += gridDim.x * blockDim.x) {
     const int yy = k / S, xx = k - yy * S;
     const int Y = c.z + yy, X = c.w + xx;
     double a = 0.0, t = 0.0;
     if (Y >= 0 && Y < n && X >= 0 && X < n) {
-      a = states[base + (size_t)Y * n + X];
-      t = states[base2 + (size_t)Y * n + X] - a;
+      a = states[off + (size_t)Y * n + X];
+      t = states[off2 + (size_t)Y * n + X] - (base ? base[off + (size_t)Y * n + X] : a);
     }
     in[(size_t)b * S * S + k] = (float)a;
     tgt[(size_t)b * S * S + k] = (float)t;
@@ -565,13 +566,14 @@ cudaError_t GTheta::forward_acts(const void* in, bool in64, int batch, int S, cu
   return cudaGetLastError();
 }
 
-cudaError_t GTheta::forward64(const double* in, double* out, int batch, int S, cudaStream_t st) {
+cudaError_t GTheta::forward64(const double* in, const double* base, double* out, int batch, int S,
+                              cudaStream_t st) {
   cudaError_t e = ensure(batch, S);
   if (e != cudaSuccess) return e;
   e = forward_acts(in, true, batch, S, st);
   if (e != cudaSuccess) return e;
   const dim3 grid((S + kTile - 1) / kTile, (S + kTile - 1) / kTile, batch);
-  k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], nullptr, master_, S, in, out);
+  k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], nullptr, master_, S, base ? base : in, out);
   return cudaGetLastError();
 }
 
@@ -610,8 +612,8 @@ cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, i
   return cudaGetLastError();
 }
 
-cudaError_t GTheta::train(const double* states, int ntraj, int nsnap, int n, int stride, int steps, int batch,
-                          double lr, unsigned long long seed, cudaStream_t st) {
+cudaError_t GTheta::train(const double* states, const double* base, int ntraj, int nsnap, int n, int stride,
+                          int steps, int batch, double lr, unsigned long long seed, cudaStream_t st) {
   // Crops of 76 x 76 with the loss on the central 64 x 64: the 13 x 13 receptive field of the
   // window stays inside the crop. A grid smaller than the window is taken whole (S = n + 12).
   const int margin = kTrainMargin, S = train_crop(n);
@@ -631,7 +633,8 @@ cudaError_t GTheta::train(const double* states, int ntraj, int nsnap, int n, int
     }
     e = cudaMemcpyAsync(crops_, crops.data(), batch * sizeof(int4), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) break;
-    k_crops<<<dim3((S * S + 255) / 256, batch), 256, 0, st>>>(states, crops_, nsnap, n, stride, S, a0_, tgt_);
+    k_crops<<<dim3((S * S + 255) / 256, batch), 256, 0, st>>>(states, base, crops_, nsnap, n, stride, S, a0_,
+                                                                       tgt_);
     // a0_ doubles as the crop input buffer: k_conv_first re-writes the same values into it
     e = grad_step(a0_, tgt_, batch, S, margin, it, st);
     if (e != cudaSuccess) break;

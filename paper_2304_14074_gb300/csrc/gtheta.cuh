@@ -23,15 +23,17 @@ class GTheta {
   void release();
   cudaError_t set_params(const float* host, cudaStream_t st);
   cudaError_t get_params(float* host, cudaStream_t st);
-  // out = U + R(U) for `batch` FP64 fields of size S x S (out may alias in).
-  cudaError_t forward64(const double* in, double* out, int batch, int S, cudaStream_t st);
+  // out = base + R(in) for `batch` FP64 fields of size S x S (base = in when null; out may alias
+  // in or base).
+  cudaError_t forward64(const double* in, const double* base, double* out, int batch, int S, cudaStream_t st);
   // One forward / backward on FP32 crops (size S, loss on the window [margin, S - margin)^2);
   // leaves the gradients in grad_ and the loss in loss_dev_[slot].
   cudaError_t grad_step(const float* in, const float* target, int batch, int S, int margin, int slot,
                         cudaStream_t st);
-  // Adam over `steps` minibatches of random crops of pairs (states[t][s], states[t][s + stride]);
-  // states: FP64 [ntraj][nsnap][n][n].
-  cudaError_t train(const double* states, int ntraj, int nsnap, int n, int stride, int steps, int batch,
+  // Adam over `steps` minibatches of random crops of pairs (states[t][s], states[t][s + stride]),
+  // fitting R(states[t][s]) to states[t][s + stride] - base[t][s] (base = states when null);
+  // states, base: FP64 [ntraj][nsnap][n][n].
+  cudaError_t train(const double* states, const double* base, int ntraj, int nsnap, int n, int stride, int steps, int batch,
                     double lr, unsigned long long seed, cudaStream_t st);
   cudaError_t read_losses(float* host, int count, cudaStream_t st);
   const float* grads() const { return grad_; }

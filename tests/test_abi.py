@@ -94,10 +94,10 @@ def test_gtheta_entry_points_reject_invalid_arguments_without_device():
     assert lib.ch_gtheta_last_error(None).decode() == "NULL handle"
     assert lib.ch_gtheta_set_params(None, None, 0) == 1
     assert lib.ch_gtheta_get_params(None, None, 0) == 1
-    assert lib.ch_gtheta_forward(None, None, None, 1, 8) == 1
+    assert lib.ch_gtheta_forward(None, None, None, None, 1, 8) == 1
     assert lib.ch_gtheta_gradients(None, None, None, 1, 8, 1, None, 0, None) == 1
-    assert lib.ch_gtheta_train(None, None, 1, 2, 8, 1, 1, 1, 1e-3, 0, None) == 1
-    assert lib.ch_parareal_set_coarse_model(None, None, 0) == 1
+    assert lib.ch_gtheta_train(None, None, None, 1, 2, 8, 1, 1, 1, 1e-3, 0, None) == 1
+    assert lib.ch_parareal_set_coarse_model(None, None, 0, 0) == 1
     assert lib.ch_parareal_get_reference_device(None, None, 0) == 1
 
 
