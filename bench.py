@@ -63,13 +63,17 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 FINE_SWEEP_1D_TRAFFIC = 223.7e6
 
 
-# 2D fine sweep, algorithmic HBM bytes per grid point: a sine-transform pass reads and writes an
-# FP32 field (8 B); a CG iteration = 4 passes + the pointwise sweeps (t = dt (wc - wbar) p: 12 B,
-# q = m p + That: 12 B, x/r update: 24 B, p update: 12 B); a Newton iteration adds the FP64
-# residual (z: 16 B, H: 28 B), weights (12 B), 4 passes for H and the correction, and the FP64
-# update (20 B).
-BYTES_CG_2D = 4 * 8 + 12 + 12 + 24 + 12
-BYTES_NEWTON_2D = 16 + 28 + 12 + 4 * 8 + 20
+# 2D fine sweep, algorithmic DRAM/L2 bytes per grid point and unit, each array read or written
+# once per phase. CG iteration (6 phases): p to physical space (read p, write t: 8), times
+# dt (wc - wbar) (read t, wc, write t2: 12), back to sine space (8), q = M p + That with (p, q)
+# (read t, p, write q: 12), x/r update with (r, r/m) (read p, x, r, q, write x, r: 24), p update
+# (read p, r, write p: 12). Newton iteration: z = c1 lap Y - dt g (read Y, write z FP64: 16), H and
+# weights (read Y, Yhat, z, write H, wc: 32), H to sine space and CG start (8 + 16), correction to
+# physical space (8), FP64 update (read d, Y, write Y: 20). Step: right-hand side (16) and
+# predictor (read Y, Yprev, write both: 32).
+BYTES_CG_2D = 8 + 12 + 8 + 12 + 24 + 12
+BYTES_NEWTON_2D = 16 + 32 + 8 + 16 + 8 + 20
+BYTES_STEP_2D = 16 + 32
 
 
 def u0_batch(w, rank):
@@ -264,10 +268,9 @@ def bench_ours(args, w, rank, world, local_rank):
                     "newton_iters_per_step_point": round(newton_per_step / (B * N * J), 3),
                     "algorithmic_fp64_flops_per_launch": alg_flops}
     else:
-        # 2D: newton_total sums Newton iterations over units; CG iterations are counted per batched
-        # iteration of all B N units
+        # 2D: newton_total and inner_iterations (CG) are summed over the B N units
         units = B * N
-        alg_bytes = pts * (newton_per_step * BYTES_NEWTON_2D + units * cg_per_step * BYTES_CG_2D)
+        alg_bytes = pts * (newton_per_step * BYTES_NEWTON_2D + cg_per_step * BYTES_CG_2D + units * J * BYTES_STEP_2D)
         achieved = alg_bytes / (fine_ms_per_launch / 1e3) / 1e9
         peak = measured_peaks().get("hbm_gbs", 6800.0)
         roofline = {"bound": "hbm", "kernel": "2D fine sweep (sine-transform passes + pointwise sweeps)",
@@ -276,7 +279,7 @@ def bench_ours(args, w, rank, world, local_rank):
                     "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
                     "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
                     "newton_iterations_per_unit_step": round(newton_per_step / (units * J), 3),
-                    "batched_cg_iterations_per_step": round(cg_per_step / J, 3),
+                    "cg_iterations_per_unit_step": round(cg_per_step / (units * J), 3),
                     "algorithmic_bytes_per_launch": alg_bytes,
                     "note": "working set per field 8.3 MB: L2-resident, so HBM bandwidth is a bound, not the limit"}
 

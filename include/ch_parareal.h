@@ -111,8 +111,8 @@ typedef struct {
   double coarse_sweep_ms;
   int fine_sweep_launches;
   int kernel_launches;
-  long long inner_iterations;     /* 2D: CG iterations of the fine sweeps (one count per batched
-                                     iteration of all units)                                  */
+  long long inner_iterations;     /* 2D: CG iterations of the fine sweeps, summed over the units
+                                     (problem-slices) they ran on                             */
   int coarse_model;               /* 1: this problem's coarse sweeps started with the learned
                                      propagator G_theta (ch_parareal_set_coarse_model)          */
   int coarse_fallback_iter;       /* iteration after which G_theta was replaced by the plain

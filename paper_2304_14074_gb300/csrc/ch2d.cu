@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -215,75 +217,8 @@ __device__ __forceinline__ double lap5(const double* X, int n, int i, int j) {
   return (w + e) + (s + no) - 4.0 * c;
 }
 
-// out = X - dt ih2 lap(X)   ((I - dt D_h) X)
-__global__ void k2_yhat(const double* __restrict__ X, double* __restrict__ out, int n, double dtih2) {
-  const size_t pts = (size_t)n * n;
-  const int u = blockIdx.y;
-  const double* Xu = X + u * pts;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    out[u * pts + k] = Xu[k] - dtih2 * lap5(Xu, n, i, j);
-  }
-}
-
 // Right-hand side of Eq. 2.5: b = u + dt D_h v, v = u^3 - 3u (frozen model: v = -2u).
 __device__ __forceinline__ double lin2_v(double u, int frozen) { return frozen ? -2.0 * u : u * u * u - 3.0 * u; }
-__global__ void k2_lin2_rhs(const double* __restrict__ X, double* __restrict__ out, int n, double dtih2, int frozen) {
-  const size_t pts = (size_t)n * n;
-  const int u = blockIdx.y;
-  const double* Xu = X + u * pts;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    const double c = lin2_v(Xu[k], frozen);
-    const double w = (j > 0) ? lin2_v(Xu[k - 1], frozen) : 0.0;
-    const double e = (j < n - 1) ? lin2_v(Xu[k + 1], frozen) : 0.0;
-    const double s = (i > 0) ? lin2_v(Xu[k - n], frozen) : 0.0;
-    const double no = (i < n - 1) ? lin2_v(Xu[k + n], frozen) : 0.0;
-    out[u * pts + k] = Xu[k] + dtih2 * ((w + e) + (s + no) - 4.0 * c);
-  }
-}
-
-// Newton predictor: g = 2 Y - Yprev (if have_prev) else Y; Yprev = Y; Y = g.
-__global__ void k2_predict(double* __restrict__ Y, double* __restrict__ Yp, size_t total, int have_prev) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
-    const double y = Y[k];
-    const double g = have_prev ? 2.0 * y - Yp[k] : y;
-    Yp[k] = y;
-    Y[k] = g;
-  }
-}
-
-// z = c1 lap(X) - dt g(X), g = X^3 (nonlinear, frozen: X), or wlin X (linear; wlin from W64 or const).
-__global__ void k2_z(const double* __restrict__ X, double* __restrict__ z, int n, double c1, double dt, int mode,
-                     const double* __restrict__ W64, double wconst, const int* __restrict__ skip) {
-  const size_t pts = (size_t)n * n;
-  const int u = blockIdx.y;
-  if (skip && skip[2 * u]) return;
-  const double* Xu = X + u * pts;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    const double x = Xu[k];
-    double g;
-    if (mode == 0) g = x * x * x;
-    else if (mode == 1) g = x;
-    else if (mode == 2) g = W64[u * pts + k] * W64[u * pts + k] * x;
-    else g = wconst * x;
-    z[u * pts + k] = c1 * lap5(Xu, n, i, j) - dt * g;
-  }
-}
-
-// H = (X - Bv) + ih2 lap(z), stored in FP32 for the solve.
-__global__ void k2_resid(const double* __restrict__ X, const double* __restrict__ Bv, const double* __restrict__ z,
-                         float* __restrict__ H, int n, double ih2, const int* __restrict__ skip) {
-  const size_t pts = (size_t)n * n;
-  const int u = blockIdx.y;
-  if (skip && skip[2 * u]) return;
-  const double* zu = z + u * pts;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / n), j = (int)(k - (size_t)i * n);
-    H[u * pts + k] = float((X[u * pts + k] - Bv[u * pts + k]) + ih2 * lap5(zu, n, i, j));
-  }
-}
 
 // Block reduction (fixed tree): sum or min/max of doubles.
 template <int OP>  // 0 sum, 1 max, 2 min
@@ -301,251 +236,8 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
   return r;
 }
 
-// Jacobian weights wc (FP32) and per-block min / max for wbar.
-// mode 0: wc = 3 Y^2; 1: wc = 1 (frozen); 2: wc = W64^2; 3: wc = const.
-__global__ void k2_weights(const double* __restrict__ Y, const double* __restrict__ W64, float* __restrict__ wc,
-                           int mode, double wconst, size_t pts, double* __restrict__ part, const int* __restrict__ skip) {
-  __shared__ double sh[kThreads / 32];
-  const int u = blockIdx.y;
-  if (skip && skip[2 * u]) return;
-  double lo = 1e300, hi = -1e300;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    float w;
-    if (mode == 0) {
-      const float y = float(Y[u * pts + k]);
-      w = 3.f * y * y;
-    } else if (mode == 1) {
-      w = 1.f;
-    } else if (mode == 2) {
-      const float y = float(W64[u * pts + k]);
-      w = y * y;
-    } else {
-      w = float(wconst);
-    }
-    wc[u * pts + k] = w;
-    lo = fmin(lo, (double)w);
-    hi = fmax(hi, (double)w);
-  }
-  const double bl = block_reduce<2>(lo, sh);
-  const double bh = block_reduce<1>(hi, sh);
-  if (threadIdx.x == 0) {
-    part[(size_t)u * 2 * kBlk + blockIdx.x] = bl;
-    part[(size_t)u * 2 * kBlk + kBlk + blockIdx.x] = bh;
-  }
-}
-
-// wbar per unit = (min wc + max wc) / 2 (minimises max |wc - wbar|).
-__global__ void k2_wbar(const double* __restrict__ part, double* __restrict__ scal, int units, const int* skip) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units || (skip && skip[2 * u])) return;
-  double lo = 1e300, hi = -1e300;
-  for (int b = 0; b < kBlk; ++b) {
-    lo = fmin(lo, part[(size_t)u * 2 * kBlk + b]);
-    hi = fmax(hi, part[(size_t)u * 2 * kBlk + kBlk + b]);
-  }
-  scal[u * 8 + 4] = 0.5 * (lo + hi);
-}
-
-__device__ __forceinline__ double sum_partials(const double* part, int u) {
-  double s = 0.0;
-  for (int b = 0; b < kBlk; ++b) s += part[(size_t)u * kBlk + b];
-  return s;
-}
-
 // m(p,q) = 1/mu + e2dt mu + cdt wbar (diagonal of the preconditioner M in sine space)
 __device__ __forceinline__ float mdiag(float mu, float e2dt, float cwb) { return 1.f / mu + e2dt * mu + cwb; }
-
-// Sine-space pointwise kernels: block b of unit u walks rows i = b, b + kBlk, ..., threads walk
-// columns; per-thread partial sums are FP32 (tens of terms), the block reduction is FP64.
-
-// CG start: bh = Hh / mu; x = 0; r = bh; p = r / m; rho partial = (r, r/m).
-__global__ void k2_cg_init(const float* __restrict__ Hh, float* __restrict__ xh, float* __restrict__ rh,
-                           float* __restrict__ ph, const float* __restrict__ mu1, int n, float e2dt, float cdt,
-                           const double* __restrict__ scal, double* __restrict__ part, const int* __restrict__ skip) {
-  __shared__ double sh[kThreads / 32];
-  const int u = blockIdx.y;
-  if (skip && skip[2 * u]) return;
-  const size_t pts = (size_t)n * n;
-  const float cwb = cdt * float(scal[u * 8 + 4]);
-  float acc = 0.f;
-  for (int i = blockIdx.x; i < n; i += kBlk) {
-    const float mi = mu1[i];
-    for (int j = threadIdx.x; j < n; j += kThreads) {
-      const size_t k = u * pts + (size_t)i * n + j;
-      const float mu = mi + mu1[j];
-      const float r = Hh[k] / mu;
-      const float z = r * __frcp_rn(mdiag(mu, e2dt, cwb));
-      xh[k] = 0.f;
-      rh[k] = r;
-      ph[k] = z;
-      acc += r * z;
-    }
-  }
-  const double s = block_reduce<0>((double)acc, sh);
-  if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = s;
-}
-
-// rho0 = rho = sum of partials; cg_done = 0 (or 1 if rho == 0).
-__global__ void k2_cg_start(const double* __restrict__ part, double* __restrict__ scal, int* __restrict__ flag,
-                            int units) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units || flag[2 * u]) return;
-  const double rho = sum_partials(part, u);
-  scal[u * 8 + 0] = rho;
-  scal[u * 8 + 1] = rho;
-  flag[2 * u + 1] = (rho <= 0.0) ? 1 : 0;
-}
-
-// t = cdt (wc - wbar) p  (physical space)
-__global__ void k2_cg_wprod(const float* __restrict__ p, const float* __restrict__ wc, float* __restrict__ t,
-                            size_t pts, float cdt, const double* __restrict__ scal, const int* __restrict__ flag) {
-  const int u = blockIdx.y;
-  if (flag[2 * u] || flag[2 * u + 1]) return;
-  const float wb = float(scal[u * 8 + 4]);
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x)
-    t[u * pts + k] = cdt * (wc[u * pts + k] - wb) * p[u * pts + k];
-}
-
-// q = m p + That; sigma partial = (p, q)
-__global__ void k2_cg_q(const float* __restrict__ ph, float* __restrict__ qh, const float* __restrict__ mu1, int n,
-                        float e2dt, float cdt, const double* __restrict__ scal, double* __restrict__ part,
-                        const int* __restrict__ flag) {
-  __shared__ double sh[kThreads / 32];
-  const int u = blockIdx.y;
-  if (flag[2 * u] || flag[2 * u + 1]) return;
-  const size_t pts = (size_t)n * n;
-  const float cwb = cdt * float(scal[u * 8 + 4]);
-  float acc = 0.f;
-  for (int i = blockIdx.x; i < n; i += kBlk) {
-    const float mi = mu1[i];
-    for (int j = threadIdx.x; j < n; j += kThreads) {
-      const size_t k = u * pts + (size_t)i * n + j;
-      const float p = ph[k];
-      const float q = mdiag(mi + mu1[j], e2dt, cwb) * p + qh[k];
-      qh[k] = q;
-      acc += p * q;
-    }
-  }
-  const double s = block_reduce<0>((double)acc, sh);
-  if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = s;
-}
-
-// alpha = rho / sigma; x += alpha p; r -= alpha q; rho' partial = (r, r/m)
-__global__ void k2_cg_step(float* __restrict__ xh, float* __restrict__ rh, const float* __restrict__ ph,
-                           const float* __restrict__ qh, const float* __restrict__ mu1, int n, float e2dt, float cdt,
-                           const double* __restrict__ scal, const double* __restrict__ part_sig,
-                           double* __restrict__ part, const int* __restrict__ flag) {
-  __shared__ double sh[kThreads / 32];
-  const int u = blockIdx.y;
-  if (flag[2 * u] || flag[2 * u + 1]) return;
-  const size_t pts = (size_t)n * n;
-  const double sig = sum_partials(part_sig, u);
-  const float alpha = (sig > 0.0) ? float(scal[u * 8 + 0] / sig) : 0.f;
-  const float cwb = cdt * float(scal[u * 8 + 4]);
-  float acc = 0.f;
-  for (int i = blockIdx.x; i < n; i += kBlk) {
-    const float mi = mu1[i];
-    for (int j = threadIdx.x; j < n; j += kThreads) {
-      const size_t k = u * pts + (size_t)i * n + j;
-      xh[k] += alpha * ph[k];
-      const float r = rh[k] - alpha * qh[k];
-      rh[k] = r;
-      acc += r * r * __frcp_rn(mdiag(mi + mu1[j], e2dt, cwb));
-    }
-  }
-  const double s = block_reduce<0>((double)acc, sh);
-  if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = s;
-}
-
-// beta = rho'/rho; p = r/m + beta p. Convergence when rho' <= tol^2 rho0.
-__global__ void k2_cg_dir(float* __restrict__ ph, const float* __restrict__ rh, const float* __restrict__ mu1, int n,
-                          float e2dt, float cdt, double* __restrict__ scal, const double* __restrict__ part,
-                          int* __restrict__ flag, double tol2) {
-  const int u = blockIdx.y;
-  if (flag[2 * u] || flag[2 * u + 1]) return;
-  const size_t pts = (size_t)n * n;
-  const double rho_new = sum_partials(part, u);
-  const double rho = scal[u * 8 + 0];
-  const float beta = (rho > 0.0) ? float(rho_new / rho) : 0.f;
-  const float cwb = cdt * float(scal[u * 8 + 4]);
-  for (int i = blockIdx.x; i < n; i += kBlk) {
-    const float mi = mu1[i];
-    for (int j = threadIdx.x; j < n; j += kThreads) {
-      const size_t k = u * pts + (size_t)i * n + j;
-      ph[k] = rh[k] * __frcp_rn(mdiag(mi + mu1[j], e2dt, cwb)) + beta * ph[k];
-    }
-  }
-}
-
-// Scalar bookkeeping after k2_cg_dir (one thread per unit): rho = rho', done test.
-__global__ void k2_cg_end(double* __restrict__ scal, const double* __restrict__ part, int* __restrict__ flag,
-                          int units, double tol2) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units || flag[2 * u] || flag[2 * u + 1]) return;
-  const double rho_new = sum_partials(part, u);
-  scal[u * 8 + 0] = rho_new;
-  if (!(rho_new > tol2 * scal[u * 8 + 1])) flag[2 * u + 1] = 1;  // also catches NaN
-}
-
-// X -= d (FP64 update from the FP32 correction); per-block max |d|; non-finite check.
-__global__ void k2_update(double* __restrict__ X, const float* __restrict__ d, size_t pts, double* __restrict__ part,
-                          const int* __restrict__ flag, unsigned* __restrict__ status) {
-  __shared__ double sh[kThreads / 32];
-  const int u = blockIdx.y;
-  if (flag[2 * u]) return;
-  double m = 0.0;
-  bool bad = false;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
-    const float v = d[u * pts + k];
-    bad |= !isfinite(v);
-    X[u * pts + k] -= (double)v;
-    m = fmax(m, (double)fabsf(v));
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
-  const double bm = block_reduce<1>(m, sh);
-  if (threadIdx.x == 0) part[(size_t)u * kBlk + blockIdx.x] = bm;
-}
-
-// Newton bookkeeping per unit: stop on max|d| <= tol or at the FP64 rounding floor (an
-// increment below sqrt(tol) that fails to halve the previous one); count iterations.
-// ctr[0] is the 0-based Newton iteration of the batch; the last allowed one flags failure.
-__global__ void k2_newton_end(double* __restrict__ scal, const double* __restrict__ part, int* __restrict__ flag,
-                              int* __restrict__ cnt, int units, double tol, double floor_, const int* __restrict__ ctr,
-                              int newton_max, unsigned* status) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int last = (ctr[0] >= newton_max - 1);
-  if (u >= units || flag[2 * u]) return;
-  double dm = 0.0;
-  for (int b = 0; b < kBlk; ++b) dm = fmax(dm, part[(size_t)u * kBlk + b]);
-  const int m = ++cnt[u];
-  const double prev = scal[u * 8 + 6];
-  bool done = dm <= tol || (m >= 2 && dm <= floor_ && dm > 0.5 * prev);
-  scal[u * 8 + 6] = dm;
-  if (!done && last) {
-    atomicOr(status, ST_NEWTON);
-    done = true;
-  }
-  if (done) flag[2 * u] = 1;
-}
-
-// Loop control of the device-driven Newton and CG loops (single block). which = 0: Newton
-// (continue while a unit is not converged and fewer than lim iterations ran); 1: CG.
-__global__ void k2_loop_cond(cudaGraphConditionalHandle hnd, const int* __restrict__ flag, int units,
-                             int* __restrict__ ctr, int which, int lim, unsigned long long* __restrict__ total) {
-  __shared__ int c;
-  if (threadIdx.x == 0) c = 0;
-  __syncthreads();
-  int local = 0;
-  for (int u = threadIdx.x; u < units; u += blockDim.x)
-    local += (which == 0) ? (flag[2 * u] == 0) : (flag[2 * u] == 0 && flag[2 * u + 1] == 0);
-  if (local) atomicAdd(&c, local);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int it = ++ctr[which];
-    if (total) *total += 1ull;
-    cudaGraphSetConditional(hnd, (c > 0 && it < lim) ? 1u : 0u);
-  }
-}
 
 // Start of a loop: counter = 0 and, for a nested loop, its condition = 1.
 __global__ void k2_loop_start(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, int which, int set_cond) {
@@ -556,29 +248,6 @@ __global__ void k2_loop_start(cudaGraphConditionalHandle hnd, int* __restrict__ 
 }
 
 
-
-__global__ void k2_reset_flags(int* __restrict__ flag, int* __restrict__ cnt, double* __restrict__ scal, int units) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units) return;
-  flag[2 * u] = 0;
-  flag[2 * u + 1] = 0;
-  cnt[u] = 0;
-  scal[u * 8 + 6] = 0.0;
-}
-
-__global__ void k2_cg_reopen(int* __restrict__ flag, int units) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < units) flag[2 * u + 1] = 0;
-}
-
-// Newton statistics of one step into device totals.
-__global__ void k2_newton_stats(const int* __restrict__ cnt, int units, unsigned long long* __restrict__ tot,
-                                int* __restrict__ peak) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units) return;
-  atomicAdd(tot, (unsigned long long)cnt[u]);
-  atomicMax(peak, cnt[u]);
-}
 
 template <typename K>
 cudaError_t prep(K kernel, size_t smem) {
@@ -733,6 +402,11 @@ size_t correct_partials(int count) { return (size_t)count * 3 * kBlk; }
 
 cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   if (!supported_n(p.n) || cap < 1) return cudaErrorInvalidValue;
+  // CH_2D_STEP=persistent selects the one-kernel execution of a propagation (default: graphs)
+  const char* env = std::getenv("CH_2D_STEP");
+  path_ = (env && std::strcmp(env, "persistent") == 0) ? PATH_PERSISTENT : PATH_GRAPH;
+  const char* mb = std::getenv("CH_2D_MINB");
+  persist_minb_ = mb ? std::atoi(mb) : 3;
   p_ = p;
   cap_ = cap;
   pts_ = (size_t)p.n * p.n;
@@ -763,7 +437,11 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   al((void**)&newton_cnt_, (size_t)cap * sizeof(int));
   al((void**)&status_, 4 * sizeof(unsigned) + sizeof(unsigned long long));
   al((void**)&ctr_, 4 * sizeof(int));
-  al((void**)&cg_dev_, 2 * sizeof(unsigned long long));  // [0] CG, [1] Newton loop passes (batched)
+  // [0] CG iterations (batched), [1] Newton passes (batched), [2] CG iterations summed over units
+  al((void**)&cg_dev_, 4 * sizeof(unsigned long long));
+  al((void**)&ppart_, (size_t)7 * cap * ((p.n + kDstRows - 1) / kDstRows) * sizeof(double));
+  al((void**)&active_, 4 * sizeof(int));
+  al((void**)&bar_, 4 * sizeof(unsigned));
   if (e != cudaSuccess) return e;
   e = cudaHostAlloc((void**)&host_cnt_, 4 * sizeof(int), 0);
   if (e != cudaSuccess) return e;
@@ -780,7 +458,7 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   e = cudaMemcpyAsync(mu_, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 4 * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
@@ -789,7 +467,7 @@ void Prop2D::release() {
   for (auto& c : graphs_) cudaGraphExecDestroy(c.second);
   graphs_.clear();
   void* ptrs[] = {yhat_, yprev_, z_, xacc_, w_, rhs_, xh_, rh_, ph_, qh_, tmp_, tmp2_, mu_, tw_, part_, scal_, flag_,
-                  newton_cnt_, status_, ctr_, cg_dev_};
+                  newton_cnt_, status_, ctr_, cg_dev_, ppart_, active_, bar_};
   for (void* q : ptrs) cudaFree(q);
   if (host_cnt_) cudaFreeHost(host_cnt_);
   host_cnt_ = nullptr;
@@ -800,6 +478,9 @@ void Prop2D::release() {
   flag_ = newton_cnt_ = ctr_ = nullptr;
   status_ = nullptr;
   cg_dev_ = nullptr;
+  ppart_ = nullptr;
+  active_ = nullptr;
+  bar_ = nullptr;
 }
 
 cudaError_t Prop2D::dst2(const float* in, float* out, int units, cudaStream_t st) {
@@ -808,25 +489,6 @@ cudaError_t Prop2D::dst2(const float* in, float* out, int units, cudaStream_t st
   return e;
 }
 
-
-// One CG iteration in sine space (enqueued on st; the body of the CG loop).
-cudaError_t Prop2D::enqueue_cg_iteration(int units, double dt, cudaStream_t st) {
-  const dim3 grid(kBlk, units);
-  const float fe2dt = float(p_.eps2 * dt), fdt = float(dt);
-  cudaError_t e = dst2(ph_, tmp_, units, st);  // p (physical)
-  if (e != cudaSuccess) return e;
-  k2_cg_wprod<<<grid, kThreads, 0, st>>>(tmp_, w_, tmp_, pts_, fdt, scal_, flag_);
-  e = dst2(tmp_, qh_, units, st);  // That
-  if (e != cudaSuccess) return e;
-  k2_cg_q<<<grid, kThreads, 0, st>>>(ph_, qh_, mu_, p_.n, fe2dt, fdt, scal_, part_, flag_);
-  k2_cg_step<<<grid, kThreads, 0, st>>>(xh_, rh_, ph_, qh_, mu_, p_.n, fe2dt, fdt, scal_, part_,
-                                        part_ + (size_t)cap_ * kBlk, flag_);
-  k2_cg_dir<<<grid, kThreads, 0, st>>>(ph_, rh_, mu_, p_.n, fe2dt, fdt, scal_, part_ + (size_t)cap_ * kBlk, flag_,
-                                       p_.cg_tol * p_.cg_tol);
-  k2_cg_end<<<(units + 255) / 256, 256, 0, st>>>(scal_, part_ + (size_t)cap_ * kBlk, flag_, units,
-                                                  p_.cg_tol * p_.cg_tol);
-  return cudaGetLastError();
-}
 
 namespace {
 
@@ -866,127 +528,9 @@ cudaError_t capture_graph(cudaStream_t st, cudaGraph_t* g) {
 // Captures one implicit step of the batch as a graph: the right-hand side kernels, then a
 // device-driven Newton loop whose body forms the FP64 residual, runs a device-driven CG loop
 // in sine space and applies the correction. Nothing returns to the host inside the step.
-cudaError_t Prop2D::build_step(const StepKey& k, cudaGraphExec_t* out) {
-  const int units = k.units;
-  const dim3 grid(kBlk, units);
-  const double dt = k.dt, ih2 = 1.0 / (p_.h * p_.h), c1 = p_.eps2 * dt * ih2;
-  double* Y = k.Y;
-  const size_t total = (size_t)units * pts_;
-  int zmode, wmode;
-  const double* W64 = nullptr;
-  double wconst = 0.0;
-  if (k.scheme == SCHEME_NL) {
-    zmode = wmode = p_.frozen ? 1 : 0;
-  } else if (k.scheme == SCHEME_LIN1) {
-    zmode = wmode = p_.frozen ? 3 : 2;
-    W64 = yprev_;
-    wconst = 1.0;
-  } else {
-    zmode = wmode = 3;
-    wconst = 2.0;
-  }
-  cudaStream_t cs = nullptr, bs = nullptr, bs2 = nullptr;
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs2, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  cudaGraphConditionalHandle hN = 0, hC = 0;
-  if (e == cudaSuccess) {
-    // right-hand side b (in yhat_) and starting point
-    if (k.scheme == SCHEME_NL) {
-      k2_yhat<<<grid, kThreads, 0, cs>>>(Y, yhat_, p_.n, dt * ih2);
-      k2_predict<<<(unsigned)((total + 1023) / 1024), 1024, 0, cs>>>(Y, yprev_, total, k.have_prev);
-    } else {
-      cudaMemcpyAsync(yprev_, Y, total * sizeof(double), cudaMemcpyDeviceToDevice, cs);
-      if (k.scheme == SCHEME_LIN1) k2_yhat<<<grid, kThreads, 0, cs>>>(yprev_, yhat_, p_.n, dt * ih2);
-      else k2_lin2_rhs<<<grid, kThreads, 0, cs>>>(yprev_, yhat_, p_.n, dt * ih2, p_.frozen);
-    }
-    k2_reset_flags<<<(units + 255) / 256, 256, 0, cs>>>(flag_, newton_cnt_, scal_, units);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = capture_graph(cs, &g);
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hN, g, 1, cudaGraphCondAssignDefault);
-  if (e == cudaSuccess) {
-    k2_loop_start<<<1, 32, 0, cs>>>(hN, ctr_, 0, 0);
-    e = cudaGetLastError();
-  }
-  cudaGraph_t bodyN = nullptr;
-  if (e == cudaSuccess) e = add_while(cs, &hN, 1, cudaGraphCondAssignDefault, &bodyN);
-  // ---- Newton body
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    k2_z<<<grid, kThreads, 0, bs>>>(Y, z_, p_.n, c1, dt, zmode, W64, wconst, flag_);
-    k2_resid<<<grid, kThreads, 0, bs>>>(Y, yhat_, z_, rhs_, p_.n, ih2, flag_);
-    k2_weights<<<grid, kThreads, 0, bs>>>(Y, W64, w_, wmode, wconst, pts_, part_, flag_);
-    k2_wbar<<<(units + 255) / 256, 256, 0, bs>>>(part_, scal_, units, flag_);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = dst2(rhs_, qh_, units, bs);  // H in sine space
-  if (e == cudaSuccess) {
-    const float fe2dt = float(p_.eps2 * dt), fdt = float(dt);
-    k2_cg_reopen<<<(units + 255) / 256, 256, 0, bs>>>(flag_, units);
-    k2_cg_init<<<grid, kThreads, 0, bs>>>(qh_, xh_, rh_, ph_, mu_, p_.n, fe2dt, fdt, scal_, part_, flag_);
-    k2_cg_start<<<(units + 255) / 256, 256, 0, bs>>>(part_, scal_, flag_, units);
-    e = cudaGetLastError();
-  }
-  cudaGraph_t gN = nullptr;
-  if (e == cudaSuccess) e = capture_graph(bs, &gN);
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hC, gN, 0, 0);
-  if (e == cudaSuccess) {
-    k2_loop_start<<<1, 32, 0, bs>>>(hC, ctr_, 1, 1);
-    e = cudaGetLastError();
-  }
-  cudaGraph_t bodyC = nullptr;
-  if (e == cudaSuccess) e = add_while(bs, &hC, 0, 0, &bodyC);
-  // ---- CG body
-  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs2, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) e = enqueue_cg_iteration(units, dt, bs2);
-  if (e == cudaSuccess) {
-    k2_loop_cond<<<1, 256, 0, bs2>>>(hC, flag_, units, ctr_, 1, p_.cg_max, cg_dev_);
-    e = cudaGetLastError();
-  }
-  {
-    cudaGraph_t dummy = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(bs2, &dummy);
-    if (e == cudaSuccess) e = e2;
-  }
-  // ---- back in the Newton body: correction d = S^{-1} ... in physical space, update, stop test
-  if (e == cudaSuccess) e = dst2(xh_, tmp_, units, bs);
-  if (e == cudaSuccess) {
-    k2_update<<<grid, kThreads, 0, bs>>>(Y, tmp_, pts_, part_, flag_, status_);
-    k2_newton_end<<<(units + 255) / 256, 256, 0, bs>>>(scal_, part_, flag_, newton_cnt_, units, p_.newton_tol,
-                                                        std::sqrt(p_.newton_tol), ctr_, p_.newton_max, status_);
-    k2_loop_cond<<<1, 256, 0, bs>>>(hN, flag_, units, ctr_, 0, p_.newton_max, cg_dev_ + 1);
-    e = cudaGetLastError();
-  }
-  {
-    cudaGraph_t dummy = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(bs, &dummy);
-    if (e == cudaSuccess) e = e2;
-  }
-  if (e == cudaSuccess) {
-    k2_newton_stats<<<(units + 255) / 256, 256, 0, cs>>>(newton_cnt_, units,
-                                                          reinterpret_cast<unsigned long long*>((int*)status_ + 4),
-                                                          (int*)status_ + 3);
-    e = cudaGetLastError();
-  }
-  {
-    cudaGraph_t dummy = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(cs, &dummy);
-    if (e == cudaSuccess) e = e2;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
-  if (g) cudaGraphDestroy(g);
-  if (cs) cudaStreamDestroy(cs);
-  if (bs) cudaStreamDestroy(bs);
-  if (bs2) cudaStreamDestroy(bs2);
-  return e;
-}
-
 cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
   if (units > cap_ || units < 1) return cudaErrorInvalidValue;
+  if (path_ == PATH_PERSISTENT) return propagate_persistent(Y, units, scheme, dt, nsteps, st);
   for (int j = 0; j < nsteps; ++j) {
     StepKey k{Y, units, scheme, dt, (scheme == SCHEME_NL && j > 0) ? 1 : 0};
     cudaGraphExec_t ex = nullptr;
@@ -1009,7 +553,7 @@ cudaError_t Prop2D::reset_counters(cudaStream_t st) {
   newton_peak_ = 0;
   cg_total_ = 0;
   cudaError_t e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 4 * sizeof(unsigned long long), st);
   return e;
 }
 
@@ -1018,14 +562,903 @@ unsigned Prop2D::read_status(cudaStream_t st) {
   unsigned long long tot = 0;
   cudaMemcpyAsync(s, status_, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&tot, (int*)status_ + 4, sizeof(tot), cudaMemcpyDeviceToHost, st);
-  unsigned long long cgt[2] = {0, 0};
+  unsigned long long cgt[4] = {0, 0, 0, 0};
   cudaMemcpyAsync(cgt, cg_dev_, sizeof(cgt), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   cg_total_ = (long long)cgt[0];
   newton_passes_ = (long long)cgt[1];
+  cg_unit_total_ = (long long)cgt[2];
   newton_total_ = tot;
   newton_peak_ = (int)s[3];
   return s[0];
+}
+
+// ------------------------------------------------------------------ persistent fine sweep
+//
+// The whole propagation (nsteps implicit steps, each an FP64 Newton loop around FP32 CG in sine
+// space) as one cooperative kernel. Work items are (unit, block of kDstRows rows); every phase
+// below is a loop of the grid's blocks over the items of the units that are still active,
+// and phases are separated by a grid barrier (all blocks are co-resident: cooperative launch).
+// The transform passes carry the pointwise work of the graph path in their epilogues. Loop
+// exits are decided from counters read after a barrier, so every block takes the same
+// branches; a barrier that waits too long sets ST_TIMEOUT and every block returns.
+// Arguments of the step phases (shared by the graph and the persistent execution).
+struct PArgs {
+  double* Y;
+  double* yhat;
+  double* yprev;
+  double* z;
+  float* w;
+  float* rhs;
+  float* xh;
+  float* rh;
+  float* ph;
+  float* qh;
+  float* tmp;
+  float* t2;
+  const float* mu1;
+  const float2* tw;
+  double* pmin;   // [units][nb] per item: min wc
+  double* pmax;   //                 max wc
+  double* psig;   //                 (p, q)
+  double* prho;   // [2][units][nb]  (r, r / m)
+  double* prho0;  // [units][nb]     rho at the start of CG
+  double* pd;     // [units][nb]     max |d|
+  int* flag;      // [units][2]: Newton done, CG done
+  int* cnt;       // [units] Newton iterations of the step
+  double* scal;   // [units][8]: [6] previous max |d|
+  unsigned* status;
+  unsigned long long* totals;  // [0] batched CG iterations, [1] batched Newton passes
+  int* active;    // [0..1] CG, [2..3] Newton: units still iterating (parity slots)
+  unsigned* bar;  // [0] arrivals, [1] generation, [2] abort
+  int* ctr;       // graph path: [0] Newton, [1] CG iteration of the loop being replayed
+  const double* W64;
+  double wconst, dt, ih2, c1, tol, floor_, cg_tol2;
+  float fe2dt, fdt;
+  int units, nsteps, scheme, zmode, newton_max, cg_max, have_prev0, frozen;
+};
+
+namespace {
+
+constexpr unsigned kBarrierSpins = 1u << 22;  // x ~0.5 us sleeps: a stuck barrier gives up in ~2 s
+
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = bar + 1;
+    volatile unsigned* abort_ = bar + 2;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*gen == g) {
+        if (*abort_ || ++spins > kBarrierSpins) {
+          ok = 0;
+          atomicExch(bar + 2, 1u);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int N>
+__device__ __forceinline__ double unit_wbar(const PArgs& a, int u) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  double lo = 1e300, hi = -1e300;
+  for (int b = 0; b < nb; ++b) {
+    lo = fmin(lo, a.pmin[(size_t)u * nb + b]);
+    hi = fmax(hi, a.pmax[(size_t)u * nb + b]);
+  }
+  return 0.5 * (lo + hi);
+}
+
+template <int N>
+__device__ __forceinline__ double unit_sum(const double* p, int u) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += p[(size_t)u * nb + b];
+  return s;
+}
+
+// Calls f as a separate function: the persistent kernel's register allocation is then that of
+// its largest phase, not of all phases inlined together.
+template <typename F>
+__device__ __noinline__ void noinl(const F& f) {
+  f();
+}
+
+enum Epi { E_PLAIN = 0, E_WPROD, E_Q, E_INIT, E_UPDATE };
+
+// One transform pass over the items of active units: rows [a0, a0 + kDstRows) of `in` ->
+// DST-I -> column a of the output (transposed), then the epilogue.
+//   E_PLAIN: out = v;  E_WPROD: out = dt (wc - wbar) v;  E_Q: q = m p + v, sum p q;
+//   E_INIT: b = v / mu, r = b, p = r / m, x = 0, sum r p;  E_UPDATE: Y -= v, max |v|.
+// `act` selects the units: 0 = not Newton-done, 1 = not Newton-done and not CG-done.
+template <int N, int EPI>
+__device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const float2* twd, const float* in, float* out,
+                                         int act, double* part, int item) {
+  constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int U = 2;  // epilogue elements per thread whose loads are issued together
+  __shared__ double sh[kThreads / 32];
+  const size_t pts = (size_t)n * n;
+  const float sc = 0.5f * sqrtf(2.0f / N);
+  const float* __restrict__ mu1 = a.mu1;
+  const float* __restrict__ wv = a.w;
+  const float* __restrict__ ph = a.ph;
+  float* __restrict__ qh = a.qh;
+  float* __restrict__ xh = a.xh;
+  float* __restrict__ rh = a.rh;
+  float* __restrict__ pw = a.ph;
+  double* __restrict__ Y = a.Y;
+  float* __restrict__ dst = out;
+  {
+    const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+    if (a.flag[2 * u] || (act == 1 && a.flag[2 * u + 1])) return;  // block-uniform
+    fft_rows<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
+    float cwb = 0.f;
+    if (EPI == E_WPROD || EPI == E_Q || EPI == E_INIT) cwb = float(unit_wbar<N>(a, u));
+    const float fcwb = a.fdt * cwb;
+    double acc = 0.0;
+    bool bad = false;
+    for (int i0 = threadIdx.x; i0 < n * kDstRows; i0 += U * kThreads) {
+      float v[U], ld[U];
+      size_t o[U];
+      int kk[U], cc[U];
+      bool ok[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int idx = i0 + q * kThreads;
+        const int k = idx / kDstRows, r = idx - k * kDstRows;
+        kk[q] = k;
+        cc[q] = a0 + r;
+        ok[q] = idx < n * kDstRows && cc[q] < n;
+        o[q] = u * pts + (size_t)k * n + cc[q];
+        v[q] = 0.f;
+        ld[q] = 0.f;
+        if (ok[q]) {
+          const float2 c = buf[pad8((r >> 1) * L + k + 1)];
+          v[q] = (r & 1) ? c.x * sc : -c.y * sc;
+          if (EPI == E_WPROD) ld[q] = wv[o[q]];
+          if (EPI == E_Q) ld[q] = ph[o[q]];
+        }
+      }
+      double yv[U];
+      if (EPI == E_UPDATE) {
+#pragma unroll
+        for (int q = 0; q < U; ++q) yv[q] = ok[q] ? Y[o[q]] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (!ok[q]) continue;
+        if (EPI == E_PLAIN) {
+          dst[o[q]] = v[q];
+        } else if (EPI == E_WPROD) {
+          dst[o[q]] = a.fdt * (ld[q] - cwb) * v[q];
+        } else if (EPI == E_Q) {
+          const float qv = mdiag(mu1[kk[q]] + mu1[cc[q]], a.fe2dt, fcwb) * ld[q] + v[q];
+          qh[o[q]] = qv;
+          acc += (double)(ld[q] * qv);
+        } else if (EPI == E_INIT) {
+          const float mu = mu1[kk[q]] + mu1[cc[q]];
+          const float r0 = v[q] / mu;
+          const float z = r0 * __frcp_rn(mdiag(mu, a.fe2dt, fcwb));
+          xh[o[q]] = 0.f;
+          rh[o[q]] = r0;
+          pw[o[q]] = z;
+          acc += (double)(r0 * z);
+        } else {  // E_UPDATE
+          bad |= !isfinite(v[q]);
+          Y[o[q]] = yv[q] - (double)v[q];
+          acc = fmax(acc, (double)fabsf(v[q]));
+        }
+      }
+    }
+    if (EPI == E_UPDATE) {
+      if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
+      const double m = block_reduce<1>(acc, sh);
+      if (threadIdx.x == 0) part[(size_t)u * nb + b] = m;
+    } else if (EPI == E_Q || EPI == E_INIT) {
+      const double s = block_reduce<0>(acc, sh);
+      if (threadIdx.x == 0) {
+        part[(size_t)u * nb + b] = s;
+        if (EPI == E_INIT) a.prho0[(size_t)u * nb + b] = s;
+      }
+    }
+  }
+}
+
+// A transform phase of the persistent kernel: its blocks walk the items (one call per item keeps
+// the transform's register allocation that of a single item).
+template <int N, int EPI>
+__device__ __forceinline__ void dst_phase(const PArgs& a, float2* buf, const float2* twd, const float* in, float* out,
+                                          int act, double* part) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    __syncthreads();  // the previous item's epilogue has finished reading buf
+    noinl([&] { dst_item<N, EPI>(a, buf, twd, in, out, act, part, item); });
+  }
+}
+
+// Rows [a0, a0 + kDstRows) of unit u, element e of the item: (i, j), or false past the grid.
+template <int N>
+__device__ __forceinline__ bool item_elem(int a0, int e, int& i, int& j) {
+  constexpr int n = N - 1;
+  i = a0 + e / n;
+  j = e - (e / n) * n;
+  return i < n;
+}
+
+// The phases of the persistent kernel, each compiled as its own function (keeps the kernel's
+// register allocation to that of its largest phase). `a` lives in shared memory.
+template <int N>
+__device__ __forceinline__ void ph_prologue(const PArgs& a, int step) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
+  const size_t pts = (size_t)n * n;
+  (void)step;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    const int u = item / nb, a0 = (item - u * nb) * kDstRows;
+    const double* Yu = a.Y + u * pts;
+#pragma unroll 1
+    for (int e = threadIdx.x; e < kDstRows * n; e += kThreads) {
+      int i, j;
+      if (!item_elem<N>(a0, e, i, j)) continue;
+      const size_t k = (size_t)i * n + j;
+      if (a.scheme == SCHEME_NL) {
+        a.yhat[u * pts + k] = Yu[k] - a.dt * a.ih2 * lap5(Yu, n, i, j);
+      } else {
+        a.yprev[u * pts + k] = Yu[k];
+        if (a.scheme == SCHEME_LIN1) {
+          a.yhat[u * pts + k] = Yu[k] - a.dt * a.ih2 * lap5(Yu, n, i, j);
+        } else {
+          const double c = lin2_v(Yu[k], a.frozen);
+          const double w_ = (j > 0) ? lin2_v(Yu[k - 1], a.frozen) : 0.0;
+          const double e_ = (j < n - 1) ? lin2_v(Yu[k + 1], a.frozen) : 0.0;
+          const double s_ = (i > 0) ? lin2_v(Yu[k - n], a.frozen) : 0.0;
+          const double no = (i < n - 1) ? lin2_v(Yu[k + n], a.frozen) : 0.0;
+          a.yhat[u * pts + k] = Yu[k] + a.dt * a.ih2 * ((w_ + e_) + (s_ + no) - 4.0 * c);
+        }
+      }
+    }
+  }
+  for (int u = blockIdx.x * kThreads + threadIdx.x; u < a.units; u += gridDim.x * kThreads) {
+    a.flag[2 * u] = 0;
+    a.flag[2 * u + 1] = 0;
+    a.cnt[u] = 0;
+    a.scal[u * 8 + 6] = 0.0;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void ph_predict(const PArgs& a, int have_prev) {
+  constexpr int n = N - 1;
+  const size_t total = (size_t)a.units * n * n;
+  if (a.scheme == SCHEME_NL)
+    for (size_t k = blockIdx.x * (size_t)kThreads + threadIdx.x; k < total; k += (size_t)gridDim.x * kThreads) {
+      const double y = a.Y[k];
+      const double g = have_prev ? 2.0 * y - a.yprev[k] : y;
+      a.yprev[k] = y;
+      a.Y[k] = g;
+    }
+  if (blockIdx.x == 0 && threadIdx.x < 4) a.active[threadIdx.x] = 0;
+}
+
+// Five-point Laplacian of X at (i, j) of an n x n grid (zero outside), restrict loads.
+template <int n>
+__device__ __forceinline__ double lap5r(const double* __restrict__ X, int i, int j) {
+  const size_t k = (size_t)i * n + j;
+  const double c = X[k];
+  const double w = (j > 0) ? X[k - 1] : 0.0;
+  const double e = (j < n - 1) ? X[k + 1] : 0.0;
+  const double s = (i > 0) ? X[k - n] : 0.0;
+  const double no = (i < n - 1) ? X[k + n] : 0.0;
+  return (w + e) + (s + no) - 4.0 * c;
+}
+
+// N1: z = c1 lap(Y) - dt g(Y)
+template <int N>
+__device__ __forceinline__ void ph_z(const PArgs& a) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 2;
+  const size_t pts = (size_t)n * n;
+  double* __restrict__ z = a.z;
+  const double* __restrict__ W64 = a.W64;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    const int u = item / nb, a0 = (item - u * nb) * kDstRows;
+    if (a.flag[2 * u]) continue;
+    const double* __restrict__ Yu = a.Y + u * pts;
+    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
+      double lv[U], xv[U], wv[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          const int i = a0 + e / n, j = e - (e / n) * n;
+          const size_t k = (size_t)i * n + j;
+          lv[q] = lap5r<n>(Yu, i, j);
+          xv[q] = Yu[k];
+          wv[q] = (a.zmode == 2) ? W64[u * pts + k] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          const double x = xv[q];
+          double g;
+          if (a.zmode == 0) g = x * x * x;
+          else if (a.zmode == 1) g = x;
+          else if (a.zmode == 2) g = wv[q] * wv[q] * x;
+          else g = a.wconst * x;
+          z[u * pts + (size_t)a0 * n + e] = a.c1 * lv[q] - a.dt * g;
+        }
+      }
+    }
+  }
+}
+
+// N2: H = (Y - Yhat) + ih2 lap(z) in FP32; Jacobian weights and their range per item
+template <int N>
+__device__ __forceinline__ void ph_resid(const PArgs& a) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 2;
+  __shared__ double sh[kThreads / 32];
+  const size_t pts = (size_t)n * n;
+  const double* __restrict__ Y = a.Y;
+  const double* __restrict__ yhat = a.yhat;
+  const double* __restrict__ W64 = a.W64;
+  float* __restrict__ rhs = a.rhs;
+  float* __restrict__ w = a.w;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+    if (a.flag[2 * u]) continue;
+    const double* __restrict__ zu = a.z + u * pts;
+    const size_t base = u * pts + (size_t)a0 * n;
+    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    double lo = 1e300, hi = -1e300;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
+      double lz[U], yv[U], hv[U], w64[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          const int i = a0 + e / n, j = e - (e / n) * n;
+          lz[q] = lap5r<n>(zu, i, j);
+          yv[q] = Y[base + e];
+          hv[q] = yhat[base + e];
+          w64[q] = (a.zmode == 2) ? W64[base + e] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          rhs[base + e] = float((yv[q] - hv[q]) + a.ih2 * lz[q]);
+          float wq;
+          if (a.zmode == 0) {
+            const float y = float(yv[q]);
+            wq = 3.f * y * y;
+          } else if (a.zmode == 1) {
+            wq = 1.f;
+          } else if (a.zmode == 2) {
+            const float y = float(w64[q]);
+            wq = y * y;
+          } else {
+            wq = float(a.wconst);
+          }
+          w[base + e] = wq;
+          lo = fmin(lo, (double)wq);
+          hi = fmax(hi, (double)wq);
+        }
+      }
+    }
+    const double bl = block_reduce<2>(lo, sh);
+    const double bh = block_reduce<1>(hi, sh);
+    if (threadIdx.x == 0) {
+      a.pmin[(size_t)u * nb + b] = bl;
+      a.pmax[(size_t)u * nb + b] = bh;
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void ph_cg_reset(const PArgs& a) {
+  for (int u = blockIdx.x * kThreads + threadIdx.x; u < a.units; u += gridDim.x * kThreads) a.flag[2 * u + 1] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 2) a.active[threadIdx.x] = 0;
+}
+
+// P5: x += alpha p, r -= alpha q, (r, r / m)
+template <int N>
+__device__ __forceinline__ void ph_cg_step(const PArgs& a, const double* rho_cur, double* rho_new) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
+  __shared__ double sh[kThreads / 32];
+  const size_t pts = (size_t)n * n;
+  float* __restrict__ xh = a.xh;
+  float* __restrict__ rh = a.rh;
+  const float* __restrict__ ph = a.ph;
+  const float* __restrict__ qh = a.qh;
+  const float* __restrict__ mu1 = a.mu1;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+    if (a.flag[2 * u] || a.flag[2 * u + 1]) continue;
+    const double sig = unit_sum<N>(a.psig, u);
+    const float alpha = (sig > 0.0) ? float(unit_sum<N>(rho_cur, u) / sig) : 0.f;
+    const float cwb = a.fdt * float(unit_wbar<N>(a, u));
+    const size_t base = u * pts + (size_t)a0 * n;
+    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    float acc = 0.f;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
+      float pv[U], xv[U], rv[U], qv[U], mv[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          pv[q] = ph[base + e];
+          xv[q] = xh[base + e];
+          rv[q] = rh[base + e];
+          qv[q] = qh[base + e];
+          const int i = a0 + e / n;
+          mv[q] = mu1[i] + mu1[e - (e / n) * n];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          xh[base + e] = xv[q] + alpha * pv[q];
+          const float r = rv[q] - alpha * qv[q];
+          rh[base + e] = r;
+          acc += r * r * __frcp_rn(mdiag(mv[q], a.fe2dt, cwb));
+        }
+      }
+    }
+    const double s = block_reduce<0>((double)acc, sh);
+    if (threadIdx.x == 0) rho_new[(size_t)u * nb + b] = s;
+  }
+}
+
+// P6: p = r / m + beta p; convergence of each unit's CG (tested by the unit's first item)
+template <int N>
+__device__ __forceinline__ void ph_cg_dir(const PArgs& a, const double* rho_cur, const double* rho_new, int it) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
+  const size_t pts = (size_t)n * n;
+  float* __restrict__ ph = a.ph;
+  const float* __restrict__ rh = a.rh;
+  const float* __restrict__ mu1 = a.mu1;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+    if (a.flag[2 * u] || a.flag[2 * u + 1]) continue;
+    const double rn = unit_sum<N>(rho_new, u), ro = unit_sum<N>(rho_cur, u);
+    const float beta = (ro > 0.0) ? float(rn / ro) : 0.f;
+    const float cwb = a.fdt * float(unit_wbar<N>(a, u));
+    const size_t base = u * pts + (size_t)a0 * n;
+    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
+      float pv[U], rv[U], mv[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          pv[q] = ph[base + e];
+          rv[q] = rh[base + e];
+          const int i = a0 + e / n;
+          mv[q] = mu1[i] + mu1[e - (e / n) * n];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) ph[base + e] = rv[q] * __frcp_rn(mdiag(mv[q], a.fe2dt, cwb)) + beta * pv[q];
+      }
+    }
+    if (b == 0 && threadIdx.x == 0) {
+      atomicAdd(a.totals + 2, 1ull);
+      if (!(rn > a.cg_tol2 * unit_sum<N>(a.prho0, u))) a.flag[2 * u + 1] = 1;  // also catches NaN
+      else atomicAdd(a.active + (it & 1), 1);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.active[(it + 1) & 1] = 0;
+    a.totals[0] += 1ull;
+  }
+}
+
+// N7: Newton stop test per unit (tolerance, or the FP64 floor rule)
+template <int N>
+__device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  const int last = (it_n >= a.newton_max - 1);
+  for (int u = blockIdx.x * kThreads + threadIdx.x; u < a.units; u += gridDim.x * kThreads) {
+    if (a.flag[2 * u]) continue;
+    double dm = 0.0;
+    for (int b = 0; b < nb; ++b) dm = fmax(dm, a.pd[(size_t)u * nb + b]);
+    const int mm = ++a.cnt[u];
+    const double prev = a.scal[u * 8 + 6];
+    bool done = dm <= a.tol || (mm >= 2 && dm <= a.floor_ && dm > 0.5 * prev);
+    a.scal[u * 8 + 6] = dm;
+    if (!done && last) {
+      atomicOr(a.status, ST_NEWTON);
+      done = true;
+    }
+    if (done) {
+      a.flag[2 * u] = 1;
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.status + 4), (unsigned long long)mm);
+      atomicMax(reinterpret_cast<int*>(a.status + 3), mm);
+    } else {
+      atomicAdd(a.active + 2 + (it_n & 1), 1);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.active[2 + ((it_n + 1) & 1)] = 0;
+    a.totals[1] += 1ull;
+  }
+}
+
+template <int N, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
+  constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int FL = (kDstRows / 2) * L;
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
+  float2* twd = smem2 + FL + FL / 8;
+  __shared__ PArgs a;
+  if (threadIdx.x == 0) a = args;
+  for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = args.tw[m];
+  __syncthreads();
+#define CH_BAR()                                                  \
+  if (!grid_barrier(a.bar)) {                                     \
+    if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);         \
+    return;                                                       \
+  }
+  for (int step = 0; step < a.nsteps; ++step) {
+    noinl([&] { ph_prologue<N>(a, step); });
+    CH_BAR();
+    noinl([&] { ph_predict<N>(a, (a.scheme == SCHEME_NL) && (step > 0 || a.have_prev0)); });
+    CH_BAR();
+    for (int it_n = 0; it_n < a.newton_max; ++it_n) {
+      noinl([&] { ph_z<N>(a); });
+      CH_BAR();
+      noinl([&] { ph_resid<N>(a); });
+      CH_BAR();
+      noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, 0, nullptr); });  // H to sine space
+      CH_BAR();
+      noinl([&] { dst_phase<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, a.prho); });  // CG start
+      noinl([&] { ph_cg_reset<N>(a); });
+      CH_BAR();
+      for (int it = 0; it < a.cg_max; ++it) {
+        const double* rho_cur = a.prho + (size_t)(it & 1) * a.units * nb;
+        double* rho_new = a.prho + (size_t)((it + 1) & 1) * a.units * nb;
+        noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.ph, a.tmp, 1, nullptr); });  // p to physical space
+        CH_BAR();
+        noinl([&] { dst_phase<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr); });  // dt (wc - wbar) p
+        CH_BAR();
+        noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr); });  // back to sine space
+        CH_BAR();
+        noinl([&] { dst_phase<N, E_Q>(a, buf, twd, a.tmp, nullptr, 1, a.psig); });    // q = M p + That, (p, q)
+        CH_BAR();
+        noinl([&] { ph_cg_step<N>(a, rho_cur, rho_new); });
+        CH_BAR();
+        noinl([&] { ph_cg_dir<N>(a, rho_cur, rho_new, it); });
+        CH_BAR();
+        if (*(volatile int*)(a.active + (it & 1)) == 0) break;
+      }
+      noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr); });  // correction to physical space
+      CH_BAR();
+      noinl([&] { dst_phase<N, E_UPDATE>(a, buf, twd, a.tmp, nullptr, 0, a.pd); });  // Y -= d, max |d|
+      CH_BAR();
+      noinl([&] { ph_newton_end<N>(a, it_n); });
+      CH_BAR();
+      if (*(volatile int*)(a.active + 2 + (it_n & 1)) == 0) break;
+    }
+  }
+#undef CH_BAR
+}
+
+template <int N, int MINB>
+cudaError_t launch_persist(const PArgs& a, int* grid_out, cudaStream_t st) {
+  constexpr int FL = (kDstRows / 2) * 2 * N;
+  const size_t smem = (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2);
+  cudaError_t e = prep(k2_persist<N, MINB>, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2_persist<N, MINB>, kThreads, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  int grid = sms * per_sm;
+  if (grid > a.units * nb) grid = a.units * nb;
+  *grid_out = grid;
+  PArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)k2_persist<N, MINB>, dim3(grid), dim3(kThreads), params, smem, st);
+}
+
+// Compiled for two blocks per SM (128 registers per thread): measured fastest at n = 255 among
+// 2, 3 and 4, and it keeps the length-1024 transform of n = 511 out of local memory.
+template <int N>
+cudaError_t launch_persist_sel(const PArgs& a, int minb, int* grid_out, cudaStream_t st) {
+  (void)minb;
+  return launch_persist<N, 2>(a, grid_out, st);
+}
+
+}  // namespace
+
+void Prop2D::make_args(PArgs& a, double* Y, int units, int scheme, double dt, int nsteps) const {
+  a = PArgs{};
+  const int nb = (p_.n + kDstRows - 1) / kDstRows;
+  const size_t np = (size_t)cap_ * nb;
+  a.Y = Y;
+  a.yhat = yhat_;
+  a.yprev = yprev_;
+  a.z = z_;
+  a.w = w_;
+  a.rhs = rhs_;
+  a.xh = xh_;
+  a.rh = rh_;
+  a.ph = ph_;
+  a.qh = qh_;
+  a.tmp = tmp_;
+  a.t2 = tmp2_;
+  a.mu1 = mu_;
+  a.tw = tw_;
+  a.pmin = ppart_;
+  a.pmax = ppart_ + np;
+  a.psig = ppart_ + 2 * np;
+  a.prho = ppart_ + 3 * np;  // two parity slots
+  a.prho0 = ppart_ + 5 * np;
+  a.pd = ppart_ + 6 * np;
+  a.flag = flag_;
+  a.cnt = newton_cnt_;
+  a.scal = scal_;
+  a.status = status_;
+  a.totals = cg_dev_;
+  a.active = active_;
+  a.bar = bar_;
+  a.units = units;
+  a.nsteps = nsteps;
+  a.scheme = scheme;
+  a.newton_max = p_.newton_max;
+  a.cg_max = p_.cg_max;
+  a.have_prev0 = 0;
+  a.frozen = p_.frozen;
+  a.dt = dt;
+  a.ih2 = 1.0 / (p_.h * p_.h);
+  a.c1 = p_.eps2 * dt * a.ih2;
+  a.tol = p_.newton_tol;
+  a.floor_ = std::sqrt(p_.newton_tol);
+  a.cg_tol2 = p_.cg_tol * p_.cg_tol;
+  a.fe2dt = float(p_.eps2 * dt);
+  a.fdt = float(dt);
+  if (scheme == SCHEME_NL) {
+    a.zmode = p_.frozen ? 1 : 0;
+  } else if (scheme == SCHEME_LIN1) {
+    a.zmode = p_.frozen ? 3 : 2;
+    a.W64 = yprev_;
+    a.wconst = 1.0;
+  } else {
+    a.zmode = 3;
+    a.wconst = 2.0;
+  }
+  a.ctr = ctr_;
+}
+
+cudaError_t Prop2D::propagate_persistent(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
+  if (units > cap_ || units < 1) return cudaErrorInvalidValue;
+  if (nsteps < 1) return cudaSuccess;
+  PArgs a;
+  make_args(a, Y, units, scheme, dt, nsteps);
+  cudaError_t e = cudaMemsetAsync(bar_, 0, 4 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  int grid = 0;
+  const int minb = persist_minb_;
+  switch (p_.n + 1) {
+    case 16: e = launch_persist_sel<16>(a, minb, &grid, st); break;
+    case 32: e = launch_persist_sel<32>(a, minb, &grid, st); break;
+    case 64: e = launch_persist_sel<64>(a, minb, &grid, st); break;
+    case 128: e = launch_persist_sel<128>(a, minb, &grid, st); break;
+    case 256: e = launch_persist_sel<256>(a, minb, &grid, st); break;
+    case 512: e = launch_persist_sel<512>(a, minb, &grid, st); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) step_kernels_ += 1;
+  return e;
+}
+
+
+// ------------------------------------------------------------------ graph execution
+//
+// The same phases as separate kernels (each at its own occupancy), one CUDA graph per step with
+// the Newton and CG loops as conditional WHILE nodes. Loop indices live in device counters
+// (ctr[0] Newton, ctr[1] CG), advanced by the condition kernels.
+namespace {
+
+enum Phase {
+  PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_STEP, PH_DIR,
+  PH_X1, PH_X2, PH_NEWTON_END
+};
+
+__host__ __device__ constexpr bool is_dst_phase(int ph) {
+  return ph == PH_H1 || ph == PH_H2 || ph == PH_P1 || ph == PH_P2 || ph == PH_P3 || ph == PH_P4 || ph == PH_X1 ||
+         ph == PH_X2;
+}
+
+template <int N, int PH>
+__global__ void __launch_bounds__(kThreads) k2_phase(PArgs a, int have_prev) {
+  constexpr int L = 2 * N, FL = (kDstRows / 2) * L, nb = (N - 1 + kDstRows - 1) / kDstRows;
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
+  float2* twd = smem2 + FL + FL / 8;
+  if constexpr (is_dst_phase(PH)) {
+    for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = a.tw[m];
+    __syncthreads();
+  }
+  const int it = a.ctr[1];
+  const double* rho_cur = a.prho + (size_t)(it & 1) * a.units * nb;
+  double* rho_new = a.prho + (size_t)((it + 1) & 1) * a.units * nb;
+  if constexpr (PH == PH_PROLOGUE) ph_prologue<N>(a, 0);
+  if constexpr (PH == PH_PREDICT) ph_predict<N>(a, have_prev);
+  if constexpr (PH == PH_Z) ph_z<N>(a);
+  if constexpr (PH == PH_RESID) ph_resid<N>(a);
+  if constexpr (PH == PH_H1) dst_item<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, 0, nullptr, blockIdx.x);
+  if constexpr (PH == PH_H2) {
+    dst_item<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, a.prho, blockIdx.x);
+    ph_cg_reset<N>(a);
+  }
+  if constexpr (PH == PH_P1) dst_item<N, E_PLAIN>(a, buf, twd, a.ph, a.tmp, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P2) dst_item<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P3) dst_item<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P4) dst_item<N, E_Q>(a, buf, twd, a.tmp, nullptr, 1, a.psig, blockIdx.x);
+  if constexpr (PH == PH_STEP) ph_cg_step<N>(a, rho_cur, rho_new);
+  if constexpr (PH == PH_DIR) ph_cg_dir<N>(a, rho_cur, rho_new, it);
+  if constexpr (PH == PH_X1) dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
+  if constexpr (PH == PH_X2) dst_item<N, E_UPDATE>(a, buf, twd, a.tmp, nullptr, 0, a.pd, blockIdx.x);
+  if constexpr (PH == PH_NEWTON_END) ph_newton_end<N>(a, a.ctr[0]);
+}
+
+// End of a loop iteration: continue while units remain active and the cap is not reached.
+// which = 0: Newton (active slots 2, 3), 1: CG (slots 0, 1).
+__global__ void k2_cond(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, const int* __restrict__ active,
+                        int which, int lim) {
+  if (threadIdx.x == 0) {
+    const int it = ctr[which];
+    const int c = active[(which == 0 ? 2 : 0) + (it & 1)];
+    ctr[which] = it + 1;
+    cudaGraphSetConditional(hnd, (c > 0 && it + 1 < lim) ? 1u : 0u);
+  }
+}
+
+template <int N, int PH>
+cudaError_t phase_launch(const PArgs& a, int have_prev, cudaStream_t st) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  constexpr int FL = (kDstRows / 2) * 2 * N;
+  const size_t smem = is_dst_phase(PH) ? (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2) : 0;
+  k2_phase<N, PH><<<a.units * nb, kThreads, smem, st>>>(a, have_prev);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t phase_prepare() {
+  constexpr int FL = (kDstRows / 2) * 2 * N;
+  const size_t smem = (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2);
+  cudaError_t e = prep(k2_phase<N, PH_H1>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_H2>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_P1>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_P2>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_P3>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_P4>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_X1>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_X2>, smem);
+  return e;
+}
+
+// The step graph of one grid size.
+template <int N>
+cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_max, int* ctr, int* active,
+                         cudaGraphExec_t* out) {
+  cudaError_t e = phase_prepare<N>();
+  if (e != cudaSuccess) return e;
+  cudaStream_t cs = nullptr, bs = nullptr, bs2 = nullptr;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  cudaGraphConditionalHandle hN = 0, hC = 0;
+  if (e == cudaSuccess) e = phase_launch<N, PH_PROLOGUE>(a, have_prev, cs);
+  if (e == cudaSuccess) e = phase_launch<N, PH_PREDICT>(a, have_prev, cs);
+  if (e == cudaSuccess) e = capture_graph(cs, &g);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hN, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    k2_loop_start<<<1, 32, 0, cs>>>(hN, ctr, 0, 0);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t bodyN = nullptr;
+  if (e == cudaSuccess) e = add_while(cs, &hN, 1, cudaGraphCondAssignDefault, &bodyN);
+  // ---- Newton body
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = phase_launch<N, PH_Z>(a, have_prev, bs);
+  if (e == cudaSuccess) e = phase_launch<N, PH_RESID>(a, have_prev, bs);
+  if (e == cudaSuccess) e = phase_launch<N, PH_H1>(a, have_prev, bs);
+  if (e == cudaSuccess) e = phase_launch<N, PH_H2>(a, have_prev, bs);
+  cudaGraph_t gN = nullptr;
+  if (e == cudaSuccess) e = capture_graph(bs, &gN);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hC, gN, 0, 0);
+  if (e == cudaSuccess) {
+    k2_loop_start<<<1, 32, 0, bs>>>(hC, ctr, 1, 1);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t bodyC = nullptr;
+  if (e == cudaSuccess) e = add_while(bs, &hC, 0, 0, &bodyC);
+  // ---- CG body
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs2, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P1>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_STEP>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_DIR>(a, have_prev, bs2);
+  if (e == cudaSuccess) {
+    k2_cond<<<1, 32, 0, bs2>>>(hC, ctr, active, 1, cg_max);
+    e = cudaGetLastError();
+  }
+  {
+    cudaGraph_t dummy = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bs2, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  // ---- back in the Newton body: correction to physical space, update, stop test
+  if (e == cudaSuccess) e = phase_launch<N, PH_X1>(a, have_prev, bs);
+  if (e == cudaSuccess) e = phase_launch<N, PH_X2>(a, have_prev, bs);
+  if (e == cudaSuccess) e = phase_launch<N, PH_NEWTON_END>(a, have_prev, bs);
+  if (e == cudaSuccess) {
+    k2_cond<<<1, 32, 0, bs>>>(hN, ctr, active, 0, newton_max);
+    e = cudaGetLastError();
+  }
+  {
+    cudaGraph_t dummy = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bs, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  {
+    cudaGraph_t dummy = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (bs) cudaStreamDestroy(bs);
+  if (bs2) cudaStreamDestroy(bs2);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t Prop2D::build_step(const StepKey& k, cudaGraphExec_t* out) {
+  PArgs a;
+  make_args(a, k.Y, k.units, k.scheme, k.dt, 1);
+  switch (p_.n + 1) {
+    case 16: return build_step_n<16>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+    case 32: return build_step_n<32>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+    case 64: return build_step_n<64>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+    case 128: return build_step_n<128>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+    case 256: return build_step_n<256>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+    case 512: return build_step_n<512>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace chg2

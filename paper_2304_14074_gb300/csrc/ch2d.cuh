@@ -7,8 +7,15 @@
 
 namespace chg2 {
 
+struct PArgs;
+
 enum Scheme { SCHEME_LIN1 = 0, SCHEME_NL = 1, SCHEME_LIN2 = 2 };
-enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u };
+enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u, ST_TIMEOUT = 8u };
+
+// How a batch of implicit steps is executed: one CUDA graph per step (each phase a kernel; the
+// Newton and CG loops conditional WHILE nodes, 7 kernels per CG iteration), or one persistent
+// cooperative kernel per propagate call (the same phases separated by grid barriers).
+enum StepPath { PATH_GRAPH = 0, PATH_PERSISTENT = 1 };
 
 // Grid sizes the sine transform supports: n + 1 a power of two (radix-2 FFT of length 2(n+1)).
 bool supported_n(int n);
@@ -34,24 +41,29 @@ class Prop2D {
   // FP64 device array. Accumulates Newton iterations per unit into newton (device, may be null)
   // and ORs error bits into *status_dev.
   cudaError_t propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
+  cudaError_t propagate_persistent(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
+  void set_path(StepPath p) { path_ = p; }
+  StepPath path() const { return path_; }
   // Orthonormal 2D DST-I (its own inverse) of `units` FP32 fields; in and out must differ and
   // must not be the internal scratch buffers.
   cudaError_t dst2(const float* in, float* out, int units, cudaStream_t st);
   unsigned read_status(cudaStream_t st);  // synchronises
   unsigned long long newton_iterations() const { return newton_total_; }
   long long cg_iterations() const { return cg_total_; }
+  long long cg_unit_iterations() const { return cg_unit_total_; }  // summed over units
   int newton_peak() const { return newton_peak_; }
   // Kernels launched by the step graphs since the last reset (as of the last read_status): each
   // step runs a fixed prologue and epilogue, each batched Newton pass kNewtonKernels and each
   // batched CG iteration kCgKernels.
   long long kernel_launches() const {
-    return step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
+    return path_ == PATH_PERSISTENT ? step_kernels_
+                                    : step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
   }
-  static constexpr int kStepKernelsNL = 5;   // yhat, predict, reset_flags, loop_start, newton_stats
-  static constexpr int kStepKernelsLin = 4;  // right-hand side, reset_flags, loop_start, newton_stats
-  static constexpr int kNewtonKernels = 15;  // z, resid, weights, wbar, 2 DST, reopen, init, start,
-                                             // loop_start, 2 DST, update, newton_end, loop_cond
-  static constexpr int kCgKernels = 10;      // 4 DST, wprod, q, step, dir, end, loop_cond
+  static constexpr int kStepKernelsNL = 3;   // prologue, predictor, loop start
+  static constexpr int kStepKernelsLin = 3;
+  static constexpr int kNewtonKernels = 9;   // z, residual, 2 transform passes (the second starts CG),
+                                             // CG loop start, 2 passes (update), stop test, condition
+  static constexpr int kCgKernels = 7;       // 4 transform passes, step, direction, condition
   // Zeroes the device status bits and the Newton / CG counters (enqueued on st).
   cudaError_t reset_counters(cudaStream_t st);
   size_t bytes() const { return bytes_; }
@@ -68,7 +80,7 @@ class Prop2D {
     }
   };
   cudaError_t build_step(const StepKey& k, cudaGraphExec_t* out);
-  cudaError_t enqueue_cg_iteration(int units, double dt, cudaStream_t st);
+  void make_args(PArgs& a, double* Y, int units, int scheme, double dt, int nsteps) const;
   std::vector<std::pair<StepKey, cudaGraphExec_t>> graphs_;
 
   Params2D p_{};
@@ -105,7 +117,13 @@ class Prop2D {
   int newton_peak_ = 0;
   long long cg_total_ = 0;
   long long newton_passes_ = 0;
+  long long cg_unit_total_ = 0;
   long long step_kernels_ = 0;
+  StepPath path_ = PATH_GRAPH;
+  int persist_minb_ = 3;      // persistent path: blocks per SM it is compiled for (2, 3, 4)
+  double* ppart_ = nullptr;   // persistent path: per-item partial sums [7][cap][rows / 16]
+  int* active_ = nullptr;     // persistent path: units still iterating (parity slots)
+  unsigned* bar_ = nullptr;   // persistent path: grid barrier (arrivals, generation, abort)
 };
 
 // Parareal correction of one slice for `count` problems list[0..count) (Eq. 2.2), fused with

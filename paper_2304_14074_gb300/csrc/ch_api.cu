@@ -63,7 +63,7 @@ struct ch_parareal {
   std::vector<std::vector<double>> h_inc, h_el2, h_emx;
   std::vector<int> h_iters, h_conv;
   unsigned long long fine_newton = 0;  // Newton iterations (summed over units) of the fine sweeps
-  long long fine_cg = 0;               // CG iterations (batched) of the fine sweeps
+  long long fine_cg = 0;               // CG iterations (summed over units) of the fine sweeps
   // learned coarse propagator (2D): null = plain coarse step
   chg3::GTheta* gt = nullptr;
   int gt_form = CH_GTHETA_RESIDUAL;
@@ -150,6 +150,7 @@ chg2::Params2D params2d(const ch_config* c) {
 }
 
 ch_status device_status(ch_parareal* h, unsigned status) {
+  if (status & chg2::ST_TIMEOUT) return fail(h, CH_ERR_TIMEOUT, "a grid barrier of the 2D solver timed out");
   if (status & chg::ST_NONFINITE) return fail(h, CH_ERR_LINSOLVE, "a solve produced a non-finite value");
   if (status & chg::ST_NEWTON) return fail(h, CH_ERR_NEWTON, "a Newton solve reached newton_max");
   return CH_OK;
@@ -293,7 +294,7 @@ ch_status run2d(ch_parareal* h) {
       }
     h->p2->read_status(h->st);
     const unsigned long long n0 = h->p2->newton_iterations();
-    const long long c0 = h->p2->cg_iterations();
+    const long long c0 = h->p2->cg_unit_iterations();
     CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
     if ((s = gather_units(h, h->U, uoff, true)) != CH_OK) return s;
     if ((s = prop2(h, (int)uoff.size(), fine2(h), h->p.dt, h->p.J)) != CH_OK) return s;
@@ -301,7 +302,7 @@ ch_status run2d(ch_parareal* h) {
     CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
     h->p2->read_status(h->st);
     h->fine_newton += h->p2->newton_iterations() - n0;
-    h->fine_cg += h->p2->cg_iterations() - c0;
+    h->fine_cg += h->p2->cg_unit_iterations() - c0;
     // sequential coarse sweep with the correction of Eq. 2.2 and the norms
     CH_CUDA(h, cudaMemcpyAsync(h->dlist, L.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
     CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 3 * B * sizeof(double), h->st));
@@ -827,6 +828,7 @@ ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, i
     prop.release();
     if (e == cudaErrorMemoryAllocation) return CH_ERR_OOM;
     if (e != cudaSuccess) return CH_ERR_CUDA;
+    if (status & chg2::ST_TIMEOUT) return CH_ERR_TIMEOUT;
     if (status & chg2::ST_NONFINITE) return CH_ERR_LINSOLVE;
     if (status & chg2::ST_NEWTON) return CH_ERR_NEWTON;
     return CH_OK;

@@ -164,3 +164,46 @@ def test_c3_grid_full_size_steps(gpu_lib):
         ref = o2.propagate(p, scheme, step, 2, u0)
         tol = 64 * step_bound_2d(n, eps, step, c=c) * 2
         assert np.max(np.abs(out - ref)) <= tol, (scheme, np.max(np.abs(out - ref)), tol)
+
+
+@pytest.fixture
+def persistent_path(monkeypatch):
+    """Selects the persistent one-kernel execution of the 2D steps (read when a solver is created)."""
+    monkeypatch.setenv("CH_2D_STEP", "persistent")
+
+
+@pytest.mark.parametrize("n", [15, 63, 255])
+@pytest.mark.parametrize("scheme", ["lin1", "lin2", "nl"])
+def test_persistent_path_matches_oracle(gpu_lib, persistent_path, n, scheme):
+    """The persistent execution (the default is one graph per step) against the oracle."""
+    ch = gpu_lib
+    h = 1.0 / (n + 1)
+    eps = 0.05
+    dt = min(1e-3, 2000.0 * h ** 4 / eps ** 2)
+    nsteps, B = 2, 2
+    u0 = np.stack([ch_inputs.initial_condition(2, n, 170 + b, amp=0.6) for b in range(B)])
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    out = ch.propagate(cfg, scheme, dt, nsteps, dev(u0)).cpu().numpy()
+    p = o2.Params(n=n, eps=eps, T=1.0, N=1, J=1, newton_tol=1e-12)
+    tol = 64 * step_bound_2d(n, eps, dt) * nsteps + 1e-13
+    for b in range(B):
+        ref = o2.propagate(p, scheme, dt, nsteps, u0[b])
+        assert np.max(np.abs(out[b] - ref)) <= tol, (b, np.max(np.abs(out[b] - ref)), tol)
+
+
+@pytest.mark.parametrize("n", [31, 255])
+def test_persistent_and_graph_paths_agree(gpu_lib, monkeypatch, n):
+    """Both executions run the same phase functions in the same order on the same data; compiled
+    in different contexts they may contract multiply-adds differently, so they agree to the
+    step's rounding floor. Each is deterministic."""
+    ch = gpu_lib
+    eps, dt, nsteps, B = 0.01, 1.5625e-4, 3, 4
+    u0 = np.stack([ch_inputs.initial_condition(2, n, 300 + b, kind="normal", amp=0.05) for b in range(B)])
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    g = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+    g2 = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+    monkeypatch.setenv("CH_2D_STEP", "persistent")
+    a = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+    a2 = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+    assert np.array_equal(g, g2) and np.array_equal(a, a2)
+    assert np.max(np.abs(a - g)) <= 64 * step_bound_2d(n, eps, dt) * nsteps
