@@ -44,6 +44,13 @@ WORKLOADS = {
     "c3": dict(name="2D nonlinear Parareal NPA-I 256x256 grid (n=255) eps=0.01 T=0.5 N=32 J=100 u0=0.05*N(0,1) seed 1",
                dim=2, n=255, eps=0.01, T=0.5, N=32, J=100, batch=1, variant="NPA-I", newton_tol=1e-12,
                amp=0.05, kind="normal", seed0=1, precision=1, ttol=True),
+    # profiling case of the 2D kernels: c3's grid, slices and step size, 10 fine steps per slice
+    "c3-profile": dict(name="2D NPA-I 256x256 (n=255) eps=0.01 N=32 J=10 (dt as c3), profiling case",
+                       dim=2, n=255, eps=0.01, T=0.05, N=32, J=10, batch=1, variant="NPA-I", newton_tol=1e-12,
+                       amp=0.05, kind="normal", seed0=1, precision=1, ttol=False),
+    "c4": dict(name="2D nonlinear Parareal NPA-I 512x512 grid (n=511) eps=0.01 T=2 N=64 J=100 u0=0.05*N(0,1) seed 2000",
+               dim=2, n=511, eps=0.01, T=2.0, N=64, J=100, batch=1, variant="NPA-I", newton_tol=1e-12,
+               amp=0.05, kind="normal", seed0=2000, precision=1, ttol=False),
     "c1": dict(name="1D linear Parareal PA-I M=128 eps=0.05 T=0.1 N=16 dt=1e-5 batch=1",
                n=128, eps=0.05, T=0.1, N=16, J=625, batch=1, variant="PA-I", newton_tol=1e-12,
                amp=0.1, precision=0, ttol=True),
@@ -309,6 +316,9 @@ def bench_ours(args, w, rank, world, local_rank):
     ttol = None
     if w.get("ttol") and not args.no_ttol and rank == 0:
         ttol = time_to_tolerance(ch, w, u0, stream)
+    if not args.no_learned and rank == 0:
+        ttol = dict(ttol or {})
+        ttol["learned_vs_plain_G"] = learned_vs_plain(ch, stream)
     return dict(value=value, total_ms=total_ms, step_ms=step_ms, roofline=roofline, e2e=e2e,
                 clocks=clk.summary(), launches=launches, ttol=ttol)
 
@@ -345,8 +355,97 @@ def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
     pr.close()
     return {"coarse": "plain (one LIN1 step per slice)", "err_tol": err_tol, "seconds": round(t_ms / 1e3, 4),
             "iterations": int(iters), "converged_all": status == 0, "worst_final_err_l2": worst,
-            "serial_fine_seconds_same_gpu": round(serial_ms / 1e3, 4),
-            "learned_coarse": "not built (no G_theta in this version)"}
+            "serial_fine_seconds_same_gpu": round(serial_ms / 1e3, 4)}
+
+
+# Learned against plain coarse propagator, time to 1e-8: a 2D problem small enough to train G_theta
+# and run both Parareal forms within the benchmark (the 512^2, N = 64 configuration takes tens of
+# minutes per form).
+LEARNED_CASE = dict(n=63, eps=0.05, T=0.3, N=16, J=8, stride=4, train_seeds=64, eval_seed=5000,
+                    steps=((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)), batch=32)
+
+
+def learned_vs_plain(ch, stream, err_tol=1e-8):
+    """Trains G_theta (correction form G(U) + R(U)) on fine-solver snapshot pairs and on pairs
+    from perturbed snapshots, all produced by the library on the GPU, then runs Parareal to
+    err_tol with the plain and with the learned coarse step from a held-out initial condition."""
+    import numpy as np
+    import torch
+
+    import ch_inputs
+    c = LEARNED_CASE
+    n, eps, T, N, J, stride = c["n"], c["eps"], c["T"], c["N"], c["J"], c["stride"]
+    dT = T / N
+    t0 = time.perf_counter()
+    gen = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N * stride, fine_steps=J // stride, variant="NPA-I",
+                    newton_tol=1e-12)
+    seeds = range(1000, 1000 + c["train_seeds"])
+    pr = ch.Parareal(gen, batch=len(seeds), stream=stream)
+    pr.set_initial_batch(np.stack([ch_inputs.initial_condition(2, n, s, kind="normal", amp=0.05) for s in seeds]))
+    pr.compute_reference()
+    states = torch.empty((len(seeds), N * stride + 1, n * n), dtype=torch.float64, device="cuda")
+    pr.get_reference_device(states)
+    pr.close()
+    one = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    base = ch.propagate(one, "lin1", dT, 1, states.reshape(-1, n * n)).reshape(states.shape)
+    # perturbed pairs (U + eta, F(U + eta)) around the slice-boundary states teach the step's
+    # response to perturbations, which is what the Parareal correction differences
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    X = states[:, ::stride].reshape(-1, n * n)
+    pairs = []
+    for amp, smooth in ((0.05, False), (0.2, True), (0.05, True)):
+        eta = torch.randn(X.shape, device="cuda", dtype=torch.float64, generator=g)
+        if smooth:
+            for _ in range(3):
+                eta = ch.propagate(one, "lin1", dT, 1, eta.contiguous())
+            eta = eta / eta.abs().amax(dim=1, keepdim=True)
+        Xp = (X + amp * eta).contiguous()
+        pairs.append(torch.stack([Xp, ch.propagate(one, "nl", dT / J, J, Xp)], 1))
+    pert = torch.cat(pairs).contiguous()
+    pbase = ch.propagate(one, "lin1", dT, 1, pert.reshape(-1, n * n)).reshape(pert.shape)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = ch.GTheta(seed=1)
+    t1 = time.perf_counter()
+    losses = []
+    for lr, steps in c["steps"]:
+        for rep in range(4):
+            losses.append(net.train(states, stride=stride, steps=steps // 8, batch=c["batch"], lr=lr,
+                                    seed=rep + int(lr * 1e6), base=base))
+            losses.append(net.train(pert, stride=1, steps=steps // 8, batch=c["batch"], lr=lr,
+                                    seed=50 + rep + int(lr * 1e6), base=pbase))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    params = net.get_params()
+    losses = np.concatenate(losses)
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N, fine_steps=J, variant="NPA-I", newton_tol=1e-12,
+                    err_tol=err_tol)
+    u0 = ch_inputs.initial_condition(2, n, c["eval_seed"], kind="normal", amp=0.05)[None]
+    out = {}
+    for name, p in (("plain", None), ("learned", params)):
+        h = ch.Parareal(cfg, batch=1, stream=stream)
+        h.set_initial_batch(u0)
+        h.compute_reference()
+        if p is not None:
+            h.set_coarse_model(p, "correction")
+        st = h.run()
+        s0 = h.stats(0)
+        k = s0["iterations"]
+        out[name] = {"iterations": int(k), "seconds": round(s0["t_iter_ms"][k] / 1e3, 4), "converged": st == 0,
+                     "final_err_l2": float(s0["err_l2"][k]), "err_l2_first_iterations":
+                     [float("%.3g" % v) for v in s0["err_l2"][:min(k, 6) + 1]],
+                     "coarse_fallback_iter": int(s0["coarse_fallback_iter"])}
+        h.close()
+    out["speedup_learned_over_plain"] = round(out["plain"]["seconds"] / max(out["learned"]["seconds"], 1e-9), 3)
+    out["config"] = (f"2D NPA-I n={n} eps={eps} T={T} N={N} J={J}, u0 = 0.05 N(0,1) seed {c['eval_seed']}; "
+                     f"G_theta correction form trained on {len(seeds)} trajectories (seeds 1000..) "
+                     f"x {N * stride - stride + 1} snapshot pairs + {pert.shape[0]} perturbed pairs, "
+                     f"{len(losses)} Adam steps")
+    out["data_seconds"] = round(t_data, 2)
+    out["training_seconds"] = round(t_train, 2)
+    out["final_training_loss"] = float(losses[-200:].mean())
+    return out
 
 
 # ------------------------------------------------------------------------------ main
@@ -361,6 +460,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-ttol", action="store_true", help="skip the time-to-1e-8 run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain coarse propagator run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -258,8 +258,37 @@ typedef enum {
  * plain step (G(U_n^k) recomputed with it). CH_ERR_INVALID for dim = 1. */
 ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host, size_t len, int form);
 
+/* Per-problem interface parameter eps (host array of `batch` values > 0) for a 2D handle,
+ * replacing cfg->eps; each fine and coarse step of problem b then uses eps[b] (Eq. 1.1). The
+ * reference solution must be recomputed afterwards. CH_ERR_INVALID for dim = 1. */
+ch_status ch_parareal_set_eps(ch_parareal* h, const double* eps_host, size_t len);
+
 /* Reference slices of all problems to device memory: batch (N+1) n^d values. */
 ch_status ch_parareal_get_reference_device(ch_parareal* h, double* out_dev, size_t len);
+
+/* ---------------------------------------------------------------------------------------
+ * Ensembles of 2D problems on uneven grids and with different eps. The paper has no
+ * counterpart (it solves one problem at a time); this batches independent 2D problems of
+ * Eq. 1.1 whose grids differ. Problems are grouped by grid size n; each group is one Parareal
+ * handle (all its (problem, slice) units batched in every launch, per-problem eps as in
+ * ch_parareal_set_eps) on a stream of its own, and the groups run concurrently, each driven
+ * by a host thread of the call. cfg gives everything but n and eps (dim must be 2);
+ * n_per_problem / eps_per_problem: `nprob` values each (host). Problem indices are the
+ * ensemble's own; buffers as for the single-problem calls of the problem's handle.
+ * ch_ensemble_run returns CH_ERR_NOT_CONVERGED when some group did not meet its stop rule. */
+typedef struct ch_ensemble ch_ensemble;
+
+ch_status ch_ensemble_create(const ch_config* cfg, int nprob, const int* n_per_problem, const double* eps_per_problem,
+                             ch_ensemble** out);
+ch_status ch_ensemble_set_initial(ch_ensemble* e, int problem, const double* u0_host, size_t len);
+ch_status ch_ensemble_compute_reference(ch_ensemble* e);
+ch_status ch_ensemble_run(ch_ensemble* e);
+ch_status ch_ensemble_get_slices(ch_ensemble* e, int problem, double* out_host, size_t len);
+ch_status ch_ensemble_get_reference(ch_ensemble* e, int problem, double* out_host, size_t len);
+ch_status ch_ensemble_get_stats(ch_ensemble* e, int problem, ch_stats* out);
+int ch_ensemble_groups(const ch_ensemble* e);
+void ch_ensemble_destroy(ch_ensemble* e);
+const char* ch_ensemble_last_error(const ch_ensemble* e);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free solve. The paper has no counterpart: this is a library-level service.

@@ -29,12 +29,14 @@ EXPORTED_SYMBOLS = [
     "ch_parareal_get_slices_device", "ch_parareal_get_reference", "ch_parareal_get_stats",
     "ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_propagate",
     "ch_parareal_solve_noalloc", "ch_sine_transform_2d", "ch_parareal_set_coarse_model",
-    "ch_parareal_get_reference_device", "ch_gtheta_create", "ch_gtheta_destroy", "ch_gtheta_last_error",
+    "ch_parareal_get_reference_device", "ch_parareal_set_eps", "ch_gtheta_create", "ch_gtheta_destroy", "ch_gtheta_last_error",
     "ch_gtheta_set_params", "ch_gtheta_get_params", "ch_gtheta_forward", "ch_gtheta_gradients",
-    "ch_gtheta_train",
+    "ch_gtheta_train", "ch_ensemble_create", "ch_ensemble_set_initial", "ch_ensemble_compute_reference",
+    "ch_ensemble_run", "ch_ensemble_get_slices", "ch_ensemble_get_reference", "ch_ensemble_get_stats",
+    "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error",
 ]
 _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
-              "ch_gtheta_last_error")
+              "ch_gtheta_last_error", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_ensemble_groups")
 
 CH_GTHETA_PARAMS = 37601
 GTHETA_FORMS = {"residual": 0, "correction": 1}
@@ -130,6 +132,7 @@ def load(build_if_missing: bool = True):
     f = C.POINTER(C.c_float)
     lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz, C.c_int]
     lib.ch_parareal_get_reference_device.argtypes = [vp, vp, sz]
+    lib.ch_parareal_set_eps.argtypes = [vp, d, sz]
     lib.ch_gtheta_create.argtypes = [C.c_ulonglong, vp, C.POINTER(vp)]
     lib.ch_gtheta_destroy.argtypes = [vp]
     lib.ch_gtheta_destroy.restype = None
@@ -141,6 +144,20 @@ def load(build_if_missing: bool = True):
     lib.ch_gtheta_gradients.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, f, sz, f]
     lib.ch_gtheta_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                     C.c_ulonglong, f]
+    ip = C.POINTER(C.c_int)
+    lib.ch_ensemble_create.argtypes = [C.POINTER(_Config), C.c_int, ip, d, C.POINTER(vp)]
+    lib.ch_ensemble_set_initial.argtypes = [vp, C.c_int, d, sz]
+    lib.ch_ensemble_compute_reference.argtypes = [vp]
+    lib.ch_ensemble_run.argtypes = [vp]
+    lib.ch_ensemble_get_slices.argtypes = [vp, C.c_int, d, sz]
+    lib.ch_ensemble_get_reference.argtypes = [vp, C.c_int, d, sz]
+    lib.ch_ensemble_get_stats.argtypes = [vp, C.c_int, C.POINTER(_Stats)]
+    lib.ch_ensemble_groups.argtypes = [vp]
+    lib.ch_ensemble_groups.restype = C.c_int
+    lib.ch_ensemble_destroy.argtypes = [vp]
+    lib.ch_ensemble_destroy.restype = None
+    lib.ch_ensemble_last_error.argtypes = [vp]
+    lib.ch_ensemble_last_error.restype = C.c_char_p
     for name in EXPORTED_SYMBOLS:
         if name not in _NO_STATUS:
             getattr(lib, name).restype = C.c_int
@@ -265,6 +282,12 @@ class Parareal:
         p = np.ascontiguousarray(params, dtype=np.float32)
         self._check(self.lib.ch_parareal_set_coarse_model(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size,
                                                           f), "ch_parareal_set_coarse_model")
+
+    def set_eps(self, eps) -> None:
+        """Per-problem eps (2D): one value per problem of the batch."""
+        e = _host(eps)
+        self._check(self.lib.ch_parareal_set_eps(self._h, e.ctypes.data_as(C.POINTER(C.c_double)), e.size),
+                    "ch_parareal_set_eps")
 
     def get_reference_device(self, out_dev) -> None:
         self._check(self.lib.ch_parareal_get_reference_device(self._h, _dptr(out_dev), out_dev.numel()),
@@ -404,3 +427,76 @@ def gtheta_flatten(W, b) -> np.ndarray:
     """Inverse of gtheta_unflatten (FP32)."""
     return np.concatenate([np.concatenate([np.asarray(w).ravel(), np.asarray(bb).ravel()])
                            for w, bb in zip(W, b)]).astype(np.float32)
+
+
+class Ensemble:
+    """2D problems of several grid sizes and eps (ch_ensemble_*): grouped by grid size, one
+    batched handle per size on its own stream, the groups run concurrently."""
+
+    def __init__(self, cfg: Config, n_per_problem, eps_per_problem):
+        self.lib = load()
+        self.cfg = cfg
+        self.n = [int(v) for v in n_per_problem]
+        nn = np.ascontiguousarray(self.n, dtype=np.int32)
+        ee = _host(eps_per_problem)
+        if ee.size != nn.size:
+            raise ValueError("one eps per problem")
+        self._h = C.c_void_p()
+        self._cc = cfg.c()
+        s = self.lib.ch_ensemble_create(C.byref(self._cc), nn.size, nn.ctypes.data_as(C.POINTER(C.c_int)),
+                                        ee.ctypes.data_as(C.POINTER(C.c_double)), C.byref(self._h))
+        if s != 0:
+            raise ChError(s, "ch_ensemble_create")
+
+    def _check(self, s, what, ok=(0,)):
+        if s not in ok:
+            detail = self.lib.ch_ensemble_last_error(self._h).decode() if self._h else ""
+            raise ChError(s, what, detail)
+        return s
+
+    @property
+    def groups(self) -> int:
+        return self.lib.ch_ensemble_groups(self._h)
+
+    def set_initial(self, problem: int, u0) -> None:
+        u = _host(u0)
+        self._check(self.lib.ch_ensemble_set_initial(self._h, problem, u.ctypes.data_as(C.POINTER(C.c_double)),
+                                                     u.size), "ch_ensemble_set_initial")
+
+    def compute_reference(self) -> None:
+        self._check(self.lib.ch_ensemble_compute_reference(self._h), "ch_ensemble_compute_reference")
+
+    def run(self, allow_not_converged: bool = True) -> int:
+        ok = (0, 6) if allow_not_converged else (0,)
+        return self._check(self.lib.ch_ensemble_run(self._h), "ch_ensemble_run", ok)
+
+    def _slices(self, fn, what, problem):
+        out = np.empty((self.cfg.n_slices + 1, self.n[problem] ** 2))
+        self._check(fn(self._h, problem, out.ctypes.data_as(C.POINTER(C.c_double)), out.size), what)
+        return out
+
+    def get_slices(self, problem: int) -> np.ndarray:
+        return self._slices(self.lib.ch_ensemble_get_slices, "ch_ensemble_get_slices", problem)
+
+    def get_reference(self, problem: int) -> np.ndarray:
+        return self._slices(self.lib.ch_ensemble_get_reference, "ch_ensemble_get_reference", problem)
+
+    def stats(self, problem: int) -> dict:
+        st = _Stats()
+        self._check(self.lib.ch_ensemble_get_stats(self._h, problem, C.byref(st)), "ch_ensemble_get_stats")
+        k = st.iterations
+        return {"iterations": k, "converged": bool(st.converged), "inc": np.array(st.inc[:k]),
+                "err_l2": np.array(st.err_l2[:k + 1]), "t_iter_ms": np.array(st.t_iter_ms[:k + 1]),
+                "fine_point_steps": st.fine_point_steps, "newton_total": st.newton_total,
+                "inner_iterations": st.inner_iterations, "kernel_launches": st.kernel_launches}
+
+    def close(self) -> None:
+        if self._h:
+            self.lib.ch_ensemble_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -720,13 +720,37 @@ static cudaError_t prep(K kernel, size_t smem) {
 // The fine propagator is the nonlinear scheme with FP32 Jacobian solves: use the mixed-form path.
 static bool fast_fine(const Params1D& p) { return p.fine_scheme == SCHEME_NL && p.precision == 1; }
 
+// Fine-sweep mapping of the mixed-form path with the autotuned alternative: alt = 1 halves the
+// threads per CTA and doubles the block rows per thread (more CTAs resident per SM, longer
+// per-thread Thomas chunks, a shorter PCR on the separators).
+#define CH_DISPATCH_TP_FINE(n, alt, ...)                  \
+  do {                                                    \
+    if (!(alt) || (n) <= 128) {                           \
+      CH_DISPATCH_TP_FAST(n, __VA_ARGS__);                \
+    } else if ((n) <= 256) {                              \
+      constexpr int T_ = 32, P_ = 4;                      \
+      __VA_ARGS__;                                        \
+    } else if ((n) <= 512) {                              \
+      constexpr int T_ = 64, P_ = 4;                      \
+      __VA_ARGS__;                                        \
+    } else if ((n) <= 1024) {                             \
+      constexpr int T_ = 128, P_ = 4;                     \
+      __VA_ARGS__;                                        \
+    } else {                                              \
+      constexpr int T_ = 128, P_ = 8;                     \
+      __VA_ARGS__;                                        \
+    }                                                     \
+  } while (0)
+
+bool fine_sweep_has_alt(const Params1D& p) { return fast_fine(p) && p.n > 128; }
+
 cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   if (fast_fine(p)) {
-    CH_DISPATCH_TP_FAST(p.n, {
+    CH_DISPATCH_TP_FINE(p.n, p.alt, {
       const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_fine_sweep<T_, P_, true>, smem);
       if (e == cudaSuccess)
@@ -752,7 +776,7 @@ cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctr
                               int grid, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (fast_fine(p)) {
-    CH_DISPATCH_TP_FAST(p.n, {
+    CH_DISPATCH_TP_FINE(p.n, p.alt, {
       const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_fine_sweep<T_, P_, true>, smem);
       if (e == cudaSuccess) k_fine_sweep<T_, P_, true><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
@@ -790,7 +814,7 @@ cudaError_t launch_tally(const Params1D& p, Ctrl* ctrl, ProblemState ps, int* ho
 cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (fast_fine(p)) {
-    CH_DISPATCH_TP_FAST(p.n, {
+    CH_DISPATCH_TP_FINE(p.n, p.alt, {
       const size_t smem = sizeof(Smem1D<T_>);
       e = prep(k_reference<T_, P_, true>, smem);
       if (e == cudaSuccess) k_reference<T_, P_, true><<<p.B, T_, smem, st>>>(p, Uref, ctrl);

@@ -51,7 +51,11 @@ struct Params1D {
   double newton_tol;
   double tol;        // Parareal increment tolerance (<= 0: never)
   double err_tol;    // stop once the L2_h error against the reference is <= err_tol (<= 0: never)
+  int alt;           // fine-sweep CTA mapping: 0 = default (T, P), 1 = (T/2, 2P) (autotuned)
 };
+
+// Whether the fine sweep of p has an alternative CTA mapping (T/2 threads, 2P block rows each).
+bool fine_sweep_has_alt(const Params1D& p);
 
 // Launch helpers (implemented in ch1d.cu). All return cudaError_t of the launch.
 cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl,

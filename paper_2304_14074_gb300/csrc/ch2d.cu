@@ -315,11 +315,12 @@ __global__ void k2_correct(double* __restrict__ U, const double* __restrict__ F,
   const double* Fb = F + (size_t)b * fstride;
   double* Gb = Gold + (size_t)b * fstride;
   double* gi = g + (size_t)i * pts;
-  double inc = 0.0, e2 = 0.0, em = 0.0;
+  double inc = 0.0, e2 = 0.0, em = 0.0, um = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pts; k += (size_t)gridDim.x * blockDim.x) {
     const double gv = gi[k];
     const double nw = init ? gv : Fb[k] + (gv - Gb[k]);
     if (!init) inc = fmax(inc, fabs(nw - Ub[k]));
+    um = isfinite(nw) ? fmax(um, fabs(nw)) : INFINITY;
     Ub[k] = nw;
     Gb[k] = gv;
     gi[k] = nw;
@@ -332,10 +333,12 @@ __global__ void k2_correct(double* __restrict__ U, const double* __restrict__ F,
   const double r0 = block_reduce<1>(inc, sh);
   const double r1 = block_reduce<0>(e2, sh);
   const double r2 = block_reduce<1>(em, sh);
+  const double r3 = block_reduce<1>(um, sh);
   if (threadIdx.x == 0) {
-    part[((size_t)i * 3 + 0) * kBlk + blockIdx.x] = r0;
-    part[((size_t)i * 3 + 1) * kBlk + blockIdx.x] = r1;
-    part[((size_t)i * 3 + 2) * kBlk + blockIdx.x] = r2;
+    part[((size_t)i * 4 + 0) * kBlk + blockIdx.x] = r0;
+    part[((size_t)i * 4 + 1) * kBlk + blockIdx.x] = r1;
+    part[((size_t)i * 4 + 2) * kBlk + blockIdx.x] = r2;
+    part[((size_t)i * 4 + 3) * kBlk + blockIdx.x] = r3;
   }
 }
 
@@ -344,16 +347,18 @@ __global__ void k2_correct_fold(const double* __restrict__ part, const int* __re
                                 double* __restrict__ acc, double h2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  double inc = 0.0, e2 = 0.0, em = 0.0;
+  double inc = 0.0, e2 = 0.0, em = 0.0, um = 0.0;
   for (int k = 0; k < kBlk; ++k) {
-    inc = fmax(inc, part[((size_t)i * 3 + 0) * kBlk + k]);
-    e2 += part[((size_t)i * 3 + 1) * kBlk + k];
-    em = fmax(em, part[((size_t)i * 3 + 2) * kBlk + k]);
+    inc = fmax(inc, part[((size_t)i * 4 + 0) * kBlk + k]);
+    e2 += part[((size_t)i * 4 + 1) * kBlk + k];
+    em = fmax(em, part[((size_t)i * 4 + 2) * kBlk + k]);
+    um = fmax(um, part[((size_t)i * 4 + 3) * kBlk + k]);
   }
   const int b = list[i];
-  acc[b * 3 + 0] = fmax(acc[b * 3 + 0], inc);
-  acc[b * 3 + 1] = fmax(acc[b * 3 + 1], sqrt(h2 * e2));
-  acc[b * 3 + 2] = fmax(acc[b * 3 + 2], em);
+  acc[b * 4 + 0] = fmax(acc[b * 4 + 0], inc);
+  acc[b * 4 + 1] = fmax(acc[b * 4 + 1], sqrt(h2 * e2));
+  acc[b * 4 + 2] = fmax(acc[b * 4 + 2], em);
+  acc[b * 4 + 3] = fmax(acc[b * 4 + 3], um);
 }
 
 // Gather rows: dst[i] = src + off[i] (element offsets), pts each.
@@ -396,15 +401,17 @@ cudaError_t launch_scatter(double* dst, const double* src, const long long* off,
   return cudaGetLastError();
 }
 
-size_t correct_partials(int count) { return (size_t)count * 3 * kBlk; }
+size_t correct_partials(int count) { return (size_t)count * 4 * kBlk; }
 
 // ---------------------------------------------------------------------------- Prop2D
 
 cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   if (!supported_n(p.n) || cap < 1) return cudaErrorInvalidValue;
-  // CH_2D_STEP=persistent selects the one-kernel execution of a propagation (default: graphs)
+  // CH_2D_STEP=persistent | host selects another execution of the same phases (default: graphs)
   const char* env = std::getenv("CH_2D_STEP");
-  path_ = (env && std::strcmp(env, "persistent") == 0) ? PATH_PERSISTENT : PATH_GRAPH;
+  path_ = PATH_GRAPH;
+  if (env && std::strcmp(env, "persistent") == 0) path_ = PATH_PERSISTENT;
+  if (env && std::strcmp(env, "host") == 0) path_ = PATH_HOST;
   const char* mb = std::getenv("CH_2D_MINB");
   persist_minb_ = mb ? std::atoi(mb) : 3;
   p_ = p;
@@ -443,7 +450,7 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   al((void**)&active_, 4 * sizeof(int));
   al((void**)&bar_, 4 * sizeof(unsigned));
   if (e != cudaSuccess) return e;
-  e = cudaHostAlloc((void**)&host_cnt_, 4 * sizeof(int), 0);
+  e = cudaHostAlloc((void**)&host_cnt_, 8 * sizeof(int), 0);
   if (e != cudaSuccess) return e;
   if ((e = dst_prepare(p.n)) != cudaSuccess) return e;  // kernel attributes, before any capture
   // eigenvalues of A = -D_1: mu_p = (4/h^2) sin^2(p pi / (2(n+1))), p = 1..n (host libm)
@@ -531,6 +538,7 @@ cudaError_t capture_graph(cudaStream_t st, cudaGraph_t* g) {
 cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
   if (units > cap_ || units < 1) return cudaErrorInvalidValue;
   if (path_ == PATH_PERSISTENT) return propagate_persistent(Y, units, scheme, dt, nsteps, st);
+  if (path_ == PATH_HOST) return propagate_host(Y, units, scheme, dt, nsteps, st);
   for (int j = 0; j < nsteps; ++j) {
     StepKey k{Y, units, scheme, dt, (scheme == SCHEME_NL && j > 0) ? 1 : 0};
     cudaGraphExec_t ex = nullptr;
@@ -615,6 +623,8 @@ struct PArgs {
   const double* W64;
   double wconst, dt, ih2, c1, tol, floor_, cg_tol2;
   float fe2dt, fdt;
+  double eps2;           // eps^2 of every unit, unless eps2u is set
+  const double* eps2u;   // per-unit eps^2 [units] (device) or null
   int units, nsteps, scheme, zmode, newton_max, cg_max, have_prev0, frozen;
 };
 
@@ -679,6 +689,12 @@ __device__ __noinline__ void noinl(const F& f) {
   f();
 }
 
+// eps^2 dt of unit u (FP32 for the sine-space solver) and c1 = eps^2 dt / h^2 (FP64 residual).
+__device__ __forceinline__ float unit_fe2dt(const PArgs& a, int u) {
+  return a.eps2u ? float(a.eps2u[u] * a.dt) : a.fe2dt;
+}
+__device__ __forceinline__ double unit_c1(const PArgs& a, int u) { return a.eps2u ? a.eps2u[u] * a.dt * a.ih2 : a.c1; }
+
 enum Epi { E_PLAIN = 0, E_WPROD, E_Q, E_INIT, E_UPDATE };
 
 // One transform pass over the items of active units: rows [a0, a0 + kDstRows) of `in` ->
@@ -710,6 +726,7 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
     float cwb = 0.f;
     if (EPI == E_WPROD || EPI == E_Q || EPI == E_INIT) cwb = float(unit_wbar<N>(a, u));
     const float fcwb = a.fdt * cwb;
+    const float fe2dt = unit_fe2dt(a, u);
     double acc = 0.0;
     bool bad = false;
     for (int i0 = threadIdx.x; i0 < n * kDstRows; i0 += U * kThreads) {
@@ -747,13 +764,13 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
         } else if (EPI == E_WPROD) {
           dst[o[q]] = a.fdt * (ld[q] - cwb) * v[q];
         } else if (EPI == E_Q) {
-          const float qv = mdiag(mu1[kk[q]] + mu1[cc[q]], a.fe2dt, fcwb) * ld[q] + v[q];
+          const float qv = mdiag(mu1[kk[q]] + mu1[cc[q]], fe2dt, fcwb) * ld[q] + v[q];
           qh[o[q]] = qv;
           acc += (double)(ld[q] * qv);
         } else if (EPI == E_INIT) {
           const float mu = mu1[kk[q]] + mu1[cc[q]];
           const float r0 = v[q] / mu;
-          const float z = r0 * __frcp_rn(mdiag(mu, a.fe2dt, fcwb));
+          const float z = r0 * __frcp_rn(mdiag(mu, fe2dt, fcwb));
           xh[o[q]] = 0.f;
           rh[o[q]] = r0;
           pw[o[q]] = z;
@@ -878,6 +895,7 @@ __device__ __forceinline__ void ph_z(const PArgs& a) {
     if (a.flag[2 * u]) continue;
     const double* __restrict__ Yu = a.Y + u * pts;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    const double c1 = unit_c1(a, u);
     for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
       double lv[U], xv[U], wv[U];
 #pragma unroll
@@ -901,7 +919,7 @@ __device__ __forceinline__ void ph_z(const PArgs& a) {
           else if (a.zmode == 1) g = x;
           else if (a.zmode == 2) g = wv[q] * wv[q] * x;
           else g = a.wconst * x;
-          z[u * pts + (size_t)a0 * n + e] = a.c1 * lv[q] - a.dt * g;
+          z[u * pts + (size_t)a0 * n + e] = c1 * lv[q] - a.dt * g;
         }
       }
     }
@@ -994,6 +1012,7 @@ __device__ __forceinline__ void ph_cg_step(const PArgs& a, const double* rho_cur
     const double sig = unit_sum<N>(a.psig, u);
     const float alpha = (sig > 0.0) ? float(unit_sum<N>(rho_cur, u) / sig) : 0.f;
     const float cwb = a.fdt * float(unit_wbar<N>(a, u));
+    const float fe2dt = unit_fe2dt(a, u);
     const size_t base = u * pts + (size_t)a0 * n;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
     float acc = 0.f;
@@ -1018,7 +1037,7 @@ __device__ __forceinline__ void ph_cg_step(const PArgs& a, const double* rho_cur
           xh[base + e] = xv[q] + alpha * pv[q];
           const float r = rv[q] - alpha * qv[q];
           rh[base + e] = r;
-          acc += r * r * __frcp_rn(mdiag(mv[q], a.fe2dt, cwb));
+          acc += r * r * __frcp_rn(mdiag(mv[q], fe2dt, cwb));
         }
       }
     }
@@ -1041,6 +1060,7 @@ __device__ __forceinline__ void ph_cg_dir(const PArgs& a, const double* rho_cur,
     const double rn = unit_sum<N>(rho_new, u), ro = unit_sum<N>(rho_cur, u);
     const float beta = (ro > 0.0) ? float(rn / ro) : 0.f;
     const float cwb = a.fdt * float(unit_wbar<N>(a, u));
+    const float fe2dt = unit_fe2dt(a, u);
     const size_t base = u * pts + (size_t)a0 * n;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
     for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
@@ -1058,7 +1078,7 @@ __device__ __forceinline__ void ph_cg_dir(const PArgs& a, const double* rho_cur,
 #pragma unroll
       for (int q = 0; q < U; ++q) {
         const int e = e0 + q * kThreads;
-        if (e < cnt) ph[base + e] = rv[q] * __frcp_rn(mdiag(mv[q], a.fe2dt, cwb)) + beta * pv[q];
+        if (e < cnt) ph[base + e] = rv[q] * __frcp_rn(mdiag(mv[q], fe2dt, cwb)) + beta * pv[q];
       }
     }
     if (b == 0 && threadIdx.x == 0) {
@@ -1240,6 +1260,8 @@ void Prop2D::make_args(PArgs& a, double* Y, int units, int scheme, double dt, in
   a.floor_ = std::sqrt(p_.newton_tol);
   a.cg_tol2 = p_.cg_tol * p_.cg_tol;
   a.fe2dt = float(p_.eps2 * dt);
+  a.eps2 = p_.eps2;
+  a.eps2u = eps2u_;
   a.fdt = float(dt);
   if (scheme == SCHEME_NL) {
     a.zmode = p_.frozen ? 1 : 0;
@@ -1459,6 +1481,79 @@ cudaError_t Prop2D::build_step(const StepKey& k, cudaGraphExec_t* out) {
     case 512: return build_step_n<512>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
   }
   return cudaErrorInvalidValue;
+}
+
+
+// Host-driven execution of the same phases (plain launches; the loop conditions are read back
+// after each iteration). Slower than the graphs, but every kernel is an ordinary launch, which
+// profilers can attribute one by one (they cannot inside graphs with conditional nodes).
+namespace {
+
+template <int N>
+cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_max, int* ctr, int* active,
+                        int* host_buf, cudaStream_t st) {
+  cudaError_t e = phase_prepare<N>();
+  if (e != cudaSuccess) return e;
+  int* hc = host_buf;      // [0..1] loop counters
+  int* act = host_buf + 2; // [0..3] active counts
+#define CH_TRY(x)                             \
+  do {                                        \
+    if ((e = (x)) != cudaSuccess) return e;   \
+  } while (0)
+  CH_TRY((phase_launch<N, PH_PROLOGUE>(a, have_prev, st)));
+  CH_TRY((phase_launch<N, PH_PREDICT>(a, have_prev, st)));
+  for (int itn = 0; itn < newton_max; ++itn) {
+    hc[0] = itn;
+    hc[1] = 0;
+    CH_TRY(cudaMemcpyAsync(ctr, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CH_TRY((phase_launch<N, PH_Z>(a, have_prev, st)));
+    CH_TRY((phase_launch<N, PH_RESID>(a, have_prev, st)));
+    CH_TRY((phase_launch<N, PH_H1>(a, have_prev, st)));
+    CH_TRY((phase_launch<N, PH_H2>(a, have_prev, st)));
+    for (int it = 0; it < cg_max; ++it) {
+      hc[1] = it;
+      CH_TRY(cudaMemcpyAsync(ctr, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+      CH_TRY((phase_launch<N, PH_P1>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_STEP>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_DIR>(a, have_prev, st)));
+      CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CH_TRY(cudaStreamSynchronize(st));
+      if (act[it & 1] == 0) break;
+    }
+    CH_TRY((phase_launch<N, PH_X1>(a, have_prev, st)));
+    CH_TRY((phase_launch<N, PH_X2>(a, have_prev, st)));
+    CH_TRY((phase_launch<N, PH_NEWTON_END>(a, have_prev, st)));
+    CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CH_TRY(cudaStreamSynchronize(st));
+    if (act[2 + (itn & 1)] == 0) break;
+  }
+#undef CH_TRY
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t Prop2D::propagate_host(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
+  for (int j = 0; j < nsteps; ++j) {
+    PArgs a;
+    make_args(a, Y, units, scheme, dt, 1);
+    const int hp = (scheme == SCHEME_NL && j > 0) ? 1 : 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (p_.n + 1) {
+      case 16: e = host_step_n<16>(a, hp, p_.newton_max, p_.cg_max, ctr_, active_, host_cnt_, st); break;
+      case 32: e = host_step_n<32>(a, hp, p_.newton_max, p_.cg_max, ctr_, active_, host_cnt_, st); break;
+      case 64: e = host_step_n<64>(a, hp, p_.newton_max, p_.cg_max, ctr_, active_, host_cnt_, st); break;
+      case 128: e = host_step_n<128>(a, hp, p_.newton_max, p_.cg_max, ctr_, active_, host_cnt_, st); break;
+      case 256: e = host_step_n<256>(a, hp, p_.newton_max, p_.cg_max, ctr_, active_, host_cnt_, st); break;
+      case 512: e = host_step_n<512>(a, hp, p_.newton_max, p_.cg_max, ctr_, active_, host_cnt_, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    step_kernels_ += 2;  // prologue, predictor
+  }
+  return cudaSuccess;
 }
 
 }  // namespace chg2

@@ -14,8 +14,9 @@ enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u, ST_TIMEOU
 
 // How a batch of implicit steps is executed: one CUDA graph per step (each phase a kernel; the
 // Newton and CG loops conditional WHILE nodes, 7 kernels per CG iteration), or one persistent
-// cooperative kernel per propagate call (the same phases separated by grid barriers).
-enum StepPath { PATH_GRAPH = 0, PATH_PERSISTENT = 1 };
+// cooperative kernel per propagate call (the same phases separated by grid barriers), or plain
+// launches with the loops driven from the host (for profiling single kernels).
+enum StepPath { PATH_GRAPH = 0, PATH_PERSISTENT = 1, PATH_HOST = 2 };
 
 // Grid sizes the sine transform supports: n + 1 a power of two (radix-2 FFT of length 2(n+1)).
 bool supported_n(int n);
@@ -42,7 +43,17 @@ class Prop2D {
   // and ORs error bits into *status_dev.
   cudaError_t propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
   cudaError_t propagate_persistent(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
+  cudaError_t propagate_host(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
   void set_path(StepPath p) { path_ = p; }
+  // Per-unit eps^2 (device array [units], row i of the next propagate calls) or null (all units
+  // use Params2D::eps2). Graphs built afterwards read the array at every replay.
+  void set_unit_eps2(const double* eps2_dev) {
+    if (eps2_dev != eps2u_) {
+      for (auto& c : graphs_) cudaGraphExecDestroy(c.second);
+      graphs_.clear();
+    }
+    eps2u_ = eps2_dev;
+  }
   StepPath path() const { return path_; }
   // Orthonormal 2D DST-I (its own inverse) of `units` FP32 fields; in and out must differ and
   // must not be the internal scratch buffers.
@@ -56,8 +67,9 @@ class Prop2D {
   // step runs a fixed prologue and epilogue, each batched Newton pass kNewtonKernels and each
   // batched CG iteration kCgKernels.
   long long kernel_launches() const {
-    return path_ == PATH_PERSISTENT ? step_kernels_
-                                    : step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
+    if (path_ == PATH_PERSISTENT) return step_kernels_;
+    if (path_ == PATH_HOST) return step_kernels_ + (kNewtonKernels - 2) * newton_passes_ + (kCgKernels - 1) * cg_total_;
+    return step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
   }
   static constexpr int kStepKernelsNL = 3;   // prologue, predictor, loop start
   static constexpr int kStepKernelsLin = 3;
@@ -120,6 +132,7 @@ class Prop2D {
   long long cg_unit_total_ = 0;
   long long step_kernels_ = 0;
   StepPath path_ = PATH_GRAPH;
+  const double* eps2u_ = nullptr;  // per-unit eps^2 or null
   int persist_minb_ = 3;      // persistent path: blocks per SM it is compiled for (2, 3, 4)
   double* ppart_ = nullptr;   // persistent path: per-item partial sums [7][cap][rows / 16]
   int* active_ = nullptr;     // persistent path: units still iterating (parity slots)
@@ -129,8 +142,9 @@ class Prop2D {
 // Parareal correction of one slice for `count` problems list[0..count) (Eq. 2.2), fused with
 // the increment and error norms: U_{s+1} = F_s + (g - Gold_s) (init: U_{s+1} = g), Gold_s = g,
 // and g (work rows, contiguous) is overwritten with U_{s+1}. U, F, Gold point at slice s+1 / s
-// of problem 0; ustride / fstride are the per-problem strides. acc[b] = {inc, err_l2, err_max}
-// are running maxima over slices (h2 = h^d for the L2_h norm). part: correct_partials(count).
+// of problem 0; ustride / fstride are the per-problem strides. acc[b] = {inc, err_l2, err_max,
+// max |U_{s+1}| (infinite if not finite)} are running maxima over slices (h2 = h^d for the L2_h
+// norm). part: correct_partials(count).
 cudaError_t launch_correct(double* U, const double* F, double* g, double* Gold, const double* Uref, const int* list,
                            int count, size_t pts, size_t ustride, size_t fstride, int init, double* part, double* acc,
                            double h2, cudaStream_t st);

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <new>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -39,6 +42,8 @@ struct ch_parareal {
   bool ref_valid = false;
   bool ran = false;
   int grid = 0;
+  size_t ps_bytes = 0;
+  bool tuned = false;  // 1D fine-sweep launch configuration chosen by measurement
   // Each iteration replays two graphs, [fine sweep] then [coarse sweep + correction, tally];
   // timing events are recorded on the stream between them (events inside a graph cannot time).
   cudaGraphExec_t gfine = nullptr;
@@ -71,6 +76,8 @@ struct ch_parareal {
   std::vector<int> h_learned, h_fallback;
   long long gt_launches = 0;
   long long aux_launches = 0;  // gather / scatter / correction kernels of the 2D driver
+  std::vector<double> eps_prob;   // per-problem eps (2D, ch_parareal_set_eps); empty = cfg.eps
+  double* eps2u_dev = nullptr;    // eps^2 of the gathered work rows [B N]
 };
 
 namespace {
@@ -166,6 +173,16 @@ ch_status gather_units(ch_parareal* h, double* src, const std::vector<long long>
   if (off.empty()) return CH_OK;
   CH_CUDA(h, cudaMemcpyAsync(h->doff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, h->st));
   h->aux_launches += 1;
+  if (to_w && h->eps2u_dev) {
+    // eps^2 of each work row, from the problem its offset (into U) belongs to
+    const size_t us = (size_t)(h->p.N + 1) * h->pts;
+    std::vector<double> e2(off.size());
+    for (size_t i = 0; i < off.size(); ++i) {
+      const double e = h->eps_prob[(size_t)off[i] / us];
+      e2[i] = e * e;
+    }
+    CH_CUDA(h, cudaMemcpyAsync(h->eps2u_dev, e2.data(), e2.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  }
   if (to_w) {
     CH_CUDA(h, chg2::launch_gather(h->W, src, h->doff, (int)off.size(), h->pts, h->st));
   } else {
@@ -241,7 +258,7 @@ ch_status run2d(ch_parareal* h) {
   h->h_fallback.assign(B, -1);
   std::vector<int> active(B, 1);
   std::vector<int>& learned = h->h_learned;
-  std::vector<double> acc(3 * B);
+  std::vector<double> acc(4 * B);
   int nl = 0;  // active problems still on G_theta: listed first
   auto list_of = [&](std::vector<int>& L) {
     L.clear();
@@ -252,16 +269,45 @@ ch_status run2d(ch_parareal* h) {
     for (int b : L) nl += learned[b];
   };
   auto pull_acc = [&]() -> ch_status {
-    CH_CUDA(h, cudaMemcpyAsync(acc.data(), h->acc, 3 * B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CH_CUDA(h, cudaMemcpyAsync(acc.data(), h->acc, 4 * B * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CH_CUDA(h, cudaStreamSynchronize(h->st));
     return CH_OK;
   };
+  // Restart of the coarse guess from slice s0 with the plain step for the problems `R` (their
+  // slices <= s0 are exact): U_{s+1} = G(U_s), Gold_s = G(U_s) for s >= s0 (Section 4's
+  // initial sweep from s0). Their norms are recomputed.
+  auto restart_plain = [&](const std::vector<int>& R, int s0) -> ch_status {
+    if (R.empty() || s0 >= N) return CH_OK;
+    for (int b : R) {
+      CH_CUDA(h, cudaMemsetAsync(h->acc + 4 * b, 0, 4 * sizeof(double), h->st));
+      // slice s0 is the fine result F(U_{s0-1}) (exact), whatever the learned step produced
+      if (s0 > 0)
+        CH_CUDA(h, cudaMemcpyAsync(h->U + b * us + s0 * pts, h->F + b * fs + (s0 - 1) * pts, pts * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, h->st));
+    }
+    CH_CUDA(h, cudaMemcpyAsync(h->dlist, R.data(), R.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    std::vector<long long> o(R.size());
+    for (size_t i = 0; i < R.size(); ++i) o[i] = (long long)(R[i] * us + s0 * pts);
+    ch_status st = gather_units(h, h->U, o, true);
+    for (int sl = s0; sl < N && st == CH_OK; ++sl) {
+      st = prop2(h, (int)R.size(), coarse2(h), h->p.dtc, h->p.coarse_steps);
+      if (st != CH_OK) break;
+      CH_CUDA(h, chg2::launch_correct(h->U + (sl + 1) * pts, h->F + sl * pts, h->W, h->Gold + sl * pts,
+                                      ref ? ref + (sl + 1) * pts : nullptr, h->dlist, (int)R.size(), pts, us, fs, 1,
+                                      h->cpart, h->acc, h2, h->st));
+      h->aux_launches += 2;
+    }
+    return st;
+  };
+  // A learned coarse state that is not finite or leaves [-kGuard, kGuard] (Cahn-Hilliard states
+  // stay near [-1, 1]) is a failed prediction: the problem leaves G_theta.
+  constexpr double kGuard = 4.0;
   CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
   // coarse initial guess (Section 4): U_{s+1} = G(U_s), Gold_s = U_{s+1}
   std::vector<int> L;
   list_of(L);
   CH_CUDA(h, cudaMemcpyAsync(h->dlist, L.data(), L.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
-  CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 3 * B * sizeof(double), h->st));
+  CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 4 * B * sizeof(double), h->st));
   std::vector<long long> off(L.size());
   for (size_t i = 0; i < L.size(); ++i) off[i] = (long long)(L[i] * us);
   ch_status s = gather_units(h, h->U, off, true);
@@ -275,9 +321,22 @@ ch_status run2d(ch_parareal* h) {
   }
   if (s != CH_OK) return s;
   if ((s = pull_acc()) != CH_OK) return s;
+  {
+    std::vector<int> R;
+    for (int b = 0; b < B; ++b)
+      if (learned[b] && !(acc[4 * b + 3] <= kGuard)) {
+        learned[b] = 0;
+        h->h_fallback[b] = 0;
+        R.push_back(b);
+      }
+    if (!R.empty()) {
+      if ((s = restart_plain(R, 0)) != CH_OK) return s;
+      if ((s = pull_acc()) != CH_OK) return s;
+    }
+  }
   for (int b = 0; b < B; ++b) {
-    h->h_el2[b].push_back(ref ? acc[3 * b + 1] : -1.0);
-    h->h_emx[b].push_back(ref ? acc[3 * b + 2] : -1.0);
+    h->h_el2[b].push_back(ref ? acc[4 * b + 1] : -1.0);
+    h->h_emx[b].push_back(ref ? acc[4 * b + 2] : -1.0);
   }
   CH_CUDA(h, cudaEventRecord(h->ev[1], h->st));
   int k = 0;
@@ -305,7 +364,7 @@ ch_status run2d(ch_parareal* h) {
     h->fine_cg += h->p2->cg_unit_iterations() - c0;
     // sequential coarse sweep with the correction of Eq. 2.2 and the norms
     CH_CUDA(h, cudaMemcpyAsync(h->dlist, L.data(), nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
-    CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 3 * B * sizeof(double), h->st));
+    CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 4 * B * sizeof(double), h->st));
     off.resize(nb);
     for (int i = 0; i < nb; ++i) off[i] = (long long)(L[i] * us + k * pts);
     if ((s = gather_units(h, h->U, off, true)) != CH_OK) return s;
@@ -325,8 +384,19 @@ ch_status run2d(ch_parareal* h) {
     h->fine_ms += fm;
     h->coarse_ms += cm;
     std::vector<long long> goff, uoff2;  // G(U_n^k) of problems leaving G_theta, slices > k
+    std::vector<int> R;                  // problems whose learned coarse states broke the guard
+    for (int b : L)
+      if (learned[b] && !(acc[4 * b + 3] <= kGuard)) {
+        learned[b] = 0;
+        h->h_fallback[b] = k + 1;
+        R.push_back(b);
+      }
+    if (!R.empty()) {
+      if ((s = restart_plain(R, k + 1)) != CH_OK) return s;
+      if ((s = pull_acc()) != CH_OK) return s;
+    }
     for (int b : L) {
-      const double inc = acc[3 * b], el2 = acc[3 * b + 1], emx = acc[3 * b + 2];
+      const double inc = acc[4 * b], el2 = acc[4 * b + 1], emx = acc[4 * b + 2];
       h->h_inc[b].push_back(inc);
       h->h_el2[b].push_back(ref ? el2 : -1.0);
       h->h_emx[b].push_back(ref ? emx : -1.0);
@@ -366,6 +436,149 @@ ch_status run2d(ch_parareal* h) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ 1D fine-sweep autotuner
+//
+// The fine sweep's launch configuration (CTA mapping T x P of one system per CTA, and the
+// persistent grid: all resident CTAs or half of them) is chosen by timing each candidate once
+// on the handle's own first fine sweep (after the coarse initial guess), with the control
+// block and problem state restored after each trial. Choices are cached per process, keyed by
+// (n, units, scheme path), and in the file named by CH_AUTOTUNE_CACHE when that is set.
+// CH_AUTOTUNE=0 keeps the default configuration.
+namespace {
+
+struct TuneChoice {
+  int alt = 0;
+  int div = 1;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const Params1D& p) {
+  return "fine1d n=" + std::to_string(p.n) + " units=" + std::to_string(p.B * p.N) + " scheme=" +
+         std::to_string(p.fine_scheme) + " precision=" + std::to_string(p.precision);
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("CH_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    std::string l(line);
+    const size_t bar = l.find('|');
+    if (bar == std::string::npos) continue;
+    TuneChoice c;
+    if (std::sscanf(l.c_str() + bar + 1, " alt=%d div=%d", &c.alt, &c.div) == 2) g_tune[l.substr(0, bar)] = c;
+  }
+  std::fclose(f);
+}
+
+void tune_save_locked() {
+  const char* path = std::getenv("CH_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tune) std::fprintf(f, "%s| alt=%d div=%d\n", kv.first.c_str(), kv.second.alt, kv.second.div);
+  std::fclose(f);
+}
+
+ch_status tune_fine_sweep(ch_parareal* h) {
+  const char* off = std::getenv("CH_AUTOTUNE");
+  if (off && std::strcmp(off, "0") == 0) return CH_OK;
+  const std::string key = tune_key(h->p);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      Params1D q = h->p;
+      q.alt = chg::fine_sweep_has_alt(q) ? it->second.alt : 0;
+      int grid = 0;
+      CH_CUDA(h, chg::fine_sweep_max_grid(q, &grid));
+      h->p.alt = q.alt;
+      h->grid = std::max(1, grid / std::max(1, it->second.div));
+      return CH_OK;
+    }
+  }
+  void* snap = nullptr;
+  CH_CUDA(h, cudaMalloc(&snap, sizeof(Ctrl) + h->ps_bytes));
+  char* sc = static_cast<char*>(snap);
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaMemcpyAsync(sc, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sc + sizeof(Ctrl), h->ps_block, h->ps_bytes, cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  TuneChoice best;
+  float best_ms = 1e30f;
+  const int nalt = chg::fine_sweep_has_alt(h->p) ? 2 : 1;
+  for (int alt = 0; alt < nalt && e == cudaSuccess; ++alt)
+    for (int div = 1; div <= 2 && e == cudaSuccess; ++div) {
+      Params1D q = h->p;
+      q.alt = alt;
+      int grid = 0;
+      e = chg::fine_sweep_max_grid(q, &grid);
+      if (e != cudaSuccess) break;
+      grid = std::max(1, grid / div);
+      e = cudaMemcpyAsync(h->ctrl, sc, sizeof(Ctrl), cudaMemcpyDeviceToDevice, h->st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->ps_block, sc + sizeof(Ctrl), h->ps_bytes, cudaMemcpyDeviceToDevice, h->st);
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->st);
+      if (e == cudaSuccess) e = chg::launch_fine_sweep(q, h->U, h->F, h->ctrl, h->ps, grid, h->st);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best.alt = alt;
+        best.div = div;
+      }
+    }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctrl, sc, sizeof(Ctrl), cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->ps_block, sc + sizeof(Ctrl), h->ps_bytes, cudaMemcpyDeviceToDevice, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(snap);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fine-sweep autotuning");
+  Params1D q = h->p;
+  q.alt = best.alt;
+  int grid = 0;
+  CH_CUDA(h, chg::fine_sweep_max_grid(q, &grid));
+  h->p.alt = best.alt;
+  h->grid = std::max(1, grid / best.div);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  tune_save_locked();
+  return CH_OK;
+}
+
+// Tunes once per handle, before its first reference or run, so that both use the same fine-sweep
+// configuration (the sequential reference then equals the Parareal iterate at k = N bit for bit).
+// The trial sweeps run on a coarse initial guess written into U (overwritten by run).
+ch_status ensure_tuned(ch_parareal* h) {
+  if (h->tuned) return CH_OK;
+  std::vector<int> ones(h->B, 1);
+  CH_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->st));
+  CH_CUDA(h, cudaMemsetAsync(h->ps_block, 0, h->ps_bytes, h->st));
+  CH_CUDA(h, cudaMemcpyAsync(h->ps.active, ones.data(), h->B * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, nullptr, h->ctrl, h->ps, 1, h->st));
+  ch_status s = tune_fine_sweep(h);
+  if (s != CH_OK) return s;
+  h->tuned = true;
+  if (h->gfine) {
+    cudaGraphExecDestroy(h->gfine);
+    h->gfine = nullptr;
+  }
+  return CH_OK;
+}
+
+}  // namespace
+
 
 extern "C" {
 
@@ -415,6 +628,7 @@ void ch_parareal_destroy(ch_parareal* h) {
     delete h->gt;
   }
   cudaFree(h->Wtmp);
+  cudaFree(h->eps2u_dev);
   delete h;
 }
 
@@ -455,6 +669,7 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
   const size_t nd = B * maxit + 2 * B * (maxit + 1);
   const size_t bytes = nd * sizeof(double) + B * sizeof(unsigned long long) + 4 * B * sizeof(int);
   if ((e = cudaMalloc(&h->ps_block, bytes))) return bail(e, "cudaMalloc(problem state)");
+  h->ps_bytes = bytes;
   char* q = static_cast<char*>(h->ps_block);
   h->ps.inc = reinterpret_cast<double*>(q);
   h->ps.err_l2 = h->ps.inc + B * maxit;
@@ -480,7 +695,7 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
     }
     if ((e = h->p2->init(params2d(cfg), (int)(B * N), h->st))) return bail(e, "2D work space");
     if ((e = cudaMalloc(&h->W, B * N * pts * sizeof(double)))) return bail(e, "cudaMalloc(W)");
-    if ((e = cudaMalloc(&h->acc, B * 3 * sizeof(double)))) return bail(e, "cudaMalloc(acc)");
+    if ((e = cudaMalloc(&h->acc, B * 4 * sizeof(double)))) return bail(e, "cudaMalloc(acc)");
     if ((e = cudaMalloc(&h->cpart, chg2::correct_partials((int)B) * sizeof(double)))) return bail(e, "cudaMalloc");
     if ((e = cudaMalloc(&h->dlist, B * sizeof(int)))) return bail(e, "cudaMalloc(list)");
     if ((e = cudaMalloc(&h->doff, B * N * sizeof(long long)))) return bail(e, "cudaMalloc(offsets)");
@@ -535,6 +750,10 @@ ch_status ch_parareal_compute_reference(ch_parareal* h) {
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "compute_reference before set_initial");
   if (h->dim == 2) return reference2d(h);
+  {
+    ch_status s = ensure_tuned(h);
+    if (s != CH_OK) return s;
+  }
   const size_t N = h->p.N, pts = h->pts;
   CH_CUDA(h, cudaMemcpy2DAsync(h->Uref, (N + 1) * pts * sizeof(double), h->U, (N + 1) * pts * sizeof(double),
                                pts * sizeof(double), h->B, cudaMemcpyDeviceToDevice, h->st));
@@ -550,6 +769,7 @@ ch_status ch_parareal_compute_reference(ch_parareal* h) {
 }
 
 }  // extern "C"
+
 
 // Captures the work enqueued by `enqueue` on a private stream into an executable graph.
 template <typename F>
@@ -584,8 +804,12 @@ ch_status ch_parareal_run(ch_parareal* h) {
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "run before set_initial");
   if (h->dim == 2) return run2d(h);
   const int B = h->B, maxit = h->p.maxit;
-  // reset control and per-problem state
   std::vector<int> ones(B, 1);
+  {
+    ch_status s = ensure_tuned(h);
+    if (s != CH_OK) return s;
+  }
+  // reset control and per-problem state
   CH_CUDA(h, cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->st));
   CH_CUDA(h, cudaMemsetAsync(h->ps_block, 0,
                              (size_t)B * maxit * sizeof(double) + 2 * (size_t)B * (maxit + 1) * sizeof(double) +
@@ -776,6 +1000,19 @@ ch_status ch_parareal_set_coarse_model(ch_parareal* h, const float* params_host,
     CH_CUDA(h, cudaMalloc(&h->Wtmp, (size_t)h->B * h->pts * sizeof(double)));
   CH_CUDA(h, h->gt->set_params(params_host, h->st));
   h->gt_form = form;
+  return CH_OK;
+}
+
+ch_status ch_parareal_set_eps(ch_parareal* h, const double* eps_host, size_t len) {
+  if (!h) return CH_ERR_INVALID;
+  if (h->dim != 2) return fail(h, CH_ERR_INVALID, "set_eps: per-problem eps is supported in 2D");
+  if (!eps_host || len != (size_t)h->B) return fail(h, CH_ERR_INVALID, "set_eps: len must equal the batch");
+  for (size_t b = 0; b < len; ++b)
+    if (!(eps_host[b] > 0.0) || !std::isfinite(eps_host[b])) return fail(h, CH_ERR_INVALID, "set_eps: eps must be > 0");
+  if (!h->eps2u_dev) CH_CUDA(h, cudaMalloc(&h->eps2u_dev, (size_t)h->B * h->p.N * sizeof(double)));
+  h->eps_prob.assign(eps_host, eps_host + len);
+  h->p2->set_unit_eps2(h->eps2u_dev);
+  h->ref_valid = false;
   return CH_OK;
 }
 

@@ -99,6 +99,12 @@ def test_gtheta_entry_points_reject_invalid_arguments_without_device():
     assert lib.ch_gtheta_train(None, None, None, 1, 2, 8, 1, 1, 1, 1e-3, 0, None) == 1
     assert lib.ch_parareal_set_coarse_model(None, None, 0, 0) == 1
     assert lib.ch_parareal_get_reference_device(None, None, 0) == 1
+    assert lib.ch_parareal_set_eps(None, None, 0) == 1
+    assert lib.ch_ensemble_create(None, 1, None, None, None) == 1
+    assert lib.ch_ensemble_run(None) == 1
+    assert lib.ch_ensemble_groups(None) == 0
+    lib.ch_ensemble_destroy(None)
+    assert lib.ch_ensemble_last_error(None).decode() == "NULL handle"
 
 
 def test_gtheta_parameter_layout_matches_header():

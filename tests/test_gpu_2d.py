@@ -207,3 +207,59 @@ def test_persistent_and_graph_paths_agree(gpu_lib, monkeypatch, n):
     a2 = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
     assert np.array_equal(g, g2) and np.array_equal(a, a2)
     assert np.max(np.abs(a - g)) <= 64 * step_bound_2d(n, eps, dt) * nsteps
+
+
+def test_per_problem_eps_matches_oracle(gpu_lib):
+    """A batch whose problems have different eps (ch_parareal_set_eps): each problem's sequential
+    fine solution and Parareal iterates follow the oracle run with its own eps."""
+    ch = gpu_lib
+    n, N, J = 31, 4, 3
+    eps = [0.03, 0.05, 0.08]
+    cfg = ch.Config(dim=2, n=n, eps=0.05, T=0.01, n_slices=N, fine_steps=J, variant="NPA-I", newton_tol=1e-12,
+                    max_iters=2)
+    u0s = [ch_inputs.initial_condition(2, n, 400 + b, kind="normal", amp=0.1) for b in range(3)]
+    pr = ch.Parareal(cfg, batch=3)
+    pr.set_initial_batch(np.stack(u0s))
+    pr.set_eps(eps)
+    pr.compute_reference()
+    pr.run()
+    for b in range(3):
+        c = ch.Config(dim=2, n=n, eps=eps[b], T=0.01, n_slices=N, fine_steps=J, variant="NPA-I",
+                      newton_tol=1e-12, max_iters=2)
+        p = oracle_params(c)
+        Uf = o2.fine_solution(p, u0s[b])
+        r = o2.parareal(p, u0s[b], Uf, max_iters=2)
+        tol = 64 * step_bound_2d(n, eps[b], 0.01 / N) * (2 * N + J * N) + 1e-12
+        assert np.max(np.abs(pr.get_reference(b) - Uf)) <= tol
+        assert np.max(np.abs(pr.get_slices(b) - r.U)) <= tol
+    pr.close()
+
+
+def test_ensemble_of_uneven_grids_matches_single_problem_runs(gpu_lib):
+    """An ensemble groups its problems by grid size (one batched handle per size, run
+    concurrently); each problem's iterates and reference equal those of its own single-problem
+    handle (the 2D kernels treat every unit independently)."""
+    ch = gpu_lib
+    ns = [15, 31, 15, 31, 63]
+    eps = [0.04, 0.06, 0.05, 0.03, 0.05]
+    cfg = ch.Config(dim=2, n=15, eps=0.05, T=0.01, n_slices=4, fine_steps=3, variant="NPA-I", newton_tol=1e-12,
+                    max_iters=3)
+    u0s = [ch_inputs.initial_condition(2, n, 500 + i, kind="normal", amp=0.1) for i, n in enumerate(ns)]
+    ens = ch.Ensemble(cfg, ns, eps)
+    assert ens.groups == 3
+    for i, u in enumerate(u0s):
+        ens.set_initial(i, u)
+    ens.compute_reference()
+    ens.run()
+    for i, (n, e) in enumerate(zip(ns, eps)):
+        c = ch.Config(dim=2, n=n, eps=e, T=0.01, n_slices=4, fine_steps=3, variant="NPA-I", newton_tol=1e-12,
+                      max_iters=3)
+        pr = ch.Parareal(c, batch=1)
+        pr.set_initial(0, u0s[i])
+        pr.compute_reference()
+        pr.run()
+        assert np.array_equal(ens.get_slices(i), pr.get_slices(0)), i
+        assert np.array_equal(ens.get_reference(i), pr.get_reference(0)), i
+        assert ens.stats(i)["iterations"] == 3
+        pr.close()
+    ens.close()

@@ -237,3 +237,22 @@ def test_plain_coarse_model_can_be_restored(gpu_lib):
     assert pr.stats(0)["coarse_model"] == 0
     plain.close()
     pr.close()
+
+
+def test_guard_restarts_runaway_learned_coarse_sweep_with_plain_step(gpu_lib):
+    """G(U) = 11 U leaves the range of Cahn-Hilliard states within two slices: the guard sends
+    the problem back to the plain step at the initial sweep, after which the run is the plain
+    run, bit for bit."""
+    ch = gpu_lib
+    n, N = 31, 6
+    cfg = ch.Config(dim=2, n=n, eps=0.05, T=0.03, n_slices=N, fine_steps=4, variant="NPA-I", newton_tol=1e-12,
+                    max_iters=3)
+    u0 = ch_inputs.initial_condition(2, n, 77, kind="normal", amp=0.05)[None]
+    plain = run_parareal(ch, cfg, u0)
+    pr = run_parareal(ch, cfg, u0, params=scaling_net(ch, 10.0), form="residual")
+    st = pr.stats(0)
+    assert st["coarse_model"] == 1 and st["coarse_fallback_iter"] == 0
+    assert np.array_equal(pr.get_slices(0), plain.get_slices(0))
+    assert np.array_equal(st["err_l2"], plain.stats(0)["err_l2"])
+    plain.close()
+    pr.close()
