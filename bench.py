@@ -71,14 +71,14 @@ FINE_SWEEP_1D_TRAFFIC = 223.7e6
 
 
 # 2D fine sweep, algorithmic DRAM/L2 bytes per grid point and unit, each array read or written
-# once per phase. CG iteration (6 phases): p to physical space (read p, write t: 8), times
-# dt (wc - wbar) (read t, wc, write t2: 12), back to sine space (8), q = M p + That with (p, q)
-# (read t, p, write q: 12), x/r update with (r, r/m) (read p, x, r, q, write x, r: 24), p update
-# (read p, r, write p: 12). Newton iteration: z = c1 lap Y - dt g (read Y, write z FP64: 16), H and
-# weights (read Y, Yhat, z, write H, wc: 32), H to sine space and CG start (8 + 16), correction to
+# once per phase. CG iteration (5 phases): u to physical space (read u, write t: 8), times
+# dt (wc - wbar) (read t, wc, write t2: 12), back to sine space (8), w = M u + That with (w, u)
+# and (r, u) (read t, u, r, write w: 16), update of p, s, x, r, u (read u, w, p, s, x, r, write
+# p, s, x, r, u: 44). Newton iteration: z = c1 lap Y - dt g (read Y, write z FP64: 16), H and
+# weights (read Y, Yhat, z, write H, wc: 32), H to sine space and CG start (8 + 16: write x, r, u), correction to
 # physical space (8), FP64 update (read d, Y, write Y: 20). Step: right-hand side (16) and
 # predictor (read Y, Yprev, write both: 32).
-BYTES_CG_2D = 8 + 12 + 8 + 12 + 24 + 12
+BYTES_CG_2D = 8 + 12 + 8 + 16 + 44
 BYTES_NEWTON_2D = 16 + 32 + 8 + 16 + 8 + 20
 BYTES_STEP_2D = 16 + 32
 

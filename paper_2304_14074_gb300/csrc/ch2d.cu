@@ -26,6 +26,7 @@
 // transposed, so two passes give S X S (S the orthonormal DST-I matrix, S^2 = I).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -443,11 +444,14 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   al((void**)&flag_, (size_t)cap * 2 * sizeof(int));
   al((void**)&newton_cnt_, (size_t)cap * sizeof(int));
   al((void**)&status_, 4 * sizeof(unsigned) + sizeof(unsigned long long));
-  al((void**)&ctr_, 4 * sizeof(int));
+  al((void**)&ctr_, 4 * kMaxGroups * sizeof(int));
   // [0] CG iterations (batched), [1] Newton passes (batched), [2] CG iterations summed over units
   al((void**)&cg_dev_, 4 * sizeof(unsigned long long));
   al((void**)&ppart_, (size_t)7 * cap * ((p.n + kDstRows - 1) / kDstRows) * sizeof(double));
-  al((void**)&active_, 4 * sizeof(int));
+  al((void**)&active_, 4 * kMaxGroups * sizeof(int));
+  al((void**)&cgs_, (size_t)cap * 8 * sizeof(double));
+  al((void**)&uh_, v32);
+  al((void**)&sh_, v32);
   al((void**)&bar_, 4 * sizeof(unsigned));
   if (e != cudaSuccess) return e;
   e = cudaHostAlloc((void**)&host_cnt_, 8 * sizeof(int), 0);
@@ -473,8 +477,16 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
 void Prop2D::release() {
   for (auto& c : graphs_) cudaGraphExecDestroy(c.second);
   graphs_.clear();
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (gs_[g]) cudaStreamDestroy(gs_[g]);
+    if (gev_[g]) cudaEventDestroy(gev_[g]);
+    gs_[g] = nullptr;
+    gev_[g] = nullptr;
+  }
+  if (gfork_) cudaEventDestroy(gfork_);
+  gfork_ = nullptr;
   void* ptrs[] = {yhat_, yprev_, z_, xacc_, w_, rhs_, xh_, rh_, ph_, qh_, tmp_, tmp2_, mu_, tw_, part_, scal_, flag_,
-                  newton_cnt_, status_, ctr_, cg_dev_, ppart_, active_, bar_};
+                  newton_cnt_, status_, ctr_, cg_dev_, ppart_, active_, bar_, cgs_, uh_, sh_};
   for (void* q : ptrs) cudaFree(q);
   if (host_cnt_) cudaFreeHost(host_cnt_);
   host_cnt_ = nullptr;
@@ -488,6 +500,8 @@ void Prop2D::release() {
   ppart_ = nullptr;
   active_ = nullptr;
   bar_ = nullptr;
+  cgs_ = nullptr;
+  uh_ = sh_ = nullptr;
 }
 
 cudaError_t Prop2D::dst2(const float* in, float* out, int units, cudaStream_t st) {
@@ -539,19 +553,42 @@ cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int n
   if (units > cap_ || units < 1) return cudaErrorInvalidValue;
   if (path_ == PATH_PERSISTENT) return propagate_persistent(Y, units, scheme, dt, nsteps, st);
   if (path_ == PATH_HOST) return propagate_host(Y, units, scheme, dt, nsteps, st);
-  for (int j = 0; j < nsteps; ++j) {
-    StepKey k{Y, units, scheme, dt, (scheme == SCHEME_NL && j > 0) ? 1 : 0};
-    cudaGraphExec_t ex = nullptr;
-    for (auto& c : graphs_)
-      if (c.first == k) ex = c.second;
-    if (!ex) {
-      const cudaError_t e = build_step(k, &ex);
+  // Independent units are split into up to kMaxGroups groups whose step graphs run concurrently
+  // on streams of their own: each phase is a chain of dependent latencies over few blocks, so
+  // concurrent groups fill the GPU that one group leaves idle.
+  const int groups = std::max(1, std::min(kMaxGroups, units / kMinGroupUnits));
+  cudaError_t e = cudaSuccess;
+  if (groups > 1) {
+    if (!gs_[0]) {
+      for (int g = 0; g < kMaxGroups && e == cudaSuccess; ++g) {
+        e = cudaStreamCreateWithFlags(&gs_[g], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gev_[g], cudaEventDisableTiming);
+      }
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gfork_, cudaEventDisableTiming);
       if (e != cudaSuccess) return e;
-      graphs_.push_back({k, ex});
     }
-    const cudaError_t e = cudaGraphLaunch(ex, st);
-    if (e != cudaSuccess) return e;
-    step_kernels_ += (scheme == SCHEME_NL) ? kStepKernelsNL : kStepKernelsLin;
+    if ((e = cudaEventRecord(gfork_, st)) != cudaSuccess) return e;
+  }
+  for (int g = 0; g < groups; ++g) {
+    const int u0 = (int)((long long)units * g / groups), u1 = (int)((long long)units * (g + 1) / groups);
+    cudaStream_t gst = (groups > 1) ? gs_[g] : st;
+    if (groups > 1 && (e = cudaStreamWaitEvent(gst, gfork_, 0)) != cudaSuccess) return e;
+    for (int j = 0; j < nsteps; ++j) {
+      StepKey k{Y + (size_t)u0 * pts_, u1 - u0, scheme, dt, (scheme == SCHEME_NL && j > 0) ? 1 : 0, u0, g};
+      cudaGraphExec_t ex = nullptr;
+      for (auto& c : graphs_)
+        if (c.first == k) ex = c.second;
+      if (!ex) {
+        if ((e = build_step(k, &ex)) != cudaSuccess) return e;
+        graphs_.push_back({k, ex});
+      }
+      if ((e = cudaGraphLaunch(ex, gst)) != cudaSuccess) return e;
+      step_kernels_ += (scheme == SCHEME_NL) ? kStepKernelsNL : kStepKernelsLin;
+    }
+    if (groups > 1) {
+      if ((e = cudaEventRecord(gev_[g], gst)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(st, gev_[g], 0)) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -608,9 +645,12 @@ struct PArgs {
   const float2* tw;
   double* pmin;   // [units][nb] per item: min wc
   double* pmax;   //                 max wc
-  double* psig;   //                 (p, q)
-  double* prho;   // [2][units][nb]  (r, r / m)
-  double* prho0;  // [units][nb]     rho at the start of CG
+  double* pdel;   //                 (w, u)
+  double* cgs;    // [units][8]      CG scalars: alpha, gamma of the last iteration (parity
+                  //                 slots 0, 1 and 2, 3), gamma_0 (slot 4)
+  float* uh;      // u = M^{-1} r (sine space)
+  float* sh;      // s = S p (sine space)
+  double* pgam;   // [units][nb]     (r, u)
   double* pd;     // [units][nb]     max |d|
   int* flag;      // [units][2]: Newton done, CG done
   int* cnt;       // [units] Newton iterations of the step
@@ -695,12 +735,12 @@ __device__ __forceinline__ float unit_fe2dt(const PArgs& a, int u) {
 }
 __device__ __forceinline__ double unit_c1(const PArgs& a, int u) { return a.eps2u ? a.eps2u[u] * a.dt * a.ih2 : a.c1; }
 
-enum Epi { E_PLAIN = 0, E_WPROD, E_Q, E_INIT, E_UPDATE };
+enum Epi { E_PLAIN = 0, E_WPROD, E_W, E_INIT, E_UPDATE };
 
 // One transform pass over the items of active units: rows [a0, a0 + kDstRows) of `in` ->
 // DST-I -> column a of the output (transposed), then the epilogue.
-//   E_PLAIN: out = v;  E_WPROD: out = dt (wc - wbar) v;  E_Q: q = m p + v, sum p q;
-//   E_INIT: b = v / mu, r = b, p = r / m, x = 0, sum r p;  E_UPDATE: Y -= v, max |v|.
+//   E_PLAIN: out = v;  E_WPROD: out = dt (wc - wbar) v;  E_W: w = m u + v (= S u), sums (w, u)
+//   and (r, u);  E_INIT: r = v / mu, u = r / m, x = 0;  E_UPDATE: Y -= v, max |v|.
 // `act` selects the units: 0 = not Newton-done, 1 = not Newton-done and not CG-done.
 template <int N, int EPI>
 __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const float2* twd, const float* in, float* out,
@@ -712,11 +752,11 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   const float sc = 0.5f * sqrtf(2.0f / N);
   const float* __restrict__ mu1 = a.mu1;
   const float* __restrict__ wv = a.w;
-  const float* __restrict__ ph = a.ph;
   float* __restrict__ qh = a.qh;
   float* __restrict__ xh = a.xh;
   float* __restrict__ rh = a.rh;
-  float* __restrict__ pw = a.ph;
+  const float* __restrict__ uh = a.uh;
+  float* __restrict__ uw = a.uh;
   double* __restrict__ Y = a.Y;
   float* __restrict__ dst = out;
   {
@@ -724,13 +764,13 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
     if (a.flag[2 * u] || (act == 1 && a.flag[2 * u + 1])) return;  // block-uniform
     fft_rows<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
     float cwb = 0.f;
-    if (EPI == E_WPROD || EPI == E_Q || EPI == E_INIT) cwb = float(unit_wbar<N>(a, u));
+    if (EPI == E_WPROD || EPI == E_W || EPI == E_INIT) cwb = float(unit_wbar<N>(a, u));
     const float fcwb = a.fdt * cwb;
     const float fe2dt = unit_fe2dt(a, u);
-    double acc = 0.0;
+    double acc = 0.0, acc2 = 0.0;
     bool bad = false;
     for (int i0 = threadIdx.x; i0 < n * kDstRows; i0 += U * kThreads) {
-      float v[U], ld[U];
+      float v[U], ld[U], ld2[U];
       size_t o[U];
       int kk[U], cc[U];
       bool ok[U];
@@ -744,11 +784,15 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
         o[q] = u * pts + (size_t)k * n + cc[q];
         v[q] = 0.f;
         ld[q] = 0.f;
+        ld2[q] = 0.f;
         if (ok[q]) {
           const float2 c = buf[pad8((r >> 1) * L + k + 1)];
           v[q] = (r & 1) ? c.x * sc : -c.y * sc;
           if (EPI == E_WPROD) ld[q] = wv[o[q]];
-          if (EPI == E_Q) ld[q] = ph[o[q]];
+          if (EPI == E_W) {
+            ld[q] = uh[o[q]];
+            ld2[q] = rh[o[q]];
+          }
         }
       }
       double yv[U];
@@ -763,18 +807,17 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
           dst[o[q]] = v[q];
         } else if (EPI == E_WPROD) {
           dst[o[q]] = a.fdt * (ld[q] - cwb) * v[q];
-        } else if (EPI == E_Q) {
-          const float qv = mdiag(mu1[kk[q]] + mu1[cc[q]], fe2dt, fcwb) * ld[q] + v[q];
-          qh[o[q]] = qv;
-          acc += (double)(ld[q] * qv);
+        } else if (EPI == E_W) {
+          const float w = mdiag(mu1[kk[q]] + mu1[cc[q]], fe2dt, fcwb) * ld[q] + v[q];
+          qh[o[q]] = w;
+          acc += (double)(w * ld[q]);
+          acc2 += (double)(ld2[q] * ld[q]);
         } else if (EPI == E_INIT) {
           const float mu = mu1[kk[q]] + mu1[cc[q]];
           const float r0 = v[q] / mu;
-          const float z = r0 * __frcp_rn(mdiag(mu, fe2dt, fcwb));
           xh[o[q]] = 0.f;
           rh[o[q]] = r0;
-          pw[o[q]] = z;
-          acc += (double)(r0 * z);
+          uw[o[q]] = r0 * __frcp_rn(mdiag(mu, fe2dt, fcwb));
         } else {  // E_UPDATE
           bad |= !isfinite(v[q]);
           Y[o[q]] = yv[q] - (double)v[q];
@@ -786,11 +829,12 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
       if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
       const double m = block_reduce<1>(acc, sh);
       if (threadIdx.x == 0) part[(size_t)u * nb + b] = m;
-    } else if (EPI == E_Q || EPI == E_INIT) {
-      const double s = block_reduce<0>(acc, sh);
+    } else if (EPI == E_W) {
+      const double wu = block_reduce<0>(acc, sh);
+      const double ru = block_reduce<0>(acc2, sh);
       if (threadIdx.x == 0) {
-        part[(size_t)u * nb + b] = s;
-        if (EPI == E_INIT) a.prho0[(size_t)u * nb + b] = s;
+        a.pdel[(size_t)u * nb + b] = wu;
+        a.pgam[(size_t)u * nb + b] = ru;
       }
     }
   }
@@ -995,101 +1039,90 @@ __device__ __forceinline__ void ph_cg_reset(const PArgs& a) {
   if (blockIdx.x == 0 && threadIdx.x < 2) a.active[threadIdx.x] = 0;
 }
 
-// P5: x += alpha p, r -= alpha q, (r, r / m)
+// The CG update of iteration `it` (Chronopoulos-Gear form: both inner products of an iteration
+// come from one reduction, gamma = (r, u) and delta = (w, u) with u = M^{-1} r and w = S u):
+//   beta = gamma / gamma_prev (0 at it = 0), alpha = gamma / (delta - beta gamma / alpha_prev),
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^{-1} r.
+// A unit whose gamma has fallen to cg_tol^2 gamma_0 is done (its x is kept).
 template <int N>
-__device__ __forceinline__ void ph_cg_step(const PArgs& a, const double* rho_cur, double* rho_new) {
+__device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
   constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
-  __shared__ double sh[kThreads / 32];
   const size_t pts = (size_t)n * n;
   float* __restrict__ xh = a.xh;
   float* __restrict__ rh = a.rh;
-  const float* __restrict__ ph = a.ph;
-  const float* __restrict__ qh = a.qh;
-  const float* __restrict__ mu1 = a.mu1;
-  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
-    const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
-    if (a.flag[2 * u] || a.flag[2 * u + 1]) continue;
-    const double sig = unit_sum<N>(a.psig, u);
-    const float alpha = (sig > 0.0) ? float(unit_sum<N>(rho_cur, u) / sig) : 0.f;
-    const float cwb = a.fdt * float(unit_wbar<N>(a, u));
-    const float fe2dt = unit_fe2dt(a, u);
-    const size_t base = u * pts + (size_t)a0 * n;
-    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
-    float acc = 0.f;
-    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
-      float pv[U], xv[U], rv[U], qv[U], mv[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int e = e0 + q * kThreads;
-        if (e < cnt) {
-          pv[q] = ph[base + e];
-          xv[q] = xh[base + e];
-          rv[q] = rh[base + e];
-          qv[q] = qh[base + e];
-          const int i = a0 + e / n;
-          mv[q] = mu1[i] + mu1[e - (e / n) * n];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int e = e0 + q * kThreads;
-        if (e < cnt) {
-          xh[base + e] = xv[q] + alpha * pv[q];
-          const float r = rv[q] - alpha * qv[q];
-          rh[base + e] = r;
-          acc += r * r * __frcp_rn(mdiag(mv[q], fe2dt, cwb));
-        }
-      }
-    }
-    const double s = block_reduce<0>((double)acc, sh);
-    if (threadIdx.x == 0) rho_new[(size_t)u * nb + b] = s;
-  }
-}
-
-// P6: p = r / m + beta p; convergence of each unit's CG (tested by the unit's first item)
-template <int N>
-__device__ __forceinline__ void ph_cg_dir(const PArgs& a, const double* rho_cur, const double* rho_new, int it) {
-  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
-  const size_t pts = (size_t)n * n;
   float* __restrict__ ph = a.ph;
-  const float* __restrict__ rh = a.rh;
+  float* __restrict__ sh = a.sh;
+  float* __restrict__ uh = a.uh;
+  const float* __restrict__ wh = a.qh;
   const float* __restrict__ mu1 = a.mu1;
+  const int cur = (it & 1) * 2, prev = ((it + 1) & 1) * 2;
   for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
     const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
     if (a.flag[2 * u] || a.flag[2 * u + 1]) continue;
-    const double rn = unit_sum<N>(rho_new, u), ro = unit_sum<N>(rho_cur, u);
-    const float beta = (ro > 0.0) ? float(rn / ro) : 0.f;
-    const float cwb = a.fdt * float(unit_wbar<N>(a, u));
-    const float fe2dt = unit_fe2dt(a, u);
-    const size_t base = u * pts + (size_t)a0 * n;
-    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
-    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
-      float pv[U], rv[U], mv[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int e = e0 + q * kThreads;
-        if (e < cnt) {
-          pv[q] = ph[base + e];
-          rv[q] = rh[base + e];
-          const int i = a0 + e / n;
-          mv[q] = mu1[i] + mu1[e - (e / n) * n];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int e = e0 + q * kThreads;
-        if (e < cnt) ph[base + e] = rv[q] * __frcp_rn(mdiag(mv[q], fe2dt, cwb)) + beta * pv[q];
-      }
+    const double gam = unit_sum<N>(a.pgam, u), del = unit_sum<N>(a.pdel, u);
+    const double gam0 = (it == 0) ? gam : a.cgs[u * 8 + 4];
+    const bool done = !(gam > a.cg_tol2 * gam0);  // also catches NaN
+    double beta = 0.0, alpha = 0.0;
+    if (it > 0) {
+      const double gp = a.cgs[u * 8 + prev + 1], ap = a.cgs[u * 8 + prev];
+      beta = (gp > 0.0) ? gam / gp : 0.0;
+      const double den = (ap != 0.0) ? del - beta * gam / ap : del;
+      alpha = (den > 0.0) ? gam / den : 0.0;
+    } else {
+      alpha = (del > 0.0) ? gam / del : 0.0;
     }
     if (b == 0 && threadIdx.x == 0) {
       atomicAdd(a.totals + 2, 1ull);
-      if (!(rn > a.cg_tol2 * unit_sum<N>(a.prho0, u))) a.flag[2 * u + 1] = 1;  // also catches NaN
-      else atomicAdd(a.active + (it & 1), 1);
+      if (done) {
+        a.flag[2 * u + 1] = 1;
+      } else {
+        atomicAdd(a.active + (it & 1), 1);
+        a.cgs[u * 8 + cur] = alpha;
+        a.cgs[u * 8 + cur + 1] = gam;
+        if (it == 0) a.cgs[u * 8 + 4] = gam;  // gamma_0 (read only for it > 0)
+      }
+    }
+    if (done) continue;
+    const float fa = float(alpha), fb = float(beta);
+    const float cwb = a.fdt * float(unit_wbar<N>(a, u));
+    const float fe2dt = unit_fe2dt(a, u);
+    const size_t base = u * pts + (size_t)a0 * n;
+    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
+      float uv[U], wv[U], pv[U], sv[U], xv[U], rv[U], mv[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          uv[q] = uh[base + e];
+          wv[q] = wh[base + e];
+          pv[q] = (it > 0) ? ph[base + e] : 0.f;
+          sv[q] = (it > 0) ? sh[base + e] : 0.f;
+          xv[q] = xh[base + e];
+          rv[q] = rh[base + e];
+          const int i = a0 + e / n;
+          mv[q] = mu1[i] + mu1[e - (e / n) * n];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int e = e0 + q * kThreads;
+        if (e < cnt) {
+          const float p = uv[q] + fb * pv[q];
+          const float sq = wv[q] + fb * sv[q];
+          const float r = rv[q] - fa * sq;
+          ph[base + e] = p;
+          sh[base + e] = sq;
+          xh[base + e] = xv[q] + fa * p;
+          rh[base + e] = r;
+          uh[base + e] = r * __frcp_rn(mdiag(mv[q], fe2dt, cwb));
+        }
+      }
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.active[(it + 1) & 1] = 0;
-    a.totals[0] += 1ull;
+    atomicAdd(a.totals, 1ull);
   }
 }
 
@@ -1120,7 +1153,7 @@ __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.active[2 + ((it_n + 1) & 1)] = 0;
-    a.totals[1] += 1ull;
+    atomicAdd(a.totals + 1, 1ull);
   }
 }
 
@@ -1152,23 +1185,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
       CH_BAR();
       noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, 0, nullptr); });  // H to sine space
       CH_BAR();
-      noinl([&] { dst_phase<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, a.prho); });  // CG start
+      noinl([&] { dst_phase<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, nullptr); });  // CG start
       noinl([&] { ph_cg_reset<N>(a); });
       CH_BAR();
       for (int it = 0; it < a.cg_max; ++it) {
-        const double* rho_cur = a.prho + (size_t)(it & 1) * a.units * nb;
-        double* rho_new = a.prho + (size_t)((it + 1) & 1) * a.units * nb;
-        noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.ph, a.tmp, 1, nullptr); });  // p to physical space
+        noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.uh, a.tmp, 1, nullptr); });  // u to physical space
         CH_BAR();
         noinl([&] { dst_phase<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr); });  // dt (wc - wbar) p
         CH_BAR();
         noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr); });  // back to sine space
         CH_BAR();
-        noinl([&] { dst_phase<N, E_Q>(a, buf, twd, a.tmp, nullptr, 1, a.psig); });    // q = M p + That, (p, q)
+        noinl([&] { dst_phase<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr); });  // w = S u, (w,u), (r,u)
         CH_BAR();
-        noinl([&] { ph_cg_step<N>(a, rho_cur, rho_new); });
-        CH_BAR();
-        noinl([&] { ph_cg_dir<N>(a, rho_cur, rho_new, it); });
+        noinl([&] { ph_cg_update<N>(a, it); });
         CH_BAR();
         if (*(volatile int*)(a.active + (it & 1)) == 0) break;
       }
@@ -1215,36 +1244,39 @@ cudaError_t launch_persist_sel(const PArgs& a, int minb, int* grid_out, cudaStre
 
 }  // namespace
 
-void Prop2D::make_args(PArgs& a, double* Y, int units, int scheme, double dt, int nsteps) const {
+void Prop2D::make_args(PArgs& a, double* Y, int units, int scheme, double dt, int nsteps, int u0, int group) const {
   a = PArgs{};
   const int nb = (p_.n + kDstRows - 1) / kDstRows;
   const size_t np = (size_t)cap_ * nb;
+  const size_t vo = (size_t)u0 * pts_, po = (size_t)u0 * nb;  // offsets of unit u0
   a.Y = Y;
-  a.yhat = yhat_;
-  a.yprev = yprev_;
-  a.z = z_;
-  a.w = w_;
-  a.rhs = rhs_;
-  a.xh = xh_;
-  a.rh = rh_;
-  a.ph = ph_;
-  a.qh = qh_;
-  a.tmp = tmp_;
-  a.t2 = tmp2_;
+  a.yhat = yhat_ + vo;
+  a.yprev = yprev_ + vo;
+  a.z = z_ + vo;
+  a.w = w_ + vo;
+  a.rhs = rhs_ + vo;
+  a.xh = xh_ + vo;
+  a.rh = rh_ + vo;
+  a.ph = ph_ + vo;
+  a.qh = qh_ + vo;
+  a.tmp = tmp_ + vo;
+  a.t2 = tmp2_ + vo;
   a.mu1 = mu_;
   a.tw = tw_;
-  a.pmin = ppart_;
-  a.pmax = ppart_ + np;
-  a.psig = ppart_ + 2 * np;
-  a.prho = ppart_ + 3 * np;  // two parity slots
-  a.prho0 = ppart_ + 5 * np;
-  a.pd = ppart_ + 6 * np;
-  a.flag = flag_;
-  a.cnt = newton_cnt_;
-  a.scal = scal_;
+  a.pmin = ppart_ + po;
+  a.pmax = ppart_ + np + po;
+  a.pdel = ppart_ + 2 * np + po;
+  a.pgam = ppart_ + 3 * np + po;
+  a.cgs = cgs_ + (size_t)u0 * 8;
+  a.uh = uh_ + vo;
+  a.sh = sh_ + vo;
+  a.pd = ppart_ + 6 * np + po;
+  a.flag = flag_ + (size_t)u0 * 2;
+  a.cnt = newton_cnt_ + u0;
+  a.scal = scal_ + (size_t)u0 * 8;
   a.status = status_;
   a.totals = cg_dev_;
-  a.active = active_;
+  a.active = active_ + 4 * group;
   a.bar = bar_;
   a.units = units;
   a.nsteps = nsteps;
@@ -1261,26 +1293,26 @@ void Prop2D::make_args(PArgs& a, double* Y, int units, int scheme, double dt, in
   a.cg_tol2 = p_.cg_tol * p_.cg_tol;
   a.fe2dt = float(p_.eps2 * dt);
   a.eps2 = p_.eps2;
-  a.eps2u = eps2u_;
+  a.eps2u = eps2u_ ? eps2u_ + u0 : nullptr;
   a.fdt = float(dt);
   if (scheme == SCHEME_NL) {
     a.zmode = p_.frozen ? 1 : 0;
   } else if (scheme == SCHEME_LIN1) {
     a.zmode = p_.frozen ? 3 : 2;
-    a.W64 = yprev_;
+    a.W64 = yprev_ + vo;
     a.wconst = 1.0;
   } else {
     a.zmode = 3;
     a.wconst = 2.0;
   }
-  a.ctr = ctr_;
+  a.ctr = ctr_ + 4 * group;
 }
 
 cudaError_t Prop2D::propagate_persistent(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
   if (units > cap_ || units < 1) return cudaErrorInvalidValue;
   if (nsteps < 1) return cudaSuccess;
   PArgs a;
-  make_args(a, Y, units, scheme, dt, nsteps);
+  make_args(a, Y, units, scheme, dt, nsteps, 0, 0);
   cudaError_t e = cudaMemsetAsync(bar_, 0, 4 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   int grid = 0;
@@ -1307,7 +1339,7 @@ cudaError_t Prop2D::propagate_persistent(double* Y, int units, int scheme, doubl
 namespace {
 
 enum Phase {
-  PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_STEP, PH_DIR,
+  PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_UPDATE,
   PH_X1, PH_X2, PH_NEWTON_END
 };
 
@@ -1327,23 +1359,21 @@ __global__ void __launch_bounds__(kThreads) k2_phase(PArgs a, int have_prev) {
     __syncthreads();
   }
   const int it = a.ctr[1];
-  const double* rho_cur = a.prho + (size_t)(it & 1) * a.units * nb;
-  double* rho_new = a.prho + (size_t)((it + 1) & 1) * a.units * nb;
+  (void)nb;
   if constexpr (PH == PH_PROLOGUE) ph_prologue<N>(a, 0);
   if constexpr (PH == PH_PREDICT) ph_predict<N>(a, have_prev);
   if constexpr (PH == PH_Z) ph_z<N>(a);
   if constexpr (PH == PH_RESID) ph_resid<N>(a);
   if constexpr (PH == PH_H1) dst_item<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, 0, nullptr, blockIdx.x);
   if constexpr (PH == PH_H2) {
-    dst_item<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, a.prho, blockIdx.x);
+    dst_item<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, nullptr, blockIdx.x);
     ph_cg_reset<N>(a);
   }
-  if constexpr (PH == PH_P1) dst_item<N, E_PLAIN>(a, buf, twd, a.ph, a.tmp, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P1) dst_item<N, E_PLAIN>(a, buf, twd, a.uh, a.tmp, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P2) dst_item<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P3) dst_item<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr, blockIdx.x);
-  if constexpr (PH == PH_P4) dst_item<N, E_Q>(a, buf, twd, a.tmp, nullptr, 1, a.psig, blockIdx.x);
-  if constexpr (PH == PH_STEP) ph_cg_step<N>(a, rho_cur, rho_new);
-  if constexpr (PH == PH_DIR) ph_cg_dir<N>(a, rho_cur, rho_new, it);
+  if constexpr (PH == PH_P4) dst_item<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_UPDATE) ph_cg_update<N>(a, it);
   if constexpr (PH == PH_X1) dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
   if constexpr (PH == PH_X2) dst_item<N, E_UPDATE>(a, buf, twd, a.tmp, nullptr, 0, a.pd, blockIdx.x);
   if constexpr (PH == PH_NEWTON_END) ph_newton_end<N>(a, a.ctr[0]);
@@ -1430,8 +1460,7 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_STEP>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_DIR>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_UPDATE>(a, have_prev, bs2);
   if (e == cudaSuccess) {
     k2_cond<<<1, 32, 0, bs2>>>(hC, ctr, active, 1, cg_max);
     e = cudaGetLastError();
@@ -1471,14 +1500,14 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
 
 cudaError_t Prop2D::build_step(const StepKey& k, cudaGraphExec_t* out) {
   PArgs a;
-  make_args(a, k.Y, k.units, k.scheme, k.dt, 1);
+  make_args(a, k.Y, k.units, k.scheme, k.dt, 1, k.u0, k.group);
   switch (p_.n + 1) {
-    case 16: return build_step_n<16>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
-    case 32: return build_step_n<32>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
-    case 64: return build_step_n<64>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
-    case 128: return build_step_n<128>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
-    case 256: return build_step_n<256>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
-    case 512: return build_step_n<512>(a, k.have_prev, p_.newton_max, p_.cg_max, ctr_, active_, out);
+    case 16: return build_step_n<16>(a, k.have_prev, p_.newton_max, p_.cg_max, a.ctr, a.active, out);
+    case 32: return build_step_n<32>(a, k.have_prev, p_.newton_max, p_.cg_max, a.ctr, a.active, out);
+    case 64: return build_step_n<64>(a, k.have_prev, p_.newton_max, p_.cg_max, a.ctr, a.active, out);
+    case 128: return build_step_n<128>(a, k.have_prev, p_.newton_max, p_.cg_max, a.ctr, a.active, out);
+    case 256: return build_step_n<256>(a, k.have_prev, p_.newton_max, p_.cg_max, a.ctr, a.active, out);
+    case 512: return build_step_n<512>(a, k.have_prev, p_.newton_max, p_.cg_max, a.ctr, a.active, out);
   }
   return cudaErrorInvalidValue;
 }
@@ -1517,8 +1546,7 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
       CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
-      CH_TRY((phase_launch<N, PH_STEP>(a, have_prev, st)));
-      CH_TRY((phase_launch<N, PH_DIR>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_UPDATE>(a, have_prev, st)));
       CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CH_TRY(cudaStreamSynchronize(st));
       if (act[it & 1] == 0) break;
@@ -1539,7 +1567,7 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
 cudaError_t Prop2D::propagate_host(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
   for (int j = 0; j < nsteps; ++j) {
     PArgs a;
-    make_args(a, Y, units, scheme, dt, 1);
+    make_args(a, Y, units, scheme, dt, 1, 0, 0);
     const int hp = (scheme == SCHEME_NL && j > 0) ? 1 : 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (p_.n + 1) {

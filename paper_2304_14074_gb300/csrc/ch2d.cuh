@@ -75,7 +75,7 @@ class Prop2D {
   static constexpr int kStepKernelsLin = 3;
   static constexpr int kNewtonKernels = 9;   // z, residual, 2 transform passes (the second starts CG),
                                              // CG loop start, 2 passes (update), stop test, condition
-  static constexpr int kCgKernels = 7;       // 4 transform passes, step, direction, condition
+  static constexpr int kCgKernels = 6;       // 4 transform passes, update, condition
   // Zeroes the device status bits and the Newton / CG counters (enqueued on st).
   cudaError_t reset_counters(cudaStream_t st);
   size_t bytes() const { return bytes_; }
@@ -87,12 +87,20 @@ class Prop2D {
     int scheme;
     double dt;
     int have_prev;
+    int u0;     // first unit of the group (offset into the work arrays)
+    int group;  // loop-control slots of the group
     bool operator==(const StepKey& o) const {
-      return Y == o.Y && units == o.units && scheme == o.scheme && dt == o.dt && have_prev == o.have_prev;
+      return Y == o.Y && units == o.units && scheme == o.scheme && dt == o.dt && have_prev == o.have_prev &&
+             u0 == o.u0 && group == o.group;
     }
   };
+  static constexpr int kMaxGroups = 4;       // concurrent unit groups of a propagation
+  static constexpr int kMinGroupUnits = 8;   // units per group at least
   cudaError_t build_step(const StepKey& k, cudaGraphExec_t* out);
-  void make_args(PArgs& a, double* Y, int units, int scheme, double dt, int nsteps) const;
+  void make_args(PArgs& a, double* Y, int units, int scheme, double dt, int nsteps, int u0, int group) const;
+  cudaStream_t gs_[4] = {};   // group streams
+  cudaEvent_t gev_[4] = {};   // group joins
+  cudaEvent_t gfork_ = nullptr;
   std::vector<std::pair<StepKey, cudaGraphExec_t>> graphs_;
 
   Params2D p_{};
@@ -137,6 +145,9 @@ class Prop2D {
   double* ppart_ = nullptr;   // persistent path: per-item partial sums [7][cap][rows / 16]
   int* active_ = nullptr;     // persistent path: units still iterating (parity slots)
   unsigned* bar_ = nullptr;   // persistent path: grid barrier (arrivals, generation, abort)
+  double* cgs_ = nullptr;     // CG scalars per unit
+  float* uh_ = nullptr;       // CG u = M^{-1} r (sine space)
+  float* sh_ = nullptr;       // CG s = S p (sine space)
 };
 
 // Parareal correction of one slice for `count` problems list[0..count) (Eq. 2.2), fused with
