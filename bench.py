@@ -365,6 +365,36 @@ LEARNED_CASE = dict(n=63, eps=0.05, T=0.3, N=16, J=8, stride=4, train_seeds=64, 
                     steps=((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)), batch=32)
 
 
+# G_theta forward arithmetic per pixel: four 32 -> 32 layers (2 x 32 x 288 flops each) and the
+# 1 -> 32 and 32 -> 1 layers (2 x 32 x 9 and 2 x 288).
+GTHETA_FLOPS_PER_PIXEL = 4 * 2 * 32 * 288 + 2 * 32 * 9 + 2 * 288
+
+
+def gtheta_forward_roofline(ch, net, batch=8, n=511):
+    """Tensor-core roofline of the G_theta forward pass on `batch` fields of the 512^2 grid, timed
+    with CUDA events (the four 32 -> 32 layers are BF16 mma on the tensor cores)."""
+    import torch
+    x = (0.5 * torch.randn(batch, n, n, dtype=torch.float64, device="cuda")).contiguous()
+    for _ in range(3):
+        y = net.forward(x)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    a.record()
+    for _ in range(reps):
+        y = net.forward(x, out=y)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    flops = GTHETA_FLOPS_PER_PIXEL * batch * n * n
+    peak = measured_peaks().get("bf16_tflops", 1900.0)
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "workload": f"G_theta forward, {batch} fields of {n}^2", "ms": round(ms, 4),
+            "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+            "algorithmic_flops_per_pixel": GTHETA_FLOPS_PER_PIXEL}
+
+
 def learned_vs_plain(ch, stream, err_tol=1e-8):
     """Trains G_theta (correction form G(U) + R(U)) on fine-solver snapshot pairs and on pairs
     from perturbed snapshots, all produced by the library on the GPU, then runs Parareal to
@@ -438,6 +468,7 @@ def learned_vs_plain(ch, stream, err_tol=1e-8):
                      "coarse_fallback_iter": int(s0["coarse_fallback_iter"])}
         h.close()
     out["speedup_learned_over_plain"] = round(out["plain"]["seconds"] / max(out["learned"]["seconds"], 1e-9), 3)
+    out["gtheta_forward_roofline"] = gtheta_forward_roofline(ch, net)
     out["config"] = (f"2D NPA-I n={n} eps={eps} T={T} N={N} J={J}, u0 = 0.05 N(0,1) seed {c['eval_seed']}; "
                      f"G_theta correction form trained on {len(seeds)} trajectories (seeds 1000..) "
                      f"x {N * stride - stride + 1} snapshot pairs + {pert.shape[0]} perturbed pairs, "

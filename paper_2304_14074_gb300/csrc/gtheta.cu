@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -54,6 +55,30 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros (the halo outside the
+// field).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Issues the asynchronous loads of the 18 x 18 halo tile at (ty0, tx0) of a [S][S][32] field.
+__device__ __forceinline__ void load_halo_async(bf16* tile, const bf16* __restrict__ x, int S, int ty0, int tx0) {
+  for (int c = threadIdx.x; c < kHalo * kHalo * 4; c += kThreads) {
+    const int pix = c >> 2, part = c & 3;
+    const int yy = pix / kHalo, xx = pix - yy * kHalo;
+    const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+    const bool in = gy >= 0 && gy < S && gx >= 0 && gx < S;
+    const bf16* src = in ? x + ((size_t)gy * S + gx) * kC + part * 8 : x;
+    cp_async16(tile + pix * kPix + part * 8, src, in ? 16 : 0);
+  }
+}
+
 // Loads the 18 x 18 halo tile of a [S][S][32] BF16 field into shared memory (zeros outside).
 __device__ __forceinline__ void load_halo(bf16* tile, const bf16* __restrict__ x, int S, int ty0, int tx0) {
   for (int c = threadIdx.x; c < kHalo * kHalo * 4; c += kThreads) {
@@ -67,78 +92,119 @@ __device__ __forceinline__ void load_halo(bf16* tile, const bf16* __restrict__ x
   }
 }
 
-// 32 -> 32 convolution on the tensor cores.
+// 32 -> 32 convolution on the tensor cores, persistent over 16 x 16 output tiles: a CTA loads the
+// layer's weights into shared memory once and walks tiles (t = blockIdx.x, + gridDim.x, ...;
+// tile t = (image, tile row, tile column)); the halo of the next tile is fetched with cp.async
+// into the second of two buffers while the current one is multiplied.
 // mode 0 (forward): y = relu(conv(x, W) + b); mode 1 (backward data): y = conv(x, W) * (mask > 0).
-__global__ void __launch_bounds__(kThreads) k_conv_mid(const bf16* __restrict__ x, bf16* __restrict__ y,
-                                                       const bf16* __restrict__ W, const float* __restrict__ bias,
-                                                       const bf16* __restrict__ mask, int S, int mode) {
-  __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
-  __shared__ __align__(16) bf16 ws[9 * kC * kPix];
-  const int img = blockIdx.z, ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
-  const size_t off = (size_t)img * S * S * kC;
-  load_halo(tile, x + off, S, ty0, tx0);
+constexpr int kHaloElems = kHalo * kHalo * kPix;
+constexpr size_t kConvSmem = (2 * kHaloElems + 9 * kC * kPix) * sizeof(bf16);
+
+__global__ void __launch_bounds__(kThreads, 2) k_conv_mid(const bf16* __restrict__ x, bf16* __restrict__ y,
+                                                          const bf16* __restrict__ W, const float* __restrict__ bias,
+                                                          const bf16* __restrict__ mask, int S, int tiles_x,
+                                                          int tiles, int mode) {
+  extern __shared__ __align__(16) unsigned char conv_smem[];
+  bf16* halo = reinterpret_cast<bf16*>(conv_smem);  // two buffers
+  bf16* ws = halo + 2 * kHaloElems;
+  const int per_img = tiles_x * tiles_x;
+  auto tile_origin = [&](int tl, int& img, int& ty0, int& tx0) {
+    img = tl / per_img;
+    const int r = tl - img * per_img;
+    ty0 = (r / tiles_x) * kTile;
+    tx0 = (r % tiles_x) * kTile;
+  };
+  if (blockIdx.x < tiles) {
+    int img, ty0, tx0;
+    tile_origin(blockIdx.x, img, ty0, tx0);
+    load_halo_async(halo, x + (size_t)img * S * S * kC, S, ty0, tx0);
+  }
+  cp_async_commit();
   for (int c = threadIdx.x; c < 9 * kC * 4; c += kThreads) {
     const int row = c >> 2, part = c & 3;  // row = tap * 32 + output channel
     *reinterpret_cast<uint4*>(ws + row * kPix + part * 8) = *reinterpret_cast<const uint4*>(W + row * kC + part * 8);
   }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
   const int akof = (lane >> 4) * 8;
-  float acc[2][4][4];
+  float bv[4][2];
 #pragma unroll
-  for (int m = 0; m < 2; ++m)
+  for (int j = 0; j < 4; ++j) {
+    bv[j][0] = (mode == 0) ? bias[j * 8 + 2 * t] : 0.f;
+    bv[j][1] = (mode == 0) ? bias[j * 8 + 2 * t + 1] : 0.f;
+  }
+  int buf = 0;
+  for (int tl = blockIdx.x; tl < tiles; tl += gridDim.x, buf ^= 1) {
+    int img, ty0, tx0;
+    tile_origin(tl, img, ty0, tx0);
+    const size_t off = (size_t)img * S * S * kC;
+    const int nxt = tl + gridDim.x;
+    if (nxt < tiles) {  // the other buffer was released by the barrier closing the previous tile
+      int im2, y2, x2;
+      tile_origin(nxt, im2, y2, x2);
+      load_halo_async(halo + (buf ^ 1) * kHaloElems, x + (size_t)im2 * S * S * kC, S, y2, x2);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // this tile's group has landed (the next one may still be in flight)
+    __syncthreads();
+    const bf16* tile = halo + buf * kHaloElems;
+    float acc[2][4][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int m = 0; m < 2; ++m)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.f;
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap - 3 * dy;
+        for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.f;
 #pragma unroll
-    for (int kh = 0; kh < 2; ++kh) {
-      const int c0 = kh * 16;
-      unsigned a[2][4];
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap - 3 * dy;
 #pragma unroll
-      for (int m = 0; m < 2; ++m) {
-        const int oy = warp * 2 + m;
-        ldsm_x4(a[m][0], a[m][1], a[m][2], a[m][3], tile + ((oy + dy) * kHalo + arow + dx) * kPix + c0 + akof);
+      for (int kh = 0; kh < 2; ++kh) {
+        const int c0 = kh * 16;
+        unsigned a[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const int oy = warp * 2 + m;
+          ldsm_x4(a[m][0], a[m][1], a[m][2], a[m][3], tile + ((oy + dy) * kHalo + arow + dx) * kPix + c0 + akof);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bf16* wb = ws + (tap * kC + j * 8 + g) * kPix + c0 + 2 * t;
+          const unsigned b0 = *reinterpret_cast<const unsigned*>(wb);
+          const unsigned b1 = *reinterpret_cast<const unsigned*>(wb + 8);
+#pragma unroll
+          for (int m = 0; m < 2; ++m) mma16816(acc[m][j], a[m], b0, b1);
+        }
       }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int Y = ty0 + warp * 2 + m;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const bf16* wb = ws + (tap * kC + j * 8 + g) * kPix + c0 + 2 * t;
-        const unsigned b0 = *reinterpret_cast<const unsigned*>(wb);
-        const unsigned b1 = *reinterpret_cast<const unsigned*>(wb + 8);
+        const int co = j * 8 + 2 * t;
 #pragma unroll
-        for (int m = 0; m < 2; ++m) mma16816(acc[m][j], a[m], b0, b1);
-      }
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    const int Y = ty0 + warp * 2 + m;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int co = j * 8 + 2 * t;
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const int X = tx0 + g + 8 * hf;
-        if (Y >= S || X >= S) continue;
-        const size_t o = off + ((size_t)Y * S + X) * kC + co;
-        float v0 = acc[m][j][2 * hf], v1 = acc[m][j][2 * hf + 1];
-        if (mode == 0) {
-          v0 = fmaxf(v0 + bias[co], 0.f);
-          v1 = fmaxf(v1 + bias[co + 1], 0.f);
-        } else {
-          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + o);
-          v0 = (__bfloat162float(mk.x) > 0.f) ? v0 : 0.f;
-          v1 = (__bfloat162float(mk.y) > 0.f) ? v1 : 0.f;
+        for (int hf = 0; hf < 2; ++hf) {
+          const int X = tx0 + g + 8 * hf;
+          if (Y >= S || X >= S) continue;
+          const size_t o = off + ((size_t)Y * S + X) * kC + co;
+          float v0 = acc[m][j][2 * hf], v1 = acc[m][j][2 * hf + 1];
+          if (mode == 0) {
+            v0 = fmaxf(v0 + bv[j][0], 0.f);
+            v1 = fmaxf(v1 + bv[j][1], 0.f);
+          } else {
+            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + o);
+            v0 = (__bfloat162float(mk.x) > 0.f) ? v0 : 0.f;
+            v1 = (__bfloat162float(mk.y) > 0.f) ? v1 : 0.f;
+          }
+          *reinterpret_cast<__nv_bfloat162*>(y + o) = __floats2bfloat162_rn(v0, v1);
         }
-        *reinterpret_cast<__nv_bfloat162*>(y + o) = __floats2bfloat162_rn(v0, v1);
       }
     }
+    __syncthreads();  // every warp is done with this buffer before the next prefetch reuses it
   }
+  cp_async_wait<0>();
 }
 
 // First layer 1 -> 32: a1 = relu(conv(U, W1) + b1); U FP64 (inference) or FP32 (training).
@@ -276,8 +342,23 @@ __global__ void __launch_bounds__(kThreads) k_last_bwd(const float* __restrict__
   }
 }
 
-// Weight gradient of a 32 -> 32 layer over one 16 x 16 tile: partial[tile][tap][co][ci] =
-// sum_p g[p][co] x[p + tap - 1][ci]; partial bias sum_p g[p][co] after the 9216 weights.
+// Weight gradient of a 32 -> 32 layer over one 16 x 16 tile on the tensor cores:
+// partial[tile][tap][co][ci] = sum_p g[p][co] x[p + tap - 1][ci], i.e. per tap the product
+// G^T (32 x 256 pixels) X_tap (256 x 32) with K = the tile's pixels in chunks of one output row.
+// Warp w owns output block (co 16 (w & 1) .., ci 8 (w >> 1) ..) for all nine taps. Both operands
+// are pixel-major in shared memory and are read with ldmatrix.trans. The bias partial
+// sum_p g[p][co] follows the 9216 weights.
+__device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned& r0, unsigned& r1, const void* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
 __global__ void __launch_bounds__(kThreads) k_wgrad_mid(const bf16* __restrict__ g, const bf16* __restrict__ x,
                                                         float* __restrict__ part, int S) {
   __shared__ __align__(16) bf16 tile[kHalo * kHalo * kPix];
@@ -293,35 +374,47 @@ __global__ void __launch_bounds__(kThreads) k_wgrad_mid(const bf16* __restrict__
     *reinterpret_cast<uint4*>(gt + pix * kPix + part4 * 8) = v;
   }
   __syncthreads();
-  const int co = threadIdx.x >> 3, ci0 = (threadIdx.x & 7) * 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int co0 = (warp & 1) * 16, ci0 = (warp >> 1) * 8;
+  const int mat = lane >> 3, i8 = lane & 7;
   float acc[9][4];
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[tap][q] = 0.f;
-  float bsum = 0.f;
-  for (int pix = 0; pix < kTile * kTile; ++pix) {
-    const float gv = __bfloat162float(gt[pix * kPix + co]);
-    bsum += gv;
-    const int oy = pix / kTile, ox = pix - oy * kTile;
+  for (int oy = 0; oy < kTile; ++oy) {  // K chunk: the 16 pixels of output row oy
+    unsigned a[4];
+    // A = G^T block (co0.. co0+15, pixels): matrix m reads pixels (m >> 1) * 8 + i8, columns
+    // co0 + (m & 1) * 8
+    ldsm_x4_t(a[0], a[1], a[2], a[3], gt + (oy * kTile + (mat >> 1) * 8 + i8) * kPix + co0 + (mat & 1) * 8);
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const bf16* p = tile + ((oy + tap / 3) * kHalo + ox + tap % 3) * kPix + ci0;
-      const float2 v0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-      const float2 v1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + 2));
-      acc[tap][0] += gv * v0.x;
-      acc[tap][1] += gv * v0.y;
-      acc[tap][2] += gv * v1.x;
-      acc[tap][3] += gv * v1.y;
+      const int dy = tap / 3, dx = tap - 3 * dy;
+      // B = X_tap block (pixels, ci0.. ci0+7): lanes 0-7 rows of pixels 0-7, lanes 8-15 pixels 8-15
+      const int px = ((mat & 1) * 8 + i8);
+      unsigned b0, b1;
+      ldsm_x2_t(b0, b1, tile + ((oy + dy) * kHalo + px + dx) * kPix + ci0);
+      mma16816(acc[tap], a, b0, b1);
     }
   }
   const size_t tileid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   float* pp = part + tileid * (9 * kC * kC + kC);
+  const int gq = lane >> 2, t = lane & 3;
 #pragma unroll
-  for (int tap = 0; tap < 9; ++tap)
+  for (int tap = 0; tap < 9; ++tap) {
+    float* o = pp + (size_t)tap * kC * kC;
+    o[(co0 + gq) * kC + ci0 + 2 * t] = acc[tap][0];
+    o[(co0 + gq) * kC + ci0 + 2 * t + 1] = acc[tap][1];
+    o[(co0 + gq + 8) * kC + ci0 + 2 * t] = acc[tap][2];
+    o[(co0 + gq + 8) * kC + ci0 + 2 * t + 1] = acc[tap][3];
+  }
+  // bias: 8 threads per output channel, pixels strided by 8, then a shuffle tree
+  const int co = threadIdx.x >> 3, sub = threadIdx.x & 7;
+  float bsum = 0.f;
+  for (int pix = sub; pix < kTile * kTile; pix += 8) bsum += __bfloat162float(gt[pix * kPix + co]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) pp[(tap * kC + co) * kC + ci0 + q] = acc[tap][q];
-  if ((threadIdx.x & 7) == 0) pp[9 * kC * kC + co] = bsum;
+  for (int o = 4; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+  if (sub == 0) pp[9 * kC * kC + co] = bsum;
 }
 
 // Weight gradients of the first layer (x = a0 scalar, g = gz1 [32]) or the last (x = a5 [32],
@@ -377,14 +470,26 @@ __global__ void __launch_bounds__(kThreads) k_wgrad_edge(const float* __restrict
   }
 }
 
-// Sum over tiles (in tile order) of part[tile * stride + j], j < len: the weights (j < wlen) go
-// to grad[dst_w + j], the biases to grad[dst_b + j - wlen].
-__global__ void k_reduce(const float* __restrict__ part, int tiles, int stride, int len, float* __restrict__ grad,
-                         int dst_w, int wlen, int dst_b) {
+// Sum over tiles of part[tile * stride + j], j < len, in two fixed-order levels: chunks of
+// kChunk tiles (blockIdx.y) into part2[chunk][len], then the chunks (k_reduce); the weights
+// (j < wlen) go to grad[dst_w + j], the biases to grad[dst_b + j - wlen].
+constexpr int kChunk = 32;
+__global__ void k_reduce_chunks(const float* __restrict__ part, int tiles, int stride, int len,
+                                double* __restrict__ part2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  const int t0 = blockIdx.y * kChunk, t1 = min(tiles, t0 + kChunk);
+  double s = 0.0;
+  for (int tl = t0; tl < t1; ++tl) s += part[(size_t)tl * stride + j];
+  part2[(size_t)blockIdx.y * len + j] = s;
+}
+
+__global__ void k_reduce(const double* __restrict__ part2, int chunks, int len, float* __restrict__ grad, int dst_w,
+                         int wlen, int dst_b) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= len) return;
   double s = 0.0;
-  for (int tl = 0; tl < tiles; ++tl) s += part[(size_t)tl * stride + j];
+  for (int c = 0; c < chunks; ++c) s += part2[(size_t)c * len + j];
   if (j < wlen) grad[dst_w + j] = (float)s;
   else grad[dst_b + (j - wlen)] = (float)s;
 }
@@ -435,6 +540,24 @@ __global__ void k_crops(const double* __restrict__ states, const double* __restr
   }
 }
 
+// Persistent launch of k_conv_mid: as many CTAs as fit on the GPU (at most one per tile).
+void conv_mid(const bf16* x, bf16* y, const bf16* W, const float* bias, const bf16* mask, int batch, int S, int mode,
+              cudaStream_t st) {
+  static int slots[64] = {};  // resident CTAs of k_conv_mid, per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  dev &= 63;
+  if (slots[dev] == 0) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_conv_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_mid, kThreads, kConvSmem);
+    slots[dev] = std::max(1, sms * std::max(1, per_sm));
+  }
+  const int tx = (S + kTile - 1) / kTile, tiles = tx * tx * batch;
+  k_conv_mid<<<std::min(tiles, slots[dev]), kThreads, kConvSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode);
+}
+
 uint64_t splitmix(uint64_t& s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -476,11 +599,12 @@ cudaError_t GTheta::init(unsigned long long seed, cudaStream_t st) {
 
 void GTheta::release() {
   void* ptrs[] = {master_, grad_, m_, v_, wmid_, wbwd_, loss_dev_, a0_, r_, dr_, part_, tgt_, crops_, lpart_,
-                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1]};
+                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part2_};
   for (void* q : ptrs) cudaFree(q);
   master_ = grad_ = m_ = v_ = nullptr;
   wmid_ = wbwd_ = nullptr;
   loss_dev_ = a0_ = r_ = dr_ = part_ = tgt_ = nullptr;
+  part2_ = nullptr;
   crops_ = nullptr;
   lpart_ = nullptr;
   for (auto& a : act_) a = nullptr;
@@ -512,7 +636,7 @@ cudaError_t GTheta::get_params(float* host, cudaStream_t st) {
 cudaError_t GTheta::ensure(int batch, int S) {
   if (batch <= cap_batch_ && S <= cap_S_) return cudaSuccess;
   const int B = std::max(batch, cap_batch_), SS = std::max(S, cap_S_);
-  void* old[] = {a0_, r_, dr_, tgt_, act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part_, crops_};
+  void* old[] = {a0_, r_, dr_, tgt_, act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part_, crops_, part2_};
   for (void* q : old) cudaFree(q);
   const size_t f = (size_t)B * SS * SS;
   const size_t tiles = (size_t)B * ((SS + kTile - 1) / kTile) * ((SS + kTile - 1) / kTile);
@@ -528,6 +652,7 @@ cudaError_t GTheta::ensure(int batch, int S) {
   for (auto& gg : g_) al((void**)&gg, f * kC * sizeof(bf16));
   part_cap_ = tiles * (9 * kC * kC + kC);
   al((void**)&part_, part_cap_ * sizeof(float));
+  al((void**)&part2_, ((tiles + kChunk - 1) / kChunk) * (size_t)(9 * kC * kC + kC) * sizeof(double));
   al((void**)&crops_, (size_t)B * sizeof(int4));
   if (e == cudaSuccess) {
     cap_batch_ = B;
@@ -561,8 +686,7 @@ cudaError_t GTheta::forward_acts(const void* in, bool in64, int batch, int S, cu
     k_conv_first<float><<<grid, kThreads, 0, st>>>((const float*)in, act_[0], master_, S,
                                                    in == a0_ ? nullptr : a0_);
   for (int l = 0; l < 4; ++l)
-    k_conv_mid<<<grid, kThreads, 0, st>>>(act_[l], act_[l + 1], wmid_ + (size_t)l * 9 * kC * kC,
-                                          master_ + kOffB[l + 1], nullptr, S, 0);
+    conv_mid(act_[l], act_[l + 1], wmid_ + (size_t)l * 9 * kC * kC, master_ + kOffB[l + 1], nullptr, batch, S, 0, st);
   return cudaGetLastError();
 }
 
@@ -575,6 +699,12 @@ cudaError_t GTheta::forward64(const double* in, const double* base, double* out,
   const dim3 grid((S + kTile - 1) / kTile, (S + kTile - 1) / kTile, batch);
   k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], nullptr, master_, S, base ? base : in, out);
   return cudaGetLastError();
+}
+
+void GTheta::reduce_tiles(int tiles, int stride, int len, int dst_w, int wlen, int dst_b, cudaStream_t st) {
+  const int chunks = (tiles + kChunk - 1) / kChunk;
+  k_reduce_chunks<<<dim3((len + 255) / 256, chunks), 256, 0, st>>>(part_, tiles, stride, len, part2_);
+  k_reduce<<<(len + 255) / 256, 256, 0, st>>>(part2_, chunks, len, grad_, dst_w, wlen, dst_b);
 }
 
 cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, int S, int margin, int slot,
@@ -593,7 +723,7 @@ cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, i
   // last layer: weights from (dr, a5), gradient into a5
   const int le = 9 * kC + kC;
   k_wgrad_edge<<<grid, kThreads, 0, st>>>(nullptr, nullptr, dr_, act_[4], part_, S, 0);
-  k_reduce<<<(le + 255) / 256, 256, 0, st>>>(part_, tiles, le, 9 * kC + 1, grad_, kOffW[5], 9 * kC, kOffB[5]);
+  reduce_tiles(tiles, le, 9 * kC + 1, kOffW[5], 9 * kC, kOffB[5], st);
   k_last_bwd<<<grid, kThreads, 0, st>>>(dr_, act_[4], g_[0], master_, S);
   // 32 -> 32 layers 5, 4, 3, 2 (indices l + 1 = 4..1): weights from (g, input activation), then
   // gradient through the layer into the activation below (masked by its ReLU)
@@ -601,14 +731,13 @@ cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, i
   const int lm = 9 * kC * kC + kC;
   for (int l = 3; l >= 0; --l) {
     k_wgrad_mid<<<grid, kThreads, 0, st>>>(g_[cur], act_[l], part_, S);
-    k_reduce<<<(lm + 255) / 256, 256, 0, st>>>(part_, tiles, lm, lm, grad_, kOffW[l + 1], 9 * kC * kC,
-                                               kOffB[l + 1]);
-    k_conv_mid<<<grid, kThreads, 0, st>>>(g_[cur], g_[cur ^ 1], wbwd_ + (size_t)l * 9 * kC * kC, nullptr, act_[l], S, 1);
+    reduce_tiles(tiles, lm, lm, kOffW[l + 1], 9 * kC * kC, kOffB[l + 1], st);
+    conv_mid(g_[cur], g_[cur ^ 1], wbwd_ + (size_t)l * 9 * kC * kC, nullptr, act_[l], batch, S, 1, st);
     cur ^= 1;
   }
   // first layer: weights from (g1, a0)
   k_wgrad_edge<<<grid, kThreads, 0, st>>>(a0_, g_[cur], nullptr, nullptr, part_, S, 1);
-  k_reduce<<<(le + 255) / 256, 256, 0, st>>>(part_, tiles, le, le, grad_, kOffW[0], 9 * kC, kOffB[0]);
+  reduce_tiles(tiles, le, le, kOffW[0], 9 * kC, kOffB[0], st);
   return cudaGetLastError();
 }
 

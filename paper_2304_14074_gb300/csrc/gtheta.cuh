@@ -43,6 +43,7 @@ class GTheta {
   cudaError_t ensure_losses(int count, cudaStream_t st);
   cudaError_t refresh_bf16(cudaStream_t st);
   cudaError_t forward_acts(const void* in, bool in64, int batch, int S, cudaStream_t st);
+  void reduce_tiles(int tiles, int stride, int len, int dst_w, int wlen, int dst_b, cudaStream_t st);
 
   float* master_ = nullptr;  // kParams
   float* grad_ = nullptr;
@@ -60,7 +61,8 @@ class GTheta {
   float* r_ = nullptr;              // [B][S][S] R(U)
   float* dr_ = nullptr;             // [B][S][S] dLoss/dR
   __nv_bfloat16* g_[2] = {};        // gradient ping-pong [B][S][S][32]
-  float* part_ = nullptr;           // weight-gradient partials
+  float* part_ = nullptr;           // weight-gradient partials [tiles][len]
+  double* part2_ = nullptr;         // their sums over chunks of tiles
   size_t part_cap_ = 0;
   float* tgt_ = nullptr;            // [B][S][S] crop targets
   int4* crops_ = nullptr;           // crop descriptors

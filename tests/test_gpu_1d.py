@@ -350,3 +350,28 @@ def test_non_default_stream(gpu_lib):
         pr.close()
     r = o.parareal(oracle_params(cfg), u0)
     assert np.max(np.abs(U - r.U)) <= 1e-11
+
+
+def test_autotuned_launch_is_cached_and_consistent(gpu_lib, tmp_path, monkeypatch):
+    """The fine-sweep launch chosen by measurement is written to the cache file; a second handle
+    reads it back and runs the same configuration (bitwise identical results), and the
+    reference computed after tuning equals the Parareal iterate at k = N bit for bit."""
+    ch = gpu_lib
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("CH_AUTOTUNE_CACHE", str(cache))
+    n, N = 300, 4
+    cfg = ch.Config(n=n, eps=0.03, T=0.02, n_slices=N, fine_steps=10, variant="NPA-I", newton_tol=1e-12,
+                    precision=1)
+    u0 = ch_inputs.initial_condition(1, n, 77, amp=0.1)
+    outs = []
+    for rep in range(2):
+        with ch.Parareal(cfg, batch=3) as pr:
+            for b in range(3):
+                pr.set_initial(b, u0 if b == 0 else ch_inputs.initial_condition(1, n, 78 + b, amp=0.1))
+            pr.compute_reference()
+            pr.run()
+            outs.append(pr.get_slices(0))
+            assert np.array_equal(pr.get_slices(0), pr.get_reference(0))
+    assert np.array_equal(outs[0], outs[1])
+    text = cache.read_text()
+    assert "fine1d n=300 units=12" in text and "alt=" in text and "div=" in text
