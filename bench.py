@@ -176,9 +176,9 @@ def cpu_oracle(w, problems, u0s, steps=1):
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
+    u0s = [u0s[b % len(u0s)] for b in range(problems)]  # a batch smaller than the sample repeats
     if w.get("dim", 1) == 2:
         pts = ORACLE_2D_STEPS * w["n"] ** 2
-        u0s = [u0s[b % len(u0s)] for b in range(problems)]
     else:
         pts = w["N"] * w["J"] * w["n"]
     times = []
@@ -522,8 +522,8 @@ def main():
                 "cpu_baseline": {"value": value, "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
                                  "sample": (f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice per step"
                                             if w.get("dim", 1) == 2 else
-                                            f"{problems} of {w['batch']} problems per step, one process each "
-                                            "(coarse sweep + full fine sweep + correction)")},
+                                            f"{problems} problems of the batch per step (repeated when the batch is "
+                                            "smaller), one process each (coarse sweep + full fine sweep + correction)")},
                 "e2e": {"value": value, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -535,7 +535,8 @@ def main():
         problems = cpu_sample_size()
         pts, times = cpu_oracle(w, problems, u0, steps=1)
         what = (f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice (sparse LU)"
-                if w.get("dim", 1) == 2 else f"{problems} of {w['batch']} problems, one step each, one process per problem")
+                if w.get("dim", 1) == 2 else f"{problems} problems of the batch (repeated when the batch is smaller), "
+                "one step each, one process per problem")
         cpu = {"value": pts / times[0], "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle", "sample": what}
     if world > 1:
         import torch

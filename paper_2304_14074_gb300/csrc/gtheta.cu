@@ -18,6 +18,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <cstdint>
 #include <mutex>
 #include <set>
@@ -205,6 +207,216 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid(const bf16* __restrict
     __syncthreads();  // every warp is done with this buffer before the next prefetch reuses it
   }
   cp_async_wait<0>();
+}
+
+
+// ---------------------------------------------------------------- tcgen05 (5th-generation) path
+//
+// The same 32 -> 32 convolution issued as tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, one CTA)
+// with the accumulators in tensor memory. Operands are read by the tensor core through shared-
+// memory matrix descriptors in the K-major layout without swizzle: a core matrix is 8 rows of
+// 16 bytes (8 channels), consecutive in memory; LBO is the distance between the two 8-channel
+// halves of a K = 16 step, SBO the distance between groups of 8 rows. The halo is stored
+// chunk-major, [channel chunk c (4)][y (18)][x (18)][8 channels], so that any 8 consecutive
+// pixels of a row - whatever the tap's x shift - form one core matrix: for tap (dy, dx) and
+// pixel half h, A is the 128 x 16 block of rows (output row oy, pixels 8h..8h+7) at
+// start + ((2 ks) 18 + dy) 18 + dx + 8h (x 16 B), SBO = one halo row (288 B), LBO = one chunk
+// (5184 B). B (weights, N = 32 output channels x K) is [tap][c][co][8]: SBO = 128 B, LBO = 512 B.
+// Per tile: 2 halves x 9 taps x 2 K steps = 36 MMAs of 128 x 32 x 16 into two 32-column
+// accumulators; one thread issues them and commits to an mbarrier; every wait is bounded.
+constexpr int kHaloChunk = kHalo * kHalo * 8;                 // bf16 elements of one channel chunk
+constexpr int kHaloTc = 4 * kHaloChunk;                        // one halo buffer
+// Shared memory: two halo buffers, the weights, the mbarrier and the TMEM address, padded so that
+// every address a descriptor of this kernel can form (start + 15 row groups + the second K half,
+// whichever stride either offset were taken as) stays inside the allocation.
+constexpr size_t kConvTcUsed = (2 * kHaloTc + 9 * 4 * kC * 8) * sizeof(bf16) + 64;
+constexpr size_t kConvTcSmem = 112 * 1024;
+static_assert(kConvTcUsed <= kConvTcSmem, "tcgen05 conv shared memory");
+constexpr size_t kTcStartMax = (size_t)kHaloTc * 2 + 2 * kHaloChunk * 2 + 2 * kHalo * 16 + 10 * 16;
+static_assert(kTcStartMax + 15 * (size_t)kHaloChunk * 2 + kHalo * 16 + 128 <= kConvTcSmem, "descriptor reach");
+constexpr unsigned kWaitSpins = 1u << 22;
+
+__device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; base offset 0, no swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void load_halo_tc(bf16* halo, const bf16* __restrict__ x, int S, int ty0, int tx0) {
+  for (int c = threadIdx.x; c < kHalo * kHalo * 4; c += kThreads) {
+    const int pix = c >> 2, part = c & 3;
+    const int yy = pix / kHalo, xx = pix - yy * kHalo;
+    const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+    const bool in = gy >= 0 && gy < S && gx >= 0 && gx < S;
+    const bf16* src = in ? x + ((size_t)gy * S + gx) * kC + part * 8 : x;
+    cp_async16(halo + part * kHaloChunk + (yy * kHalo + xx) * 8, src, in ? 16 : 0);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restrict__ x, bf16* __restrict__ y,
+                                                             const bf16* __restrict__ W,
+                                                             const float* __restrict__ bias,
+                                                             const bf16* __restrict__ mask, int S, int tiles_x,
+                                                             int tiles, int mode, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  bf16* halo = reinterpret_cast<bf16*>(tc_smem);         // two buffers
+  bf16* ws = halo + 2 * kHaloTc;                         // [tap][c][co][8]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + 9 * 4 * kC * 8);
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mbar + 1);
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per_img = tiles_x * tiles_x;
+  auto tile_origin = [&](int tl, int& img, int& ty0, int& tx0) {
+    img = tl / per_img;
+    const int r = tl - img * per_img;
+    ty0 = (r / tiles_x) * kTile;
+    tx0 = (r % tiles_x) * kTile;
+  };
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 0) {  // 64 TMEM columns: two 128-lane x 32-column FP32 accumulators
+    const unsigned slot = static_cast<unsigned>(__cvta_generic_to_shared(tmem_slot));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(slot));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (blockIdx.x < tiles) {
+    int img, ty0, tx0;
+    tile_origin(blockIdx.x, img, ty0, tx0);
+    load_halo_tc(halo, x + (size_t)img * S * S * kC, S, ty0, tx0);
+  }
+  cp_async_commit();
+  for (int c = threadIdx.x; c < 9 * kC * 4; c += kThreads) {
+    const int row = c >> 2, part = c & 3;  // row = tap * 32 + output channel, part = channel chunk
+    const int tap = row / kC, co = row - tap * kC;
+    *reinterpret_cast<uint4*>(ws + ((tap * 4 + part) * kC + co) * 8) =
+        *reinterpret_cast<const uint4*>(W + row * kC + part * 8);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const unsigned tmem = *tmem_slot;
+  const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar));
+  const unsigned wbase = static_cast<unsigned>(__cvta_generic_to_shared(ws));
+  constexpr uint32_t idesc = umma_idesc(128, 32);
+  // epilogue mapping: warp w reads TMEM lanes 32 (w % 4).. of accumulator h = w / 4
+  const int h = warp >> 2, m = (warp & 3) * 32 + lane;
+  const int oy = m >> 3, px = 8 * h + (m & 7);
+  float bv[kC];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) bv[c] = (mode == 0) ? bias[c] : 0.f;
+  unsigned phase = 0;
+  int buf = 0;
+  for (int tl = blockIdx.x; tl < tiles; tl += gridDim.x, buf ^= 1) {
+    int img, ty0, tx0;
+    tile_origin(tl, img, ty0, tx0);
+    const int nxt = tl + gridDim.x;
+    if (nxt < tiles) {
+      int im2, y2, x2;
+      tile_origin(nxt, im2, y2, x2);
+      load_halo_tc(halo + (buf ^ 1) * kHaloTc, x + (size_t)im2 * S * S * kC, S, y2, x2);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);  // halo writes -> tensor-core reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned hbase = static_cast<unsigned>(__cvta_generic_to_shared(halo + buf * kHaloTc));
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      for (int hh = 0; hh < 2; ++hh)
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap - 3 * dy;
+          for (int ks = 0; ks < 2; ++ks) {
+            const unsigned a_addr = hbase + (unsigned)(((2 * ks * kHalo + dy) * kHalo + dx + 8 * hh) * 16);
+            const unsigned b_addr = wbase + (unsigned)((tap * 4 + 2 * ks) * kC * 16);
+            const uint64_t ad = umma_desc(a_addr, kHaloChunk * 2, kHalo * 16);
+            const uint64_t bd = umma_desc(b_addr, kC * 16, 8 * 16);
+            const unsigned acc = (tap | ks) ? 1u : 0u;
+            const unsigned dt = tmem + 32u * hh;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+    }
+    // wait for the MMAs (bounded)
+    unsigned done = 0, spins = 0;
+    while (!done) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(done)
+          : "r"(mb), "r"(phase));
+      if (!done && ++spins > kWaitSpins) break;
+    }
+    if (!done) s_fail = 1;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    __syncthreads();
+    if (s_fail) break;
+    // epilogue: D[m][co] of half h -> pixel (oy, px)
+    unsigned r[32];
+    const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) + 32u * h;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+    const int Y = ty0 + oy, X = tx0 + px;
+    if (Y < S && X < S) {
+      const size_t o = (size_t)img * S * S * kC + ((size_t)Y * S + X) * kC;
+      uint4 mk[4];
+      if (mode == 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(mask + o + 8 * q);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        unsigned pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c = 8 * q + 2 * e;
+          float v0 = __uint_as_float(r[c]), v1 = __uint_as_float(r[c + 1]);
+          if (mode == 0) {
+            v0 = fmaxf(v0 + bv[c], 0.f);
+            v1 = fmaxf(v1 + bv[c + 1], 0.f);
+          } else {
+            const __nv_bfloat162 mm = reinterpret_cast<const __nv_bfloat162*>(&mk[q])[e];
+            v0 = (__bfloat162float(mm.x) > 0.f) ? v0 : 0.f;
+            v1 = (__bfloat162float(mm.y) > 0.f) ? v1 : 0.f;
+          }
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+          pk[e] = *reinterpret_cast<const unsigned*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(y + o + 8 * q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();  // TMEM read and this halo buffer released before the next tile's MMAs
+  }
+  cp_async_wait<0>();
+  if (s_fail && threadIdx.x == 0) atomicExch(err, 1);
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem));
 }
 
 // First layer 1 -> 32: a1 = relu(conv(U, W1) + b1); U FP64 (inference) or FP32 (training).
@@ -540,6 +752,25 @@ __global__ void k_crops(const double* __restrict__ states, const double* __restr
   }
 }
 
+// tcgen05 launch of the 32 -> 32 convolution (persistent, like k_conv_mid).
+void conv_mid_tc(const bf16* x, bf16* y, const bf16* W, const float* bias, const bf16* mask, int batch, int S,
+                 int mode, int* err, cudaStream_t st) {
+  static int slots[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  dev &= 63;
+  if (slots[dev] == 0) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_conv_mid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvTcSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_mid_tc, kThreads, kConvTcSmem);
+    slots[dev] = std::max(1, sms * std::max(1, std::min(per_sm, 4)));
+  }
+  const int tx = (S + kTile - 1) / kTile, tiles = tx * tx * batch;
+  k_conv_mid_tc<<<std::min(tiles, slots[dev]), kThreads, kConvTcSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode,
+                                                                            err);
+}
+
 // Persistent launch of k_conv_mid: as many CTAs as fit on the GPU (at most one per tile).
 void conv_mid(const bf16* x, bf16* y, const bf16* W, const float* bias, const bf16* mask, int batch, int S, int mode,
               cudaStream_t st) {
@@ -581,7 +812,12 @@ cudaError_t GTheta::init(unsigned long long seed, cudaStream_t st) {
   al((void**)&wmid_, 4 * 9 * kC * kC * sizeof(bf16));
   al((void**)&wbwd_, 4 * 9 * kC * kC * sizeof(bf16));
   al((void**)&lpart_, 1024 * sizeof(double));
+  al((void**)&err_, sizeof(int));
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(err_, 0, sizeof(int), st)) != cudaSuccess) return e;
+  // CH_GTHETA_CONV=tcgen05 runs the 32 -> 32 layers as tcgen05.mma (default: mma.sync)
+  const char* cv = std::getenv("CH_GTHETA_CONV");
+  tc_ = cv && std::strcmp(cv, "tcgen05") == 0;
   // He-normal initial weights (Box-Muller on SplitMix64), zero biases; the last layer scaled 0.1
   std::vector<float> p(kParams, 0.f);
   const int cin[6] = {1, 32, 32, 32, 32, 32}, cout[6] = {32, 32, 32, 32, 32, 1};
@@ -599,12 +835,13 @@ cudaError_t GTheta::init(unsigned long long seed, cudaStream_t st) {
 
 void GTheta::release() {
   void* ptrs[] = {master_, grad_, m_, v_, wmid_, wbwd_, loss_dev_, a0_, r_, dr_, part_, tgt_, crops_, lpart_,
-                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part2_};
+                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part2_, err_};
   for (void* q : ptrs) cudaFree(q);
   master_ = grad_ = m_ = v_ = nullptr;
   wmid_ = wbwd_ = nullptr;
   loss_dev_ = a0_ = r_ = dr_ = part_ = tgt_ = nullptr;
   part2_ = nullptr;
+  err_ = nullptr;
   crops_ = nullptr;
   lpart_ = nullptr;
   for (auto& a : act_) a = nullptr;
@@ -686,7 +923,12 @@ cudaError_t GTheta::forward_acts(const void* in, bool in64, int batch, int S, cu
     k_conv_first<float><<<grid, kThreads, 0, st>>>((const float*)in, act_[0], master_, S,
                                                    in == a0_ ? nullptr : a0_);
   for (int l = 0; l < 4; ++l)
-    conv_mid(act_[l], act_[l + 1], wmid_ + (size_t)l * 9 * kC * kC, master_ + kOffB[l + 1], nullptr, batch, S, 0, st);
+    if (tc_)
+      conv_mid_tc(act_[l], act_[l + 1], wmid_ + (size_t)l * 9 * kC * kC, master_ + kOffB[l + 1], nullptr, batch, S,
+                  0, err_, st);
+    else
+      conv_mid(act_[l], act_[l + 1], wmid_ + (size_t)l * 9 * kC * kC, master_ + kOffB[l + 1], nullptr, batch, S, 0,
+               st);
   return cudaGetLastError();
 }
 
@@ -732,7 +974,10 @@ cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, i
   for (int l = 3; l >= 0; --l) {
     k_wgrad_mid<<<grid, kThreads, 0, st>>>(g_[cur], act_[l], part_, S);
     reduce_tiles(tiles, lm, lm, kOffW[l + 1], 9 * kC * kC, kOffB[l + 1], st);
-    conv_mid(g_[cur], g_[cur ^ 1], wbwd_ + (size_t)l * 9 * kC * kC, nullptr, act_[l], batch, S, 1, st);
+    if (tc_)
+      conv_mid_tc(g_[cur], g_[cur ^ 1], wbwd_ + (size_t)l * 9 * kC * kC, nullptr, act_[l], batch, S, 1, err_, st);
+    else
+      conv_mid(g_[cur], g_[cur ^ 1], wbwd_ + (size_t)l * 9 * kC * kC, nullptr, act_[l], batch, S, 1, st);
     cur ^= 1;
   }
   // first layer: weights from (g1, a0)
@@ -774,6 +1019,13 @@ cudaError_t GTheta::train(const double* states, const double* base, int ntraj, i
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
+}
+
+int GTheta::wait_failures(cudaStream_t st) {
+  int v = 0;
+  if (cudaMemcpyAsync(&v, err_, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return 1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 1;
+  return v;
 }
 
 cudaError_t GTheta::read_losses(float* host, int count, cudaStream_t st) {

@@ -37,6 +37,8 @@ class GTheta {
                     double lr, unsigned long long seed, cudaStream_t st);
   cudaError_t read_losses(float* host, int count, cudaStream_t st);
   const float* grads() const { return grad_; }
+  // 1 if a bounded wait of the tcgen05 path gave up since the handle was created (synchronises).
+  int wait_failures(cudaStream_t st);
 
  private:
   cudaError_t ensure(int batch, int S);
@@ -67,6 +69,8 @@ class GTheta {
   float* tgt_ = nullptr;            // [B][S][S] crop targets
   int4* crops_ = nullptr;           // crop descriptors
   double* lpart_ = nullptr;         // loss partials
+  int* err_ = nullptr;              // a bounded tensor-core wait gave up (tcgen05 path)
+  bool tc_ = false;                 // 32 -> 32 layers on tcgen05.mma instead of mma.sync
 };
 
 }  // namespace chg3

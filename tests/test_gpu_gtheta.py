@@ -256,3 +256,52 @@ def test_guard_restarts_runaway_learned_coarse_sweep_with_plain_step(gpu_lib):
     assert np.array_equal(st["err_l2"], plain.stats(0)["err_l2"])
     plain.close()
     pr.close()
+
+
+@pytest.fixture
+def tcgen05_conv(monkeypatch):
+    """The 32 -> 32 layers on tcgen05.mma (read when a network is created)."""
+    monkeypatch.setenv("CH_GTHETA_CONV", "tcgen05")
+
+
+@pytest.mark.parametrize("n", [16, 40, 63])
+def test_tcgen05_forward_matches_oracle_and_mma_path(gpu_lib, tcgen05_conv, monkeypatch, n):
+    ch = gpu_lib
+    p, (W, b) = fp32_net(ch, *random_net(3))
+    net = ch.GTheta()
+    net.set_params(p)
+    u = np.stack([ch_inputs.initial_condition(2, n, 10 + i, kind="normal", amp=0.5).reshape(n, n) for i in range(2)])
+    out = net.forward(dev(u)).cpu().numpy()
+    monkeypatch.delenv("CH_GTHETA_CONV")
+    ref_net = ch.GTheta()
+    ref_net.set_params(p)
+    out_mma = ref_net.forward(dev(u)).cpu().numpy()
+    for i in range(2):
+        _, aq = go.forward(u[i], W, b, bf16=True)
+        r, rq = out[i] - u[i], aq[-1][..., 0]
+        assert np.linalg.norm(r - rq) <= 2e-3 * np.linalg.norm(rq)
+        assert np.abs(r - rq).max() <= 1e-2 * np.abs(rq).max()
+        rm = out_mma[i] - u[i]
+        assert np.linalg.norm(r - rm) <= 2e-3 * np.linalg.norm(rm)
+
+
+def test_tcgen05_gradients_match_oracle(gpu_lib, tcgen05_conv):
+    ch = gpu_lib
+    p, (W, b) = fp32_net(ch, *random_net(5))
+    net = ch.GTheta()
+    net.set_params(p)
+    B, S, margin = 2, 43, 6
+    rng = np.random.default_rng(S)
+    x = (0.6 * rng.standard_normal((B, S, S))).astype(np.float32)
+    t = (0.05 * rng.standard_normal((B, S, S))).astype(np.float32)
+    loss, grad = net.gradients(dev(x, torch.float32), dev(t, torch.float32), margin)
+    gW = [np.zeros_like(w) for w in W]
+    for i in range(B):
+        _, aq = go.forward(x[i].astype(np.float64), W, b, bf16=True)
+        _, dr = go.mse_crop_loss(aq[-1][..., 0], t[i].astype(np.float64), margin)
+        gWi, _ = go.backward(aq, W, dr / B, bf16=True)
+        for l in range(6):
+            gW[l] += gWi[l]
+    Wg, _ = ch.gtheta_unflatten(grad)
+    for l in range(6):
+        assert np.linalg.norm(Wg[l] - gW[l]) <= 1e-3 * np.linalg.norm(gW[l]), l
