@@ -226,14 +226,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid(const bf16* __restrict
 // accumulators; one thread issues them and commits to an mbarrier; every wait is bounded.
 constexpr int kHaloChunk = kHalo * kHalo * 8;                 // bf16 elements of one channel chunk
 constexpr int kHaloTc = 4 * kHaloChunk;                        // one halo buffer
-// Shared memory: two halo buffers, the weights, the mbarrier and the TMEM address, padded so that
-// every address a descriptor of this kernel can form (start + 15 row groups + the second K half,
-// whichever stride either offset were taken as) stays inside the allocation.
-constexpr size_t kConvTcUsed = (2 * kHaloTc + 9 * 4 * kC * 8) * sizeof(bf16) + 64;
-constexpr size_t kConvTcSmem = 112 * 1024;
-static_assert(kConvTcUsed <= kConvTcSmem, "tcgen05 conv shared memory");
+// Shared memory: two halo buffers, the weights, the mbarrier and the TMEM address. Every address a
+// descriptor forms (start + 15 row groups (SBO) + the second K half (LBO) + one core matrix)
+// stays inside the two halo buffers.
+constexpr size_t kConvTcSmem = (2 * kHaloTc + 9 * 4 * kC * 8) * sizeof(bf16) + 64;  // + 2 mbarriers, TMEM slot
 constexpr size_t kTcStartMax = (size_t)kHaloTc * 2 + 2 * kHaloChunk * 2 + 2 * kHalo * 16 + 10 * 16;
-static_assert(kTcStartMax + 15 * (size_t)kHaloChunk * 2 + kHalo * 16 + 128 <= kConvTcSmem, "descriptor reach");
+static_assert(kTcStartMax + 15 * kHalo * 16 + (size_t)kHaloChunk * 2 + 128 <= (size_t)2 * kHaloTc * 2,
+              "descriptor reach");
 constexpr unsigned kWaitSpins = 1u << 22;
 
 __device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
@@ -270,33 +269,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
   extern __shared__ __align__(128) unsigned char tc_smem[];
   bf16* halo = reinterpret_cast<bf16*>(tc_smem);         // two buffers
   bf16* ws = halo + 2 * kHaloTc;                         // [tap][c][co][8]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + 9 * 4 * kC * 8);
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + 9 * 4 * kC * 8);  // one per accumulator
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mbar + 2);
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_img = tiles_x * tiles_x;
-  auto tile_origin = [&](int tl, int& img, int& ty0, int& tx0) {
+  // tiles of this CTA: blockIdx.x + j gridDim.x, j = 0 .. count-1
+  const int count = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  auto tile_origin = [&](int j, int& img, int& ty0, int& tx0) {
+    const int tl = blockIdx.x + j * gridDim.x;
     img = tl / per_img;
     const int r = tl - img * per_img;
     ty0 = (r / tiles_x) * kTile;
     tx0 = (r % tiles_x) * kTile;
   };
+  auto prefetch = [&](int j) {  // halo of tile j into buffer j & 1
+    int img, ty0, tx0;
+    tile_origin(j, img, ty0, tx0);
+    load_halo_tc(halo + (j & 1) * kHaloTc, x + (size_t)img * S * S * kC, S, ty0, tx0);
+  };
   if (threadIdx.x == 0) {
     s_fail = 0;
-    const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    for (int b = 0; b < 2; ++b) {
+      const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
-  if (warp == 0) {  // 64 TMEM columns: two 128-lane x 32-column FP32 accumulators
+  if (warp == 0) {  // 128 TMEM columns: two pairs of 128-lane x 32-column FP32 accumulators
     const unsigned slot = static_cast<unsigned>(__cvta_generic_to_shared(tmem_slot));
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(slot));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(slot));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
-  if (blockIdx.x < tiles) {
-    int img, ty0, tx0;
-    tile_origin(blockIdx.x, img, ty0, tx0);
-    load_halo_tc(halo, x + (size_t)img * S * S * kC, S, ty0, tx0);
-  }
+  if (count > 0) prefetch(0);
+  cp_async_commit();
+  if (count > 1) prefetch(1);
   cp_async_commit();
   for (int c = threadIdx.x; c < 9 * kC * 4; c += kThreads) {
     const int row = c >> 2, part = c & 3;  // row = tap * 32 + output channel, part = channel chunk
@@ -308,53 +315,56 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const unsigned tmem = *tmem_slot;
-  const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar));
   const unsigned wbase = static_cast<unsigned>(__cvta_generic_to_shared(ws));
   constexpr uint32_t idesc = umma_idesc(128, 32);
+  // MMAs of tile j (36 of 128 x 32 x 16) into accumulator pair j & 1, committed to mbar[j & 1]
+  auto issue = [&](int j) {
+    if (threadIdx.x != 0) return;
+    const unsigned hbase = static_cast<unsigned>(__cvta_generic_to_shared(halo + (j & 1) * kHaloTc));
+    const unsigned dbase = tmem + 64u * (unsigned)(j & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    for (int hh = 0; hh < 2; ++hh)
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap - 3 * dy;
+        for (int ks = 0; ks < 2; ++ks) {
+          const unsigned a_addr = hbase + (unsigned)(((2 * ks * kHalo + dy) * kHalo + dx + 8 * hh) * 16);
+          const unsigned b_addr = wbase + (unsigned)((tap * 4 + 2 * ks) * kC * 16);
+          const uint64_t ad = umma_desc(a_addr, kHaloChunk * 2, kHalo * 16);
+          const uint64_t bd = umma_desc(b_addr, kC * 16, 8 * 16);
+          const unsigned acc = (tap | ks) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dbase + 32u * hh),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+    const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (j & 1)));
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+  };
   // epilogue mapping: warp w reads TMEM lanes 32 (w % 4).. of accumulator h = w / 4
   const int h = warp >> 2, m = (warp & 3) * 32 + lane;
   const int oy = m >> 3, px = 8 * h + (m & 7);
   float bv[kC];
 #pragma unroll
   for (int c = 0; c < kC; ++c) bv[c] = (mode == 0) ? bias[c] : 0.f;
-  unsigned phase = 0;
-  int buf = 0;
-  for (int tl = blockIdx.x; tl < tiles; tl += gridDim.x, buf ^= 1) {
-    int img, ty0, tx0;
-    tile_origin(tl, img, ty0, tx0);
-    const int nxt = tl + gridDim.x;
-    if (nxt < tiles) {
-      int im2, y2, x2;
-      tile_origin(nxt, im2, y2, x2);
-      load_halo_tc(halo + (buf ^ 1) * kHaloTc, x + (size_t)im2 * S * S * kC, S, y2, x2);
-    }
-    cp_async_commit();
-    cp_async_wait<1>();
-    asm volatile("fence.proxy.async.shared::cta;\n" ::);  // halo writes -> tensor-core reads
+  unsigned phase[2] = {0u, 0u};
+  if (count > 0) {
+    cp_async_wait<1>();  // tile 0's halo
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned hbase = static_cast<unsigned>(__cvta_generic_to_shared(halo + buf * kHaloTc));
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      for (int hh = 0; hh < 2; ++hh)
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3, dx = tap - 3 * dy;
-          for (int ks = 0; ks < 2; ++ks) {
-            const unsigned a_addr = hbase + (unsigned)(((2 * ks * kHalo + dy) * kHalo + dx + 8 * hh) * 16);
-            const unsigned b_addr = wbase + (unsigned)((tap * 4 + 2 * ks) * kC * 16);
-            const uint64_t ad = umma_desc(a_addr, kHaloChunk * 2, kHalo * 16);
-            const uint64_t bd = umma_desc(b_addr, kC * 16, 8 * 16);
-            const unsigned acc = (tap | ks) ? 1u : 0u;
-            const unsigned dt = tmem + 32u * hh;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          }
-        }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+    issue(0);
+  }
+  for (int j = 0; j < count; ++j) {
+    // (a) the next tile's MMAs, as soon as its halo is in
+    if (j + 1 < count) {
+      cp_async_wait<0>();
+      asm volatile("fence.proxy.async.shared::cta;\n" ::);
+      __syncthreads();
+      issue(j + 1);
     }
-    // wait for the MMAs (bounded)
+    // (b) this tile's MMAs done (bounded wait): its halo buffer and accumulators are free to read
+    const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (j & 1)));
     unsigned done = 0, spins = 0;
     while (!done) {
       asm volatile(
@@ -362,17 +372,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
           "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
           "selp.u32 %0, 1, 0, p;\n\t}\n"
           : "=r"(done)
-          : "r"(mb), "r"(phase));
+          : "r"(mb), "r"(phase[j & 1]));
       if (!done && ++spins > kWaitSpins) break;
     }
     if (!done) s_fail = 1;
-    phase ^= 1u;
+    phase[j & 1] ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     __syncthreads();
     if (s_fail) break;
-    // epilogue: D[m][co] of half h -> pixel (oy, px)
+    // (c) the halo of tile j + 2 into the buffer tile j used
+    if (j + 2 < count) prefetch(j + 2);
+    cp_async_commit();
+    // (d) epilogue of tile j: D[m][co] of half h -> pixel (oy, px)
+    int img, ty0, tx0;
+    tile_origin(j, img, ty0, tx0);
     unsigned r[32];
-    const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) + 32u * h;
+    const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) + 64u * (unsigned)(j & 1) + 32u * h;
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -411,12 +426,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();  // TMEM read and this halo buffer released before the next tile's MMAs
+    __syncthreads();  // accumulators of tile j read before tile j + 2's MMAs overwrite them
   }
   cp_async_wait<0>();
   if (s_fail && threadIdx.x == 0) atomicExch(err, 1);
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
 }
 
 // First layer 1 -> 32: a1 = relu(conv(U, W1) + b1); U FP64 (inference) or FP32 (training).
