@@ -83,6 +83,16 @@ BYTES_NEWTON_2D = 16 + 32 + 8 + 16 + 8 + 20
 BYTES_STEP_2D = 16 + 32
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (the slowest rank sets a weak-scaling time)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def u0_batch(w, rank):
     import ch_inputs
     import numpy as np
@@ -253,10 +263,7 @@ def bench_ours(args, w, rank, world, local_rank):
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     value = world * args.steps * fine_pts_per_step / (total_ms / 1e3)
 
     # roofline of the dominant kernel (the fine sweep), timed live between the iteration graphs
@@ -304,10 +311,7 @@ def bench_ours(args, w, rank, world, local_rank):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_mean = sum(e2e_ms) / len(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_mean = max_over_ranks(e2e_mean, dist, dev)
     e2e = {"value": world * fine_pts_per_step / (e2e_mean / 1e3), "unit": "grid-pt-steps/s",
            "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(out_pin.numel() * 8),
            "ms_per_step": round(e2e_mean, 3)}
