@@ -103,7 +103,7 @@ __device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const fl
   if (m == 0 || m == N) return make_float2(0.f, 0.f);
   const bool neg = m > N;
   const int q = neg ? L - m - 1 : m - 1;
-  const float a = r0 ? r0[q] : 0.f, b = r1 ? r1[q] : 0.f;
+  const float a = r0 ? __ldcg(r0 + q) : 0.f, b = r1 ? __ldcg(r1 + q) : 0.f;
   return neg ? make_float2(-a, -b) : make_float2(a, b);
 }
 
@@ -210,11 +210,11 @@ size_t dst_smem() {
 // ------------------------------------------------------------------ FP64 stencils
 
 __device__ __forceinline__ double lap5(const double* X, int n, int i, int j) {
-  const double c = X[(size_t)i * n + j];
-  const double w = (j > 0) ? X[(size_t)i * n + j - 1] : 0.0;
-  const double e = (j < n - 1) ? X[(size_t)i * n + j + 1] : 0.0;
-  const double s = (i > 0) ? X[(size_t)(i - 1) * n + j] : 0.0;
-  const double no = (i < n - 1) ? X[(size_t)(i + 1) * n + j] : 0.0;
+  const double c = __ldcg(X + (size_t)i * n + j);
+  const double w = (j > 0) ? __ldcg(X + (size_t)i * n + j - 1) : 0.0;
+  const double e = (j < n - 1) ? __ldcg(X + (size_t)i * n + j + 1) : 0.0;
+  const double s = (i > 0) ? __ldcg(X + (size_t)(i - 1) * n + j) : 0.0;
+  const double no = (i < n - 1) ? __ldcg(X + (size_t)(i + 1) * n + j) : 0.0;
   return (w + e) + (s + no) - 4.0 * c;
 }
 
@@ -413,6 +413,9 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   path_ = PATH_GRAPH;
   if (env && std::strcmp(env, "persistent") == 0) path_ = PATH_PERSISTENT;
   if (env && std::strcmp(env, "host") == 0) path_ = PATH_HOST;
+  if (env && std::strcmp(env, "cluster") == 0) path_ = PATH_CLUSTER;
+  const char* cl = std::getenv("CH_2D_CLUSTER");  // cluster size of the cluster execution (default: chosen)
+  cluster_force_ = cl ? std::atoi(cl) : 0;
   const char* mb = std::getenv("CH_2D_MINB");
   persist_minb_ = mb ? std::atoi(mb) : 3;
   p_ = p;
@@ -552,6 +555,7 @@ cudaError_t capture_graph(cudaStream_t st, cudaGraph_t* g) {
 cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
   if (units > cap_ || units < 1) return cudaErrorInvalidValue;
   if (path_ == PATH_PERSISTENT) return propagate_persistent(Y, units, scheme, dt, nsteps, st);
+  if (path_ == PATH_CLUSTER) return propagate_cluster(Y, units, scheme, dt, nsteps, st);
   if (path_ == PATH_HOST) return propagate_host(Y, units, scheme, dt, nsteps, st);
   // Independent units are split into up to kMaxGroups groups whose step graphs run concurrently
   // on streams of their own: each phase is a chain of dependent latencies over few blocks, so
@@ -703,13 +707,29 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar) {
   return ok != 0;
 }
 
+// Work items (unit, block of kDstRows rows) that a block walks in a phase: first, first + step,
+// ... below end. chk = 1: units whose Newton loop (and, for the CG phases, CG loop) has ended are
+// skipped, read from the per-unit flags (batched executions); chk = 0: no test (the cluster
+// execution, whose loops end per unit).
+struct Items {
+  int first, step, end, chk;
+};
+
+template <int N>
+__device__ __forceinline__ Items grid_items(const PArgs& a) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  return Items{(int)blockIdx.x, (int)gridDim.x, a.units * nb, 1};
+}
+
+// Partial sums and ranges are read with L2-coherent loads: in the persistent and cluster
+// executions they were written by other blocks of the same kernel.
 template <int N>
 __device__ __forceinline__ double unit_wbar(const PArgs& a, int u) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
   double lo = 1e300, hi = -1e300;
   for (int b = 0; b < nb; ++b) {
-    lo = fmin(lo, a.pmin[(size_t)u * nb + b]);
-    hi = fmax(hi, a.pmax[(size_t)u * nb + b]);
+    lo = fmin(lo, __ldcg(a.pmin + (size_t)u * nb + b));
+    hi = fmax(hi, __ldcg(a.pmax + (size_t)u * nb + b));
   }
   return 0.5 * (lo + hi);
 }
@@ -718,8 +738,16 @@ template <int N>
 __device__ __forceinline__ double unit_sum(const double* p, int u) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += p[(size_t)u * nb + b];
+  for (int b = 0; b < nb; ++b) s += __ldcg(p + (size_t)u * nb + b);
   return s;
+}
+
+template <int N>
+__device__ __forceinline__ double unit_max(const double* p, int u) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  double m = 0.0;
+  for (int b = 0; b < nb; ++b) m = fmax(m, __ldcg(p + (size_t)u * nb + b));
+  return m;
 }
 
 // Calls f as a separate function: the persistent kernel's register allocation is then that of
@@ -741,101 +769,95 @@ enum Epi { E_PLAIN = 0, E_WPROD, E_W, E_INIT, E_UPDATE };
 // DST-I -> column a of the output (transposed), then the epilogue.
 //   E_PLAIN: out = v;  E_WPROD: out = dt (wc - wbar) v;  E_W: w = m u + v (= S u), sums (w, u)
 //   and (r, u);  E_INIT: r = v / mu, u = r / m, x = 0;  E_UPDATE: Y -= v, max |v|.
-// `act` selects the units: 0 = not Newton-done, 1 = not Newton-done and not CG-done.
+// `act` selects the units: 0 = not Newton-done, 1 = not Newton-done and not CG-done; -1 = no
+// test, and wb is the unit's wbar (otherwise it is formed from the range partials).
+// Epilogue loads of arrays written earlier in the kernel are L2-coherent.
 template <int N, int EPI>
 __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const float2* twd, const float* in, float* out,
-                                         int act, double* part, int item) {
+                                         int act, double* part, int item, double wb = 0.0) {
   constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
-  constexpr int U = 2;  // epilogue elements per thread whose loads are issued together
+  static_assert(kThreads % kDstRows == 0, "epilogue thread layout");
+  constexpr int KS = kThreads / kDstRows;  // output rows apart of one thread's elements
+  constexpr int J = (n + KS - 1) / KS;     // epilogue elements per thread
+  constexpr int UB = J < 16 ? J : 16;      // elements whose loads are issued together
+  static_assert(J % UB == 0, "epilogue batches");
   __shared__ double sh[kThreads / 32];
   const size_t pts = (size_t)n * n;
   const float sc = 0.5f * sqrtf(2.0f / N);
   const float* __restrict__ mu1 = a.mu1;
-  const float* __restrict__ wv = a.w;
-  float* __restrict__ qh = a.qh;
-  float* __restrict__ xh = a.xh;
-  float* __restrict__ rh = a.rh;
-  const float* __restrict__ uh = a.uh;
-  float* __restrict__ uw = a.uh;
-  double* __restrict__ Y = a.Y;
-  float* __restrict__ dst = out;
-  {
-    const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
-    if (a.flag[2 * u] || (act == 1 && a.flag[2 * u + 1])) return;  // block-uniform
-    fft_rows<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
-    float cwb = 0.f;
-    if (EPI == E_WPROD || EPI == E_W || EPI == E_INIT) cwb = float(unit_wbar<N>(a, u));
-    const float fcwb = a.fdt * cwb;
-    const float fe2dt = unit_fe2dt(a, u);
-    double acc = 0.0, acc2 = 0.0;
-    bool bad = false;
-    for (int i0 = threadIdx.x; i0 < n * kDstRows; i0 += U * kThreads) {
-      float v[U], ld[U], ld2[U];
-      size_t o[U];
-      int kk[U], cc[U];
-      bool ok[U];
+  const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+  if (act >= 0 && (a.flag[2 * u] || (act == 1 && a.flag[2 * u + 1]))) return;  // block-uniform
+  fft_rows<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
+  float cwb = 0.f;
+  if (EPI == E_WPROD || EPI == E_W || EPI == E_INIT) cwb = float(act >= 0 ? unit_wbar<N>(a, u) : wb);
+  const float fcwb = a.fdt * cwb;
+  const float fe2dt = unit_fe2dt(a, u);
+  // This thread's outputs: column c = a0 + r of the rows k = k0, k0 + KS, ... (row pair
+  // (2f, 2f+1) was packed as real + i imag: S x_{2f} = -Im Y / 2, S x_{2f+1} = Re Y / 2).
+  const int r = threadIdx.x % kDstRows, k0 = threadIdx.x / kDstRows, c = a0 + r;
+  const bool cok = c < n;
+  const float mc = mu1[cok ? c : 0];
+  const size_t ob = u * pts + c;
+  double acc = 0.0, acc2 = 0.0;
+  bool bad = false;
+#pragma unroll 1
+  for (int j0 = 0; j0 < J; j0 += UB) {
+    float v[UB], ld[UB], ld2[UB];
+    double yv[UB];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int idx = i0 + q * kThreads;
-        const int k = idx / kDstRows, r = idx - k * kDstRows;
-        kk[q] = k;
-        cc[q] = a0 + r;
-        ok[q] = idx < n * kDstRows && cc[q] < n;
-        o[q] = u * pts + (size_t)k * n + cc[q];
-        v[q] = 0.f;
-        ld[q] = 0.f;
-        ld2[q] = 0.f;
-        if (ok[q]) {
-          const float2 c = buf[pad8((r >> 1) * L + k + 1)];
-          v[q] = (r & 1) ? c.x * sc : -c.y * sc;
-          if (EPI == E_WPROD) ld[q] = wv[o[q]];
-          if (EPI == E_W) {
-            ld[q] = uh[o[q]];
-            ld2[q] = rh[o[q]];
-          }
+    for (int q = 0; q < UB; ++q) {
+      const int k = k0 + (j0 + q) * KS;
+      v[q] = ld[q] = ld2[q] = 0.f;
+      yv[q] = 0.0;
+      if (cok && k < n) {
+        const size_t o = ob + (size_t)k * n;
+        if (EPI == E_WPROD) ld[q] = __ldcg(a.w + o);
+        if (EPI == E_W) {
+          ld[q] = __ldcg(a.uh + o);
+          ld2[q] = __ldcg(a.rh + o);
         }
-      }
-      double yv[U];
-      if (EPI == E_UPDATE) {
-#pragma unroll
-        for (int q = 0; q < U; ++q) yv[q] = ok[q] ? Y[o[q]] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        if (!ok[q]) continue;
-        if (EPI == E_PLAIN) {
-          dst[o[q]] = v[q];
-        } else if (EPI == E_WPROD) {
-          dst[o[q]] = a.fdt * (ld[q] - cwb) * v[q];
-        } else if (EPI == E_W) {
-          const float w = mdiag(mu1[kk[q]] + mu1[cc[q]], fe2dt, fcwb) * ld[q] + v[q];
-          qh[o[q]] = w;
-          acc += (double)(w * ld[q]);
-          acc2 += (double)(ld2[q] * ld[q]);
-        } else if (EPI == E_INIT) {
-          const float mu = mu1[kk[q]] + mu1[cc[q]];
-          const float r0 = v[q] / mu;
-          xh[o[q]] = 0.f;
-          rh[o[q]] = r0;
-          uw[o[q]] = r0 * __frcp_rn(mdiag(mu, fe2dt, fcwb));
-        } else {  // E_UPDATE
-          bad |= !isfinite(v[q]);
-          Y[o[q]] = yv[q] - (double)v[q];
-          acc = fmax(acc, (double)fabsf(v[q]));
-        }
+        if (EPI == E_UPDATE) yv[q] = __ldcg(a.Y + o);
+        const float2 cv = buf[pad8((r >> 1) * L + k + 1)];
+        v[q] = (r & 1) ? cv.x * sc : -cv.y * sc;
       }
     }
-    if (EPI == E_UPDATE) {
-      if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
-      const double m = block_reduce<1>(acc, sh);
-      if (threadIdx.x == 0) part[(size_t)u * nb + b] = m;
-    } else if (EPI == E_W) {
-      const double wu = block_reduce<0>(acc, sh);
-      const double ru = block_reduce<0>(acc2, sh);
-      if (threadIdx.x == 0) {
-        a.pdel[(size_t)u * nb + b] = wu;
-        a.pgam[(size_t)u * nb + b] = ru;
+#pragma unroll
+    for (int q = 0; q < UB; ++q) {
+      const int k = k0 + (j0 + q) * KS;
+      if (!(cok && k < n)) continue;
+      const size_t o = ob + (size_t)k * n;
+      if (EPI == E_PLAIN) {
+        out[o] = v[q];
+      } else if (EPI == E_WPROD) {
+        out[o] = a.fdt * (ld[q] - cwb) * v[q];
+      } else if (EPI == E_W) {
+        const float w = mdiag(mu1[k] + mc, fe2dt, fcwb) * ld[q] + v[q];
+        a.qh[o] = w;
+        acc += (double)(w * ld[q]);
+        acc2 += (double)(ld2[q] * ld[q]);
+      } else if (EPI == E_INIT) {
+        const float mu = mu1[k] + mc;
+        const float r0 = v[q] / mu;
+        a.xh[o] = 0.f;
+        a.rh[o] = r0;
+        a.uh[o] = r0 * __frcp_rn(mdiag(mu, fe2dt, fcwb));
+      } else {  // E_UPDATE
+        bad |= !isfinite(v[q]);
+        a.Y[o] = yv[q] - (double)v[q];
+        acc = fmax(acc, (double)fabsf(v[q]));
       }
+    }
+  }
+  if (EPI == E_UPDATE) {
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
+    const double m = block_reduce<1>(acc, sh);
+    if (threadIdx.x == 0) part[(size_t)u * nb + b] = m;
+  } else if (EPI == E_W) {
+    const double wu = block_reduce<0>(acc, sh);
+    const double ru = block_reduce<0>(acc2, sh);
+    if (threadIdx.x == 0) {
+      a.pdel[(size_t)u * nb + b] = wu;
+      a.pgam[(size_t)u * nb + b] = ru;
     }
   }
 }
@@ -864,11 +886,10 @@ __device__ __forceinline__ bool item_elem(int a0, int e, int& i, int& j) {
 // The phases of the persistent kernel, each compiled as its own function (keeps the kernel's
 // register allocation to that of its largest phase). `a` lives in shared memory.
 template <int N>
-__device__ __forceinline__ void ph_prologue(const PArgs& a, int step) {
+__device__ __forceinline__ void ph_prologue_items(const PArgs& a, Items its) {
   constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
   const size_t pts = (size_t)n * n;
-  (void)step;
-  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+  for (int item = its.first; item < its.end; item += its.step) {
     const int u = item / nb, a0 = (item - u * nb) * kDstRows;
     const double* Yu = a.Y + u * pts;
 #pragma unroll 1
@@ -876,23 +897,30 @@ __device__ __forceinline__ void ph_prologue(const PArgs& a, int step) {
       int i, j;
       if (!item_elem<N>(a0, e, i, j)) continue;
       const size_t k = (size_t)i * n + j;
+      const double yk = __ldcg(Yu + k);
       if (a.scheme == SCHEME_NL) {
-        a.yhat[u * pts + k] = Yu[k] - a.dt * a.ih2 * lap5(Yu, n, i, j);
+        a.yhat[u * pts + k] = yk - a.dt * a.ih2 * lap5(Yu, n, i, j);
       } else {
-        a.yprev[u * pts + k] = Yu[k];
+        a.yprev[u * pts + k] = yk;
         if (a.scheme == SCHEME_LIN1) {
-          a.yhat[u * pts + k] = Yu[k] - a.dt * a.ih2 * lap5(Yu, n, i, j);
+          a.yhat[u * pts + k] = yk - a.dt * a.ih2 * lap5(Yu, n, i, j);
         } else {
-          const double c = lin2_v(Yu[k], a.frozen);
-          const double w_ = (j > 0) ? lin2_v(Yu[k - 1], a.frozen) : 0.0;
-          const double e_ = (j < n - 1) ? lin2_v(Yu[k + 1], a.frozen) : 0.0;
-          const double s_ = (i > 0) ? lin2_v(Yu[k - n], a.frozen) : 0.0;
-          const double no = (i < n - 1) ? lin2_v(Yu[k + n], a.frozen) : 0.0;
-          a.yhat[u * pts + k] = Yu[k] + a.dt * a.ih2 * ((w_ + e_) + (s_ + no) - 4.0 * c);
+          const double c = lin2_v(yk, a.frozen);
+          const double w_ = (j > 0) ? lin2_v(__ldcg(Yu + k - 1), a.frozen) : 0.0;
+          const double e_ = (j < n - 1) ? lin2_v(__ldcg(Yu + k + 1), a.frozen) : 0.0;
+          const double s_ = (i > 0) ? lin2_v(__ldcg(Yu + k - n), a.frozen) : 0.0;
+          const double no = (i < n - 1) ? lin2_v(__ldcg(Yu + k + n), a.frozen) : 0.0;
+          a.yhat[u * pts + k] = yk + a.dt * a.ih2 * ((w_ + e_) + (s_ + no) - 4.0 * c);
         }
       }
     }
   }
+}
+
+template <int N>
+__device__ __forceinline__ void ph_prologue(const PArgs& a, int step) {
+  (void)step;
+  ph_prologue_items<N>(a, grid_items<N>(a));
   for (int u = blockIdx.x * kThreads + threadIdx.x; u < a.units; u += gridDim.x * kThreads) {
     a.flag[2 * u] = 0;
     a.flag[2 * u + 1] = 0;
@@ -915,28 +943,47 @@ __device__ __forceinline__ void ph_predict(const PArgs& a, int have_prev) {
   if (blockIdx.x == 0 && threadIdx.x < 4) a.active[threadIdx.x] = 0;
 }
 
+// The predictor over the rows of the given items (the cluster execution).
+template <int N>
+__device__ __forceinline__ void ph_predict_items(const PArgs& a, int have_prev, Items its) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
+  const size_t pts = (size_t)n * n;
+  if (a.scheme != SCHEME_NL) return;
+  for (int item = its.first; item < its.end; item += its.step) {
+    const int u = item / nb, a0 = (item - u * nb) * kDstRows;
+    const size_t base = u * pts + (size_t)a0 * n;
+    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+    for (int e = threadIdx.x; e < cnt; e += kThreads) {
+      const double y = __ldcg(a.Y + base + e);
+      const double g = have_prev ? 2.0 * y - __ldcg(a.yprev + base + e) : y;
+      a.yprev[base + e] = y;
+      a.Y[base + e] = g;
+    }
+  }
+}
+
 // Five-point Laplacian of X at (i, j) of an n x n grid (zero outside), restrict loads.
 template <int n>
 __device__ __forceinline__ double lap5r(const double* __restrict__ X, int i, int j) {
   const size_t k = (size_t)i * n + j;
-  const double c = X[k];
-  const double w = (j > 0) ? X[k - 1] : 0.0;
-  const double e = (j < n - 1) ? X[k + 1] : 0.0;
-  const double s = (i > 0) ? X[k - n] : 0.0;
-  const double no = (i < n - 1) ? X[k + n] : 0.0;
+  const double c = __ldcg(X + k);
+  const double w = (j > 0) ? __ldcg(X + k - 1) : 0.0;
+  const double e = (j < n - 1) ? __ldcg(X + k + 1) : 0.0;
+  const double s = (i > 0) ? __ldcg(X + k - n) : 0.0;
+  const double no = (i < n - 1) ? __ldcg(X + k + n) : 0.0;
   return (w + e) + (s + no) - 4.0 * c;
 }
 
 // N1: z = c1 lap(Y) - dt g(Y)
 template <int N>
-__device__ __forceinline__ void ph_z(const PArgs& a) {
-  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 2;
+__device__ __forceinline__ void ph_z(const PArgs& a, Items its) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
   const size_t pts = (size_t)n * n;
   double* __restrict__ z = a.z;
   const double* __restrict__ W64 = a.W64;
-  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+  for (int item = its.first; item < its.end; item += its.step) {
     const int u = item / nb, a0 = (item - u * nb) * kDstRows;
-    if (a.flag[2 * u]) continue;
+    if (its.chk && a.flag[2 * u]) continue;
     const double* __restrict__ Yu = a.Y + u * pts;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
     const double c1 = unit_c1(a, u);
@@ -949,8 +996,8 @@ __device__ __forceinline__ void ph_z(const PArgs& a) {
           const int i = a0 + e / n, j = e - (e / n) * n;
           const size_t k = (size_t)i * n + j;
           lv[q] = lap5r<n>(Yu, i, j);
-          xv[q] = Yu[k];
-          wv[q] = (a.zmode == 2) ? W64[u * pts + k] : 0.0;
+          xv[q] = __ldcg(Yu + k);
+          wv[q] = (a.zmode == 2) ? __ldcg(W64 + u * pts + k) : 0.0;
         }
       }
 #pragma unroll
@@ -972,8 +1019,8 @@ __device__ __forceinline__ void ph_z(const PArgs& a) {
 
 // N2: H = (Y - Yhat) + ih2 lap(z) in FP32; Jacobian weights and their range per item
 template <int N>
-__device__ __forceinline__ void ph_resid(const PArgs& a) {
-  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 2;
+__device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
   __shared__ double sh[kThreads / 32];
   const size_t pts = (size_t)n * n;
   const double* __restrict__ Y = a.Y;
@@ -981,9 +1028,9 @@ __device__ __forceinline__ void ph_resid(const PArgs& a) {
   const double* __restrict__ W64 = a.W64;
   float* __restrict__ rhs = a.rhs;
   float* __restrict__ w = a.w;
-  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+  for (int item = its.first; item < its.end; item += its.step) {
     const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
-    if (a.flag[2 * u]) continue;
+    if (its.chk && a.flag[2 * u]) continue;
     const double* __restrict__ zu = a.z + u * pts;
     const size_t base = u * pts + (size_t)a0 * n;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
@@ -996,9 +1043,9 @@ __device__ __forceinline__ void ph_resid(const PArgs& a) {
         if (e < cnt) {
           const int i = a0 + e / n, j = e - (e / n) * n;
           lz[q] = lap5r<n>(zu, i, j);
-          yv[q] = Y[base + e];
-          hv[q] = yhat[base + e];
-          w64[q] = (a.zmode == 2) ? W64[base + e] : 0.0;
+          yv[q] = __ldcg(Y + base + e);
+          hv[q] = __ldcg(yhat + base + e);
+          w64[q] = (a.zmode == 2) ? __ldcg(W64 + base + e) : 0.0;
         }
       }
 #pragma unroll
@@ -1039,14 +1086,27 @@ __device__ __forceinline__ void ph_cg_reset(const PArgs& a) {
   if (blockIdx.x == 0 && threadIdx.x < 2) a.active[threadIdx.x] = 0;
 }
 
-// The CG update of iteration `it` (Chronopoulos-Gear form: both inner products of an iteration
+// CG scalars of iteration `it` (Chronopoulos-Gear form: both inner products of an iteration
 // come from one reduction, gamma = (r, u) and delta = (w, u) with u = M^{-1} r and w = S u):
-//   beta = gamma / gamma_prev (0 at it = 0), alpha = gamma / (delta - beta gamma / alpha_prev),
+//   beta = gamma / gamma_prev (0 at it = 0), alpha = gamma / (delta - beta gamma / alpha_prev).
+__device__ __forceinline__ void cg_scalars(int it, double gam, double del, double gp, double ap, double& alpha,
+                                           double& beta) {
+  beta = 0.0;
+  if (it > 0) {
+    beta = (gp > 0.0) ? gam / gp : 0.0;
+    const double den = (ap != 0.0) ? del - beta * gam / ap : del;
+    alpha = (den > 0.0) ? gam / den : 0.0;
+  } else {
+    alpha = (del > 0.0) ? gam / del : 0.0;
+  }
+}
+
+// The vector updates of a CG iteration on rows [a0, a0 + kDstRows) of unit u:
 //   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^{-1} r.
-// A unit whose gamma has fallen to cg_tol^2 gamma_0 is done (its x is kept).
 template <int N>
-__device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
-  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
+__device__ __forceinline__ void cg_update_rows(const PArgs& a, int u, int a0, int it, float fa, float fb, float cwb,
+                                               float fe2dt) {
+  constexpr int n = N - 1, U = 8;  // elements per thread whose loads are issued together
   const size_t pts = (size_t)n * n;
   float* __restrict__ xh = a.xh;
   float* __restrict__ rh = a.rh;
@@ -1055,22 +1115,56 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
   float* __restrict__ uh = a.uh;
   const float* __restrict__ wh = a.qh;
   const float* __restrict__ mu1 = a.mu1;
+  const size_t base = u * pts + (size_t)a0 * n;
+  const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
+  for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
+    float uv[U], wv[U], pv[U], sv[U], xv[U], rv[U], mv[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int e = e0 + q * kThreads;
+      if (e < cnt) {
+        uv[q] = __ldcg(uh + base + e);
+        wv[q] = __ldcg(wh + base + e);
+        pv[q] = (it > 0) ? __ldcg(ph + base + e) : 0.f;
+        sv[q] = (it > 0) ? __ldcg(sh + base + e) : 0.f;
+        xv[q] = __ldcg(xh + base + e);
+        rv[q] = __ldcg(rh + base + e);
+        const int i = a0 + e / n;
+        mv[q] = mu1[i] + mu1[e - (e / n) * n];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int e = e0 + q * kThreads;
+      if (e < cnt) {
+        const float p = uv[q] + fb * pv[q];
+        const float sq = wv[q] + fb * sv[q];
+        const float r = rv[q] - fa * sq;
+        ph[base + e] = p;
+        sh[base + e] = sq;
+        xh[base + e] = xv[q] + fa * p;
+        rh[base + e] = r;
+        uh[base + e] = r * __frcp_rn(mdiag(mv[q], fe2dt, cwb));
+      }
+    }
+  }
+}
+
+// The CG update of iteration `it` over the batch; a unit whose gamma has fallen to
+// cg_tol^2 gamma_0 is done (its x is kept).
+template <int N>
+__device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
   const int cur = (it & 1) * 2, prev = ((it + 1) & 1) * 2;
   for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
     const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
     if (a.flag[2 * u] || a.flag[2 * u + 1]) continue;
     const double gam = unit_sum<N>(a.pgam, u), del = unit_sum<N>(a.pdel, u);
-    const double gam0 = (it == 0) ? gam : a.cgs[u * 8 + 4];
+    const double gam0 = (it == 0) ? gam : __ldcg(a.cgs + u * 8 + 4);
     const bool done = !(gam > a.cg_tol2 * gam0);  // also catches NaN
-    double beta = 0.0, alpha = 0.0;
-    if (it > 0) {
-      const double gp = a.cgs[u * 8 + prev + 1], ap = a.cgs[u * 8 + prev];
-      beta = (gp > 0.0) ? gam / gp : 0.0;
-      const double den = (ap != 0.0) ? del - beta * gam / ap : del;
-      alpha = (den > 0.0) ? gam / den : 0.0;
-    } else {
-      alpha = (del > 0.0) ? gam / del : 0.0;
-    }
+    double beta, alpha;
+    cg_scalars(it, gam, del, (it > 0) ? __ldcg(a.cgs + u * 8 + prev + 1) : 0.0,
+               (it > 0) ? __ldcg(a.cgs + u * 8 + prev) : 0.0, alpha, beta);
     if (b == 0 && threadIdx.x == 0) {
       atomicAdd(a.totals + 2, 1ull);
       if (done) {
@@ -1083,42 +1177,7 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
       }
     }
     if (done) continue;
-    const float fa = float(alpha), fb = float(beta);
-    const float cwb = a.fdt * float(unit_wbar<N>(a, u));
-    const float fe2dt = unit_fe2dt(a, u);
-    const size_t base = u * pts + (size_t)a0 * n;
-    const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
-    for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
-      float uv[U], wv[U], pv[U], sv[U], xv[U], rv[U], mv[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int e = e0 + q * kThreads;
-        if (e < cnt) {
-          uv[q] = uh[base + e];
-          wv[q] = wh[base + e];
-          pv[q] = (it > 0) ? ph[base + e] : 0.f;
-          sv[q] = (it > 0) ? sh[base + e] : 0.f;
-          xv[q] = xh[base + e];
-          rv[q] = rh[base + e];
-          const int i = a0 + e / n;
-          mv[q] = mu1[i] + mu1[e - (e / n) * n];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int e = e0 + q * kThreads;
-        if (e < cnt) {
-          const float p = uv[q] + fb * pv[q];
-          const float sq = wv[q] + fb * sv[q];
-          const float r = rv[q] - fa * sq;
-          ph[base + e] = p;
-          sh[base + e] = sq;
-          xh[base + e] = xv[q] + fa * p;
-          rh[base + e] = r;
-          uh[base + e] = r * __frcp_rn(mdiag(mv[q], fe2dt, cwb));
-        }
-      }
-    }
+    cg_update_rows<N>(a, u, a0, it, float(alpha), float(beta), a.fdt * float(unit_wbar<N>(a, u)), unit_fe2dt(a, u));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.active[(it + 1) & 1] = 0;
@@ -1129,12 +1188,10 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
 // N7: Newton stop test per unit (tolerance, or the FP64 floor rule)
 template <int N>
 __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
-  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
   const int last = (it_n >= a.newton_max - 1);
   for (int u = blockIdx.x * kThreads + threadIdx.x; u < a.units; u += gridDim.x * kThreads) {
     if (a.flag[2 * u]) continue;
-    double dm = 0.0;
-    for (int b = 0; b < nb; ++b) dm = fmax(dm, a.pd[(size_t)u * nb + b]);
+    const double dm = unit_max<N>(a.pd, u);
     const int mm = ++a.cnt[u];
     const double prev = a.scal[u * 8 + 6];
     bool done = dm <= a.tol || (mm >= 2 && dm <= a.floor_ && dm > 0.5 * prev);
@@ -1159,7 +1216,7 @@ __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
 
 template <int N, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
-  constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int n = N - 1, L = 2 * N;
   constexpr int FL = (kDstRows / 2) * L;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
@@ -1179,9 +1236,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
     noinl([&] { ph_predict<N>(a, (a.scheme == SCHEME_NL) && (step > 0 || a.have_prev0)); });
     CH_BAR();
     for (int it_n = 0; it_n < a.newton_max; ++it_n) {
-      noinl([&] { ph_z<N>(a); });
+      noinl([&] { ph_z<N>(a, grid_items<N>(a)); });
       CH_BAR();
-      noinl([&] { ph_resid<N>(a); });
+      noinl([&] { ph_resid<N>(a, grid_items<N>(a)); });
       CH_BAR();
       noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, 0, nullptr); });  // H to sine space
       CH_BAR();
@@ -1240,6 +1297,208 @@ template <int N>
 cudaError_t launch_persist_sel(const PArgs& a, int minb, int* grid_out, cudaStream_t st) {
   (void)minb;
   return launch_persist<N, 2>(a, grid_out, st);
+}
+
+// ------------------------------------------------------------------ cluster execution
+//
+// One thread-block cluster of C blocks per unit runs that unit's whole propagation (nsteps
+// implicit steps) in one launch. Block r of a cluster owns the row blocks r, r + C, ... of its
+// unit; the phases are the ones above, separated by cluster barriers instead of kernel
+// boundaries (barrier.cluster arrive.release / wait.acquire order each phase's global-memory
+// writes before the next phase's reads, which are L2-coherent loads), and each unit leaves its
+// CG and Newton loops as soon as it has converged instead of when the slowest unit of the batch
+// has. Every block of a cluster forms the loop decisions from the same partials summed in the
+// same order, so all blocks take the same branches and meet at the same barriers; the loops are
+// bounded by cg_max and newton_max.
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+
+__device__ __forceinline__ int cluster_blocks() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return (int)r;
+}
+
+__device__ __forceinline__ int cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return (int)r;
+}
+
+// Transform passes over this block's items, unit flags not tested (act = -1).
+template <int N, int EPI>
+__device__ __forceinline__ void dst_items(const PArgs& a, float2* buf, const float2* twd, const float* in, float* out,
+                                          double* part, Items its, double wb) {
+  for (int item = its.first; item < its.end; item += its.step) {
+    __syncthreads();  // the previous item's epilogue has finished reading buf
+    noinl([&] { dst_item<N, EPI>(a, buf, twd, in, out, -1, part, item, wb); });
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 2) k2_cluster(PArgs args) {
+  constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int FL = (kDstRows / 2) * L;
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
+  float2* twd = smem2 + FL + FL / 8;
+  __shared__ PArgs a;
+  if (threadIdx.x == 0) a = args;
+  for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = args.tw[m];
+  __syncthreads();
+  const int C = cluster_blocks(), rank = cluster_rank(), u = cluster_index();
+  if (u >= a.units) return;  // whole clusters only (the grid is units x C blocks)
+  const Items its{u * nb + rank, C, (u + 1) * nb, 0};
+  long long cg_iters = 0;
+  unsigned long long newton_sum = 0;
+  int newton_peak = 0;
+  unsigned st = 0;
+  for (int step = 0; step < a.nsteps; ++step) {
+    noinl([&] { ph_prologue_items<N>(a, its); });
+    cluster_sync();
+    noinl([&] { ph_predict_items<N>(a, (a.scheme == SCHEME_NL) && (step > 0 || a.have_prev0), its); });
+    cluster_sync();
+    double prev_dm = 0.0;
+    int m = 0;
+    for (int it_n = 0; it_n < a.newton_max; ++it_n) {
+      noinl([&] { ph_z<N>(a, its); });
+      cluster_sync();
+      noinl([&] { ph_resid<N>(a, its); });
+      // the first pass reads only the rows this block has just written
+      dst_items<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, nullptr, its, 0.0);  // H to sine space
+      cluster_sync();
+      const double wb = unit_wbar<N>(a, u);
+      dst_items<N, E_INIT>(a, buf, twd, a.tmp, nullptr, nullptr, its, wb);  // CG start
+      cluster_sync();
+      const float cwb = a.fdt * float(wb), fe2dt = unit_fe2dt(a, u);
+      double gam0 = 0.0, gp = 0.0, ap = 0.0;
+      for (int it = 0; it < a.cg_max; ++it) {
+        dst_items<N, E_PLAIN>(a, buf, twd, a.uh, a.tmp, nullptr, its, wb);  // u to physical space
+        cluster_sync();
+        dst_items<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, nullptr, its, wb);  // dt (wc - wbar) u
+        cluster_sync();
+        dst_items<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, nullptr, its, wb);  // back to sine space
+        cluster_sync();
+        dst_items<N, E_W>(a, buf, twd, a.tmp, nullptr, nullptr, its, wb);  // w = S u, (w,u), (r,u)
+        cluster_sync();
+        const double gam = unit_sum<N>(a.pgam, u), del = unit_sum<N>(a.pdel, u);
+        if (it == 0) gam0 = gam;
+        ++cg_iters;
+        if (!(gam > a.cg_tol2 * gam0)) break;  // also catches NaN
+        double alpha, beta;
+        cg_scalars(it, gam, del, gp, ap, alpha, beta);
+        gp = gam;
+        ap = alpha;
+        // the next pass reads only the rows this block updates here
+        noinl([&] {
+          for (int item = its.first; item < its.end; item += its.step)
+            cg_update_rows<N>(a, u, (item - u * nb) * kDstRows, it, float(alpha), float(beta), cwb, fe2dt);
+        });
+      }
+      dst_items<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, nullptr, its, 0.0);  // correction to physical space
+      cluster_sync();
+      dst_items<N, E_UPDATE>(a, buf, twd, a.tmp, nullptr, a.pd, its, 0.0);  // Y -= d, max |d|
+      cluster_sync();
+      const double dm = unit_max<N>(a.pd, u);
+      ++m;
+      bool done = dm <= a.tol || (m >= 2 && dm <= a.floor_ && dm > 0.5 * prev_dm);
+      prev_dm = dm;
+      if (!done && it_n == a.newton_max - 1) {
+        st |= ST_NEWTON;
+        done = true;
+      }
+      if (done) break;
+    }
+    newton_sum += (unsigned long long)m;
+    newton_peak = m > newton_peak ? m : newton_peak;
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    if (st) atomicOr(a.status, st);
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.status + 4), newton_sum);
+    atomicMax(reinterpret_cast<int*>(a.status + 3), newton_peak);
+    atomicAdd(a.totals + 2, (unsigned long long)cg_iters);
+  }
+}
+
+template <int N>
+cudaError_t cluster_prepare() {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(dev)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k2_cluster<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dst_smem<N>());
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_cluster<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) done.insert(dev);
+  return e;
+}
+
+template <int N>
+void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int units, int C, cudaStream_t st) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3((unsigned)(units * C));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = dst_smem<N>();
+  cfg.stream = st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+}
+
+// Cluster size for `units` units: the largest power of two up to min(16, row blocks) for which
+// all clusters are resident at once, else 1 (one block per unit, in waves). `force` > 0 takes
+// that size if it divides the row blocks.
+template <int N>
+cudaError_t cluster_choose(int units, int force, int* C_out) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  cudaError_t e = cluster_prepare<N>();
+  if (e != cudaSuccess) return e;
+  if (force > 0 && force <= 16 && nb % force == 0) {
+    *C_out = force;
+    return cudaSuccess;
+  }
+  for (int C = nb < 16 ? nb : 16; C > 1; C /= 2) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    cluster_config<N>(cfg, at, units, C, nullptr);
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, k2_cluster<N>, &cfg);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (ncl >= units) {
+      *C_out = C;
+      return cudaSuccess;
+    }
+  }
+  *C_out = 1;
+  return cudaSuccess;
+}
+
+template <int N>
+cudaError_t launch_cluster(const PArgs& a, int force, int* C_out, cudaStream_t st) {
+  int C = 1;
+  cudaError_t e = cluster_choose<N>(a.units, force, &C);
+  if (e != cudaSuccess) return e;
+  *C_out = C;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  cluster_config<N>(cfg, at, a.units, C, st);
+  return cudaLaunchKernelEx(&cfg, k2_cluster<N>, a);
 }
 
 }  // namespace
@@ -1331,6 +1590,30 @@ cudaError_t Prop2D::propagate_persistent(double* Y, int units, int scheme, doubl
 }
 
 
+cudaError_t Prop2D::propagate_cluster(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st) {
+  if (units > cap_ || units < 1) return cudaErrorInvalidValue;
+  if (nsteps < 1) return cudaSuccess;
+  PArgs a;
+  make_args(a, Y, units, scheme, dt, nsteps, 0, 0);
+  a.have_prev0 = 0;
+  cudaError_t e = cudaSuccess;
+  int C = 1;
+  switch (p_.n + 1) {
+    case 16: e = launch_cluster<16>(a, cluster_force_, &C, st); break;
+    case 32: e = launch_cluster<32>(a, cluster_force_, &C, st); break;
+    case 64: e = launch_cluster<64>(a, cluster_force_, &C, st); break;
+    case 128: e = launch_cluster<128>(a, cluster_force_, &C, st); break;
+    case 256: e = launch_cluster<256>(a, cluster_force_, &C, st); break;
+    case 512: e = launch_cluster<512>(a, cluster_force_, &C, st); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) {
+    step_kernels_ += 1;
+    cluster_size_ = C;
+  }
+  return e;
+}
+
 // ------------------------------------------------------------------ graph execution
 //
 // The same phases as separate kernels (each at its own occupancy), one CUDA graph per step with
@@ -1348,8 +1631,10 @@ __host__ __device__ constexpr bool is_dst_phase(int ph) {
          ph == PH_X2;
 }
 
+// Four blocks per SM (a batch's items all resident at n = 255), two for the length-1024
+// transforms of n = 511, whose butterflies need the registers.
 template <int N, int PH>
-__global__ void __launch_bounds__(kThreads) k2_phase(PArgs a, int have_prev) {
+__global__ void __launch_bounds__(kThreads, (N >= 512 ? 2 : 4)) k2_phase(PArgs a, int have_prev) {
   constexpr int L = 2 * N, FL = (kDstRows / 2) * L, nb = (N - 1 + kDstRows - 1) / kDstRows;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
@@ -1362,8 +1647,8 @@ __global__ void __launch_bounds__(kThreads) k2_phase(PArgs a, int have_prev) {
   (void)nb;
   if constexpr (PH == PH_PROLOGUE) ph_prologue<N>(a, 0);
   if constexpr (PH == PH_PREDICT) ph_predict<N>(a, have_prev);
-  if constexpr (PH == PH_Z) ph_z<N>(a);
-  if constexpr (PH == PH_RESID) ph_resid<N>(a);
+  if constexpr (PH == PH_Z) ph_z<N>(a, grid_items<N>(a));
+  if constexpr (PH == PH_RESID) ph_resid<N>(a, grid_items<N>(a));
   if constexpr (PH == PH_H1) dst_item<N, E_PLAIN>(a, buf, twd, a.rhs, a.tmp, 0, nullptr, blockIdx.x);
   if constexpr (PH == PH_H2) {
     dst_item<N, E_INIT>(a, buf, twd, a.tmp, nullptr, 0, nullptr, blockIdx.x);

@@ -15,8 +15,9 @@ enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u, ST_TIMEOU
 // How a batch of implicit steps is executed: one CUDA graph per step (each phase a kernel; the
 // Newton and CG loops conditional WHILE nodes, 7 kernels per CG iteration), or one persistent
 // cooperative kernel per propagate call (the same phases separated by grid barriers), or plain
-// launches with the loops driven from the host (for profiling single kernels).
-enum StepPath { PATH_GRAPH = 0, PATH_PERSISTENT = 1, PATH_HOST = 2 };
+// launches with the loops driven from the host (for profiling single kernels), or one
+// thread-block cluster per unit running that unit's whole propagation in one launch.
+enum StepPath { PATH_GRAPH = 0, PATH_PERSISTENT = 1, PATH_HOST = 2, PATH_CLUSTER = 3 };
 
 // Grid sizes the sine transform supports: n + 1 a power of two (radix-2 FFT of length 2(n+1)).
 bool supported_n(int n);
@@ -44,6 +45,7 @@ class Prop2D {
   cudaError_t propagate(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
   cudaError_t propagate_persistent(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
   cudaError_t propagate_host(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
+  cudaError_t propagate_cluster(double* Y, int units, int scheme, double dt, int nsteps, cudaStream_t st);
   void set_path(StepPath p) { path_ = p; }
   // Per-unit eps^2 (device array [units], row i of the next propagate calls) or null (all units
   // use Params2D::eps2). Graphs built afterwards read the array at every replay.
@@ -55,6 +57,7 @@ class Prop2D {
     eps2u_ = eps2_dev;
   }
   StepPath path() const { return path_; }
+  int cluster_size() const { return cluster_size_; }
   // Orthonormal 2D DST-I (its own inverse) of `units` FP32 fields; in and out must differ and
   // must not be the internal scratch buffers.
   cudaError_t dst2(const float* in, float* out, int units, cudaStream_t st);
@@ -67,7 +70,7 @@ class Prop2D {
   // step runs a fixed prologue and epilogue, each batched Newton pass kNewtonKernels and each
   // batched CG iteration kCgKernels.
   long long kernel_launches() const {
-    if (path_ == PATH_PERSISTENT) return step_kernels_;
+    if (path_ == PATH_PERSISTENT || path_ == PATH_CLUSTER) return step_kernels_;
     if (path_ == PATH_HOST) return step_kernels_ + (kNewtonKernels - 2) * newton_passes_ + (kCgKernels - 1) * cg_total_;
     return step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
   }
@@ -141,7 +144,9 @@ class Prop2D {
   long long step_kernels_ = 0;
   StepPath path_ = PATH_GRAPH;
   const double* eps2u_ = nullptr;  // per-unit eps^2 or null
-  int persist_minb_ = 3;      // persistent path: blocks per SM it is compiled for (2, 3, 4)
+  int persist_minb_ = 3;
+  int cluster_force_ = 0;     // cluster execution: cluster size (0: chosen by residency)
+  int cluster_size_ = 0;      // cluster size of the last cluster launch      // persistent path: blocks per SM it is compiled for (2, 3, 4)
   double* ppart_ = nullptr;   // persistent path: per-item partial sums [7][cap][rows / 16]
   int* active_ = nullptr;     // persistent path: units still iterating (parity slots)
   unsigned* bar_ = nullptr;   // persistent path: grid barrier (arrivals, generation, abort)

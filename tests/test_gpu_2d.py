@@ -166,16 +166,19 @@ def test_c3_grid_full_size_steps(gpu_lib):
         assert np.max(np.abs(out - ref)) <= tol, (scheme, np.max(np.abs(out - ref)), tol)
 
 
-@pytest.fixture
-def persistent_path(monkeypatch):
-    """Selects the persistent one-kernel execution of the 2D steps (read when a solver is created)."""
-    monkeypatch.setenv("CH_2D_STEP", "persistent")
+@pytest.fixture(params=["persistent", "cluster"])
+def alt_path(request, monkeypatch):
+    """Selects another execution of the 2D steps (read when a solver is created): the persistent
+    cooperative kernel, or one thread-block cluster per unit."""
+    monkeypatch.setenv("CH_2D_STEP", request.param)
+    return request.param
 
 
 @pytest.mark.parametrize("n", [15, 63, 255])
 @pytest.mark.parametrize("scheme", ["lin1", "lin2", "nl"])
-def test_persistent_path_matches_oracle(gpu_lib, persistent_path, n, scheme):
-    """The persistent execution (the default is one graph per step) against the oracle."""
+def test_other_paths_match_oracle(gpu_lib, alt_path, n, scheme):
+    """The persistent and cluster executions (the default is one graph per step) against the
+    oracle."""
     ch = gpu_lib
     h = 1.0 / (n + 1)
     eps = 0.05
@@ -209,10 +212,62 @@ def test_persistent_and_graph_paths_agree(gpu_lib, monkeypatch, n):
     assert np.max(np.abs(a - g)) <= 64 * step_bound_2d(n, eps, dt) * nsteps
 
 
-def test_per_problem_eps_matches_oracle(gpu_lib):
+@pytest.mark.parametrize("n", [31, 255, 511])
+def test_cluster_path_agrees_and_is_independent_of_cluster_size(gpu_lib, monkeypatch, n):
+    """The cluster execution runs the graph path's phase functions per unit, so it agrees with it
+    to the step's rounding floor; and each unit's arithmetic (row blocks, partial sums in block
+    order) does not depend on how many blocks share the unit, so every cluster size gives the
+    same bits."""
+    ch = gpu_lib
+    eps, dt, nsteps, B = 0.01, 1.5625e-4, 2, 3
+    u0 = np.stack([ch_inputs.initial_condition(2, n, 330 + b, kind="normal", amp=0.05) for b in range(B)])
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    g = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+    monkeypatch.setenv("CH_2D_STEP", "cluster")
+    c = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+    assert np.max(np.abs(c - g)) <= 64 * step_bound_2d(n, eps, dt) * nsteps
+    nb = (n + 15) // 16
+    for size in (1, 2, 4, 8, 16):
+        if nb % size:
+            continue
+        monkeypatch.setenv("CH_2D_CLUSTER", str(size))
+        cs = ch.propagate(cfg, "nl", dt, nsteps, dev(u0)).cpu().numpy()
+        assert np.array_equal(cs, c), size
+
+
+@pytest.mark.parametrize("path", ["graph", "cluster"])
+def test_parareal_2d_iterates_match_oracle_on_each_path(gpu_lib, monkeypatch, path):
+    """Parareal (NPA-I) on a batch of two problems with the chosen 2D execution: the reference
+    fine solution and two iterates follow the oracle."""
+    ch = gpu_lib
+    if path != "graph":
+        monkeypatch.setenv("CH_2D_STEP", path)
+    n, N, J, eps, T = 31, 4, 3, 0.05, 0.01
+    cfg = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N, fine_steps=J, variant="NPA-I", newton_tol=1e-12,
+                    max_iters=2)
+    u0s = [ch_inputs.initial_condition(2, n, 440 + b, kind="normal", amp=0.1) for b in range(2)]
+    pr = ch.Parareal(cfg, batch=2)
+    pr.set_initial_batch(np.stack(u0s))
+    pr.compute_reference()
+    pr.run()
+    p = oracle_params(cfg)
+    tol = 64 * step_bound_2d(n, eps, T / N) * (2 * N + J * N) + 1e-12
+    for b in range(2):
+        Uf = o2.fine_solution(p, u0s[b])
+        r = o2.parareal(p, u0s[b], Uf, max_iters=2)
+        assert np.max(np.abs(pr.get_reference(b) - Uf)) <= tol
+        assert np.max(np.abs(pr.get_slices(b) - r.U)) <= tol
+        assert pr.stats(b)["iterations"] == 2
+    pr.close()
+
+
+@pytest.mark.parametrize("path", ["graph", "cluster"])
+def test_per_problem_eps_matches_oracle(gpu_lib, monkeypatch, path):
     """A batch whose problems have different eps (ch_parareal_set_eps): each problem's sequential
     fine solution and Parareal iterates follow the oracle run with its own eps."""
     ch = gpu_lib
+    if path != "graph":
+        monkeypatch.setenv("CH_2D_STEP", path)
     n, N, J = 31, 4, 3
     eps = [0.03, 0.05, 0.08]
     cfg = ch.Config(dim=2, n=n, eps=0.05, T=0.01, n_slices=N, fine_steps=J, variant="NPA-I", newton_tol=1e-12,
