@@ -190,6 +190,22 @@ ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, i
                        const double* u_in_dev, double* u_out_dev, int* newton_dev,
                        void* cuda_stream);
 
+/* A-priori Parareal error bound of Section 3 for cfg's variant, grid and time stepping:
+ *     max_j ||E_j^k|| <= factor_k max_j ||E_j^0||,
+ *     factor_k = a^k min{ ((1 - b^(N-1)) / (1 - b))^k, C(N-1, k) }   (0 for k >= N),
+ * a = ||P_J - P_c||, b = ||P_c|| for PA-I / PA-II / PA-III (Theorems 3.7, 3.9, 3.11: P_c the
+ * coarse propagator P_1, P_2, P_1 applied cfg->coarse_steps times, P_J the fine one P_1, P_2, P_2
+ * with dT / J applied J times, all of the frozen model diag(u^2) = I); a = lte_const dT^2 and
+ * b = ||P_1|| (NPA-I, Theorem 3.16) or ||P_3|| (NPA-II, Theorem 3.21), lte_const > 0 being the
+ * constant C_1 / C_2 of the local truncation error, which the paper fits to measurements.
+ * Norms are Euclidean 2-norms, formed over the eigenvalues of D_h (1D: n modes, 2D: n^2;
+ * n in 1..2048 for both dims). Writes out_host[0] = a, out_host[1] = b, out_host[2 + k] =
+ * factor_k for k = 0..kmax (len >= kmax + 3). Runs on `cuda_stream` and synchronises it.
+ * Errors: CH_ERR_INVALID (cfg fields out of range, kmax < 0, len too small, lte_const <= 0
+ * for the nonlinear variants), CH_ERR_OOM, CH_ERR_CUDA. */
+ch_status ch_parareal_theory_bound(const ch_config* cfg, double lte_const, int kmax, double* out_host,
+                                   size_t len, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------------------
  * Learned coarse propagator G_theta(U) = U + R(U). The paper has none: it replaces the plain
  * coarse step G of Eq. 2.2 (one LIN1 step of Delta T), and Parareal still reaches the fine

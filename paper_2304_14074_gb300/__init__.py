@@ -6,10 +6,11 @@ implemented as hand-written CUDA behind the C ABI of ``include/ch_parareal.h``. 
 package is the thin Python binding of that ABI.
 """
 from ._lib import (CH_GTHETA_PARAMS, CH_MAX_ITERS, EXPORTED_SYMBOLS, SCHEMES, STATUS, VARIANTS, ChError, Config,
-                   Ensemble, GTheta, Parareal, gtheta_flatten, gtheta_unflatten, load, propagate, sine_transform_2d)
+                   Ensemble, GTheta, Parareal, gtheta_flatten, gtheta_unflatten, load, propagate, sine_transform_2d,
+                   theory_bound)
 from .build import LIB as LIBRARY_PATH
 from .build import build
 
 __all__ = ["CH_GTHETA_PARAMS", "CH_MAX_ITERS", "EXPORTED_SYMBOLS", "SCHEMES", "STATUS", "VARIANTS", "ChError",
            "Config", "Ensemble", "GTheta", "Parareal", "gtheta_flatten", "gtheta_unflatten", "load", "propagate",
-           "sine_transform_2d", "build", "LIBRARY_PATH"]
+           "sine_transform_2d", "theory_bound", "build", "LIBRARY_PATH"]

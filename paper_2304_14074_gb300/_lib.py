@@ -33,7 +33,7 @@ EXPORTED_SYMBOLS = [
     "ch_gtheta_set_params", "ch_gtheta_get_params", "ch_gtheta_forward", "ch_gtheta_gradients",
     "ch_gtheta_train", "ch_ensemble_create", "ch_ensemble_set_initial", "ch_ensemble_compute_reference",
     "ch_ensemble_run", "ch_ensemble_get_slices", "ch_ensemble_get_reference", "ch_ensemble_get_stats",
-    "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error",
+    "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_parareal_theory_bound",
 ]
 _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
               "ch_gtheta_last_error", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_ensemble_groups")
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True):
     lib.ch_status_string.restype = C.c_char_p
     lib.ch_propagate.argtypes = [C.POINTER(_Config), C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp]
     lib.ch_sine_transform_2d.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+    lib.ch_parareal_theory_bound.argtypes = [C.POINTER(_Config), C.c_double, C.c_int, d, sz, vp]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     f = C.POINTER(C.c_float)
     lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz, C.c_int]
@@ -324,6 +325,20 @@ def propagate(cfg: Config, scheme: str, dt: float, nsteps: int, u_in, u_out=None
     if s != 0:
         raise ChError(s, "ch_propagate")
     return u_out
+
+
+def theory_bound(cfg: Config, kmax: int, lte_const: float = 0.0, stream=None):
+    """Section 3 a-priori bound (ch_parareal_theory_bound): returns (a, b, factors[0..kmax]),
+    max_j ||E_j^k|| <= factors[k] max_j ||E_j^0||. lte_const: C_1 / C_2 for NPA-I / NPA-II."""
+    import numpy as np
+    lib = load()
+    out = np.zeros(kmax + 3)
+    cc = cfg.c()
+    s = lib.ch_parareal_theory_bound(C.byref(cc), lte_const, kmax, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                     out.size, _stream_ptr(stream))
+    if s != 0:
+        raise ChError(s, "ch_parareal_theory_bound")
+    return float(out[0]), float(out[1]), out[2:].copy()
 
 
 def sine_transform_2d(x, out=None, stream=None):

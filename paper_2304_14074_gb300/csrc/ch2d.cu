@@ -96,15 +96,19 @@ __device__ __forceinline__ void dft_small<8>(float2 (&v)[8]) {
 }
 
 // Odd extension of a row pair: y_m = (x0[m-1], x1[m-1]) for 0 < m < N, 0 at m = 0 and m = N,
-// y_{L-m} = -y_m.
+// y_{L-m} = -y_m. r0, r1 are valid rows; v0, v1 = false stands for a zero row past the grid.
+// The loads are unconditional (from a valid element), so all of a thread's loads of a stage
+// are in flight together; the zeros are selected afterwards.
 template <int N>
-__device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const float* __restrict__ r1, int m) {
+__device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const float* __restrict__ r1, bool v0,
+                                          bool v1, int m) {
   constexpr int L = 2 * N;
-  if (m == 0 || m == N) return make_float2(0.f, 0.f);
-  const bool neg = m > N;
-  const int q = neg ? L - m - 1 : m - 1;
-  const float a = r0 ? __ldcg(r0 + q) : 0.f, b = r1 ? __ldcg(r1 + q) : 0.f;
-  return neg ? make_float2(-a, -b) : make_float2(a, b);
+  const bool zero = (m == 0 || m == N), neg = m > N;
+  const int q = zero ? 0 : (neg ? L - m - 1 : m - 1);
+  const float a = __ldcg(r0 + q), b = __ldcg(r1 + q);
+  const float sa = (zero || !v0) ? 0.f : (neg ? -a : a);
+  const float sb = (zero || !v1) ? 0.f : (neg ? -b : b);
+  return make_float2(sa, sb);
 }
 
 // Shared-memory index with one padding element every 8 complex values: the radix-8 stores of
@@ -114,9 +118,11 @@ __device__ __forceinline__ int pad8(int x) { return x + (x >> 3); }
 
 // One Stockham stage of radix R on the F complex FFTs of length L held in buf (in place: all
 // items are loaded to registers, then the block synchronises, then results are stored).
-// Stage 0 reads the odd extension of the input rows straight from global memory.
+// Stage 0 (Ns = 1, all twiddles 1) reads the odd extension of the input rows straight from
+// global memory. The twiddles of a later stage are tws[(r - 1) Ns + k] = exp(-2 pi i r k /
+// (R Ns)), r = 1..R-1, k < Ns: the threads of a warp read consecutive k (no bank conflicts).
 template <int N, int R, int F, bool FIRST>
-__device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns, const float* src, int a0) {
+__device__ __forceinline__ void fft_stage(float2* buf, const float2* tws, int Ns, const float* src, int a0) {
   constexpr int L = 2 * N, LR = L / R, ITEMS = F * LR;
   constexpr int IPT = (ITEMS + kThreads - 1) / kThreads;
   constexpr int n = N - 1;
@@ -128,10 +134,10 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns
       const int f = it / LR, j = it - f * LR;
       if (FIRST) {
         const int ra = a0 + 2 * f, rb = ra + 1;
-        const float* r0 = (ra < n) ? src + (size_t)ra * n : nullptr;
-        const float* r1 = (rb < n) ? src + (size_t)rb * n : nullptr;
+        const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
+        const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = odd_ext<N>(r0, r1, j + r * LR);
+        for (int r = 0; r < R; ++r) v[q][r] = odd_ext<N>(r0, r1, ra < n, rb < n, j + r * LR);
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[q][r] = buf[pad8(f * L + j + r * LR)];
@@ -144,10 +150,11 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns
     const int it = threadIdx.x + q * kThreads;
     if (it < ITEMS) {
       const int f = it / LR, j = it - f * LR;
-      const int k = j & (Ns - 1);
-      const int step = k * (L / (R * Ns));
+      const int k = FIRST ? 0 : (j & (Ns - 1));
+      if (!FIRST) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], twd[r * step]);
+        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], tws[(r - 1) * Ns + k]);
+      }
       dft_small<R>(v[q]);
       const int o = f * L + (j - k) * R + k;
 #pragma unroll
@@ -158,6 +165,8 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* twd, int Ns
 }
 
 // Complex FFT of length L = 2N of F rows: radix-8 stages, then one radix-2 or radix-4 stage.
+// twd: the per-stage twiddle tables of the stages after the first, one after the other
+// (twiddle_table below).
 template <int N, int F>
 __device__ __forceinline__ void fft_rows(float2* buf, const float2* twd, const float* src, int a0) {
   constexpr int L = 2 * N;
@@ -165,14 +174,15 @@ __device__ __forceinline__ void fft_rows(float2* buf, const float2* twd, const f
   constexpr int n8 = lg / 3, rem = lg - 3 * n8;
   static_assert(n8 >= 1, "transform length too short");
   fft_stage<N, 8, F, true>(buf, twd, 1, src, a0);
-  int Ns = 8;
+  int Ns = 8, off = 0;
 #pragma unroll
   for (int s = 1; s < n8; ++s) {
-    fft_stage<N, 8, F, false>(buf, twd, Ns, nullptr, 0);
+    fft_stage<N, 8, F, false>(buf, twd + off, Ns, nullptr, 0);
+    off += 7 * Ns;
     Ns *= 8;
   }
-  if constexpr (rem == 1) fft_stage<N, 2, F, false>(buf, twd, Ns, nullptr, 0);
-  if constexpr (rem == 2) fft_stage<N, 4, F, false>(buf, twd, Ns, nullptr, 0);
+  if constexpr (rem == 1) fft_stage<N, 2, F, false>(buf, twd + off, Ns, nullptr, 0);
+  if constexpr (rem == 2) fft_stage<N, 4, F, false>(buf, twd + off, Ns, nullptr, 0);
 }
 
 // One transform pass: rows of `in` ([units][n][n]) -> orthonormal DST-I -> written transposed.
@@ -406,6 +416,30 @@ size_t correct_partials(int count) { return (size_t)count * 4 * kBlk; }
 
 // ---------------------------------------------------------------------------- Prop2D
 
+// Twiddles of the stages after the first of fft_rows<N> (radix 8 with Ns = 8, 64, ..., then the
+// radix-2 or radix-4 stage), stage after stage: entry (r - 1) Ns + k = exp(-2 pi i m / L) with
+// m = r k L / (R Ns), r = 1..R-1, k < Ns (host libm, rounded to FP32). At most L entries.
+static std::vector<float2> twiddle_table(int N) {
+  const int L = 2 * N;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int n8 = lg / 3, rem = lg - 3 * n8;
+  std::vector<float2> tw;
+  auto stage = [&](int R, int Ns) {
+    for (int r = 1; r < R; ++r)
+      for (int k = 0; k < Ns; ++k) {
+        const long long m = (long long)r * k * (L / (R * Ns));
+        tw.push_back(make_float2(float(std::cos(-2.0 * M_PI * m / L)), float(std::sin(-2.0 * M_PI * m / L))));
+      }
+  };
+  int Ns = 8;
+  for (int s = 1; s < n8; ++s, Ns *= 8) stage(8, Ns);
+  if (rem == 1) stage(2, Ns);
+  if (rem == 2) stage(4, Ns);
+  tw.resize(L, make_float2(0.f, 0.f));
+  return tw;
+}
+
 cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   if (!supported_n(p.n) || cap < 1) return cudaErrorInvalidValue;
   // CH_2D_STEP=persistent | host selects another execution of the same phases (default: graphs)
@@ -466,9 +500,7 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
     const double s = std::sin(q * M_PI / (2.0 * (p.n + 1)));
     mu[q - 1] = float(4.0 / (p.h * p.h) * s * s);
   }
-  const int L = 2 * (p.n + 1);
-  std::vector<float2> tw(L);
-  for (int m = 0; m < L; ++m) tw[m] = make_float2(float(std::cos(-2.0 * M_PI * m / L)), float(std::sin(-2.0 * M_PI * m / L)));
+  const std::vector<float2> tw = twiddle_table(p.n + 1);
   e = cudaMemcpyAsync(mu_, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
@@ -798,7 +830,9 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   const bool cok = c < n;
   const float mc = mu1[cok ? c : 0];
   const size_t ob = u * pts + c;
-  double acc = 0.0, acc2 = 0.0;
+  // per-thread partial sums / maxima in FP32 (GB300's FP64 pipe is 1/64 of FP32), combined across
+  // the block in FP64
+  float acc = 0.f, acc2 = 0.f;
   bool bad = false;
 #pragma unroll 1
   for (int j0 = 0; j0 < J; j0 += UB) {
@@ -833,8 +867,8 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
       } else if (EPI == E_W) {
         const float w = mdiag(mu1[k] + mc, fe2dt, fcwb) * ld[q] + v[q];
         a.qh[o] = w;
-        acc += (double)(w * ld[q]);
-        acc2 += (double)(ld2[q] * ld[q]);
+        acc = fmaf(w, ld[q], acc);
+        acc2 = fmaf(ld2[q], ld[q], acc2);
       } else if (EPI == E_INIT) {
         const float mu = mu1[k] + mc;
         const float r0 = v[q] / mu;
@@ -844,17 +878,17 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
       } else {  // E_UPDATE
         bad |= !isfinite(v[q]);
         a.Y[o] = yv[q] - (double)v[q];
-        acc = fmax(acc, (double)fabsf(v[q]));
+        acc = fmaxf(acc, fabsf(v[q]));
       }
     }
   }
   if (EPI == E_UPDATE) {
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
-    const double m = block_reduce<1>(acc, sh);
+    const double m = block_reduce<1>((double)acc, sh);
     if (threadIdx.x == 0) part[(size_t)u * nb + b] = m;
   } else if (EPI == E_W) {
-    const double wu = block_reduce<0>(acc, sh);
-    const double ru = block_reduce<0>(acc2, sh);
+    const double wu = block_reduce<0>((double)acc, sh);
+    const double ru = block_reduce<0>((double)acc2, sh);
     if (threadIdx.x == 0) {
       a.pdel[(size_t)u * nb + b] = wu;
       a.pgam[(size_t)u * nb + b] = ru;
@@ -1103,10 +1137,11 @@ __device__ __forceinline__ void cg_scalars(int it, double gam, double del, doubl
 
 // The vector updates of a CG iteration on rows [a0, a0 + kDstRows) of unit u:
 //   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^{-1} r.
-template <int N>
+// U: elements per thread whose loads are issued together.
+template <int N, int U>
 __device__ __forceinline__ void cg_update_rows(const PArgs& a, int u, int a0, int it, float fa, float fb, float cwb,
                                                float fe2dt) {
-  constexpr int n = N - 1, U = 8;  // elements per thread whose loads are issued together
+  constexpr int n = N - 1;
   const size_t pts = (size_t)n * n;
   float* __restrict__ xh = a.xh;
   float* __restrict__ rh = a.rh;
@@ -1118,7 +1153,7 @@ __device__ __forceinline__ void cg_update_rows(const PArgs& a, int u, int a0, in
   const size_t base = u * pts + (size_t)a0 * n;
   const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
   for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
-    float uv[U], wv[U], pv[U], sv[U], xv[U], rv[U], mv[U];
+    float uv[U], wv[U], pv[U], sv[U], xv[U], rv[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const int e = e0 + q * kThreads;
@@ -1129,14 +1164,13 @@ __device__ __forceinline__ void cg_update_rows(const PArgs& a, int u, int a0, in
         sv[q] = (it > 0) ? __ldcg(sh + base + e) : 0.f;
         xv[q] = __ldcg(xh + base + e);
         rv[q] = __ldcg(rh + base + e);
-        const int i = a0 + e / n;
-        mv[q] = mu1[i] + mu1[e - (e / n) * n];
       }
     }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const int e = e0 + q * kThreads;
       if (e < cnt) {
+        const float mv = mu1[a0 + e / n] + mu1[e - (e / n) * n];
         const float p = uv[q] + fb * pv[q];
         const float sq = wv[q] + fb * sv[q];
         const float r = rv[q] - fa * sq;
@@ -1144,7 +1178,7 @@ __device__ __forceinline__ void cg_update_rows(const PArgs& a, int u, int a0, in
         sh[base + e] = sq;
         xh[base + e] = xv[q] + fa * p;
         rh[base + e] = r;
-        uh[base + e] = r * __frcp_rn(mdiag(mv[q], fe2dt, cwb));
+        uh[base + e] = r * __frcp_rn(mdiag(mv, fe2dt, cwb));
       }
     }
   }
@@ -1177,7 +1211,8 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
       }
     }
     if (done) continue;
-    cg_update_rows<N>(a, u, a0, it, float(alpha), float(beta), a.fdt * float(unit_wbar<N>(a, u)), unit_fe2dt(a, u));
+    cg_update_rows<N, 4>(a, u, a0, it, float(alpha), float(beta), a.fdt * float(unit_wbar<N>(a, u)),
+                         unit_fe2dt(a, u));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.active[(it + 1) & 1] = 0;
@@ -1216,7 +1251,7 @@ __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
 
 template <int N, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
-  constexpr int n = N - 1, L = 2 * N;
+  constexpr int L = 2 * N;
   constexpr int FL = (kDstRows / 2) * L;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
@@ -1400,7 +1435,7 @@ __global__ void __launch_bounds__(kThreads, 2) k2_cluster(PArgs args) {
         // the next pass reads only the rows this block updates here
         noinl([&] {
           for (int item = its.first; item < its.end; item += its.step)
-            cg_update_rows<N>(a, u, (item - u * nb) * kDstRows, it, float(alpha), float(beta), cwb, fe2dt);
+            cg_update_rows<N, 8>(a, u, (item - u * nb) * kDstRows, it, float(alpha), float(beta), cwb, fe2dt);
         });
       }
       dst_items<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, nullptr, its, 0.0);  // correction to physical space

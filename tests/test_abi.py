@@ -75,6 +75,25 @@ def test_propagate_rejects_invalid_arguments_without_device():
     assert lib.ch_propagate(C.byref(cc), 1, 0, 1e-3, 1, None, C.c_void_p(8), None, None) == 1
 
 
+def test_theory_bound_rejects_invalid_arguments_without_device():
+    lib = ch.load()
+    cc = _cfg()
+    out = (C.c_double * 8)()
+    assert lib.ch_parareal_theory_bound(None, 0.0, 2, out, 8, None) == 1
+    assert lib.ch_parareal_theory_bound(C.byref(cc), 0.0, 2, None, 8, None) == 1
+    assert lib.ch_parareal_theory_bound(C.byref(cc), 0.0, -1, out, 8, None) == 1
+    assert lib.ch_parareal_theory_bound(C.byref(cc), 0.0, 6, out, 8, None) == 1  # needs kmax + 3
+    for field, value in (("n", 0), ("eps", 0.0), ("T", -1.0), ("n_slices", 0), ("fine_steps", 0),
+                         ("coarse_steps", 0), ("variant", 5), ("dim", 3)):
+        bad = _cfg()
+        setattr(bad, field, value)
+        assert lib.ch_parareal_theory_bound(C.byref(bad), 0.0, 2, out, 8, None) == 1, field
+    npa = _cfg()
+    npa.variant = 3  # NPA-I needs the LTE constant
+    assert lib.ch_parareal_theory_bound(C.byref(npa), 0.0, 2, out, 8, None) == 1
+    assert lib.ch_parareal_theory_bound(C.byref(npa), float("nan"), 2, out, 8, None) == 1
+
+
 def test_destroy_accepts_null_and_last_error_on_null():
     lib = ch.load()
     lib.ch_parareal_destroy(None)
