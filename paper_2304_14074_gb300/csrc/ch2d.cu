@@ -116,6 +116,18 @@ __device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const fl
 // banks (16-way conflicts at stride 8).
 __device__ __forceinline__ int pad8(int x) { return x + (x >> 3); }
 
+// Row stride (complex values) of the transform buffer: a padded row of L = 2N plus one value,
+// so that the eight row pairs an epilogue half-warp reads start in eight different banks (a
+// stride of 9L/8 complex values is a multiple of 32 words: all eight in one bank).
+template <int N>
+__host__ __device__ constexpr int buf_row() {
+  return 2 * N + (2 * N) / 8 + 1;
+}
+template <int N>
+__host__ __device__ constexpr int buf_elems() {
+  return (kDstRows / 2) * buf_row<N>();
+}
+
 // One Stockham stage of radix R on the F complex FFTs of length L held in buf (in place: all
 // items are loaded to registers, then the block synchronises, then results are stored).
 // Stage 0 (Ns = 1, all twiddles 1) reads the odd extension of the input rows straight from
@@ -140,7 +152,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tws, int Ns
         for (int r = 0; r < R; ++r) v[q][r] = odd_ext<N>(r0, r1, ra < n, rb < n, j + r * LR);
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q][r] = buf[pad8(f * L + j + r * LR)];
+        for (int r = 0; r < R; ++r) v[q][r] = buf[f * buf_row<N>() + pad8(j + r * LR)];
       }
     }
   }
@@ -156,9 +168,9 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tws, int Ns
         for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], tws[(r - 1) * Ns + k]);
       }
       dft_small<R>(v[q]);
-      const int o = f * L + (j - k) * R + k;
+      const int o = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad8(o + r * Ns)] = v[q][r];
+      for (int r = 0; r < R; ++r) buf[f * buf_row<N>() + pad8(o + r * Ns)] = v[q][r];
     }
   }
   __syncthreads();
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__
   constexpr int n = N - 1, L = 2 * N, F = kDstRows / 2;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
-  float2* twd = smem2 + F * L + F * L / 8;
+  float2* twd = smem2 + buf_elems<N>();
   const int u = blockIdx.y;
   const int a0 = blockIdx.x * kDstRows;
   const float* src = in + (size_t)u * n * n;
@@ -206,15 +218,14 @@ __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__
     const int k = idx / kDstRows, r = idx - k * kDstRows;
     const int a = a0 + r;
     if (a >= n) continue;
-    const float2 v = buf[pad8((r >> 1) * L + k + 1)];
+    const float2 v = buf[(r >> 1) * buf_row<N>() + pad8(k + 1)];
     dst[(size_t)k * n + a] = (r & 1) ? v.x * sc : -v.y * sc;
   }
 }
 
 template <int N>
 size_t dst_smem() {
-  constexpr int FL = (kDstRows / 2) * 2 * N;
-  return (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2);
+  return (size_t)(buf_elems<N>() + 2 * N) * sizeof(float2);
 }
 
 // ------------------------------------------------------------------ FP64 stencils
@@ -247,8 +258,10 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
   return r;
 }
 
-// m(p,q) = 1/mu + e2dt mu + cdt wbar (diagonal of the preconditioner M in sine space)
-__device__ __forceinline__ float mdiag(float mu, float e2dt, float cwb) { return 1.f / mu + e2dt * mu + cwb; }
+// m(p,q) = 1/mu + e2dt mu + cdt wbar (diagonal of the preconditioner M in sine space). 1/mu by
+// the correctly rounded reciprocal: the same value as the IEEE quotient 1.f / mu, without the
+// division routine's slow-path call inside the epilogue loops.
+__device__ __forceinline__ float mdiag(float mu, float e2dt, float cwb) { return __frcp_rn(mu) + e2dt * mu + cwb; }
 
 // Start of a loop: counter = 0 and, for a nested loop, its condition = 1.
 __global__ void k2_loop_start(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, int which, int set_cond) {
@@ -690,7 +703,7 @@ struct PArgs {
   double* pd;     // [units][nb]     max |d|
   int* flag;      // [units][2]: Newton done, CG done
   int* cnt;       // [units] Newton iterations of the step
-  double* scal;   // [units][8]: [6] previous max |d|
+  double* scal;   // [units][8]: [4] wbar of the Newton iteration, [6] previous max |d|
   unsigned* status;
   unsigned long long* totals;  // [0] batched CG iterations, [1] batched Newton passes
   int* active;    // [0..1] CG, [2..3] Newton: units still iterating (parity slots)
@@ -753,34 +766,64 @@ __device__ __forceinline__ Items grid_items(const PArgs& a) {
   return Items{(int)blockIdx.x, (int)gridDim.x, a.units * nb, 1};
 }
 
-// Partial sums and ranges are read with L2-coherent loads: in the persistent and cluster
-// executions they were written by other blocks of the same kernel.
+// Per-unit scalars from the nb per-item partials. Partials are read with L2-coherent loads (in
+// the persistent and cluster executions other blocks of the same kernel wrote them). The block
+// versions are formed by the first warp (lane b holds partial b, a fixed shuffle tree) and handed
+// to every thread through shared memory: the same reduction in all threads would queue the whole
+// block on GB300's narrow FP64 pipe. They synchronise the block: call them from block-uniform
+// code only.
 template <int N>
 __device__ __forceinline__ double unit_wbar(const PArgs& a, int u) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
-  double lo = 1e300, hi = -1e300;
-  for (int b = 0; b < nb; ++b) {
-    lo = fmin(lo, __ldcg(a.pmin + (size_t)u * nb + b));
-    hi = fmax(hi, __ldcg(a.pmax + (size_t)u * nb + b));
+  static_assert(nb <= 32, "one partial per lane");
+  __shared__ double res;
+  __syncthreads();  // earlier readers of res are done
+  if (threadIdx.x < 32) {
+    double lo = 1e300, hi = -1e300;
+    if (threadIdx.x < nb) {
+      lo = __ldcg(a.pmin + (size_t)u * nb + threadIdx.x);
+      hi = __ldcg(a.pmax + (size_t)u * nb + threadIdx.x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (threadIdx.x == 0) res = 0.5 * (lo + hi);
   }
-  return 0.5 * (lo + hi);
+  __syncthreads();
+  return res;
 }
 
-template <int N>
-__device__ __forceinline__ double unit_sum(const double* p, int u) {
+// OP 0: sum of the partials; 1: their maximum (and 0).
+template <int N, int OP>
+__device__ __forceinline__ double unit_reduce(const double* p, int u) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += __ldcg(p + (size_t)u * nb + b);
-  return s;
+  static_assert(nb <= 32, "one partial per lane");
+  __shared__ double res;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < nb) ? __ldcg(p + (size_t)u * nb + threadIdx.x) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = (OP == 0) ? v + w : fmax(v, w);
+    }
+    if (threadIdx.x == 0) res = v;
+  }
+  __syncthreads();
+  return res;
 }
 
+// Maximum of the partials (and 0) in the calling thread alone.
 template <int N>
-__device__ __forceinline__ double unit_max(const double* p, int u) {
+__device__ __forceinline__ double unit_max_thread(const double* p, int u) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
   double m = 0.0;
   for (int b = 0; b < nb; ++b) m = fmax(m, __ldcg(p + (size_t)u * nb + b));
   return m;
 }
+
 
 // Calls f as a separate function: the persistent kernel's register allocation is then that of
 // its largest phase, not of all phases inlined together.
@@ -807,7 +850,7 @@ enum Epi { E_PLAIN = 0, E_WPROD, E_W, E_INIT, E_UPDATE };
 template <int N, int EPI>
 __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const float2* twd, const float* in, float* out,
                                          int act, double* part, int item, double wb = 0.0) {
-  constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
   static_assert(kThreads % kDstRows == 0, "epilogue thread layout");
   constexpr int KS = kThreads / kDstRows;  // output rows apart of one thread's elements
   constexpr int J = (n + KS - 1) / KS;     // epilogue elements per thread
@@ -821,7 +864,14 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   if (act >= 0 && (a.flag[2 * u] || (act == 1 && a.flag[2 * u + 1]))) return;  // block-uniform
   fft_rows<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
   float cwb = 0.f;
-  if (EPI == E_WPROD || EPI == E_W || EPI == E_INIT) cwb = float(act >= 0 ? unit_wbar<N>(a, u) : wb);
+  // wbar: formed from the range partials in the CG-start pass, which keeps it for the CG passes
+  if (act >= 0 && EPI == E_INIT) {
+    wb = unit_wbar<N>(a, u);
+    if (b == 0 && threadIdx.x == 0) a.scal[u * 8 + 4] = wb;
+  } else if (act >= 0 && (EPI == E_WPROD || EPI == E_W)) {
+    wb = __ldcg(a.scal + u * 8 + 4);
+  }
+  if (EPI == E_WPROD || EPI == E_W || EPI == E_INIT) cwb = float(wb);
   const float fcwb = a.fdt * cwb;
   const float fe2dt = unit_fe2dt(a, u);
   // This thread's outputs: column c = a0 + r of the rows k = k0, k0 + KS, ... (row pair
@@ -851,7 +901,7 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
           ld2[q] = __ldcg(a.rh + o);
         }
         if (EPI == E_UPDATE) yv[q] = __ldcg(a.Y + o);
-        const float2 cv = buf[pad8((r >> 1) * L + k + 1)];
+        const float2 cv = buf[(r >> 1) * buf_row<N>() + pad8(k + 1)];
         v[q] = (r & 1) ? cv.x * sc : -cv.y * sc;
       }
     }
@@ -887,9 +937,24 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
     const double m = block_reduce<1>((double)acc, sh);
     if (threadIdx.x == 0) part[(size_t)u * nb + b] = m;
   } else if (EPI == E_W) {
-    const double wu = block_reduce<0>((double)acc, sh);
-    const double ru = block_reduce<0>((double)acc2, sh);
+    // FP32 shuffle tree within each warp, the warps' sums added in FP64 in a fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+    }
+    __shared__ float ws[2][kThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+      ws[0][threadIdx.x >> 5] = acc;
+      ws[1][threadIdx.x >> 5] = acc2;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      double wu = 0.0, ru = 0.0;
+      for (int i = 0; i < kThreads / 32; ++i) {
+        wu += (double)ws[0][i];
+        ru += (double)ws[1][i];
+      }
       a.pdel[(size_t)u * nb + b] = wu;
       a.pgam[(size_t)u * nb + b] = ru;
     }
@@ -1185,34 +1250,70 @@ __device__ __forceinline__ void cg_update_rows(const PArgs& a, int u, int a0, in
 }
 
 // The CG update of iteration `it` over the batch; a unit whose gamma has fallen to
-// cg_tol^2 gamma_0 is done (its x is kept).
+// cg_tol^2 gamma_0 is done (its x is kept). The first warp loads the unit's flags, partials,
+// wbar and CG history in one round trip, sums the partials with the tree of unit_reduce, and
+// thread 0 forms the scalars for the block.
 template <int N>
 __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
   constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
+  static_assert(nb <= 32, "one partial per lane");
   const int cur = (it & 1) * 2, prev = ((it + 1) & 1) * 2;
+  __shared__ float sab[3];
+  __shared__ int sact;
   for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
     const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
-    if (a.flag[2 * u] || a.flag[2 * u + 1]) continue;
-    const double gam = unit_sum<N>(a.pgam, u), del = unit_sum<N>(a.pdel, u);
-    const double gam0 = (it == 0) ? gam : __ldcg(a.cgs + u * 8 + 4);
-    const bool done = !(gam > a.cg_tol2 * gam0);  // also catches NaN
-    double beta, alpha;
-    cg_scalars(it, gam, del, (it > 0) ? __ldcg(a.cgs + u * 8 + prev + 1) : 0.0,
-               (it > 0) ? __ldcg(a.cgs + u * 8 + prev) : 0.0, alpha, beta);
-    if (b == 0 && threadIdx.x == 0) {
-      atomicAdd(a.totals + 2, 1ull);
-      if (done) {
-        a.flag[2 * u + 1] = 1;
-      } else {
-        atomicAdd(a.active + (it & 1), 1);
-        a.cgs[u * 8 + cur] = alpha;
-        a.cgs[u * 8 + cur + 1] = gam;
-        if (it == 0) a.cgs[u * 8 + 4] = gam;  // gamma_0 (read only for it > 0)
+    __syncthreads();  // the previous item's readers of sab / sact are done
+    if (threadIdx.x < 32) {
+      const int l = threadIdx.x;
+      double g = (l < nb) ? __ldcg(a.pgam + (size_t)u * nb + l) : 0.0;
+      double d = (l < nb) ? __ldcg(a.pdel + (size_t)u * nb + l) : 0.0;
+      int f0 = 0, f1 = 0;
+      double wbv = 0.0, g0 = 0.0, gp = 0.0, ap = 0.0;
+      if (l == 0) {
+        // the CG-done flag of u may be set during this phase by the block of u's first item
+        f0 = __ldcg(a.flag + 2 * u);
+        f1 = __ldcg(a.flag + 2 * u + 1);
+        wbv = __ldcg(a.scal + u * 8 + 4);
+        if (it > 0) {
+          g0 = __ldcg(a.cgs + u * 8 + 4);
+          gp = __ldcg(a.cgs + u * 8 + prev + 1);
+          ap = __ldcg(a.cgs + u * 8 + prev);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+      }
+      if (l == 0) {
+        int act = !(f0 || f1);
+        double alpha = 0.0, beta = 0.0;
+        if (act) {
+          const double gam0 = (it == 0) ? g : g0;
+          const bool done = !(g > a.cg_tol2 * gam0);  // also catches NaN
+          cg_scalars(it, g, d, gp, ap, alpha, beta);
+          if (b == 0) {
+            atomicAdd(a.totals + 2, 1ull);
+            if (done) {
+              a.flag[2 * u + 1] = 1;
+            } else {
+              atomicAdd(a.active + (it & 1), 1);
+              a.cgs[u * 8 + cur] = alpha;
+              a.cgs[u * 8 + cur + 1] = g;
+              if (it == 0) a.cgs[u * 8 + 4] = g;  // gamma_0 (read only for it > 0)
+            }
+          }
+          act = !done;
+        }
+        sab[0] = float(alpha);
+        sab[1] = float(beta);
+        sab[2] = a.fdt * float(wbv);
+        sact = act;
       }
     }
-    if (done) continue;
-    cg_update_rows<N, 4>(a, u, a0, it, float(alpha), float(beta), a.fdt * float(unit_wbar<N>(a, u)),
-                         unit_fe2dt(a, u));
+    __syncthreads();
+    if (!sact) continue;
+    cg_update_rows<N, 4>(a, u, a0, it, sab[0], sab[1], sab[2], unit_fe2dt(a, u));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.active[(it + 1) & 1] = 0;
@@ -1226,7 +1327,7 @@ __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
   const int last = (it_n >= a.newton_max - 1);
   for (int u = blockIdx.x * kThreads + threadIdx.x; u < a.units; u += gridDim.x * kThreads) {
     if (a.flag[2 * u]) continue;
-    const double dm = unit_max<N>(a.pd, u);
+    const double dm = unit_max_thread<N>(a.pd, u);
     const int mm = ++a.cnt[u];
     const double prev = a.scal[u * 8 + 6];
     bool done = dm <= a.tol || (mm >= 2 && dm <= a.floor_ && dm > 0.5 * prev);
@@ -1252,10 +1353,9 @@ __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
 template <int N, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
   constexpr int L = 2 * N;
-  constexpr int FL = (kDstRows / 2) * L;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
-  float2* twd = smem2 + FL + FL / 8;
+  float2* twd = smem2 + buf_elems<N>();
   __shared__ PArgs a;
   if (threadIdx.x == 0) a = args;
   for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = args.tw[m];
@@ -1307,8 +1407,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
 
 template <int N, int MINB>
 cudaError_t launch_persist(const PArgs& a, int* grid_out, cudaStream_t st) {
-  constexpr int FL = (kDstRows / 2) * 2 * N;
-  const size_t smem = (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2);
+  const size_t smem = (size_t)(buf_elems<N>() + 2 * N) * sizeof(float2);
   cudaError_t e = prep(k2_persist<N, MINB>, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -1381,10 +1480,9 @@ __device__ __forceinline__ void dst_items(const PArgs& a, float2* buf, const flo
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2) k2_cluster(PArgs args) {
   constexpr int n = N - 1, L = 2 * N, nb = (n + kDstRows - 1) / kDstRows;
-  constexpr int FL = (kDstRows / 2) * L;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
-  float2* twd = smem2 + FL + FL / 8;
+  float2* twd = smem2 + buf_elems<N>();
   __shared__ PArgs a;
   if (threadIdx.x == 0) a = args;
   for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = args.tw[m];
@@ -1424,12 +1522,19 @@ __global__ void __launch_bounds__(kThreads, 2) k2_cluster(PArgs args) {
         cluster_sync();
         dst_items<N, E_W>(a, buf, twd, a.tmp, nullptr, nullptr, its, wb);  // w = S u, (w,u), (r,u)
         cluster_sync();
-        const double gam = unit_sum<N>(a.pgam, u), del = unit_sum<N>(a.pdel, u);
+        const double gam = unit_reduce<N, 0>(a.pgam, u), del = unit_reduce<N, 0>(a.pdel, u);
         if (it == 0) gam0 = gam;
         ++cg_iters;
         if (!(gam > a.cg_tol2 * gam0)) break;  // also catches NaN
-        double alpha, beta;
-        cg_scalars(it, gam, del, gp, ap, alpha, beta);
+        __shared__ double sab[2];
+        if (threadIdx.x == 0) {
+          double al, be;
+          cg_scalars(it, gam, del, gp, ap, al, be);
+          sab[0] = al;
+          sab[1] = be;
+        }
+        __syncthreads();
+        const double alpha = sab[0], beta = sab[1];
         gp = gam;
         ap = alpha;
         // the next pass reads only the rows this block updates here
@@ -1442,7 +1547,7 @@ __global__ void __launch_bounds__(kThreads, 2) k2_cluster(PArgs args) {
       cluster_sync();
       dst_items<N, E_UPDATE>(a, buf, twd, a.tmp, nullptr, a.pd, its, 0.0);  // Y -= d, max |d|
       cluster_sync();
-      const double dm = unit_max<N>(a.pd, u);
+      const double dm = unit_reduce<N, 1>(a.pd, u);
       ++m;
       bool done = dm <= a.tol || (m >= 2 && dm <= a.floor_ && dm > 0.5 * prev_dm);
       prev_dm = dm;
@@ -1670,10 +1775,10 @@ __host__ __device__ constexpr bool is_dst_phase(int ph) {
 // transforms of n = 511, whose butterflies need the registers.
 template <int N, int PH>
 __global__ void __launch_bounds__(kThreads, (N >= 512 ? 2 : 4)) k2_phase(PArgs a, int have_prev) {
-  constexpr int L = 2 * N, FL = (kDstRows / 2) * L, nb = (N - 1 + kDstRows - 1) / kDstRows;
+  constexpr int L = 2 * N, nb = (N - 1 + kDstRows - 1) / kDstRows;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
-  float2* twd = smem2 + FL + FL / 8;
+  float2* twd = smem2 + buf_elems<N>();
   if constexpr (is_dst_phase(PH)) {
     for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = a.tw[m];
     __syncthreads();
@@ -1714,16 +1819,14 @@ __global__ void k2_cond(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, c
 template <int N, int PH>
 cudaError_t phase_launch(const PArgs& a, int have_prev, cudaStream_t st) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
-  constexpr int FL = (kDstRows / 2) * 2 * N;
-  const size_t smem = is_dst_phase(PH) ? (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2) : 0;
+  const size_t smem = is_dst_phase(PH) ? (size_t)(buf_elems<N>() + 2 * N) * sizeof(float2) : 0;
   k2_phase<N, PH><<<a.units * nb, kThreads, smem, st>>>(a, have_prev);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t phase_prepare() {
-  constexpr int FL = (kDstRows / 2) * 2 * N;
-  const size_t smem = (size_t)(FL + FL / 8 + 2 * N) * sizeof(float2);
+  const size_t smem = (size_t)(buf_elems<N>() + 2 * N) * sizeof(float2);
   cudaError_t e = prep(k2_phase<N, PH_H1>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_H2>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_P1>, smem);
