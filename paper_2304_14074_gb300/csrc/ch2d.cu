@@ -696,7 +696,8 @@ struct PArgs {
   double* pmax;   //                 max wc
   double* pdel;   //                 (w, u)
   double* cgs;    // [units][8]      CG scalars: alpha, gamma of the last iteration (parity
-                  //                 slots 0, 1 and 2, 3), gamma_0 (slot 4)
+                  //                 slots 0, 1 and 2, 3), gamma_0 (slot 4), beta (parity
+                  //                 slots 5, 6)
   float* uh;      // u = M^{-1} r (sine space)
   float* sh;      // s = S p (sine space)
   double* pgam;   // [units][nb]     (r, u)
@@ -1120,7 +1121,7 @@ __device__ __forceinline__ void ph_z(const PArgs& a, Items its) {
 template <int N>
 __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
   constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
-  __shared__ double sh[kThreads / 32];
+  __shared__ float sh[2][kThreads / 32];
   const size_t pts = (size_t)n * n;
   const double* __restrict__ Y = a.Y;
   const double* __restrict__ yhat = a.yhat;
@@ -1133,7 +1134,8 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
     const double* __restrict__ zu = a.z + u * pts;
     const size_t base = u * pts + (size_t)a0 * n;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
-    double lo = 1e300, hi = -1e300;
+    // range of the FP32 weights: exact in FP32 (min and max round nothing)
+    float lo = INFINITY, hi = -INFINITY;
     for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
       double lz[U], yv[U], hv[U], w64[U];
 #pragma unroll
@@ -1165,16 +1167,29 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
             wq = float(a.wconst);
           }
           w[base + e] = wq;
-          lo = fmin(lo, (double)wq);
-          hi = fmax(hi, (double)wq);
+          lo = fminf(lo, wq);
+          hi = fmaxf(hi, wq);
         }
       }
     }
-    const double bl = block_reduce<2>(lo, sh);
-    const double bh = block_reduce<1>(hi, sh);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __syncthreads();  // the previous item's readers of sh are done
+    if ((threadIdx.x & 31) == 0) {
+      sh[0][threadIdx.x >> 5] = lo;
+      sh[1][threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      a.pmin[(size_t)u * nb + b] = bl;
-      a.pmax[(size_t)u * nb + b] = bh;
+      for (int i = 1; i < kThreads / 32; ++i) {
+        lo = fminf(lo, sh[0][i]);
+        hi = fmaxf(hi, sh[1][i]);
+      }
+      a.pmin[(size_t)u * nb + b] = (double)lo;
+      a.pmax[(size_t)u * nb + b] = (double)hi;
     }
   }
 }
@@ -1319,6 +1334,72 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
     a.active[(it + 1) & 1] = 0;
     atomicAdd(a.totals, 1ull);
   }
+}
+
+// The CG scalars of iteration `it` for every unit still in both loops, in one block (the graph
+// execution's loop condition): gamma and delta from the unit's item partials (one warp per
+// unit, the shuffle tree of unit_reduce), the stop test (a unit whose gamma has fallen to
+// cg_tol^2 gamma_0 is done: flag set, x kept), and alpha, beta into cgs. Returns, in every
+// thread, the number of units that go on.
+template <int N>
+__device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  static_assert(nb <= 32, "one partial per lane");
+  const int cur = (it & 1) * 2, prev = ((it + 1) & 1) * 2;
+  __shared__ int going;
+  __shared__ unsigned long long evaluated;
+  if (threadIdx.x == 0) {
+    going = 0;
+    evaluated = 0ull;
+  }
+  __syncthreads();
+  const int l = threadIdx.x & 31;
+  for (int u = threadIdx.x >> 5; u < a.units; u += blockDim.x >> 5) {
+    if (__ldcg(a.flag + 2 * u) || __ldcg(a.flag + 2 * u + 1)) continue;  // warp-uniform
+    double g = (l < nb) ? __ldcg(a.pgam + (size_t)u * nb + l) : 0.0;
+    double d = (l < nb) ? __ldcg(a.pdel + (size_t)u * nb + l) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      g += __shfl_xor_sync(0xffffffffu, g, o);
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if (l == 0) {
+      double* cg = a.cgs + u * 8;
+      const double gam0 = (it == 0) ? g : cg[4];
+      double alpha, beta;
+      cg_scalars(it, g, d, (it > 0) ? cg[prev + 1] : 0.0, (it > 0) ? cg[prev] : 0.0, alpha, beta);
+      atomicAdd(&evaluated, 1ull);
+      if (!(g > a.cg_tol2 * gam0)) {  // also catches NaN
+        a.flag[2 * u + 1] = 1;
+      } else {
+        cg[cur] = alpha;
+        cg[cur + 1] = g;
+        cg[5 + (it & 1)] = beta;
+        if (it == 0) cg[4] = g;
+        atomicAdd(&going, 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(a.totals + 2, evaluated);
+    atomicAdd(a.totals, 1ull);
+  }
+  return going;
+}
+
+// The vector updates of CG iteration j, with the scalars cg_scalars_all stored, on the rows of
+// `item`, if its unit is still in both loops; the block's writes are visible to the block
+// afterwards (the transform that follows reads them).
+template <int N>
+__device__ __forceinline__ void cg_update_item(const PArgs& a, int item, int j) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  const int u = item / nb, a0 = (item - u * nb) * kDstRows;
+  if (a.flag[2 * u] || a.flag[2 * u + 1]) return;  // block-uniform: not written during the phase
+  const double* cg = a.cgs + u * 8;
+  const float alpha = float(__ldcg(cg + (j & 1) * 2)), beta = float(__ldcg(cg + 5 + (j & 1)));
+  cg_update_rows<N, 4>(a, u, a0, j, alpha, beta, a.fdt * float(__ldcg(a.scal + u * 8 + 4)), unit_fe2dt(a, u));
+  __syncthreads();
 }
 
 // N7: Newton stop test per unit (tolerance, or the FP64 floor rule)
@@ -1761,14 +1842,16 @@ cudaError_t Prop2D::propagate_cluster(double* Y, int units, int scheme, double d
 // (ctr[0] Newton, ctr[1] CG), advanced by the condition kernels.
 namespace {
 
+// PH_P1U: the CG update of the previous iteration on the item's rows, then P1 on them;
+// PH_X1U: the update of the last iteration for units that left the CG loop at cg_max, then X1.
 enum Phase {
   PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_UPDATE,
-  PH_X1, PH_X2, PH_NEWTON_END
+  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U
 };
 
 __host__ __device__ constexpr bool is_dst_phase(int ph) {
   return ph == PH_H1 || ph == PH_H2 || ph == PH_P1 || ph == PH_P2 || ph == PH_P3 || ph == PH_P4 || ph == PH_X1 ||
-         ph == PH_X2;
+         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U;
 }
 
 // Four blocks per SM (a batch's items all resident at n = 255), two for the length-1024
@@ -1800,12 +1883,40 @@ __global__ void __launch_bounds__(kThreads, (N >= 512 ? 2 : 4)) k2_phase(PArgs a
   if constexpr (PH == PH_P4) dst_item<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_UPDATE) ph_cg_update<N>(a, it);
   if constexpr (PH == PH_X1) dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P1U) {
+    if (it > 0) cg_update_item<N>(a, blockIdx.x, it - 1);
+    dst_item<N, E_PLAIN>(a, buf, twd, a.uh, a.tmp, 1, nullptr, blockIdx.x);
+  }
+  if constexpr (PH == PH_X1U) {
+    if (it > 0) cg_update_item<N>(a, blockIdx.x, it - 1);  // it = CG iterations run
+    dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
+  }
   if constexpr (PH == PH_X2) dst_item<N, E_UPDATE>(a, buf, twd, a.tmp, nullptr, 0, a.pd, blockIdx.x);
   if constexpr (PH == PH_NEWTON_END) ph_newton_end<N>(a, a.ctr[0]);
 }
 
 // End of a loop iteration: continue while units remain active and the cap is not reached.
 // which = 0: Newton (active slots 2, 3), 1: CG (slots 0, 1).
+// End of a CG iteration of the graph execution: the scalars of every unit (cg_scalars_all), then
+// continue while units go on and the cap is not reached.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k2_cg_cond(PArgs a, cudaGraphConditionalHandle hnd, int lim) {
+  const int it = a.ctr[1];
+  const int going = cg_scalars_all<N>(a, it);
+  if (threadIdx.x == 0) {
+    a.ctr[1] = it + 1;
+    cudaGraphSetConditional(hnd, (going > 0 && it + 1 < lim) ? 1u : 0u);
+  }
+}
+
+// The same for the host-driven execution: the count goes to active[it & 1] for the host.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k2_cg_host(PArgs a) {
+  const int it = a.ctr[1];
+  const int going = cg_scalars_all<N>(a, it);
+  if (threadIdx.x == 0) a.active[it & 1] = going;
+}
+
 __global__ void k2_cond(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, const int* __restrict__ active,
                         int which, int lim) {
   if (threadIdx.x == 0) {
@@ -1835,6 +1946,8 @@ cudaError_t phase_prepare() {
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_P4>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X1>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X2>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_P1U>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_X1U>, smem);
   return e;
 }
 
@@ -1879,13 +1992,12 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   if (e == cudaSuccess) e = add_while(bs, &hC, 0, 0, &bodyC);
   // ---- CG body
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs2, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) e = phase_launch<N, PH_P1>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P1U>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_UPDATE>(a, have_prev, bs2);
   if (e == cudaSuccess) {
-    k2_cond<<<1, 32, 0, bs2>>>(hC, ctr, active, 1, cg_max);
+    k2_cg_cond<N><<<1, kThreads, 0, bs2>>>(a, hC, cg_max);
     e = cudaGetLastError();
   }
   {
@@ -1893,8 +2005,8 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
     const cudaError_t e2 = cudaStreamEndCapture(bs2, &dummy);
     if (e == cudaSuccess) e = e2;
   }
-  // ---- back in the Newton body: correction to physical space, update, stop test
-  if (e == cudaSuccess) e = phase_launch<N, PH_X1>(a, have_prev, bs);
+  // ---- back in the Newton body: last CG update, correction to physical space, update, stop test
+  if (e == cudaSuccess) e = phase_launch<N, PH_X1U>(a, have_prev, bs);
   if (e == cudaSuccess) e = phase_launch<N, PH_X2>(a, have_prev, bs);
   if (e == cudaSuccess) e = phase_launch<N, PH_NEWTON_END>(a, have_prev, bs);
   if (e == cudaSuccess) {
@@ -1962,19 +2074,24 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
     CH_TRY((phase_launch<N, PH_RESID>(a, have_prev, st)));
     CH_TRY((phase_launch<N, PH_H1>(a, have_prev, st)));
     CH_TRY((phase_launch<N, PH_H2>(a, have_prev, st)));
+    int ran = 0;
     for (int it = 0; it < cg_max; ++it) {
       hc[1] = it;
       CH_TRY(cudaMemcpyAsync(ctr, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
-      CH_TRY((phase_launch<N, PH_P1>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_P1U>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
-      CH_TRY((phase_launch<N, PH_UPDATE>(a, have_prev, st)));
+      k2_cg_host<N><<<1, kThreads, 0, st>>>(a);
+      CH_TRY(cudaGetLastError());
       CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CH_TRY(cudaStreamSynchronize(st));
+      ++ran;
       if (act[it & 1] == 0) break;
     }
-    CH_TRY((phase_launch<N, PH_X1>(a, have_prev, st)));
+    hc[1] = ran;  // CG iterations run: the last one's update is applied with the correction pass
+    CH_TRY(cudaMemcpyAsync(ctr, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    CH_TRY((phase_launch<N, PH_X1U>(a, have_prev, st)));
     CH_TRY((phase_launch<N, PH_X2>(a, have_prev, st)));
     CH_TRY((phase_launch<N, PH_NEWTON_END>(a, have_prev, st)));
     CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));

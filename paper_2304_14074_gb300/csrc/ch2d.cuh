@@ -13,7 +13,7 @@ enum Scheme { SCHEME_LIN1 = 0, SCHEME_NL = 1, SCHEME_LIN2 = 2 };
 enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u, ST_TIMEOUT = 8u };
 
 // How a batch of implicit steps is executed: one CUDA graph per step (each phase a kernel; the
-// Newton and CG loops conditional WHILE nodes, 7 kernels per CG iteration), or one persistent
+// Newton and CG loops conditional WHILE nodes, 5 kernels per CG iteration), or one persistent
 // cooperative kernel per propagate call (the same phases separated by grid barriers), or plain
 // launches with the loops driven from the host (for profiling single kernels), or one
 // thread-block cluster per unit running that unit's whole propagation in one launch.
@@ -71,14 +71,16 @@ class Prop2D {
   // batched CG iteration kCgKernels.
   long long kernel_launches() const {
     if (path_ == PATH_PERSISTENT || path_ == PATH_CLUSTER) return step_kernels_;
-    if (path_ == PATH_HOST) return step_kernels_ + (kNewtonKernels - 2) * newton_passes_ + (kCgKernels - 1) * cg_total_;
+    if (path_ == PATH_HOST) return step_kernels_ + (kNewtonKernels - 2) * newton_passes_ + kCgKernels * cg_total_;
     return step_kernels_ + kNewtonKernels * newton_passes_ + kCgKernels * cg_total_;
   }
   static constexpr int kStepKernelsNL = 3;   // prologue, predictor, loop start
   static constexpr int kStepKernelsLin = 3;
   static constexpr int kNewtonKernels = 9;   // z, residual, 2 transform passes (the second starts CG),
-                                             // CG loop start, 2 passes (update), stop test, condition
-  static constexpr int kCgKernels = 6;       // 4 transform passes, update, condition
+                                             // CG loop start, 2 passes (last CG update, Newton
+                                             // update), stop test, condition
+  static constexpr int kCgKernels = 5;       // 4 transform passes (the first applies the previous
+                                             // iteration's update), scalars and condition
   // Zeroes the device status bits and the Newton / CG counters (enqueued on st).
   cudaError_t reset_counters(cudaStream_t st);
   size_t bytes() const { return bytes_; }
