@@ -63,6 +63,9 @@ COARSE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin1", "NPA-I": "lin1",
 # residual H(Y) = Y - Yhat + D_h(eps^2 dt D_h Y - dt Y^3) and the update Y -= dY.
 FP64_FLOPS_RHS = 5
 FP64_FLOPS_NEWTON = 15
+# A step of a linear scheme (Eq. 2.4 / 2.5) in FP64: the right-hand side and the assembly of the
+# pentadiagonal rows (about 20 flops per point) and its banded LU solve (about 25).
+FP64_FLOPS_LINEAR_STEP = 45
 # GB300 FP64: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) of one 1D fine-sweep launch at c2's batch and slices, from the ncu
@@ -71,7 +74,8 @@ FINE_SWEEP_1D_TRAFFIC = 223.7e6
 
 
 # 2D fine sweep, algorithmic DRAM/L2 bytes per grid point and unit, each array read or written
-# once per phase. CG iteration (5 phases): u to physical space (read u, write t: 8), times
+# once per phase (the executions fuse some phases; the count is the algorithm's, not a kernel's).
+# CG iteration (5 phases): u to physical space (read u, write t: 8), times
 # dt (wc - wbar) (read t, wc, write t2: 12), back to sine space (8), w = M u + That with (w, u)
 # and (r, u) (read t, u, r, write w: 16), update of p, s, x, r, u (read u, w, p, s, x, r, write
 # p, s, x, r, u: 44). Newton iteration: z = c1 lap Y - dt g (read Y, write z FP64: 16), H and
@@ -270,7 +274,10 @@ def bench_ours(args, w, rank, world, local_rank):
     fine_ms_per_launch = fine_ms / args.steps
     newton_per_step = newton_total  # Newton iterations (summed over problems) in one step
     if dim == 1:
-        alg_flops = fine_pts_per_step * FP64_FLOPS_RHS + newton_per_step * n * FP64_FLOPS_NEWTON
+        if FINE_OF[w["variant"]] == "nl":
+            alg_flops = fine_pts_per_step * FP64_FLOPS_RHS + newton_per_step * n * FP64_FLOPS_NEWTON
+        else:
+            alg_flops = fine_pts_per_step * FP64_FLOPS_LINEAR_STEP
         achieved = alg_flops / (fine_ms_per_launch / 1e3) / 1e9
         roofline = {"bound": "alu", "kernel": "k_fine_sweep (FP64 pipe)", "achieved": round(achieved, 2),
                     "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
@@ -320,6 +327,10 @@ def bench_ours(args, w, rank, world, local_rank):
     ttol = None
     if w.get("ttol") and not args.no_ttol and rank == 0:
         ttol = time_to_tolerance(ch, w, u0, stream)
+        if w["variant"].startswith("PA"):
+            ttol["theory_bound"] = theory_vs_measured(ch, w, u0, stream, ttol.pop("err_ratio"))
+        else:
+            ttol.pop("err_ratio")
     if not args.no_learned and rank == 0:
         ttol = dict(ttol or {})
         ttol["learned_vs_plain_G"] = learned_vs_plain(ch, stream)
@@ -356,10 +367,33 @@ def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
     iters = max(s["iterations"] for s in stats)
     t_ms = stats[0]["t_iter_ms"][iters]
     worst = max(s["err_l2"][s["iterations"]] for s in stats)
+    e = stats[0]["err_l2"]
     pr.close()
     return {"coarse": "plain (one LIN1 step per slice)", "err_tol": err_tol, "seconds": round(t_ms / 1e3, 4),
             "iterations": int(iters), "converged_all": status == 0, "worst_final_err_l2": worst,
-            "serial_fine_seconds_same_gpu": round(serial_ms / 1e3, 4)}
+            "serial_fine_seconds_same_gpu": round(serial_ms / 1e3, 4),
+            "err_ratio": [float(e[k] / e[0]) for k in range(1, min(len(e), 9))]}
+
+
+def theory_vs_measured(ch, w, u0, stream, ratio_actual):
+    """Section 3 bound (ch_parareal_theory_bound) beside measured error reductions E^k / E^0 of
+    problem 0: the linear variant's run above, and the same configuration on the frozen model
+    diag(u^2) = I for which the theorems are proved (Theorems 3.7, 3.9, 3.11)."""
+    N = w["N"]
+    kw = dict(dim=w.get("dim", 1), n=w["n"], eps=w["eps"], T=w["T"], n_slices=N, fine_steps=w["J"],
+              variant=w["variant"], newton_tol=w["newton_tol"], max_iters=N, precision=w["precision"])
+    alpha, beta, f = ch.theory_bound(ch.Config(**kw), N)
+    pr = ch.Parareal(ch.Config(**kw, frozen=True), batch=1, stream=stream)
+    pr.set_initial(0, u0[0])
+    pr.compute_reference()
+    pr.run()
+    e = pr.stats(0)["err_l2"]
+    pr.close()
+    kmax = min(len(ratio_actual), len(e) - 1)
+    return {"alpha": alpha, "beta": beta, "k": list(range(1, kmax + 1)),
+            "bound_factor": [float("%.4g" % f[k]) for k in range(1, kmax + 1)],
+            "measured_frozen": [float("%.4g" % (e[k] / e[0])) for k in range(1, kmax + 1)],
+            "measured_scheme": [float("%.4g" % r) for r in ratio_actual[:kmax]]}
 
 
 # Learned against plain coarse propagator, time to 1e-8: a 2D problem small enough to train G_theta
@@ -503,9 +537,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    ubytes = w["batch"] * (w["N"] + 1) * w["n"] ** w.get("dim", 1) * 8
+    l2 = (f"inputs larger than L2 (U, F, Gold {ubytes / 1e6:.0f} MB each) and" if ubytes > 129e6
+          else f"U, F, Gold {ubytes / 1e6:.3g} MB each (smaller than L2);") + " a 256 MB L2 flush between steps"
     config = {"workload": w["name"], "global_batch": w["batch"] * world, "slices": w["N"], "fine_steps": w["J"],
-              "grid": w["n"], "parallelism": f"replicas{world}" if world > 1 else "single",
-              "l2": "inputs larger than L2 (U, F, Gold 136 MB each) and a 256 MB L2 flush between steps",
+              "grid": w["n"], "parallelism": f"replicas{world}" if world > 1 else "single", "l2": l2,
               "step": "coarse initial sweep + one fine sweep over all slices + coarse sweep/correction/norms"}
 
     if args.impl == "reference":
