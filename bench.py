@@ -54,6 +54,12 @@ WORKLOADS = {
     "c1": dict(name="1D linear Parareal PA-I M=128 eps=0.05 T=0.1 N=16 dt=1e-5 batch=1",
                n=128, eps=0.05, T=0.1, N=16, J=625, batch=1, variant="PA-I", newton_tol=1e-12,
                amp=0.1, precision=0, ttol=True),
+    # the Neumann-Neumann fine solver of Section 4.6 on the paper's grid for it (h = 1/128, 8 equal
+    # subdomains, theta = 1/4, interface tolerance 1e-10), PA-I with eps = 0.0725, J = 200
+    "c1-nn": dict(name="1D PA-I with the Neumann-Neumann fine solver, n=127 (h=1/128) eps=0.0725 T=0.1 N=16 J=200 "
+                       "8 subdomains theta=1/4 tol=1e-10 batch=1",
+                  n=127, eps=0.0725, T=0.1, N=16, J=200, batch=1, variant="PA-I", newton_tol=1e-12,
+                  amp=0.1, precision=0, ttol=True, nn=(8, 0.25, 1e-10, 200)),
 }
 FINE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin2", "NPA-I": "nl", "NPA-II": "nl"}
 COARSE_OF = {"PA-I": "lin1", "PA-II": "lin2", "PA-III": "lin1", "NPA-I": "lin1", "NPA-II": "nl"}
@@ -66,6 +72,11 @@ FP64_FLOPS_NEWTON = 15
 # A step of a linear scheme (Eq. 2.4 / 2.5) in FP64: the right-hand side and the assembly of the
 # pentadiagonal rows (about 20 flops per point) and its banded LU solve (about 25).
 FP64_FLOPS_LINEAR_STEP = 45
+# The Neumann-Neumann fine solver: per iteration and node a Dirichlet and a Neumann block
+# elimination with 2x2 blocks (about 30 flops each), per step the final Dirichlet solve and the
+# right-hand side (about 35).
+FP64_FLOPS_NN_ITER = 60
+FP64_FLOPS_NN_STEP = 35
 # GB300 FP64: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) of one 1D fine-sweep launch at c2's batch and slices, from the ncu
@@ -166,6 +177,7 @@ class ClockSampler:
 
 
 ORACLE_2D_STEPS = 2  # 2D sample: this many fine steps of one slice per process (sparse LU per step)
+ORACLE_NN_STEPS = 20  # Neumann-Neumann sample: this many fine steps of one slice per process
 
 
 def _oracle_step(args):
@@ -173,7 +185,10 @@ def _oracle_step(args):
     2D: ORACLE_2D_STEPS fine steps of one slice (a full 2D step takes hours with sparse LU)."""
     w, u0 = args
     t = time.perf_counter()
-    if w.get("dim", 1) == 2:
+    if w.get("nn"):
+        from oracle import nn1d
+        nn1d.nn_propagate(w["n"], w["eps"], w["T"] / w["N"] / w["J"], ORACLE_NN_STEPS, u0, *w["nn"])
+    elif w.get("dim", 1) == 2:
         from oracle import oracle2d as o2
         p = o2.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], newton_tol=w["newton_tol"])
         o2.propagate(p, FINE_OF[w["variant"]], w["T"] / w["N"] / w["J"], ORACLE_2D_STEPS, u0)
@@ -191,7 +206,9 @@ def cpu_oracle(w, problems, u0s, steps=1):
     oracle.build()
     ctx = mp.get_context("spawn")
     u0s = [u0s[b % len(u0s)] for b in range(problems)]  # a batch smaller than the sample repeats
-    if w.get("dim", 1) == 2:
+    if w.get("nn"):
+        pts = ORACLE_NN_STEPS * w["n"]
+    elif w.get("dim", 1) == 2:
         pts = ORACLE_2D_STEPS * w["n"] ** 2
     else:
         pts = w["N"] * w["J"] * w["n"]
@@ -232,6 +249,8 @@ def bench_ours(args, w, rank, world, local_rank):
                     newton_tol=w["newton_tol"], max_iters=1, precision=w["precision"])
     u0_dev = torch.as_tensor(u0, dtype=torch.float64, device=dev).contiguous()
     pr = ch.Parareal(cfg, batch=B, stream=stream)
+    if w.get("nn"):
+        pr.set_fine_nn(*w["nn"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def one_step():
@@ -276,10 +295,14 @@ def bench_ours(args, w, rank, world, local_rank):
     if dim == 1:
         if FINE_OF[w["variant"]] == "nl":
             alg_flops = fine_pts_per_step * FP64_FLOPS_RHS + newton_per_step * n * FP64_FLOPS_NEWTON
+        elif w.get("nn"):
+            # newton_total counts NN iterations here
+            alg_flops = fine_pts_per_step * FP64_FLOPS_NN_STEP + newton_per_step * n * FP64_FLOPS_NN_ITER
         else:
             alg_flops = fine_pts_per_step * FP64_FLOPS_LINEAR_STEP
         achieved = alg_flops / (fine_ms_per_launch / 1e3) / 1e9
-        roofline = {"bound": "alu", "kernel": "k_fine_sweep (FP64 pipe)", "achieved": round(achieved, 2),
+        roofline = {"bound": "alu", "kernel": ("k_nn_fine_sweep" if w.get("nn") else "k_fine_sweep") + " (FP64 pipe)",
+                    "achieved": round(achieved, 2),
                     "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
                     "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
                     "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
@@ -355,6 +378,8 @@ def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
                     variant=w["variant"], newton_tol=w["newton_tol"], max_iters=N, precision=w["precision"],
                     err_tol=err_tol)
     pr = ch.Parareal(cfg, batch=B, stream=stream)
+    if w.get("nn"):
+        pr.set_fine_nn(*w["nn"])
     pr.set_initial_batch(u0)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -384,6 +409,8 @@ def theory_vs_measured(ch, w, u0, stream, ratio_actual):
               variant=w["variant"], newton_tol=w["newton_tol"], max_iters=N, precision=w["precision"])
     alpha, beta, f = ch.theory_bound(ch.Config(**kw), N)
     pr = ch.Parareal(ch.Config(**kw, frozen=True), batch=1, stream=stream)
+    if w.get("nn"):
+        pr.set_fine_nn(*w["nn"])
     pr.set_initial(0, u0[0])
     pr.compute_reference()
     pr.run()
@@ -560,7 +587,9 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": value, "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
-                                 "sample": (f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice per step"
+                                 "sample": (f"{problems} processes x {ORACLE_NN_STEPS} Neumann-Neumann fine steps of "
+                                            "one slice per step" if w.get("nn") else
+                                            f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice per step"
                                             if w.get("dim", 1) == 2 else
                                             f"{problems} problems of the batch per step (repeated when the batch is "
                                             "smaller), one process each (coarse sweep + full fine sweep + correction)")},
@@ -574,7 +603,9 @@ def main():
         u0 = u0_batch(w, 0)
         problems = cpu_sample_size()
         pts, times = cpu_oracle(w, problems, u0, steps=1)
-        what = (f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice (sparse LU)"
+        what = (f"{problems} processes x {ORACLE_NN_STEPS} Neumann-Neumann fine steps of one slice (dense "
+                "subdomain solves)" if w.get("nn") else
+                f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice (sparse LU)"
                 if w.get("dim", 1) == 2 else f"{problems} problems of the batch (repeated when the batch is smaller), "
                 "one step each, one process per problem")
         cpu = {"value": pts / times[0], "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle", "sample": what}

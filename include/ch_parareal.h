@@ -282,6 +282,22 @@ ch_status ch_parareal_set_eps(ch_parareal* h, const double* eps_host, size_t len
 /* Reference slices of all problems to device memory: batch (N+1) n^d values. */
 ch_status ch_parareal_get_reference_device(ch_parareal* h, double* out_dev, size_t len);
 
+/* Neumann-Neumann fine solver (Section 4.6), 1D, for variants whose fine propagator is the linear
+ * scheme Eq. 2.4 (PA-I). Each fine step solves the mixed system u - dt D v = u^n,
+ * eps^2 D u - c^2 u + v = -u^n (c^2 = (u^n)^2; 1 when frozen; its elimination of v is Eq. 2.4) by
+ * Neumann-Neumann iteration over n_sub equal subdomains (n + 1 a multiple of n_sub, at least two
+ * nodes per subdomain, n_sub <= 32): Dirichlet solves on the subdomains, the residual of the global
+ * rows at the interface nodes, Neumann solves with it (interface rows shared half and half between
+ * the two subdomains), and the interface values updated by theta times the sum of the two Neumann
+ * solutions, until both updates (u and v) have Euclidean norm over the interfaces <= tol, at most
+ * max_iter iterations per step (reaching the cap sets CH_ERR_NEWTON on the next run or
+ * compute_reference). The paper's setting: n_sub = 8, theta = 1/4, tol = 1e-10. Parareal then
+ * converges to the sequential solution of this fine solver; compute_reference uses it too.
+ * ch_stats.newton_total / newton_max count NN iterations (summed over steps / largest per step).
+ * n_sub = 0 restores the monolithic fine solve. Call between runs; invalidates the reference.
+ * Errors: CH_ERR_INVALID (dim != 1, another fine scheme, arguments out of range), CH_ERR_CUDA. */
+ch_status ch_parareal_set_fine_nn(ch_parareal* h, int n_sub, double theta, double tol, int max_iter);
+
 /* ---------------------------------------------------------------------------------------
  * Ensembles of 2D problems on uneven grids and with different eps. The paper has no
  * counterpart (it solves one problem at a time); this batches independent 2D problems of

@@ -6,6 +6,8 @@ shares no code with it, and fails loudly when its own CUDA extension is missing.
 
 * ``oracle1d`` : ctypes binding of the plain-C FP64 one-dimensional oracle (``ch_oracle.c``).
 * ``oracle2d`` : numpy/scipy FP64 two-dimensional oracle (sparse matrices, direct solves).
+* ``bounds``   : the a-priori Parareal error bounds of Section 3 (numpy).
+* ``nn1d``     : the Neumann-Neumann fine solver of Section 4.6 in 1D (numpy, dense local solves).
 
 Parity status of every function, and the pins that hold it, are listed in the header of
 each module and in the tests under ``tests/test_oracle_*.py``.

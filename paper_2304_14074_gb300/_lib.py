@@ -34,6 +34,7 @@ EXPORTED_SYMBOLS = [
     "ch_gtheta_train", "ch_ensemble_create", "ch_ensemble_set_initial", "ch_ensemble_compute_reference",
     "ch_ensemble_run", "ch_ensemble_get_slices", "ch_ensemble_get_reference", "ch_ensemble_get_stats",
     "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_parareal_theory_bound",
+    "ch_parareal_set_fine_nn",
 ]
 _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
               "ch_gtheta_last_error", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_ensemble_groups")
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True):
     lib.ch_propagate.argtypes = [C.POINTER(_Config), C.c_int, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp]
     lib.ch_sine_transform_2d.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     lib.ch_parareal_theory_bound.argtypes = [C.POINTER(_Config), C.c_double, C.c_int, d, sz, vp]
+    lib.ch_parareal_set_fine_nn.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     f = C.POINTER(C.c_float)
     lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz, C.c_int]
@@ -283,6 +285,11 @@ class Parareal:
         p = np.ascontiguousarray(params, dtype=np.float32)
         self._check(self.lib.ch_parareal_set_coarse_model(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size,
                                                           f), "ch_parareal_set_coarse_model")
+
+    def set_fine_nn(self, n_sub: int, theta: float = 0.25, tol: float = 1e-10, max_iter: int = 200) -> None:
+        """Neumann-Neumann fine solver (Section 4.6, 1D PA-I) with n_sub subdomains; 0 restores the
+        monolithic solve."""
+        self._check(self.lib.ch_parareal_set_fine_nn(self._h, n_sub, theta, tol, max_iter), "ch_parareal_set_fine_nn")
 
     def set_eps(self, eps) -> None:
         """Per-problem eps (2D): one value per problem of the batch."""

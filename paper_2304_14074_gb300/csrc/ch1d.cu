@@ -745,6 +745,7 @@ static bool fast_fine(const Params1D& p) { return p.fine_scheme == SCHEME_NL && 
 bool fine_sweep_has_alt(const Params1D& p) { return fast_fine(p) && p.n > 128; }
 
 cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
+  if (p.nn_sub > 0) return nn_max_grid(p, grid);
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -774,6 +775,7 @@ cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
 
 cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps,
                               int grid, cudaStream_t st) {
+  if (p.nn_sub > 0) return launch_nn_fine_sweep(p, U, F, ctrl, ps, grid, st);
   cudaError_t e = cudaSuccess;
   if (fast_fine(p)) {
     CH_DISPATCH_TP_FINE(p.n, p.alt, {
@@ -812,6 +814,7 @@ cudaError_t launch_tally(const Params1D& p, Ctrl* ctrl, ProblemState ps, int* ho
 }
 
 cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st) {
+  if (p.nn_sub > 0) return launch_nn_reference(p, Uref, ctrl, st);
   cudaError_t e = cudaSuccess;
   if (fast_fine(p)) {
     CH_DISPATCH_TP_FINE(p.n, p.alt, {

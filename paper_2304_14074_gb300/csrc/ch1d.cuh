@@ -52,6 +52,12 @@ struct Params1D {
   double tol;        // Parareal increment tolerance (<= 0: never)
   double err_tol;    // stop once the L2_h error against the reference is <= err_tol (<= 0: never)
   int alt;           // fine-sweep CTA mapping: 0 = default (T, P), 1 = (T/2, 2P) (autotuned)
+  // Neumann-Neumann fine solver (Section 4.6; linear scheme Eq. 2.4 only): subdomains (0 = off),
+  // relaxation, tolerance on the interface updates, iteration cap per step
+  int nn_sub;
+  double nn_theta;
+  double nn_tol;
+  int nn_max;
 };
 
 // Whether the fine sweep of p has an alternative CTA mapping (T/2 threads, 2P block rows each).
@@ -70,6 +76,14 @@ cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nstep
                              double* uout, int* newton, Ctrl* ctrl, cudaStream_t st);
 // CTAs of the fine sweep that fit on the device at once (for the persistent grid).
 cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid);
+// Neumann-Neumann fine solver (implemented in ch_nn.cu): whether p's sizes are supported, the
+// persistent grid of its fine sweep, and the launches that replace the fine sweep and the
+// sequential fine solution when p.nn_sub > 0.
+bool nn_supported(const Params1D& p);
+cudaError_t nn_max_grid(const Params1D& p, int* grid);
+cudaError_t launch_nn_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps, int grid,
+                                 cudaStream_t st);
+cudaError_t launch_nn_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st);
 // Largest n the kernels support.
 constexpr int kMaxN1D = 4096;
 

@@ -1016,6 +1016,37 @@ ch_status ch_parareal_set_eps(ch_parareal* h, const double* eps_host, size_t len
   return CH_OK;
 }
 
+ch_status ch_parareal_set_fine_nn(ch_parareal* h, int n_sub, double theta, double tol, int max_iter) {
+  if (!h) return CH_ERR_INVALID;
+  if (h->dim != 1) return fail(h, CH_ERR_INVALID, "set_fine_nn: the Neumann-Neumann fine solver is 1D");
+  if (h->p.fine_scheme != chg::SCHEME_LIN1)
+    return fail(h, CH_ERR_INVALID, "set_fine_nn: the fine scheme must be the linear scheme Eq. 2.4 (PA-I)");
+  chg::Params1D q = h->p;
+  if (n_sub == 0) {
+    q.nn_sub = 0;
+  } else {
+    if (!(theta > 0.0 && theta <= 1.0) || !(tol > 0.0) || !std::isfinite(tol) || max_iter < 1 || max_iter > 100000)
+      return fail(h, CH_ERR_INVALID, "set_fine_nn: theta in (0, 1], tol > 0 and max_iter in 1..100000");
+    q.nn_sub = n_sub;
+    q.nn_theta = theta;
+    q.nn_tol = tol;
+    q.nn_max = max_iter;
+    if (!chg::nn_supported(q))
+      return fail(h, CH_ERR_INVALID, "set_fine_nn: n_sub in 1..32 dividing n + 1, at least 2 nodes per subdomain");
+  }
+  int grid = 0;
+  CH_CUDA(h, chg::fine_sweep_max_grid(q, &grid));
+  h->p = q;
+  h->grid = grid;
+  h->tuned = (n_sub > 0);  // the autotuner chooses among monolithic sweeps only
+  if (h->gfine) {
+    cudaGraphExecDestroy(h->gfine);
+    h->gfine = nullptr;
+  }
+  h->ref_valid = false;
+  return CH_OK;
+}
+
 ch_status ch_parareal_get_reference_device(ch_parareal* h, double* out_dev, size_t len) {
   if (!h) return CH_ERR_INVALID;
   const size_t want = (size_t)h->B * (h->p.N + 1) * h->pts;

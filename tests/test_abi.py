@@ -94,6 +94,11 @@ def test_theory_bound_rejects_invalid_arguments_without_device():
     assert lib.ch_parareal_theory_bound(C.byref(npa), float("nan"), 2, out, 8, None) == 1
 
 
+def test_set_fine_nn_rejects_null_handle_without_device():
+    lib = ch.load()
+    assert lib.ch_parareal_set_fine_nn(None, 8, 0.25, 1e-10, 100) == 1
+
+
 def test_destroy_accepts_null_and_last_error_on_null():
     lib = ch.load()
     lib.ch_parareal_destroy(None)
