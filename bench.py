@@ -81,7 +81,7 @@ FP64_FLOPS_NN_STEP = 35
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes (read + write) of one 1D fine-sweep launch at c2's batch and slices, from the ncu
 # capture summarised in profiles/k_fine_sweep_c2.md (independent of the fine steps per slice).
-FINE_SWEEP_1D_TRAFFIC = 223.7e6
+FINE_SWEEP_1D_TRAFFIC = 219.1e6
 
 
 # 2D fine sweep, algorithmic DRAM/L2 bytes per grid point and unit, each array read or written
