@@ -200,14 +200,15 @@ __device__ int nl_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], doub
 // rounding floor. Unknowns (d_i, v_i) form the 2x2 blocks
 //     B_i = [[1, 2 sigma], [-2 sigma - c dt w_i / s, 1]],  A_i = C_i = [[0, -sigma], [sigma, 0]].
 // FP64 is spent on the residual H and the update only; w comes from a float shadow of Y, and the
-// stop test uses the float correction. The iteration starts from the quadratic extrapolation
-// 3 u^n - 3 u^{n-1} + u^{n-2} when two earlier states of the same propagation are known, the
-// linear one 2 u^n - u^{n-1} when one is (u^n otherwise);
+// stop test uses the float correction. The iteration starts from the cubic extrapolation
+// 4 u^n - 6 u^{n-1} + 4 u^{n-2} - u^{n-3} when three earlier states of the same propagation are
+// known, the quadratic or linear one when two or one are (u^n otherwise);
 // the root it converges to is the same (the step is the unique minimiser of a strictly convex
 // functional), only the number of iterations changes.
 template <int T, int P>
 __device__ int nl_step_mixed(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double (&yp)[2 * P],
-                             double (&ypp)[2 * P], int have_prev, float (&y32)[2 * P], double dt, bool& bad) {
+                             double (&ypp)[2 * P], double (&yppp)[2 * P], int have_prev, float (&y32)[2 * P],
+                             double dt, bool& bad) {
   constexpr int R = 2 * P;
   const int r0 = threadIdx.x * R;
   double L, Rt;
@@ -221,7 +222,11 @@ __device__ int nl_step_mixed(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P]
   }
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const double g = (have_prev >= 2) ? 3.0 * (y[q] - yp[q]) + ypp[q] : (have_prev ? 2.0 * y[q] - yp[q] : y[q]);
+    const double g = (have_prev >= 3)   ? 4.0 * y[q] - 6.0 * yp[q] + 4.0 * ypp[q] - yppp[q]
+                     : (have_prev == 2) ? 3.0 * (y[q] - yp[q]) + ypp[q]
+                     : (have_prev == 1) ? 2.0 * y[q] - yp[q]
+                                        : y[q];
+    yppp[q] = ypp[q];
     ypp[q] = yp[q];
     yp[q] = y[q];
     y[q] = (r0 + q < c.n) ? g : 0.0;
@@ -435,11 +440,11 @@ __device__ bool run_steps(Smem1D<T>& sm, const StepCtx& c, int scheme, int fp32_
 template <int T, int P>
 __device__ bool run_steps_nl32(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, int nsteps,
                                unsigned long long& newton_sum, int& newton_peak, unsigned& status) {
-  double yp[2 * P], ypp[2 * P];
+  double yp[2 * P], ypp[2 * P], yppp[2 * P];
   float y32[2 * P];
   bool bad = false;
   for (int j = 0; j < nsteps; ++j) {
-    const int m = nl_step_mixed<T, P>(sm, c, y, yp, ypp, j < 2 ? j : 2, y32, dt, bad);
+    const int m = nl_step_mixed<T, P>(sm, c, y, yp, ypp, yppp, j < 3 ? j : 3, y32, dt, bad);
     const int a = (m < 0) ? -m : m;
     if (m < 0) status |= ST_NEWTON;
     newton_sum += (unsigned long long)a;
