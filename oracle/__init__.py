@@ -33,3 +33,22 @@ def build(force: bool = False) -> str:
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
+
+
+def spawn_pool(processes: int):
+    """A 'spawn' process pool for oracle work whose workers use one BLAS/OpenMP thread each (the
+    workers are the parallelism; threaded BLAS inside each of them oversubscribes the cores).
+    Spawned, not forked, so it is safe to create after the process has used the GPU."""
+    import multiprocessing as mp
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(processes)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -271,3 +271,64 @@ def test_parareal_stop_rule_on_paper_e1_parameters():
     assert r.inc[-1] < 1e-3 and np.all(r.inc[:-1] >= 1e-3)
     assert r.err_l2[r.iterations] < 1e-3
     assert np.all(np.diff(r.err_l2[:5]) < 0)
+
+
+# ------------------------------------------------------------- error norms (Section 4)
+#
+# The error and increment norms are pinned by discrete sine orthogonality, not by restating
+# them: for 1 <= q <= n, sum_{j=1..n} sin^2(q pi j/(n+1)) = (n+1)/2, so the L2_h norm
+# (h sum e^2)^(1/2) of c sin(q pi x) is |c|/sqrt(2) for every n. A wrong power of h, a missing
+# square root or a sum over the wrong slices gives another value (one that depends on n).
+
+
+@pytest.mark.parametrize("n", [7, 31, 64])
+def test_error_norms_of_planted_sine_errors(n):
+    """Uf = U^0 + c_s sin(q pi x): err_l2[0] = max_s |c_s|/sqrt(2), err_max[0] = max_s |c_s| max_j |sin|."""
+    eps, T, N, J, pm, q = 0.0725, 1.0, 6, 20, 2, 5 if n > 5 else 1
+    p = o.Params(n=n, eps=eps, T=T, N=N, J=J, fine="lin1", coarse="lin1", frozen=True, max_iters=0)
+    u0 = sine_mode(n, pm)
+    a = frozen_parareal_closed_form(n, pm, eps, T, N, J, 0)  # U_s^0 = a^s u0 (Lemma 3.1)
+    c = np.array([1e-3 * (s + 1) * (-1) ** s for s in range(N + 1)])
+    Uf = a[:, None] * u0[None, :] + c[:, None] * sine_mode(n, q)[None, :]
+    r = o.parareal(p, u0, Uf)
+    assert r.iterations == 0
+    want_l2 = np.max(np.abs(c)) / math.sqrt(2.0)
+    want_mx = np.max(np.abs(c)) * np.max(np.abs(sine_mode(n, q)))
+    # U^0 differs from the closed form by the coarse solves' rounding (~1e-13)
+    assert abs(r.err_l2[0] - want_l2) <= 1e-12
+    assert abs(r.err_max[0] - want_mx) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_error_and_increment_norms_follow_closed_form_iterates(k):
+    """Frozen PA-I on one sine mode: U_s^k = c_s^k sin(p pi x) (Lemma 3.4) and the fine solution
+    b^s sin(p pi x), so err_l2[k] = max_s |c_s^k - b^s| / sqrt(2) and
+    inc[k-1] = max_s |c_s^k - c_s^(k-1)| max_j |sin(p pi x_j)|."""
+    n, eps, T, N, J, pm = 31, 0.0725, 1.0, 8, 20, 3
+    p = o.Params(n=n, eps=eps, T=T, N=N, J=J, fine="lin1", coarse="lin1", frozen=True, max_iters=k)
+    u0 = sine_mode(n, pm)
+    y = mu(n, pm)
+    dt = T / N / J
+    b = ((1 + dt * y) / (1 + dt * y + eps ** 2 * dt * y ** 2)) ** J
+    fine_coef = np.array([b ** s for s in range(N + 1)])
+    Uf = fine_coef[:, None] * u0[None, :]
+    r = o.parareal(p, u0, Uf)
+    smax = np.max(np.abs(u0))
+    for kk in range(k + 1):
+        ck = frozen_parareal_closed_form(n, pm, eps, T, N, J, kk)
+        d = np.max(np.abs(ck - fine_coef))
+        assert abs(r.err_l2[kk] - d / math.sqrt(2.0)) <= 1e-12, kk
+        assert abs(r.err_max[kk] - d * smax) <= 1e-12, kk
+        if kk >= 1:
+            cprev = frozen_parareal_closed_form(n, pm, eps, T, N, J, kk - 1)
+            dinc = np.max(np.abs(ck - cprev)) * smax
+            assert abs(r.inc[kk - 1] - dinc) <= 1e-12, kk
+
+
+def test_energy_closed_form_on_sine_mode():
+    """Eq. 1.2 on u = A sin(p pi x): h sum sin^2 = 1/2, h sum sin^4 = 3/8 (2p not a multiple of
+    n+1) and u^T(-D_h)u = mu_p sum u^2, so E = (3A^4/8 - A^2 + n h)/4 + eps^2 mu_p A^2 / 4."""
+    n, eps, pm, A = 40, 0.2, 3, 0.7
+    h = 1.0 / (n + 1)
+    want = (3 * A ** 4 / 8 - A ** 2 + n * h) / 4 + eps ** 2 * mu(n, pm) * A ** 2 / 4
+    assert abs(o.energy(A * sine_mode(n, pm), eps) - want) <= 1e-12 * abs(want)

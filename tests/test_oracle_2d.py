@@ -176,3 +176,83 @@ def test_sine_transform_diagonalises_dh_and_is_involutory():
     v = mode2(n, 3, 5).reshape(n, n)
     V = o2.sine_transform(v)
     assert abs(V[4, 2]) > 1 and np.sum(np.abs(V) > 1e-9) == 1
+
+
+# ------------------------------------------------------------- error norms (Section 4)
+#
+# Pinned by discrete sine orthogonality: h^2 sum_{i,j} sin^2(p pi x_i) sin^2(q pi y_j) = 1/4 for
+# 1 <= p, q <= n, so the L2_h norm (h^2 sum e^2)^(1/2) of c sin(p pi x) sin(q pi y) is |c|/2.
+
+
+@pytest.mark.parametrize("n", [7, 15])
+def test_error_norms_of_planted_sine_errors_2d(n):
+    eps, T, N, J = 0.0725, 1.0, 4, 5
+    p = o2.Params(n=n, eps=eps, T=T, N=N, J=J, fine="lin1", coarse="lin1", frozen=True)
+    u0 = mode2(n, 2, 1)
+    y = mu(n, 2) + mu(n, 1)
+    dT = T / N
+    a = (1 + dT * y) / (1 + dT * y + eps ** 2 * dT * y ** 2)
+    c = np.array([2e-3 * (s + 1) * (-1) ** s for s in range(N + 1)])
+    e = mode2(n, 3, 4)
+    Uf = np.array([a ** s for s in range(N + 1)])[:, None] * u0[None, :] + c[:, None] * e[None, :]
+    r = o2.parareal(p, u0, Uf, max_iters=0)
+    want_l2 = np.max(np.abs(c)) / 2.0
+    want_mx = np.max(np.abs(c)) * np.max(np.abs(e))
+    assert abs(r.err_l2[0] - want_l2) <= 1e-12
+    assert abs(r.err_max[0] - want_mx) <= 1e-12
+
+
+def test_error_norms_follow_closed_form_iterates_2d():
+    n, eps, T, N, J = 15, 0.0725, 1.0, 6, 10
+    u0 = mode2(n, 2, 3)
+    y = mu(n, 2) + mu(n, 3)
+    dT, dt = T / N, T / N / J
+    a = (1 + dT * y) / (1 + dT * y + eps ** 2 * dT * y ** 2)
+    b = ((1 + dt * y) / (1 + dt * y + eps ** 2 * dt * y ** 2)) ** J
+    fine_coef = np.array([b ** s for s in range(N + 1)])
+    Uf = fine_coef[:, None] * u0[None, :]
+    k = 3
+    r = o2.parareal(o2.Params(n=n, eps=eps, T=T, N=N, J=J, fine="lin1", coarse="lin1", frozen=True), u0, Uf,
+                    max_iters=k)
+
+    def coef(kk):
+        return np.array([sum(math.comb(s, j) * (b - a) ** j * a ** (s - j) for j in range(min(kk, s) + 1))
+                         for s in range(N + 1)])
+
+    smax = np.max(np.abs(u0))
+    for kk in range(k + 1):
+        d = np.max(np.abs(coef(kk) - fine_coef))
+        assert abs(r.err_l2[kk] - d / 2.0) <= 1e-12
+        assert abs(r.err_max[kk] - d * smax) <= 1e-12
+        if kk >= 1:
+            dinc = np.max(np.abs(coef(kk) - coef(kk - 1))) * smax
+            assert abs(r.inc[kk - 1] - dinc) <= 1e-12
+
+
+def test_energy_closed_form_on_sine_mode_2d():
+    """Eq. 1.2 on u = A sin(p pi x) sin(q pi y): h^2 sum u^2 = A^2/4, h^2 sum u^4 = 9A^4/64 (2p, 2q
+    not multiples of n+1) and u^T(-D_h)u = (mu_p + mu_q) sum u^2, so
+    E = (9A^4/64 - A^2/2 + (n h)^2)/4 + eps^2 (mu_p + mu_q) A^2 / 8."""
+    n, eps, A = 15, 0.1, 0.8
+    h = 1.0 / (n + 1)
+    want = (9 * A ** 4 / 64 - A ** 2 / 2 + (n * h) ** 2) / 4 + eps ** 2 * (mu(n, 3) + mu(n, 2)) * A ** 2 / 8
+    assert abs(o2.energy(A * mode2(n, 3, 2), n, eps) - want) <= 1e-12 * abs(want)
+
+
+# ---------------------------------------------------- CG solver of the oracle (large grids)
+
+
+@pytest.mark.parametrize("scheme,frozen", [("lin1", False), ("lin1", True), ("lin2", False), ("nl", False),
+                                           ("nl", True)])
+@pytest.mark.parametrize("n", [15, 31])
+def test_pcg_solver_matches_sparse_direct(scheme, frozen, n):
+    """The CG path (library CG on A^{-1} J, sine-transform preconditioner, refinement) reaches the
+    sparse-LU step to rounding: a wrong operator in it (a sign, a missing eps^2 dt A term, a
+    transposed transform) moves the result by far more."""
+    u = ch_inputs.initial_condition(2, n, 21, kind="normal", amp=0.6)
+    for dt in (1e-4, 2e-2):
+        kw = dict(n=n, eps=0.03, T=1, N=1, J=1, frozen=frozen, newton_tol=1e-12)
+        a, ma = o2.step(o2.Params(**kw), scheme, dt, u)
+        b, mb = o2.step(o2.Params(**kw, solver="pcg"), scheme, dt, u)
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.max(np.abs(a))), (dt, np.max(np.abs(a - b)))
+        assert abs(ma - mb) <= 1
