@@ -79,9 +79,11 @@ FP64_FLOPS_NN_ITER = 60
 FP64_FLOPS_NN_STEP = 35
 # GB300 FP64: 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# DRAM bytes (read + write) of one 1D fine-sweep launch at c2's batch and slices, from the ncu
-# capture summarised in profiles/k_fine_sweep_c2.md (independent of the fine steps per slice).
-FINE_SWEEP_1D_TRAFFIC = 219.1e6
+# DRAM bytes (read + write) of one 1D fine-sweep launch at c2's batch and slices (256 x 64 units,
+# all slices iterating), from a one-launch ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum on the current kernel; independent of the fine steps per slice (the slice
+# state stays in registers). None when the kernel has changed since the capture.
+FINE_SWEEP_1D_TRAFFIC = {(1024, 256, 64): 219.1e6}
 
 
 # 2D fine sweep, algorithmic DRAM/L2 bytes per grid point and unit, each array read or written
@@ -190,7 +192,8 @@ def _oracle_step(args):
         nn1d.nn_propagate(w["n"], w["eps"], w["T"] / w["N"] / w["J"], ORACLE_NN_STEPS, u0, *w["nn"])
     elif w.get("dim", 1) == 2:
         from oracle import oracle2d as o2
-        p = o2.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], newton_tol=w["newton_tol"])
+        p = o2.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], newton_tol=w["newton_tol"],
+                      solver="pcg")
         o2.propagate(p, FINE_OF[w["variant"]], w["T"] / w["N"] / w["J"], ORACLE_2D_STEPS, u0)
     else:
         from oracle import oracle1d as o
@@ -200,30 +203,107 @@ def _oracle_step(args):
     return time.perf_counter() - t
 
 
+def _serial_fine(args):
+    """The sequential fine solve F^N(u0) of one problem (the classical serial method, Section 2),
+    on one core; 2D: ORACLE_2D_STEPS fine steps."""
+    w, u0 = args
+    t = time.perf_counter()
+    if w.get("dim", 1) == 2:
+        from oracle import oracle2d as o2
+        p = o2.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], newton_tol=w["newton_tol"],
+                      solver="pcg")
+        o2.propagate(p, FINE_OF[w["variant"]], w["T"] / w["N"] / w["J"], ORACLE_2D_STEPS, u0)
+    elif w.get("nn"):
+        from oracle import nn1d
+        nn1d.nn_propagate(w["n"], w["eps"], w["T"] / w["N"] / w["J"], ORACLE_NN_STEPS, u0, *w["nn"])
+    else:
+        from oracle import oracle1d as o
+        p = o.Params(n=w["n"], eps=w["eps"], T=w["T"], N=w["N"], J=w["J"], fine=FINE_OF[w["variant"]],
+                     coarse=COARSE_OF[w["variant"]], newton_tol=w["newton_tol"])
+        o.fine_solution(p, u0)
+    return time.perf_counter() - t
+
+
+def _sample_points(w):
+    """Fine grid-point steps of one oracle sample (one problem's step of the workload in 1D; a few
+    fine steps of one slice in 2D and for the Neumann-Neumann solver)."""
+    if w.get("nn"):
+        return ORACLE_NN_STEPS * w["n"]
+    if w.get("dim", 1) == 2:
+        return ORACLE_2D_STEPS * w["n"] ** 2
+    return w["N"] * w["J"] * w["n"]
+
+
+def cpu_model():
+    """The host CPU's model name (x86: 'model name'; Arm: implementer / part of /proc/cpuinfo)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        info = []
+    for key in ("model name", "Model name"):
+        for ln in info:
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    impl = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")]
+    part = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")]
+    if impl and part:
+        return f"{platform.machine()} implementer {impl[0]} part {part[0]}"
+    return platform.machine() or "unknown"
+
+
 def cpu_oracle(w, problems, u0s, steps=1):
-    """Times the oracle on `problems` problems, one process per problem (spawned)."""
+    """Times the oracle on `problems` problems, one single-threaded process per problem (spawned):
+    the all-core sample when `problems` is the core count."""
     import oracle
     oracle.build()
-    ctx = mp.get_context("spawn")
     u0s = [u0s[b % len(u0s)] for b in range(problems)]  # a batch smaller than the sample repeats
-    if w.get("nn"):
-        pts = ORACLE_NN_STEPS * w["n"]
-    elif w.get("dim", 1) == 2:
-        pts = ORACLE_2D_STEPS * w["n"] ** 2
-    else:
-        pts = w["N"] * w["J"] * w["n"]
     times = []
-    with ctx.Pool(problems) as pool:
+    with oracle.spawn_pool(problems) as pool:
         for _ in range(steps):
             t = time.perf_counter()
             pool.map(_oracle_step, [(w, u0s[b]) for b in range(problems)])
             times.append(time.perf_counter() - t)
-    return problems * pts, times
+    return problems * _sample_points(w), times
+
+
+def cpu_serial_fine(w, u0):
+    """The 1-core sequential fine solve of one problem, timed in a spawned process; returns
+    (grid-point steps, seconds)."""
+    import oracle
+    oracle.build()
+    with oracle.spawn_pool(1) as pool:
+        secs = pool.map(_serial_fine, [(w, u0)])[0]
+    if w.get("dim", 1) == 2 or w.get("nn"):
+        pts = _sample_points(w)
+    else:
+        pts = w["N"] * w["J"] * w["n"]
+    return pts, secs
 
 
 def cpu_sample_size():
-    cores = os.cpu_count() or 1
-    return max(1, min(4, cores))
+    """All host cores, one oracle process per core."""
+    return max(1, os.cpu_count() or 1)
+
+
+def cpu_baseline(w, u0, steps=1):
+    """The CPU oracle as it stands on this host: the all-core sample (one problem per core) and
+    the 1-core sequential fine solve (the serial method Parareal is measured against)."""
+    problems = cpu_sample_size()
+    pts, times = cpu_oracle(w, problems, u0, steps=steps)
+    spts, ssecs = cpu_serial_fine(w, u0[0])
+    what = (f"{problems} processes x {ORACLE_NN_STEPS} Neumann-Neumann fine steps of one slice (dense subdomain "
+            "solves)" if w.get("nn") else
+            f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice (sparse solves by library CG)"
+            if w.get("dim", 1) == 2 else
+            f"{problems} problems of the batch (repeated when the batch is smaller), one process per core, each "
+            "one step of the workload (coarse sweep + fine sweep of every slice + correction)")
+    return {"value": steps * pts / sum(times), "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
+            "sample": what, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "serial_fine_1core": {"value": spts / ssecs, "unit": "grid-pt-steps/s", "seconds": round(ssecs, 3),
+                                  "sample": ("sequential fine solve F^N(u0) of problem 0 on one core"
+                                             if w.get("dim", 1) == 1 and not w.get("nn") else
+                                             "the fine steps of the all-core sample, one process")}}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -306,26 +386,14 @@ def bench_ours(args, w, rank, world, local_rank):
                     "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
                     "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
                     "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
-                    "traffic": FINE_SWEEP_1D_TRAFFIC if (n, B, N) == (1024, 256, 64) else None,
+                    "traffic": FINE_SWEEP_1D_TRAFFIC.get((n, B, N)),
                     "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
                     "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
                     "newton_iters_per_step_point": round(newton_per_step / (B * N * J), 3),
                     "algorithmic_fp64_flops_per_launch": alg_flops}
     else:
-        # 2D: newton_total and inner_iterations (CG) are summed over the B N units
-        units = B * N
-        alg_bytes = pts * (newton_per_step * BYTES_NEWTON_2D + cg_per_step * BYTES_CG_2D + units * J * BYTES_STEP_2D)
-        achieved = alg_bytes / (fine_ms_per_launch / 1e3) / 1e9
-        peak = measured_peaks().get("hbm_gbs", 6800.0)
-        roofline = {"bound": "hbm", "kernel": "2D fine sweep (sine-transform passes + pointwise sweeps)",
-                    "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)", "traffic": None,
-                    "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
-                    "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
-                    "newton_iterations_per_unit_step": round(newton_per_step / (units * J), 3),
-                    "cg_iterations_per_unit_step": round(cg_per_step / (units * J), 3),
-                    "algorithmic_bytes_per_launch": alg_bytes,
-                    "note": "working set per field 8.3 MB: L2-resident, so HBM bandwidth is a bound, not the limit"}
+        roofline = roofline_2d(w, B, fine_ms_per_launch, newton_per_step, cg_per_step,
+                               fine_ms / total_ms if world == 1 else None)
 
     # end to end through the public API: pinned host inputs in, every slice of the result out
     u0_pin = torch.from_numpy(u0).pin_memory()
@@ -357,8 +425,72 @@ def bench_ours(args, w, rank, world, local_rank):
     if not args.no_learned and rank == 0:
         ttol = dict(ttol or {})
         ttol["learned_vs_plain_G"] = learned_vs_plain(ch, stream)
+    r2d = None
+    if dim == 1 and not args.no_2d and rank == 0:
+        r2d = c4_step_roofline(ch, stream)
     return dict(value=value, total_ms=total_ms, step_ms=step_ms, roofline=roofline, e2e=e2e,
-                clocks=clk.summary(), launches=launches, ttol=ttol)
+                clocks=clk.summary(), launches=launches, ttol=ttol, roofline_2d=r2d)
+
+
+def roofline_2d(w, B, fine_ms_per_launch, newton_total, cg_total, share):
+    """HBM roofline of the 2D fine sweep: algorithmic bytes (BYTES_* per grid point, from the
+    Newton and CG iterations summed over the units) over the live fine-sweep time."""
+    n, N, J = w["n"], w["N"], w["J"]
+    pts = n * n
+    units = B * N
+    alg_bytes = pts * (newton_total * BYTES_NEWTON_2D + cg_total * BYTES_CG_2D + units * J * BYTES_STEP_2D)
+    achieved = alg_bytes / (fine_ms_per_launch / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    field = 4 * pts * units  # one FP32 solver vector over all units
+    where = ("L2-resident (129 MB L2): HBM bandwidth is a bound, not the limit" if field < 100e6 else
+             "beyond L2: the sweeps stream from HBM")
+    return {"bound": "hbm", "kernel": "2D fine sweep (sine-transform passes + pointwise sweeps)",
+            "workload": w["name"], "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks
+                            else "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"),
+            "traffic": None,
+            "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
+            "fine_sweep_share_of_step": round(share, 4) if share is not None else None,
+            "newton_iterations_per_unit_step": round(newton_total / (units * J), 3),
+            "cg_iterations_per_unit_step": round(cg_total / (units * J), 3),
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "note": f"one FP32 solver vector over all {units} units is {field / 1e6:.1f} MB: {where}"}
+
+
+def c4_step_roofline(ch, stream, warmup=1, steps=1):
+    """One step of the 512 x 512 configuration (coarse initial sweep + fine sweep of all 64 slices
+    + coarse sweep with correction), timed live with CUDA events; the roofline of its fine sweep."""
+    import torch
+    w = WORKLOADS["c4"]
+    u0 = u0_batch(w, 0)
+    cfg = ch.Config(dim=2, n=w["n"], eps=w["eps"], T=w["T"], n_slices=w["N"], fine_steps=w["J"],
+                    variant=w["variant"], newton_tol=w["newton_tol"], max_iters=1, precision=w["precision"])
+    pr = ch.Parareal(cfg, batch=1, stream=stream)
+    u0_dev = torch.as_tensor(u0, dtype=torch.float64, device="cuda").contiguous()
+    for _ in range(warmup):
+        pr.set_initial_device(u0_dev)
+        pr.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fine_ms, newton, cg = 0.0, 0, 0
+    a.record(stream)
+    for _ in range(steps):
+        pr.set_initial_device(u0_dev)
+        pr.run()
+        st = pr.stats(0)
+        fine_ms += st["fine_sweep_ms"]
+        newton += st["newton_total"]
+        cg += st["inner_iterations"]
+    b.record(stream)
+    torch.cuda.synchronize()
+    step_ms = a.elapsed_time(b) / steps
+    pr.close()
+    r = roofline_2d(w, 1, fine_ms / steps, newton / steps, cg / steps, fine_ms / steps / step_ms)
+    r["step_ms"] = round(step_ms, 2)
+    r["grid_pt_steps_per_s"] = w["N"] * w["J"] * w["n"] ** 2 / (step_ms / 1e3)
+    return r
 
 
 def measured_peaks():
@@ -557,6 +689,7 @@ def main():
     ap.add_argument("--no-ttol", action="store_true", help="skip the time-to-1e-8 run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain coarse propagator run")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 512 x 512 2D step (roofline_2d)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -574,7 +707,6 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        import ch_inputs  # noqa: F401
         u0 = u0_batch(w, 0)
         problems = cpu_sample_size()
         for _ in range(args.warmup):
@@ -582,17 +714,18 @@ def main():
         pts, times = cpu_oracle(w, problems, u0, steps=args.steps)
         total = sum(times)
         value = args.steps * pts / total
+        what = (f"{problems} processes x {ORACLE_NN_STEPS} Neumann-Neumann fine steps of one slice per step"
+                if w.get("nn") else
+                f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice per step (sparse solves by "
+                "library CG)" if w.get("dim", 1) == 2 else
+                f"{problems} problems of the batch per step (repeated when the batch is smaller), one process per "
+                "core, each one step of the workload (coarse sweep + fine sweep of every slice + correction)")
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid-pt-steps/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": value, "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle",
-                                 "sample": (f"{problems} processes x {ORACLE_NN_STEPS} Neumann-Neumann fine steps of "
-                                            "one slice per step" if w.get("nn") else
-                                            f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice per step"
-                                            if w.get("dim", 1) == 2 else
-                                            f"{problems} problems of the batch per step (repeated when the batch is "
-                                            "smaller), one process each (coarse sweep + full fine sweep + correction)")},
+                                 "sample": what, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
                 "e2e": {"value": value, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -600,15 +733,7 @@ def main():
     # CPU oracle baseline first (spawned processes, before any GPU work in this process)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        u0 = u0_batch(w, 0)
-        problems = cpu_sample_size()
-        pts, times = cpu_oracle(w, problems, u0, steps=1)
-        what = (f"{problems} processes x {ORACLE_NN_STEPS} Neumann-Neumann fine steps of one slice (dense "
-                "subdomain solves)" if w.get("nn") else
-                f"{problems} processes x {ORACLE_2D_STEPS} fine steps of one slice (sparse LU)"
-                if w.get("dim", 1) == 2 else f"{problems} problems of the batch (repeated when the batch is smaller), "
-                "one step each, one process per problem")
-        cpu = {"value": pts / times[0], "unit": "grid-pt-steps/s", "cores": problems, "kind": "oracle", "sample": what}
+        cpu = cpu_baseline(w, u0_batch(w, 0))
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -624,7 +749,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
             "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
-            "clocks": r["clocks"], "time_to_1e-8": r["ttol"],
+            "clocks": r["clocks"], "time_to_1e-8": r["ttol"], "roofline_2d": r["roofline_2d"],
             "precision": "FP64 states, residuals, correction and norms; Newton inner solves FP32 (refined by the FP64 residual)"}
     print(json.dumps(line))
 

@@ -10,7 +10,11 @@
  *
  * Conventions shared by every entry point
  *  - Every function returns ch_status and never aborts. A handle keeps the first error
- *    ("sticky") with a message readable through ch_parareal_last_error().
+ *    ("sticky") with a message readable through ch_parareal_last_error(); later calls that
+ *    need the device return it. A Newton or linear-solve failure (CH_ERR_NEWTON,
+ *    CH_ERR_LINSOLVE: a non-converging or non-finite propagation, e.g. from non-finite initial
+ *    data) belongs to the data, not to the handle: a successful set_initial*, set_eps or
+ *    set_fine_nn clears it. Every other error stays until the handle is destroyed.
  *  - Grid: n interior nodes per direction, h = 1/(n+1); boundary values are implicit zeros.
  *    A state is the interior values, FP64, row-major (y outer, x inner in 2D), n^d entries.
  *  - Slice layout: slices 0..N of one problem are contiguous, slice 0 = u^0; problems follow
@@ -85,6 +89,13 @@ typedef struct {
   double err_tol;      /* also stop a problem once max_n ||U_n^k - U_n^fine||_{L2_h} <= err_tol
                           (the error measure of Section 4; needs ch_parareal_compute_reference);
                           <= 0: off                                                          */
+  double lin_tol;      /* 2D inner linear solves (the Jacobian system of each Newton iteration
+                          of Eq. 3.17, and the refinement sweeps of Eq. 2.4 / 2.5): CG stops once
+                          the preconditioned residual norm has dropped by this factor; in (0, 1),
+                          <= 0 selects 1e-4. Newton's FP64 residual is unchanged, so the step
+                          converges to the same FP64 root; a looser value trades more Newton
+                          iterations for fewer CG iterations. Ignored in 1D (direct solves).   */
+  int lin_max;         /* 2D: CG iterations per inner solve at most; <= 0 selects 60.         */
 } ch_config;
 
 #define CH_MAX_ITERS 1024
@@ -123,8 +134,10 @@ typedef struct ch_parareal ch_parareal;
 
 /* Create a handle for `batch` independent problems sharing `cfg`. Allocates device memory
  * for the slice states, F(U_n^k), G(U_n^k), the reference solution and the histories.
- * Errors: CH_ERR_INVALID (cfg out of range: dim != 1, n < 1 or n > 2048, N < 1, J < 1,
- * eps <= 0, T <= 0, batch < 1, max_iters outside 1..N), CH_ERR_OOM, CH_ERR_CUDA. */
+ * Errors: CH_ERR_INVALID (cfg out of range: dim not 1 or 2, n outside the grids above, N < 1 or
+ * N >= CH_MAX_ITERS, J < 1, coarse_steps < 1, eps, T or newton_tol not finite and > 0, tol,
+ * err_tol or lin_tol not finite, lin_tol >= 1, lin_max > 10000, batch < 1, max_iters outside
+ * 1..N), CH_ERR_OOM, CH_ERR_CUDA. */
 ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream, ch_parareal** out);
 
 /* u^0 of one problem from host memory, len = n^d values. */
@@ -362,6 +375,20 @@ const char* ch_ensemble_last_error(const ch_ensemble* e);
 
 ch_status ch_parareal_solve_noalloc(const ch_config* cfg, int batch, const double* u0_dev, double* U_dev,
                                     size_t len, int* iterations_host, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Diagnostics. The paper has no counterpart: these check the library itself.
+ *
+ * Failure path of the bounded device-side waits. Every wait of the library's kernels on an
+ * asynchronous event (an mbarrier completed by the tensor cores, a grid barrier) polls a bounded
+ * number of times; one that runs out records an error that the host reports as CH_ERR_TIMEOUT,
+ * and the kernel returns, so a lost event never hangs the device. This call launches one block
+ * that waits, with that same routine and at most spin_limit polls (1 .. 2^26), on an mbarrier
+ * that expects one arrival and that no thread ever arrives on. Returns CH_ERR_TIMEOUT when the
+ * wait gave up and the kernel returned (the expected outcome; the context stays usable),
+ * CH_ERR_INVALID for a spin_limit out of range, CH_ERR_OOM / CH_ERR_CUDA otherwise.
+ * Synchronises `cuda_stream`. */
+ch_status ch_wait_selftest(unsigned spin_limit, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -7,10 +7,10 @@ package is the thin Python binding of that ABI.
 """
 from ._lib import (CH_GTHETA_PARAMS, CH_MAX_ITERS, EXPORTED_SYMBOLS, SCHEMES, STATUS, VARIANTS, ChError, Config,
                    Ensemble, GTheta, Parareal, gtheta_flatten, gtheta_unflatten, load, propagate, sine_transform_2d,
-                   theory_bound)
+                   theory_bound, wait_selftest)
 from .build import LIB as LIBRARY_PATH
 from .build import build
 
 __all__ = ["CH_GTHETA_PARAMS", "CH_MAX_ITERS", "EXPORTED_SYMBOLS", "SCHEMES", "STATUS", "VARIANTS", "ChError",
            "Config", "Ensemble", "GTheta", "Parareal", "gtheta_flatten", "gtheta_unflatten", "load", "propagate",
-           "sine_transform_2d", "theory_bound", "build", "LIBRARY_PATH"]
+           "sine_transform_2d", "theory_bound", "wait_selftest", "build", "LIBRARY_PATH"]

@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "ch_gtheta_train", "ch_ensemble_create", "ch_ensemble_set_initial", "ch_ensemble_compute_reference",
     "ch_ensemble_run", "ch_ensemble_get_slices", "ch_ensemble_get_reference", "ch_ensemble_get_stats",
     "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_parareal_theory_bound",
-    "ch_parareal_set_fine_nn",
+    "ch_parareal_set_fine_nn", "ch_wait_selftest",
 ]
 _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
               "ch_gtheta_last_error", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_ensemble_groups")
@@ -57,7 +57,7 @@ class _Config(C.Structure):
                 ("n_slices", C.c_int), ("fine_steps", C.c_int), ("coarse_steps", C.c_int),
                 ("variant", C.c_int), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("tol", C.c_double), ("max_iters", C.c_int), ("precision", C.c_int), ("frozen", C.c_int),
-                ("err_tol", C.c_double)]
+                ("err_tol", C.c_double), ("lin_tol", C.c_double), ("lin_max", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -87,12 +87,14 @@ class Config:
     frozen: bool = False
     err_tol: float = 0.0
     dim: int = 1
+    lin_tol: float = 0.0  # 2D inner CG reduction factor (<= 0: 1e-4)
+    lin_max: int = 0      # 2D inner CG iterations at most (<= 0: 60)
 
     def c(self) -> _Config:
         mi = self.n_slices if self.max_iters < 0 else self.max_iters
         return _Config(self.dim, self.n, self.eps, self.T, self.n_slices, self.fine_steps, self.coarse_steps,
                        VARIANTS[self.variant], self.newton_tol, self.newton_max, self.tol, mi, self.precision,
-                       int(self.frozen), self.err_tol)
+                       int(self.frozen), self.err_tol, self.lin_tol, self.lin_max)
 
 
 _lib = None
@@ -131,6 +133,7 @@ def load(build_if_missing: bool = True):
     lib.ch_sine_transform_2d.argtypes = [vp, vp, C.c_int, C.c_int, vp]
     lib.ch_parareal_theory_bound.argtypes = [C.POINTER(_Config), C.c_double, C.c_int, d, sz, vp]
     lib.ch_parareal_set_fine_nn.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int]
+    lib.ch_wait_selftest.argtypes = [C.c_uint, vp]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     f = C.POINTER(C.c_float)
     lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz, C.c_int]
@@ -332,6 +335,13 @@ def propagate(cfg: Config, scheme: str, dt: float, nsteps: int, u_in, u_out=None
     if s != 0:
         raise ChError(s, "ch_propagate")
     return u_out
+
+
+def wait_selftest(spin_limit: int = 2000, stream=None) -> str:
+    """Runs ch_wait_selftest (a bounded wait that nothing satisfies) and returns the status name;
+    CH_ERR_TIMEOUT is the expected outcome."""
+    lib = load()
+    return STATUS.get(lib.ch_wait_selftest(spin_limit, _stream_ptr(stream)), "unknown")
 
 
 def theory_bound(cfg: Config, kmax: int, lte_const: float = 0.0, stream=None):

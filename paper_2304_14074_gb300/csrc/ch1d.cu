@@ -16,6 +16,7 @@
 #include <set>
 #include <utility>
 
+#include "ch_ctx.cuh"
 #include "ch1d.cuh"
 #include "ch_block_solver.cuh"
 
@@ -713,11 +714,11 @@ __global__ void __launch_bounds__(T) k_propagate(Params1D p, int scheme, double 
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
   static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
+  static std::set<std::pair<const void*, unsigned long long>> done;  // (kernel, context)
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), chctx::cache_key());
   if (done.count(key)) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) done.insert(key);

@@ -35,6 +35,7 @@
 #include <utility>
 #include <vector>
 
+#include "ch_ctx.cuh"
 #include "ch2d.cuh"
 
 namespace chg2 {
@@ -276,11 +277,11 @@ __global__ void k2_loop_start(cudaGraphConditionalHandle hnd, int* __restrict__ 
 template <typename K>
 cudaError_t prep(K kernel, size_t smem) {
   static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
+  static std::set<std::pair<const void*, unsigned long long>> done;  // (kernel, context)
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), chctx::cache_key());
   if (done.count(key)) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) done.insert(key);

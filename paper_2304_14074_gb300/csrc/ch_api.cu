@@ -16,6 +16,7 @@
 #include "ch1d.cuh"
 #include "ch2d.cuh"
 #include "ch_parareal.h"
+#include "ch_config_check.h"
 #include "gtheta.cuh"
 
 using chg::Ctrl;
@@ -90,6 +91,15 @@ ch_status fail(ch_parareal* h, ch_status s, const std::string& m) {
   return s;
 }
 
+// A Newton or linear-solve failure is a property of the data that was propagated, not of the
+// handle: new initial states clear it. Every other error stays.
+void clear_data_error(ch_parareal* h) {
+  if (h->sticky == CH_ERR_NEWTON || h->sticky == CH_ERR_LINSOLVE) {
+    h->sticky = CH_OK;
+    h->msg.clear();
+  }
+}
+
 ch_status cuda_fail(ch_parareal* h, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
   if (e == cudaErrorMemoryAllocation) return fail(h, CH_ERR_OOM, m);
@@ -105,17 +115,7 @@ ch_status cuda_fail(ch_parareal* h, cudaError_t e, const char* where) {
 int fine_of(int v) { return (v == CH_PA_I) ? chg::SCHEME_LIN1 : (v == CH_NPA_I || v == CH_NPA_II) ? chg::SCHEME_NL : chg::SCHEME_LIN2; }
 int coarse_of(int v) { return (v == CH_PA_II) ? chg::SCHEME_LIN2 : (v == CH_NPA_II) ? chg::SCHEME_NL : chg::SCHEME_LIN1; }
 
-bool valid_common(const ch_config* c, std::string& why) {
-  if (!c) { why = "cfg is NULL"; return false; }
-  if (c->dim != 1 && c->dim != 2) { why = "dim must be 1 or 2"; return false; }
-  if (c->dim == 1 && (c->n < 1 || c->n > 2048)) { why = "n must be in 1..2048"; return false; }
-  if (c->dim == 2 && !chg2::supported_n(c->n)) { why = "2D needs n + 1 in {16, 32, ..., 512}"; return false; }
-  if (!(c->eps > 0.0) || !std::isfinite(c->eps)) { why = "eps must be > 0"; return false; }
-  if (c->newton_max < 1 || c->newton_max > 1000) { why = "newton_max must be in 1..1000"; return false; }
-  if (!(c->newton_tol > 0.0)) { why = "newton_tol must be > 0"; return false; }
-  if (c->precision != 0 && c->precision != 1) { why = "precision must be 0 or 1"; return false; }
-  return true;
-}
+bool valid_common(const ch_config* c, std::string& why) { return chcfg::valid_common(c, chg2::supported_n, why); }
 
 Params1D make_params(const ch_config* c, int B) {
   Params1D p{};
@@ -146,13 +146,14 @@ chg2::Params2D params2d(const ch_config* c) {
   q.n = c->n;
   q.frozen = c->frozen ? 1 : 0;
   q.newton_max = c->newton_max;
-  // Inexact Newton: each CG solve reduces the preconditioned residual by 1e-4; the Newton
-  // error then contracts by ~1e-4 per iteration down to the FP64 residual floor.
-  q.cg_max = 60;
+  // Inexact Newton: each CG solve reduces the preconditioned residual by lin_tol (default 1e-4);
+  // the Newton error then contracts by about that factor per iteration down to the FP64
+  // residual floor.
+  q.cg_max = chcfg::lin_max_of(c);
   q.eps2 = c->eps * c->eps;
   q.h = 1.0 / (c->n + 1);
   q.newton_tol = c->newton_tol;
-  q.cg_tol = 1e-4;
+  q.cg_tol = chcfg::lin_tol_of(c);
   return q;
 }
 
@@ -636,11 +637,7 @@ ch_status ch_parareal_create(const ch_config* cfg, int batch, void* cuda_stream,
   if (!out) return CH_ERR_INVALID;
   *out = nullptr;
   std::string why;
-  if (!valid_common(cfg, why)) return CH_ERR_INVALID;
-  if (batch < 1 || cfg->n_slices < 1 || cfg->n_slices > CH_MAX_ITERS - 1 || cfg->fine_steps < 1 ||
-      cfg->coarse_steps < 1 || !(cfg->T > 0.0) || cfg->variant < CH_PA_I || cfg->variant > CH_NPA_II ||
-      cfg->max_iters < 1 || cfg->max_iters > cfg->n_slices)
-    return CH_ERR_INVALID;
+  if (!chcfg::valid_run(cfg, chg2::supported_n, why) || batch < 1) return CH_ERR_INVALID;
   ch_parareal* h = new (std::nothrow) ch_parareal();
   if (!h) return CH_ERR_OOM;
   (void)cudaGetLastError();  // a stale non-sticky error of an earlier call must not fail this one
@@ -716,6 +713,7 @@ ch_status ch_parareal_set_initial(ch_parareal* h, int problem, const double* u0_
   CH_CUDA(h, cudaStreamSynchronize(h->st));
   h->initial_set[problem] = 1;
   h->ref_valid = false;
+  clear_data_error(h);
   return CH_OK;
 }
 
@@ -726,6 +724,7 @@ ch_status ch_parareal_set_initial_device(ch_parareal* h, const double* u0_dev, s
                                h->pts * sizeof(double), h->B, cudaMemcpyDeviceToDevice, h->st));
   for (auto& v : h->initial_set) v = 1;
   h->ref_valid = false;
+  clear_data_error(h);
   return CH_OK;
 }
 
@@ -736,6 +735,7 @@ ch_status ch_parareal_set_initial_batch(ch_parareal* h, const double* u0_host, s
                                h->pts * sizeof(double), h->B, cudaMemcpyHostToDevice, h->st));
   for (auto& v : h->initial_set) v = 1;
   h->ref_valid = false;
+  clear_data_error(h);
   return CH_OK;
 }
 
@@ -1013,6 +1013,7 @@ ch_status ch_parareal_set_eps(ch_parareal* h, const double* eps_host, size_t len
   h->eps_prob.assign(eps_host, eps_host + len);
   h->p2->set_unit_eps2(h->eps2u_dev);
   h->ref_valid = false;
+  clear_data_error(h);
   return CH_OK;
 }
 
@@ -1044,6 +1045,7 @@ ch_status ch_parareal_set_fine_nn(ch_parareal* h, int n_sub, double theta, doubl
     h->gfine = nullptr;
   }
   h->ref_valid = false;
+  clear_data_error(h);
   return CH_OK;
 }
 

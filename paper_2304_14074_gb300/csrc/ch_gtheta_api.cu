@@ -5,6 +5,7 @@
 #include <string>
 
 #include "ch_parareal.h"
+#include "ch_wait.cuh"
 #include "gtheta.cuh"
 
 static_assert(CH_GTHETA_PARAMS == chg3::kParams, "parameter count");
@@ -30,6 +31,26 @@ ch_status gcuda(ch_gtheta* g, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return CH_OK;
   const std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
   return gfail(g, e == cudaErrorMemoryAllocation ? CH_ERR_OOM : CH_ERR_CUDA, m);
+}
+
+// A bounded tensor-core wait that gave up (tcgen05 path) makes the handle refuse further work.
+ch_status check_waits(ch_gtheta* g) {
+  if (g->net.wait_failures(g->st))
+    return gfail(g, CH_ERR_TIMEOUT, "a bounded wait of the tensor-core convolution gave up");
+  return CH_OK;
+}
+
+__global__ void k_wait_selftest(unsigned limit, int* out) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(&bar));
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  __syncthreads();
+  // expected arrivals: 1; no thread arrives, so phase 0 never completes
+  const bool ok = chwait::mbar_wait(mb, 0u, limit);
+  if (threadIdx.x == 0) *out = ok ? 1 : 2;
 }
 
 }  // namespace
@@ -98,6 +119,7 @@ ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* ta
   float loss = 0.f;
   s = gcuda(g, g->net.read_losses(&loss, 1, g->st), "gradients: loss");
   if (s == CH_OK && loss_host) *loss_host = loss;
+  if (s == CH_OK) s = check_waits(g);
   return s;
 }
 
@@ -112,7 +134,27 @@ ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, const double* 
   ch_status s =
       gcuda(g, g->net.train(states_dev, base_dev, ntraj, nsnap, n, stride, steps, batch, lr, seed, g->st), "train");
   if (s == CH_OK && losses_host) s = gcuda(g, g->net.read_losses(losses_host, steps, g->st), "train: losses");
+  if (s == CH_OK) s = check_waits(g);
   return s;
+}
+
+ch_status ch_wait_selftest(unsigned spin_limit, void* cuda_stream) {
+  if (spin_limit < 1 || spin_limit > (1u << 26)) return CH_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  (void)cudaGetLastError();
+  int* out = nullptr;
+  if (cudaMalloc(&out, sizeof(int)) != cudaSuccess) return CH_ERR_OOM;
+  int v = 0;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, st>>>(spin_limit, out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(out);
+  if (e != cudaSuccess) return CH_ERR_CUDA;
+  return v == 2 ? CH_ERR_TIMEOUT : (v == 1 ? CH_OK : CH_ERR_CUDA);
 }
 
 }  // extern "C"

@@ -23,6 +23,7 @@
 #include <mutex>
 #include <set>
 
+#include "ch_ctx.cuh"
 #include "ch1d.cuh"
 
 namespace chg {
@@ -321,12 +322,12 @@ constexpr size_t kNNMaxSmem = 200 * 1024;
 template <typename K>
 cudaError_t nn_prep(K kernel) {
   static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
+  static std::set<std::pair<const void*, unsigned long long>> done;  // (kernel, context)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), chctx::cache_key());
   if (done.count(key)) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNNMaxSmem);
   if (e == cudaSuccess) done.insert(key);

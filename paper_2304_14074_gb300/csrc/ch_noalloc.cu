@@ -10,8 +10,12 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 
 #include "ch1d.cuh"
+#include "ch2d.cuh"
+#include "ch_config_check.h"
+#include "ch_ctx.cuh"
 #include "ch_parareal.h"
 
 namespace {
@@ -20,23 +24,39 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[CH_NOALLOC_SCRA
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;  // context the address was looked up in (0: none)
+  void* addr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the scratch array on the current device. Host code must not use the
-// symbol itself (it is a host-side stand-in); the address is looked up once per device.
+// Device address of the scratch array in the current device's current context. Host code must
+// not use the symbol itself (it is a host-side stand-in). The address is looked up once per
+// device (cudaGetSymbolAddress, with that device current) and again whenever that device's
+// context has changed since, e.g. after cudaDeviceReset, which may reload the module at another
+// address. Where the driver cannot identify the context, every call looks it up.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+  const unsigned long long id = chctx::current_id();
+  if (id) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch[dev].ctx_id == id && g_scratch[dev].addr) {
+      *out = g_scratch[dev].addr;
+      return cudaSuccess;
+    }
   }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  if (id != 0) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_scratch[dev].ctx_id = id;
+    g_scratch[dev].addr = p;
+  }
+  *out = p;
   return cudaSuccess;
 }
 
@@ -52,12 +72,8 @@ extern "C" ch_status ch_parareal_solve_noalloc(const ch_config* cfg, int batch, 
                                                double* U_dev, size_t len, int* iterations_host,
                                                void* cuda_stream) {
   if (!cfg || !u0_dev || !U_dev || batch < 1) return CH_ERR_INVALID;
-  if (cfg->dim != 1 || cfg->n < 1 || cfg->n > 2048 || !(cfg->eps > 0.0) || !(cfg->T > 0.0) ||
-      cfg->n_slices < 1 || cfg->n_slices > CH_MAX_ITERS - 1 || cfg->fine_steps < 1 || cfg->coarse_steps < 1 ||
-      cfg->variant < CH_PA_I || cfg->variant > CH_NPA_II || cfg->max_iters < 1 ||
-      cfg->max_iters > cfg->n_slices || cfg->newton_max < 1 || cfg->newton_max > 1000 ||
-      !(cfg->newton_tol > 0.0) || (cfg->precision != 0 && cfg->precision != 1))
-    return CH_ERR_INVALID;
+  std::string why;
+  if (!chcfg::valid_run(cfg, chg2::supported_n, why) || cfg->dim != 1) return CH_ERR_INVALID;
   const size_t B = batch, N = cfg->n_slices, n = cfg->n, maxit = cfg->max_iters;
   if (len != B * (N + 1) * n) return CH_ERR_INVALID;
   if (CH_NOALLOC_SCRATCH_NEEDED(B, N, n, maxit) > CH_NOALLOC_SCRATCH_BYTES) return CH_ERR_INVALID;

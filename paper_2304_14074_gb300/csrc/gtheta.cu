@@ -21,11 +21,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
 #include <vector>
 
+#include "ch_ctx.cuh"
+#include "ch_wait.cuh"
 #include "gtheta.cuh"
 
 namespace chg3 {
@@ -233,7 +236,6 @@ constexpr size_t kConvTcSmem = (2 * kHaloTc + 9 * 4 * kC * 8) * sizeof(bf16) + 6
 constexpr size_t kTcStartMax = (size_t)kHaloTc * 2 + 2 * kHaloChunk * 2 + 2 * kHalo * 16 + 10 * 16;
 static_assert(kTcStartMax + 15 * kHalo * 16 + (size_t)kHaloChunk * 2 + 128 <= (size_t)2 * kHaloTc * 2,
               "descriptor reach");
-constexpr unsigned kWaitSpins = 1u << 22;
 
 __device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
   uint64_t d = 0;
@@ -349,11 +351,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
 #pragma unroll
   for (int c = 0; c < kC; ++c) bv[c] = (mode == 0) ? bias[c] : 0.f;
   unsigned phase[2] = {0u, 0u};
+  int issued = 0;  // tiles whose MMAs have been issued (and committed)
+  int fail_at = -1;
   if (count > 0) {
     cp_async_wait<1>();  // tile 0's halo
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
     __syncthreads();
     issue(0);
+    issued = 1;
   }
   for (int j = 0; j < count; ++j) {
     // (a) the next tile's MMAs, as soon as its halo is in
@@ -362,24 +367,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
       asm volatile("fence.proxy.async.shared::cta;\n" ::);
       __syncthreads();
       issue(j + 1);
+      issued = j + 2;
     }
     // (b) this tile's MMAs done (bounded wait): its halo buffer and accumulators are free to read
     const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (j & 1)));
-    unsigned done = 0, spins = 0;
-    while (!done) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\t"
-          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}\n"
-          : "=r"(done)
-          : "r"(mb), "r"(phase[j & 1]));
-      if (!done && ++spins > kWaitSpins) break;
-    }
-    if (!done) s_fail = 1;
-    phase[j & 1] ^= 1u;
+    if (!chwait::mbar_wait(mb, phase[j & 1], chwait::kSpins)) s_fail = 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     __syncthreads();
-    if (s_fail) break;
+    if (s_fail) {
+      fail_at = j;  // tile j's phase has not been consumed
+      break;
+    }
+    phase[j & 1] ^= 1u;
     // (c) the halo of tile j + 2 into the buffer tile j used
     if (j + 2 < count) prefetch(j + 2);
     cp_async_commit();
@@ -429,7 +428,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
     __syncthreads();  // accumulators of tile j read before tile j + 2's MMAs overwrite them
   }
   cp_async_wait<0>();
-  if (s_fail && threadIdx.x == 0) atomicExch(err, 1);
+  if (fail_at >= 0 && threadIdx.x == 0) {
+    atomicExch(err, 1);
+    // Issue no more MMAs; let those already issued finish (a second, longer bounded wait)
+    // before their accumulator columns are freed.
+    for (int t = fail_at; t < issued; ++t) {
+      const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (t & 1)));
+      if (!chwait::mbar_wait(mb, phase[t & 1], chwait::kDrainSpins)) break;
+      phase[t & 1] ^= 1u;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
 }
@@ -770,38 +779,46 @@ __global__ void k_crops(const double* __restrict__ states, const double* __restr
 // tcgen05 launch of the 32 -> 32 convolution (persistent, like k_conv_mid).
 void conv_mid_tc(const bf16* x, bf16* y, const bf16* W, const float* bias, const bf16* mask, int batch, int S,
                  int mode, int* err, cudaStream_t st) {
-  static int slots[64] = {};
+  static std::mutex mu;
+  static std::map<unsigned long long, int> slot_of;  // resident CTAs per context
   int dev = 0;
   cudaGetDevice(&dev);
-  dev &= 63;
-  if (slots[dev] == 0) {
+  std::unique_lock<std::mutex> lock(mu);
+  int& slots = slot_of[chctx::cache_key()];
+  if (slots == 0) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_conv_mid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvTcSmem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_mid_tc, kThreads, kConvTcSmem);
-    slots[dev] = std::max(1, sms * std::max(1, std::min(per_sm, 4)));
+    slots = std::max(1, sms * std::max(1, std::min(per_sm, 4)));
   }
   const int tx = (S + kTile - 1) / kTile, tiles = tx * tx * batch;
-  k_conv_mid_tc<<<std::min(tiles, slots[dev]), kThreads, kConvTcSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode,
+  const int grid = std::min(tiles, slots);
+  lock.unlock();
+  k_conv_mid_tc<<<grid, kThreads, kConvTcSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode,
                                                                             err);
 }
 
 // Persistent launch of k_conv_mid: as many CTAs as fit on the GPU (at most one per tile).
 void conv_mid(const bf16* x, bf16* y, const bf16* W, const float* bias, const bf16* mask, int batch, int S, int mode,
               cudaStream_t st) {
-  static int slots[64] = {};  // resident CTAs of k_conv_mid, per device
+  static std::mutex mu;
+  static std::map<unsigned long long, int> slot_of;  // resident CTAs of k_conv_mid per context
   int dev = 0;
   cudaGetDevice(&dev);
-  dev &= 63;
-  if (slots[dev] == 0) {
+  std::unique_lock<std::mutex> lock(mu);
+  int& slots = slot_of[chctx::cache_key()];
+  if (slots == 0) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_conv_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_mid, kThreads, kConvSmem);
-    slots[dev] = std::max(1, sms * std::max(1, per_sm));
+    slots = std::max(1, sms * std::max(1, per_sm));
   }
   const int tx = (S + kTile - 1) / kTile, tiles = tx * tx * batch;
-  k_conv_mid<<<std::min(tiles, slots[dev]), kThreads, kConvSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode);
+  const int grid = std::min(tiles, slots);
+  lock.unlock();
+  k_conv_mid<<<grid, kThreads, kConvSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode);
 }
 
 uint64_t splitmix(uint64_t& s) {

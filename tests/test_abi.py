@@ -45,10 +45,14 @@ def _cfg(**kw):
     return ch.Config(**base).c()
 
 
-@pytest.mark.parametrize("bad", [dict(dim=2), dict(n=0), dict(n=5000), dict(eps=0.0), dict(T=-1.0),
-                                 dict(n_slices=0), dict(fine_steps=0), dict(coarse_steps=0),
-                                 dict(max_iters=9), dict(precision=3), dict(newton_tol=0.0),
-                                 dict(variant="PA-I", newton_max=0)])
+BAD_CONFIGS = [dict(dim=2), dict(n=0), dict(n=5000), dict(eps=0.0), dict(eps=float("inf")), dict(T=-1.0),
+               dict(T=float("nan")), dict(n_slices=0), dict(fine_steps=0), dict(coarse_steps=0),
+               dict(max_iters=9), dict(precision=3), dict(newton_tol=0.0), dict(newton_tol=float("inf")),
+               dict(variant="PA-I", newton_max=0), dict(tol=float("nan")), dict(err_tol=float("inf")),
+               dict(lin_tol=1.0), dict(lin_tol=float("nan")), dict(lin_max=20000)]
+
+
+@pytest.mark.parametrize("bad", BAD_CONFIGS)
 def test_create_rejects_invalid_config_without_device(bad):
     lib = ch.load()
     cc = _cfg(**bad)
@@ -105,10 +109,26 @@ def test_destroy_accepts_null_and_last_error_on_null():
     assert lib.ch_parareal_last_error(None).decode() == "NULL handle"
 
 
-def test_binding_struct_layout_matches_header():
-    # ch_config: 2 ints, 2 doubles, 4 ints, double, int, double, 3 ints, double -> 88 bytes with padding
-    assert C.sizeof(_lib._Config) == 88
-    assert C.sizeof(_lib._Stats) == 8 + 4 * 8 * ch.CH_MAX_ITERS + 8 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 4 + 4
+def test_binding_struct_layout_matches_header(tmp_path):
+    """Sizes and field offsets of the ctypes structures equal those the C compiler gives the
+    header's structs."""
+    import subprocess
+    fields = {"ch_config": [f for f, _ in _lib._Config._fields_], "ch_stats": [f for f, _ in _lib._Stats._fields_]}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "ch_parareal.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        src.append(f'  printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            src.append(f'  printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    src += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, cls in (("ch_config", _lib._Config), ("ch_stats", _lib._Stats)):
+        assert int(got[st]) == C.sizeof(cls), st
+        for f in fields[st]:
+            assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
 
 
 def test_gtheta_entry_points_reject_invalid_arguments_without_device():
@@ -143,3 +163,15 @@ def test_gtheta_parameter_layout_matches_header():
     assert W[0].shape == (3, 3, 32, 1) and W[5].shape == (3, 3, 1, 32) and b[5].shape == (1,)
     assert W[1][0, 0, 0, 1] == 320 + 1 and b[0][0] == 288  # W_l[dy][dx][co][ci] then b_l
     assert np.array_equal(ch.gtheta_flatten(W, b), p)
+
+
+@pytest.mark.parametrize("bad", BAD_CONFIGS + [dict(dim=2, n=31)])
+def test_noalloc_rejects_invalid_config_without_device(bad):
+    """The allocation-free entry point applies the same checks as ch_parareal_create (plus
+    dim = 1) before it touches the device."""
+    lib = ch.load()
+    cc = _cfg(**bad)
+    nd = cc.n ** cc.dim if cc.n > 0 else 1
+    ns = max(cc.n_slices, 1)
+    s = lib.ch_parareal_solve_noalloc(C.byref(cc), 1, C.c_void_p(8), C.c_void_p(8), (ns + 1) * nd, None, None)
+    assert s == 1

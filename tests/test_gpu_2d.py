@@ -85,7 +85,7 @@ def oracle_params(cfg):
                      frozen=cfg.frozen, tol=cfg.tol)
 
 
-@pytest.mark.parametrize("variant", ["PA-I", "NPA-I", "PA-III"])
+@pytest.mark.parametrize("variant", ["PA-I", "PA-II", "PA-III", "NPA-I", "NPA-II"])
 def test_parareal_2d_matches_oracle_and_is_exact_at_k_equal_n(gpu_lib, variant):
     ch = gpu_lib
     n, N = 31, 4
