@@ -51,6 +51,11 @@ WORKLOADS = {
     "c4": dict(name="2D nonlinear Parareal NPA-I 512x512 grid (n=511) eps=0.01 T=2 N=64 J=100 u0=0.05*N(0,1) seed 2000",
                dim=2, n=511, eps=0.01, T=2.0, N=64, J=100, batch=1, variant="NPA-I", newton_tol=1e-12,
                amp=0.05, kind="normal", seed0=2000, precision=1, ttol=False),
+    # profiling case of the 2D kernels at the 512 x 512 grid: c4's grid, slices and step size,
+    # 2 fine steps per slice
+    "c4-profile": dict(name="2D NPA-I 512x512 (n=511) eps=0.01 N=64 J=2 (dt as c4), profiling case",
+                       dim=2, n=511, eps=0.01, T=0.04, N=64, J=2, batch=1, variant="NPA-I", newton_tol=1e-12,
+                       amp=0.05, kind="normal", seed0=2000, precision=1, ttol=False),
     "c1": dict(name="1D linear Parareal PA-I M=128 eps=0.05 T=0.1 N=16 dt=1e-5 batch=1",
                n=128, eps=0.05, T=0.1, N=16, J=625, batch=1, variant="PA-I", newton_tol=1e-12,
                amp=0.1, precision=0, ttol=True),
@@ -443,8 +448,9 @@ def roofline_2d(w, B, fine_ms_per_launch, newton_total, cg_total, share):
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
     field = 4 * pts * units  # one FP32 solver vector over all units
-    where = ("L2-resident (129 MB L2): HBM bandwidth is a bound, not the limit" if field < 100e6 else
-             "beyond L2: the sweeps stream from HBM")
+    work = 9 * field         # the CG's FP32 vectors (x, r, p, u, s, w, weights, two transform buffers)
+    where = ("its working set fits the 129 MB L2: HBM bandwidth is a bound, not the limit" if work < 100e6 else
+             "its working set is beyond the 129 MB L2: the sweeps stream from HBM")
     return {"bound": "hbm", "kernel": "2D fine sweep (sine-transform passes + pointwise sweeps)",
             "workload": w["name"], "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
@@ -456,7 +462,8 @@ def roofline_2d(w, B, fine_ms_per_launch, newton_total, cg_total, share):
             "newton_iterations_per_unit_step": round(newton_total / (units * J), 3),
             "cg_iterations_per_unit_step": round(cg_total / (units * J), 3),
             "algorithmic_bytes_per_launch": alg_bytes,
-            "note": f"one FP32 solver vector over all {units} units is {field / 1e6:.1f} MB: {where}"}
+            "note": f"one FP32 solver vector over all {units} units is {field / 1e6:.1f} MB and the CG "
+                    f"touches about nine ({work / 1e6:.0f} MB): {where}"}
 
 
 def c4_step_roofline(ch, stream, warmup=1, steps=1):
@@ -491,6 +498,45 @@ def c4_step_roofline(ch, stream, warmup=1, steps=1):
     r["step_ms"] = round(step_ms, 2)
     r["grid_pt_steps_per_s"] = w["N"] * w["J"] * w["n"] ** 2 / (step_ms / 1e3)
     return r
+
+
+def sweep2d(w, args):
+    """The fine propagation of all N slices of a 2D workload as one batched ch_propagate call
+    (the kernels of a Parareal fine sweep, without the coarse sweeps), `args.fine` fine steps from
+    the slice states of a short fine trajectory, timed with CUDA events; HBM roofline against the
+    algorithmic bytes."""
+    import numpy as np
+    import torch
+
+    import ch_inputs
+    import paper_2304_14074_gb300 as ch
+    torch.cuda.set_device(0)
+    n, N, J = w["n"], w["N"], w["J"]
+    dt = w["T"] / N / J
+    u0 = np.stack([ch_inputs.initial_condition(2, n, w.get("seed0", 0) + s, kind="normal", amp=w["amp"])
+                   for s in range(N)])
+    cfg = ch.Config(dim=2, n=n, eps=w["eps"], T=w["T"], n_slices=N, fine_steps=J, newton_tol=w["newton_tol"])
+    X0 = torch.as_tensor(u0, device="cuda")
+    # start from states past the initial transient (a few fine steps), as the slices of a sweep
+    X0 = ch.propagate(cfg, "nl", dt, 8, X0)
+    newton = torch.zeros(N, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        ch.propagate(cfg, "nl", dt, args.fine, X0)
+    torch.cuda.synchronize()
+    ms = []
+    tot_newton = 0
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ch.propagate(cfg, "nl", dt, args.fine, X0, newton=newton)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        tot_newton += int(newton.sum().item())
+    t = sum(ms) / len(ms)
+    return {"experiment": "sweep2d", "workload": w["name"], "units": N, "fine_steps": args.fine,
+            "ms_per_propagation": round(t, 3), "grid_pt_steps_per_s": N * args.fine * n * n / (t / 1e3),
+            "newton_per_unit_step": tot_newton / (args.steps * N * args.fine)}
 
 
 def measured_peaks():
@@ -555,11 +601,15 @@ def theory_vs_measured(ch, w, u0, stream, ratio_actual):
             "measured_scheme": [float("%.4g" % r) for r in ratio_actual[:kmax]]}
 
 
-# Learned against plain coarse propagator, time to 1e-8: a 2D problem small enough to train G_theta
-# and run both Parareal forms within the benchmark (the 512^2, N = 64 configuration takes tens of
-# minutes per form).
+# Learned against plain coarse propagator, time to 1e-8. LEARNED_CASE is small enough to train
+# G_theta and run both Parareal forms inside the default benchmark; LEARNED_C4 is the 512 x 512
+# configuration (eps = 0.01, T = 2, N = 64, J = 100) with 64 training trajectories (seeds
+# 1000..1063) snapshotted every dT / 5: 64 x 315 = 20160 pairs (U(t), U(t + dT)), plus perturbed
+# pairs, evaluated from the held-out seed 2000 (run by `--experiment learned-c4`).
 LEARNED_CASE = dict(n=63, eps=0.05, T=0.3, N=16, J=8, stride=4, train_seeds=64, eval_seed=5000,
-                    steps=((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)), batch=32)
+                    steps=((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)), batch=32, perturbed=None, chunk=4096)
+LEARNED_C4 = dict(n=511, eps=0.01, T=2.0, N=64, J=100, stride=5, train_seeds=64, eval_seed=2000,
+                  steps=((1e-3, 12000), (3e-4, 8000), (1e-4, 4000)), batch=32, perturbed=512, chunk=512)
 
 
 # G_theta forward arithmetic per pixel: four 32 -> 32 layers (2 x 32 x 288 flops each) and the
@@ -588,49 +638,62 @@ def gtheta_forward_roofline(ch, net, batch=8, n=511):
     achieved = flops / (ms / 1e3) / 1e12
     return {"bound": "tensor", "workload": f"G_theta forward, {batch} fields of {n}^2", "ms": round(ms, 4),
             "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)" if "bf16_tflops" in measured_peaks()
+                            else "fallback 1.9 PFLOP/s bf16 (no MEASURED_PEAKS.json)"),
             "algorithmic_flops_per_pixel": GTHETA_FLOPS_PER_PIXEL}
 
 
-def learned_vs_plain(ch, stream, err_tol=1e-8):
-    """Trains G_theta (correction form G(U) + R(U)) on fine-solver snapshot pairs and on pairs
-    from perturbed snapshots, all produced by the library on the GPU, then runs Parareal to
-    err_tol with the plain and with the learned coarse step from a held-out initial condition."""
+def _propagate_chunked(ch, cfg, scheme, dt, nsteps, X, chunk):
+    """ch.propagate over the rows of X in chunks of `chunk` fields (bounds the solver's work space)."""
+    import torch
+    out = torch.empty_like(X)
+    for i in range(0, X.shape[0], chunk):
+        ch.propagate(cfg, scheme, dt, nsteps, X[i:i + chunk].contiguous(), out[i:i + chunk])
+    return out
+
+
+def learned_vs_plain(ch, stream, err_tol=1e-8, case=None):
+    """Trains G_theta (correction form G(U) + R(U)) on fine-solver snapshot pairs (and, when the case
+    asks for them, on pairs from perturbed snapshots), all produced by the library on the GPU, then
+    runs Parareal to err_tol with the plain and with the learned coarse step from a held-out
+    initial condition."""
     import numpy as np
     import torch
 
     import ch_inputs
-    c = LEARNED_CASE
+    c = case or LEARNED_CASE
     n, eps, T, N, J, stride = c["n"], c["eps"], c["T"], c["N"], c["J"], c["stride"]
     dT = T / N
     t0 = time.perf_counter()
-    gen = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N * stride, fine_steps=J // stride, variant="NPA-I",
-                    newton_tol=1e-12)
     seeds = range(1000, 1000 + c["train_seeds"])
-    pr = ch.Parareal(gen, batch=len(seeds), stream=stream)
-    pr.set_initial_batch(np.stack([ch_inputs.initial_condition(2, n, s, kind="normal", amp=0.05) for s in seeds]))
-    pr.compute_reference()
-    states = torch.empty((len(seeds), N * stride + 1, n * n), dtype=torch.float64, device="cuda")
-    pr.get_reference_device(states)
-    pr.close()
     one = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
-    base = ch.propagate(one, "lin1", dT, 1, states.reshape(-1, n * n)).reshape(states.shape)
+    # training trajectories: the sequential fine solution of every seed, snapshotted every dT/stride
+    states = torch.empty((len(seeds), N * stride + 1, n * n), dtype=torch.float64, device="cuda")
+    states[:, 0] = torch.as_tensor(np.stack([ch_inputs.initial_condition(2, n, s, kind="normal", amp=0.05)
+                                             for s in seeds]), device="cuda")
+    for j in range(N * stride):
+        states[:, j + 1] = ch.propagate(one, "nl", dT / J, J // stride, states[:, j].contiguous())
+    base = _propagate_chunked(ch, one, "lin1", dT, 1, states.reshape(-1, n * n), c["chunk"]).reshape(states.shape)
     # perturbed pairs (U + eta, F(U + eta)) around the slice-boundary states teach the step's
     # response to perturbations, which is what the Parareal correction differences
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     X = states[:, ::stride].reshape(-1, n * n)
+    if c.get("perturbed"):
+        idx = torch.randperm(X.shape[0], generator=g, device="cuda")[:c["perturbed"]]
+        X = X[idx]
     pairs = []
-    for amp, smooth in ((0.05, False), (0.2, True), (0.05, True)):
+    kinds = ((0.05, False), (0.2, True), (0.05, True)) if not c.get("perturbed") else ((0.2, True), (0.05, False))
+    for amp, smooth in kinds:
         eta = torch.randn(X.shape, device="cuda", dtype=torch.float64, generator=g)
         if smooth:
             for _ in range(3):
-                eta = ch.propagate(one, "lin1", dT, 1, eta.contiguous())
+                eta = _propagate_chunked(ch, one, "lin1", dT, 1, eta.contiguous(), c["chunk"])
             eta = eta / eta.abs().amax(dim=1, keepdim=True)
         Xp = (X + amp * eta).contiguous()
-        pairs.append(torch.stack([Xp, ch.propagate(one, "nl", dT / J, J, Xp)], 1))
+        pairs.append(torch.stack([Xp, _propagate_chunked(ch, one, "nl", dT / J, J, Xp, c["chunk"])], 1))
     pert = torch.cat(pairs).contiguous()
-    pbase = ch.propagate(one, "lin1", dT, 1, pert.reshape(-1, n * n)).reshape(pert.shape)
+    pbase = _propagate_chunked(ch, one, "lin1", dT, 1, pert.reshape(-1, n * n), c["chunk"]).reshape(pert.shape)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     net = ch.GTheta(seed=1)
@@ -646,6 +709,10 @@ def learned_vs_plain(ch, stream, err_tol=1e-8):
     t_train = time.perf_counter() - t1
     params = net.get_params()
     losses = np.concatenate(losses)
+    npairs = len(seeds) * (N * stride - stride + 1)
+    del base, pbase, pert, pairs
+    # one-step error of each coarse propagator on held-out states (slice boundaries of the
+    # evaluation trajectory), relative to the change F(U) - U over the slice
     cfg = ch.Config(dim=2, n=n, eps=eps, T=T, n_slices=N, fine_steps=J, variant="NPA-I", newton_tol=1e-12,
                     err_tol=err_tol)
     u0 = ch_inputs.initial_condition(2, n, c["eval_seed"], kind="normal", amp=0.05)[None]
@@ -656,6 +723,9 @@ def learned_vs_plain(ch, stream, err_tol=1e-8):
         h.compute_reference()
         if p is not None:
             h.set_coarse_model(p, "correction")
+        if name == "plain":
+            ref = torch.empty((1, N + 1, n * n), dtype=torch.float64, device="cuda")
+            h.get_reference_device(ref)
         st = h.run()
         s0 = h.stats(0)
         k = s0["iterations"]
@@ -664,12 +734,23 @@ def learned_vs_plain(ch, stream, err_tol=1e-8):
                      [float("%.3g" % v) for v in s0["err_l2"][:min(k, 6) + 1]],
                      "coarse_fallback_iter": int(s0["coarse_fallback_iter"])}
         h.close()
+    U = ref[0, :N].contiguous()
+    Fu = ref[0, 1:]
+    Gu = _propagate_chunked(ch, one, "lin1", dT, 1, U, c["chunk"])
+    Lu = torch.empty_like(U)
+    net.forward(U.view(N, n, n), out=Lu.view(N, n, n), base=Gu.view(N, n, n))
+    chg = (Fu - U).norm(dim=1)
+    out["one_step_error_rel_to_change"] = {
+        "plain": float(((Gu - Fu).norm(dim=1) / chg).median()),
+        "learned": float(((Lu - Fu).norm(dim=1) / chg).median()),
+        "over": f"the {N} slices of the held-out trajectory (median over slices)"}
     out["speedup_learned_over_plain"] = round(out["plain"]["seconds"] / max(out["learned"]["seconds"], 1e-9), 3)
     out["gtheta_forward_roofline"] = gtheta_forward_roofline(ch, net)
+    net.close()
     out["config"] = (f"2D NPA-I n={n} eps={eps} T={T} N={N} J={J}, u0 = 0.05 N(0,1) seed {c['eval_seed']}; "
                      f"G_theta correction form trained on {len(seeds)} trajectories (seeds 1000..) "
-                     f"x {N * stride - stride + 1} snapshot pairs + {pert.shape[0]} perturbed pairs, "
-                     f"{len(losses)} Adam steps")
+                     f"x {N * stride - stride + 1} = {npairs} snapshot pairs + {X.shape[0] * len(kinds)} perturbed "
+                     f"pairs, {len(losses)} Adam steps")
     out["data_seconds"] = round(t_data, 2)
     out["training_seconds"] = round(t_train, 2)
     out["final_training_loss"] = float(losses[-200:].mean())
@@ -690,7 +771,27 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain coarse propagator run")
     ap.add_argument("--no-2d", action="store_true", help="skip the 512 x 512 2D step (roofline_2d)")
+    ap.add_argument("--experiment", choices=["learned-c4", "sweep2d"], default=None,
+                    help="learned-c4: learned vs plain coarse propagator to 1e-8 on the 512 x 512 configuration "
+                         "(training included); sweep2d: the 2D fine propagation of one Parareal fine sweep of a 2D "
+                         "workload (all its slices batched), `--steps` times `--fine` steps, timed alone. One JSON "
+                         "line each.")
+    ap.add_argument("--fine", type=int, default=2, help="sweep2d: fine steps per timed propagation")
     args = ap.parse_args()
+    if args.experiment == "sweep2d":
+        print(json.dumps(sweep2d(WORKLOADS[args.workload if args.workload != "c2" else "c4"], args)))
+        return
+    if args.experiment == "learned-c4":
+        import torch
+
+        import paper_2304_14074_gb300 as ch
+        torch.cuda.set_device(0)
+        t = time.perf_counter()
+        r = learned_vs_plain(ch, torch.cuda.current_stream(), case=LEARNED_C4)
+        r["experiment"] = "learned-c4"
+        r["wall_seconds"] = round(time.perf_counter() - t, 1)
+        print(json.dumps(r))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     w = WORKLOADS[args.workload]

@@ -252,6 +252,12 @@ ch_status ch_gtheta_get_params(ch_gtheta* g, float* params_host, size_t len);
 ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, const double* base_dev, double* out_dev, int batch,
                             int n);
 
+/* The forward pass of `batch` FP64 n x n fields (device, [batch][n][n]) keeping every layer's
+ * output, for checking each layer on its own: acts_dev (device, FP32) receives the hidden
+ * activations a1..a5 as stored (BF16 values), [5][batch][n][n][32], followed by R(U)
+ * [batch][n][n]; len must be batch n^2 (5 * 32 + 1). Synchronises. */
+ch_status ch_gtheta_activations(ch_gtheta* g, const double* in_dev, int batch, int n, float* acts_dev, size_t len);
+
 /* Loss and gradients for one minibatch: in_dev, target_dev FP32 [batch][S][S] (device); loss =
  * mean over the batch and the window [margin, S - margin)^2 of (R(in) - target)^2.
  * grad_host: CH_GTHETA_PARAMS FP32 values in the parameter layout (len must match);

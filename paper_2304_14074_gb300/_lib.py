@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "ch_gtheta_train", "ch_ensemble_create", "ch_ensemble_set_initial", "ch_ensemble_compute_reference",
     "ch_ensemble_run", "ch_ensemble_get_slices", "ch_ensemble_get_reference", "ch_ensemble_get_stats",
     "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_parareal_theory_bound",
-    "ch_parareal_set_fine_nn", "ch_wait_selftest",
+    "ch_parareal_set_fine_nn", "ch_wait_selftest", "ch_gtheta_activations",
 ]
 _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
               "ch_gtheta_last_error", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_ensemble_groups")
@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True):
     lib.ch_parareal_theory_bound.argtypes = [C.POINTER(_Config), C.c_double, C.c_int, d, sz, vp]
     lib.ch_parareal_set_fine_nn.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int]
     lib.ch_wait_selftest.argtypes = [C.c_uint, vp]
+    lib.ch_gtheta_activations.argtypes = [vp, vp, C.c_int, C.c_int, vp, sz]
     lib.ch_parareal_solve_noalloc.argtypes = [C.POINTER(_Config), C.c_int, vp, vp, sz, C.POINTER(C.c_int), vp]
     f = C.POINTER(C.c_float)
     lib.ch_parareal_set_coarse_model.argtypes = [vp, f, sz, C.c_int]
@@ -404,6 +405,17 @@ class GTheta:
         self._check(self.lib.ch_gtheta_forward(self._h, _dptr(u_dev), _dptr(base) if base is not None else None,
                                                _dptr(out), u_dev.shape[0], u_dev.shape[-1]), "ch_gtheta_forward")
         return out
+
+    def activations(self, u_dev):
+        """Every layer's output for a CUDA float64 tensor [batch, n, n]: (a1..a5 as a float32 tensor
+        [5, batch, n, n, 32] holding the stored BF16 values, R as [batch, n, n])."""
+        import torch
+        B, n = u_dev.shape[0], u_dev.shape[-1]
+        out = torch.empty(B * n * n * (5 * 32 + 1), dtype=torch.float32, device=u_dev.device)
+        self._check(self.lib.ch_gtheta_activations(self._h, _dptr(u_dev), B, n, _dptr(out), out.numel()),
+                    "ch_gtheta_activations")
+        per = B * n * n * 32
+        return out[:5 * per].view(5, B, n, n, 32), out[5 * per:].view(B, n, n)
 
     def gradients(self, x_dev, target_dev, margin: int):
         """(loss, flat FP32 gradient) of one minibatch: CUDA float32 tensors [batch, S, S]."""

@@ -1137,6 +1137,7 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
     // range of the FP32 weights: exact in FP32 (min and max round nothing)
     float lo = INFINITY, hi = -INFINITY;
+    bool bad = false;  // a non-finite FP64 residual: the state or the step has failed
     for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
       double lz[U], yv[U], hv[U], w64[U];
 #pragma unroll
@@ -1154,7 +1155,9 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
       for (int q = 0; q < U; ++q) {
         const int e = e0 + q * kThreads;
         if (e < cnt) {
-          rhs[base + e] = float((yv[q] - hv[q]) + a.ih2 * lz[q]);
+          const float hq = float((yv[q] - hv[q]) + a.ih2 * lz[q]);
+          bad |= !isfinite(hq);
+          rhs[base + e] = hq;
           float wq;
           if (a.zmode == 0) {
             const float y = float(yv[q]);
@@ -1178,7 +1181,9 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    __syncthreads();  // the previous item's readers of sh are done
+    // (fmin / fmax skip NaN, and a CG started from a non-finite residual can stop at once with a
+    // zero correction, so the failure is flagged here)
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
     if ((threadIdx.x & 31) == 0) {
       sh[0][threadIdx.x >> 5] = lo;
       sh[1][threadIdx.x >> 5] = hi;

@@ -104,6 +104,18 @@ ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, const double* ba
   return gcuda(g, g->net.forward64(in_dev, base_dev, out_dev, batch, n, g->st), "forward");
 }
 
+ch_status ch_gtheta_activations(ch_gtheta* g, const double* in_dev, int batch, int n, float* acts_dev, size_t len) {
+  if (!g) return CH_ERR_INVALID;
+  if (g->sticky != CH_OK) return g->sticky;
+  if (!in_dev || !acts_dev || batch < 1 || batch > 65535 || n < 1 || n > 65535 ||
+      len != (size_t)batch * n * n * (5 * 32 + 1))
+    return gfail(g, CH_ERR_INVALID, "activations: bad arguments");
+  ch_status s = gcuda(g, g->net.activations(in_dev, batch, n, acts_dev, g->st), "activations");
+  if (s == CH_OK) s = gcuda(g, cudaStreamSynchronize(g->st), "activations: synchronize");
+  if (s == CH_OK) s = check_waits(g);
+  return s;
+}
+
 ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* target_dev, int batch, int S,
                               int margin, float* grad_host, size_t len, float* loss_host) {
   if (!g) return CH_ERR_INVALID;

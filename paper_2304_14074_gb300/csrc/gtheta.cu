@@ -964,6 +964,23 @@ cudaError_t GTheta::forward_acts(const void* in, bool in64, int batch, int S, cu
   return cudaGetLastError();
 }
 
+__global__ void k_bf16_to_f32(const bf16* __restrict__ in, float* __restrict__ out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __bfloat162float(in[i]);
+}
+
+cudaError_t GTheta::activations(const double* in, int batch, int S, float* out, cudaStream_t st) {
+  cudaError_t e = ensure(batch, S);
+  if (e != cudaSuccess) return e;
+  e = forward_acts(in, true, batch, S, st);
+  if (e != cudaSuccess) return e;
+  const size_t per = (size_t)batch * S * S * kC;
+  for (int l = 0; l < 5; ++l) k_bf16_to_f32<<<1024, 256, 0, st>>>(act_[l], out + l * per, per);
+  const dim3 grid((S + kTile - 1) / kTile, (S + kTile - 1) / kTile, batch);
+  k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], out + 5 * per, master_, S, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t GTheta::forward64(const double* in, const double* base, double* out, int batch, int S,
                               cudaStream_t st) {
   cudaError_t e = ensure(batch, S);

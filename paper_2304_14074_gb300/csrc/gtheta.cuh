@@ -36,6 +36,9 @@ class GTheta {
   cudaError_t train(const double* states, const double* base, int ntraj, int nsnap, int n, int stride, int steps, int batch,
                     double lr, unsigned long long seed, cudaStream_t st);
   cudaError_t read_losses(float* host, int count, cudaStream_t st);
+  // The forward pass of `batch` FP64 fields, keeping every layer's output: out (device, FP32)
+  // receives a1..a5 as [5][batch][S][S][32] (the stored BF16 values) followed by R [batch][S][S].
+  cudaError_t activations(const double* in, int batch, int S, float* out, cudaStream_t st);
   const float* grads() const { return grad_; }
   // 1 if a bounded wait of the tcgen05 path gave up since the handle was created (synchronises).
   int wait_failures(cudaStream_t st);

@@ -305,3 +305,85 @@ def test_tcgen05_gradients_match_oracle(gpu_lib, tcgen05_conv):
     Wg, _ = ch.gtheta_unflatten(grad)
     for l in range(6):
         assert np.linalg.norm(Wg[l] - gW[l]) <= 1e-3 * np.linalg.norm(gW[l]), l
+
+
+def _trajectories(ch, n, eps, T, N, J, stride, seeds):
+    """Sequential fine solutions from u0 = 0.05 N(0,1) (seeded), snapshotted every dT / stride:
+    [len(seeds)][N stride + 1][n^2] on the device."""
+    one = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    X = torch.empty((len(seeds), N * stride + 1, n * n), dtype=torch.float64, device="cuda")
+    X[:, 0] = dev(np.stack([ch_inputs.initial_condition(2, n, s, kind="normal", amp=0.05) for s in seeds]))
+    for j in range(N * stride):
+        X[:, j + 1] = ch.propagate(one, "nl", T / N / J, J // stride, X[:, j].contiguous())
+    return X
+
+
+def test_trained_network_beats_the_plain_coarse_step_on_held_out_data(gpu_lib):
+    """What training buys: on slices of held-out trajectories (seeds not trained on), the learned
+    coarse step G(U) + R(U) predicts the fine propagator F(U) over a slice with a smaller error,
+    relative to the change F(U) - U, than the plain coarse step G(U) (one step of Eq. 2.4 over
+    the slice) alone. Training and evaluation pairs come from the library's fine solver."""
+    ch = gpu_lib
+    n, eps, T, N, J, stride = 63, 0.05, 0.3, 16, 8, 4
+    dT = T / N
+    one = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    X = _trajectories(ch, n, eps, T, N, J, stride, range(1000, 1032))
+    base = ch.propagate(one, "lin1", dT, 1, X.reshape(-1, n * n)).reshape(X.shape)
+    net = ch.GTheta(seed=1)
+    for lr, steps in ((1e-3, 3000), (3e-4, 2000), (1e-4, 1000)):
+        losses = net.train(X, stride=stride, steps=steps, batch=32, lr=lr, seed=int(lr * 1e6), base=base)
+    assert np.all(np.isfinite(losses))
+    H = _trajectories(ch, n, eps, T, N, J, stride, range(5000, 5004))[:, ::stride]  # held out, slice ends
+    U = H[:, :N].reshape(-1, n * n).contiguous()
+    F = H[:, 1:].reshape(-1, n * n)
+    G = ch.propagate(one, "lin1", dT, 1, U)
+    L = torch.empty_like(U)
+    net.forward(U.view(-1, n, n), out=L.view(-1, n, n), base=G.view(-1, n, n))
+    chg = (F - U).norm(dim=1)
+    e_plain = ((G - F).norm(dim=1) / chg).cpu().numpy()
+    e_learned = ((L - F).norm(dim=1) / chg).cpu().numpy()
+    print("one-step error / change, median: plain %.3f learned %.3f" % (np.median(e_plain), np.median(e_learned)))
+    assert np.median(e_learned) <= 0.7 * np.median(e_plain)
+    assert np.mean(e_learned < e_plain) >= 0.75
+    net.close()
+
+
+def _bf16_ulp(x):
+    """One BF16 unit in the last place at |x| (8 significant bits)."""
+    e = np.floor(np.log2(np.maximum(np.abs(x), 1e-30)))
+    return 2.0 ** (e - 7)
+
+
+@pytest.mark.parametrize("conv", ["mma", "tcgen05"])
+def test_each_layer_matches_oracle_on_its_own_input(gpu_lib, monkeypatch, conv):
+    """Layer-local parity: each layer is fed the GPU's own (stored) input, so nothing propagates
+    between layers. Hidden layers: the oracle's FP64 convolution (BF16 weights for the 32 -> 32
+    layers) with bias and ReLU, rounded to BF16, equals the GPU's stored activation except where
+    FP32 against FP64 accumulation flips a rounding (then by one BF16 ulp), for at most 2e-3 of
+    the entries. Output layer (FP32 weights, FP32 result): relative 1e-5."""
+    ch = gpu_lib
+    if conv == "tcgen05":
+        monkeypatch.setenv("CH_GTHETA_CONV", "tcgen05")
+    p, (W, b) = fp32_net(ch, *random_net(11))
+    net = ch.GTheta()
+    net.set_params(p)
+    n, B = 40, 2
+    u = np.stack([ch_inputs.initial_condition(2, n, 90 + i, kind="normal", amp=0.5).reshape(n, n) for i in range(B)])
+    acts, R = net.activations(dev(u))
+    acts = acts.double().cpu().numpy()
+    R = R.double().cpu().numpy()
+    for i in range(B):
+        layer_in = u[i].astype(np.float32).astype(np.float64)[..., None]  # the first layer reads FP32
+        for l in range(5):
+            w = W[l] if l == 0 else go.bf16_round(W[l])
+            want = go.bf16_round(np.maximum(go.conv3(layer_in, w, b[l]), 0.0))
+            got = acts[l, i]
+            d = np.abs(got - want)
+            off = d > 0
+            assert np.all(d[off] <= 1.0001 * _bf16_ulp(want[off])), (l, d.max())
+            assert off.mean() <= 2e-3, (l, off.mean())
+            layer_in = got
+        want_r = go.conv3(layer_in, W[5], b[5])[..., 0]
+        assert np.linalg.norm(R[i] - want_r) <= 1e-5 * np.linalg.norm(want_r)
+        assert np.abs(R[i] - want_r).max() <= 1e-5 * np.abs(want_r).max()
+    net.close()
