@@ -198,6 +198,104 @@ __device__ __forceinline__ void fft_rows(float2* buf, const float2* twd, const f
   if constexpr (rem == 2) fft_stage<N, 4, F, false>(buf, twd + off, Ns, nullptr, 0);
 }
 
+// ---- Four-step FFT of length 1024, one warp per FFT (the 512 x 512 grid: L = 2(n + 1) = 1024).
+// The Stockham version above makes four passes through shared memory with a block barrier
+// after each; here each 1024-point FFT (a row pair of the odd extension) is done by one warp
+// as 1024 = 32 x 32 (Cooley-Tukey four-step): lane t holds y[32 m1 + t] for m1 < 32,
+//   (1) a 32-point FFT over m1 in registers,            Z[k1][t] = sum_m1 y[32 m1 + t] W_32^(m1 k1)
+//   (2) the twiddle W_1024^(t k1) (table tw2[k1][t]),
+//   (3) a transpose through the FFT's own row of the block buffer (rows padded to 33 entries),
+//   (4) a 32-point FFT over t in registers,             Y[k1 + 32 k2] = sum_t A[k1][t] W_32^(t k2),
+// and the result is stored where the Stockham version leaves it, so the pass epilogues read it
+// unchanged. One shared-memory round trip and warp barriers only.
+
+// exp(-2 pi i j / 32), j < 16: cos and sin of the angle, rounded to FP32 (host libm values).
+__device__ __forceinline__ float2 w32(int j) {
+  switch (j) {
+    case 1: return make_float2(9.807852804e-01f, -1.950903220e-01f);
+    case 2: return make_float2(9.238795325e-01f, -3.826834324e-01f);
+    case 3: return make_float2(8.314696123e-01f, -5.555702330e-01f);
+    case 4: return make_float2(7.071067812e-01f, -7.071067812e-01f);
+    case 5: return make_float2(5.555702330e-01f, -8.314696123e-01f);
+    case 6: return make_float2(3.826834324e-01f, -9.238795325e-01f);
+    case 7: return make_float2(1.950903220e-01f, -9.807852804e-01f);
+    case 9: return make_float2(-1.950903220e-01f, -9.807852804e-01f);
+    case 10: return make_float2(-3.826834324e-01f, -9.238795325e-01f);
+    case 11: return make_float2(-5.555702330e-01f, -8.314696123e-01f);
+    case 12: return make_float2(-7.071067812e-01f, -7.071067812e-01f);
+    case 13: return make_float2(-8.314696123e-01f, -5.555702330e-01f);
+    case 14: return make_float2(-9.238795325e-01f, -3.826834324e-01f);
+    case 15: return make_float2(-9.807852804e-01f, -1.950903220e-01f);
+    default: return make_float2(1.f, 0.f);
+  }
+}
+
+// a W_32^j (j known at compile time after unrolling: 1 and -i multiply by nothing).
+__device__ __forceinline__ float2 twmul32(float2 a, int j) {
+  if (j == 0) return a;
+  if (j == 8) return make_float2(a.y, -a.x);
+  return cmul(a, w32(j));
+}
+
+// 32-point FFT in registers, radix-2 decimation in frequency: on return v[i] = X[bitrev5(i)].
+__device__ __forceinline__ void fft32_dif(float2 (&v)[32]) {
+#pragma unroll
+  for (int span = 16; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int start = 0; start < 32; start += 2 * span) {
+#pragma unroll
+      for (int j = 0; j < span; ++j) {
+        const float2 a = v[start + j], b = v[start + j + span];
+        v[start + j] = make_float2(a.x + b.x, a.y + b.y);
+        v[start + j + span] = twmul32(make_float2(a.x - b.x, a.y - b.y), j * (16 / span));
+      }
+    }
+  }
+}
+
+__host__ __device__ constexpr int bitrev5(int i) {
+  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+}
+
+template <int N>
+__device__ __forceinline__ void fft_rows_warp(float2* buf, const float2* tw2, const float* src, int a0) {
+  static_assert(N == 512 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 1024");
+  constexpr int n = N - 1;
+  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int ra = a0 + 2 * f, rb = ra + 1;
+  const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
+  const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
+  float2 v[32];
+#pragma unroll
+  for (int m1 = 0; m1 < 32; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
+  fft32_dif(v);
+  float2* s = buf + f * buf_row<N>();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int k1 = bitrev5(i);
+    s[k1 * 33 + t] = cmul(v[i], tw2[k1 * 32 + t]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int m2 = 0; m2 < 32; ++m2) v[m2] = s[t * 33 + m2];
+  __syncwarp();
+  fft32_dif(v);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) s[pad8(t + 32 * bitrev5(i))] = v[i];
+}
+
+// The row FFTs of a transform pass (four-step warp version at L = 1024); ends with a block
+// barrier, after which `buf` holds the transforms for the epilogue.
+template <int N, int F>
+__device__ __forceinline__ void fft_rows_any(float2* buf, const float2* twd, const float* src, int a0) {
+  if constexpr (N == 512) {
+    fft_rows_warp<N>(buf, twd, src, a0);
+    __syncthreads();
+  } else {
+    fft_rows<N, F>(buf, twd, src, a0);
+  }
+}
+
 // One transform pass: rows of `in` ([units][n][n]) -> orthonormal DST-I -> written transposed.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__ in, float* __restrict__ out,
@@ -211,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) k_dst_pass(const float* __restrict__
   const float* src = in + (size_t)u * n * n;
   for (int m = threadIdx.x; m < L; m += kThreads) twd[m] = tw[m];
   __syncthreads();
-  fft_rows<N, F>(buf, twd, src, a0);
+  fft_rows_any<N, F>(buf, twd, src, a0);
   // row pair (2f, 2f+1) packed as real + i imag: S x_{2f} = -Im Y / 2, S x_{2f+1} = Re Y / 2
   const float sc = 0.5f * sqrtf(2.0f / N);
   float* dst = out + (size_t)u * n * n;
@@ -432,9 +530,19 @@ size_t correct_partials(int count) { return (size_t)count * 4 * kBlk; }
 
 // Twiddles of the stages after the first of fft_rows<N> (radix 8 with Ns = 8, 64, ..., then the
 // radix-2 or radix-4 stage), stage after stage: entry (r - 1) Ns + k = exp(-2 pi i m / L) with
-// m = r k L / (R Ns), r = 1..R-1, k < Ns (host libm, rounded to FP32). At most L entries.
+// m = r k L / (R Ns), r = 1..R-1, k < Ns (host libm, rounded to FP32). At most L entries. For
+// N = 512 the four-step table of fft_rows_warp instead.
 static std::vector<float2> twiddle_table(int N) {
   const int L = 2 * N;
+  if (N == 512) {  // four-step warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / 1024), k1, t < 32
+    std::vector<float2> tw(L);
+    for (int k1 = 0; k1 < 32; ++k1)
+      for (int t = 0; t < 32; ++t) {
+        const double a = -2.0 * M_PI * k1 * t / L;
+        tw[k1 * 32 + t] = make_float2(float(std::cos(a)), float(std::sin(a)));
+      }
+    return tw;
+  }
   int lg = 0;
   while ((1 << lg) < L) ++lg;
   const int n8 = lg / 3, rem = lg - 3 * n8;
@@ -652,6 +760,13 @@ cudaError_t Prop2D::reset_counters(cudaStream_t st) {
   return e;
 }
 
+__global__ void k2_clear_status(unsigned* status, unsigned mask) { atomicAnd(status, ~mask); }
+
+cudaError_t Prop2D::clear_status(unsigned mask, cudaStream_t st) {
+  k2_clear_status<<<1, 1, 0, st>>>(status_, mask);
+  return cudaGetLastError();
+}
+
 unsigned Prop2D::read_status(cudaStream_t st) {
   unsigned s[4] = {0, 0, 0, 0};
   unsigned long long tot = 0;
@@ -864,7 +979,7 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   const float* __restrict__ mu1 = a.mu1;
   const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
   if (act >= 0 && (a.flag[2 * u] || (act == 1 && a.flag[2 * u + 1]))) return;  // block-uniform
-  fft_rows<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
+  fft_rows_any<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
   float cwb = 0.f;
   // wbar: formed from the range partials in the CG-start pass, which keeps it for the CG passes
   if (act >= 0 && EPI == E_INIT) {

@@ -62,6 +62,9 @@ class Prop2D {
   // must not be the internal scratch buffers.
   cudaError_t dst2(const float* in, float* out, int units, cudaStream_t st);
   unsigned read_status(cudaStream_t st);  // synchronises
+  // Clears status bits (enqueued on st): a failure the caller has handled (a learned coarse
+  // prediction that the guard replaces) is not reported at the end of the run.
+  cudaError_t clear_status(unsigned mask, cudaStream_t st);
   unsigned long long newton_iterations() const { return newton_total_; }
   long long cg_iterations() const { return cg_total_; }
   long long cg_unit_iterations() const { return cg_unit_total_; }  // summed over units

@@ -301,8 +301,25 @@ ch_status run2d(ch_parareal* h) {
     return st;
   };
   // A learned coarse state that is not finite or leaves [-kGuard, kGuard] (Cahn-Hilliard states
-  // stay near [-1, 1]) is a failed prediction: the problem leaves G_theta.
-  constexpr double kGuard = 4.0;
+  // stay near the wells +-1, overshooting them by a few per cent) is a failed prediction: the
+  // problem leaves G_theta before the fine solver is asked to step from it.
+  constexpr double kGuard = 2.0;
+  // The plain coarse steps of a sweep run on every row, including rows whose learned prediction
+  // has run away; their solves may then report a non-finite value. When every problem with a
+  // non-finite coarse state is one the guard sends back to the plain step (R), that report is
+  // the guard's business, not a failure: it is cleared, unless it was already set before the
+  // coarse sweep (`before`).
+  auto forgive_guarded = [&](const std::vector<int>& R, unsigned before) -> ch_status {
+    if (R.empty()) return CH_OK;
+    const unsigned now = h->p2->read_status(h->st);
+    if (!(now & chg2::ST_NONFINITE) || (before & chg2::ST_NONFINITE)) return CH_OK;
+    for (int b = 0; b < B; ++b)
+      if (active[b] && !learned[b] && !std::isfinite(acc[4 * b + 3]) &&
+          std::find(R.begin(), R.end(), b) == R.end())
+        return CH_OK;  // a plain problem failed too: keep the report
+    CH_CUDA(h, h->p2->clear_status(chg2::ST_NONFINITE, h->st));
+    return CH_OK;
+  };
   CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
   // coarse initial guess (Section 4): U_{s+1} = G(U_s), Gold_s = U_{s+1}
   std::vector<int> L;
@@ -330,6 +347,7 @@ ch_status run2d(ch_parareal* h) {
         h->h_fallback[b] = 0;
         R.push_back(b);
       }
+    if ((s = forgive_guarded(R, 0u)) != CH_OK) return s;
     if (!R.empty()) {
       if ((s = restart_plain(R, 0)) != CH_OK) return s;
       if ((s = pull_acc()) != CH_OK) return s;
@@ -360,7 +378,7 @@ ch_status run2d(ch_parareal* h) {
     if ((s = prop2(h, (int)uoff.size(), fine2(h), h->p.dt, h->p.J)) != CH_OK) return s;
     if ((s = gather_units(h, h->F, foff, false)) != CH_OK) return s;
     CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
-    h->p2->read_status(h->st);
+    const unsigned st_fine = h->p2->read_status(h->st);
     h->fine_newton += h->p2->newton_iterations() - n0;
     h->fine_cg += h->p2->cg_unit_iterations() - c0;
     // sequential coarse sweep with the correction of Eq. 2.2 and the norms
@@ -392,6 +410,7 @@ ch_status run2d(ch_parareal* h) {
         h->h_fallback[b] = k + 1;
         R.push_back(b);
       }
+    if ((s = forgive_guarded(R, st_fine)) != CH_OK) return s;
     if (!R.empty()) {
       if ((s = restart_plain(R, k + 1)) != CH_OK) return s;
       if ((s = pull_acc()) != CH_OK) return s;

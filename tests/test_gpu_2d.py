@@ -318,3 +318,27 @@ def test_ensemble_of_uneven_grids_matches_single_problem_runs(gpu_lib):
         assert ens.stats(i)["iterations"] == 3
         pr.close()
     ens.close()
+
+
+def test_ensemble_over_the_c5_grid_sizes_matches_single_problem_runs(gpu_lib):
+    """The ensemble's grid sizes of the uneven-grid configuration (64^2 .. 512^2: n = 63, 127, 255,
+    511), each problem with its own eps: every problem's iterates equal those of its own
+    single-problem handle bit for bit."""
+    ch = gpu_lib
+    ns = [63, 511, 127, 255, 63]
+    eps = [0.01, 0.02, 0.05, 0.03, 0.04]
+    kw = dict(dim=2, T=0.002, n_slices=4, fine_steps=2, variant="NPA-I", newton_tol=1e-12, max_iters=2)
+    cfg = ch.Config(n=ns[0], eps=eps[0], **kw)
+    u0s = [ch_inputs.initial_condition(2, n, 700 + i, kind="normal", amp=0.05) for i, n in enumerate(ns)]
+    ens = ch.Ensemble(cfg, ns, eps)
+    assert ens.groups == 4
+    for i, u in enumerate(u0s):
+        ens.set_initial(i, u)
+    ens.run()
+    for i, (n, e) in enumerate(zip(ns, eps)):
+        pr = ch.Parareal(ch.Config(n=n, eps=e, **kw), batch=1)
+        pr.set_initial(0, u0s[i])
+        pr.run()
+        assert np.array_equal(ens.get_slices(i), pr.get_slices(0)), (i, n)
+        pr.close()
+    ens.close()
