@@ -581,8 +581,6 @@ def ensemble_c5(args):
                          f"eps in [{eps.min():.3f}, {eps.max():.3f}], N={c['N']}, J={c['J']} at c5's dt={c['dt']:.4g} "
                          f"(T={T:.3g}), NPA-I, plain coarse step, one Parareal iteration per run"),
             "seconds_per_iteration": round(t, 4), "grid_pt_steps_per_s": pts / t,
-            "newton_per_unit_step": round(sum(x["newton_total"] for x in st) /
-                                          max(1, sum(c["N"] * c["J"] for _ in st)), 3),
             "iterations": int(st[0]["iterations"])}
 
 
@@ -821,13 +819,24 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain coarse propagator run")
     ap.add_argument("--no-2d", action="store_true", help="skip the 512 x 512 2D step (roofline_2d)")
-    ap.add_argument("--experiment", choices=["learned-c4", "sweep2d", "c5"], default=None,
+    ap.add_argument("--experiment", choices=["learned-c4", "sweep2d", "c5", "gtheta-fwd"], default=None,
                     help="learned-c4: learned vs plain coarse propagator to 1e-8 on the 512 x 512 configuration "
                          "(training included); sweep2d: the 2D fine propagation of one Parareal fine sweep of a 2D "
                          "workload (all its slices batched), `--steps` times `--fine` steps, timed alone. One JSON "
                          "line each.")
     ap.add_argument("--fine", type=int, default=2, help="sweep2d: fine steps per timed propagation")
     args = ap.parse_args()
+    if args.experiment == "gtheta-fwd":
+        import torch
+
+        import paper_2304_14074_gb300 as ch
+        torch.cuda.set_device(0)
+        net = ch.GTheta(seed=1)
+        r = gtheta_forward_roofline(ch, net)
+        r["conv"] = os.environ.get("CH_GTHETA_CONV", "mma")
+        net.close()
+        print(json.dumps(r))
+        return
     if args.experiment == "c5":
         print(json.dumps(ensemble_c5(args)))
         return

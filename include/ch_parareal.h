@@ -79,7 +79,9 @@ typedef struct {
   int variant;         /* ch_variant                                                         */
   double newton_tol;   /* Newton stop: ||Y_{m+1} - Y_m||_inf <= newton_tol, or the FP64
                           rounding floor (an increment below sqrt(newton_tol) that fails to
-                          halve the previous one)                                            */
+                          halve the previous one); in 2D also when the iteration contracts
+                          (rho = |d_m| / |d_{m-1}| < 1/2) and its estimated remaining error
+                          rho / (1 - rho) |d_m| is <= newton_tol                             */
   int newton_max;      /* Newton iteration cap per step                                      */
   double tol;          /* Parareal stop: max_n ||U_n^k - U_n^{k-1}||_inf < tol; <= 0: never   */
   int max_iters;       /* Parareal iteration cap, 1 <= max_iters <= N                         */

@@ -1190,7 +1190,21 @@ __device__ __forceinline__ double lap5r(const double* __restrict__ X, int i, int
   return (w + e) + (s + no) - 4.0 * c;
 }
 
-// N1: z = c1 lap(Y) - dt g(Y)
+// Sum of the four neighbours of X at (i, j) (zero outside), restrict loads; c = X(i, j).
+template <int n>
+__device__ __forceinline__ double nsum4r(const double* __restrict__ X, int i, int j, double& c) {
+  const size_t k = (size_t)i * n + j;
+  c = __ldcg(X + k);
+  const double w = (j > 0) ? __ldcg(X + k - 1) : 0.0;
+  const double e = (j < n - 1) ? __ldcg(X + k + 1) : 0.0;
+  const double s = (i > 0) ? __ldcg(X + k - n) : 0.0;
+  const double no = (i < n - 1) ? __ldcg(X + k + n) : 0.0;
+  return (w + e) + (s + no);
+}
+
+// N1: z = (c1 lap(Y) - dt g(Y)) / h^2, formed as c1' S4(Y) + Y (-4 c1' - dt' g(Y) / Y) with the
+// neighbour sum S4, c1' = c1 / h^2, dt' = dt / h^2: seven FP64 operations per node on GB300's
+// narrow FP64 pipe (the 1/h^2 of the residual's Laplacian is folded in here).
 template <int N>
 __device__ __forceinline__ void ph_z(const PArgs& a, Items its) {
   constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows, U = 4;
@@ -1202,17 +1216,16 @@ __device__ __forceinline__ void ph_z(const PArgs& a, Items its) {
     if (its.chk && a.flag[2 * u]) continue;
     const double* __restrict__ Yu = a.Y + u * pts;
     const int cnt = (n - a0 < kDstRows ? n - a0 : kDstRows) * n;
-    const double c1 = unit_c1(a, u);
+    const double c1s = unit_c1(a, u) * a.ih2, m4c1s = -4.0 * c1s, dts = a.dt * a.ih2;
     for (int e0 = threadIdx.x; e0 < cnt; e0 += U * kThreads) {
-      double lv[U], xv[U], wv[U];
+      double sv[U], xv[U], wv[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
         const int e = e0 + q * kThreads;
         if (e < cnt) {
           const int i = a0 + e / n, j = e - (e / n) * n;
           const size_t k = (size_t)i * n + j;
-          lv[q] = lap5r<n>(Yu, i, j);
-          xv[q] = __ldcg(Yu + k);
+          sv[q] = nsum4r<n>(Yu, i, j, xv[q]);
           wv[q] = (a.zmode == 2) ? __ldcg(W64 + u * pts + k) : 0.0;
         }
       }
@@ -1221,12 +1234,12 @@ __device__ __forceinline__ void ph_z(const PArgs& a, Items its) {
         const int e = e0 + q * kThreads;
         if (e < cnt) {
           const double x = xv[q];
-          double g;
-          if (a.zmode == 0) g = x * x * x;
-          else if (a.zmode == 1) g = x;
-          else if (a.zmode == 2) g = wv[q] * wv[q] * x;
-          else g = a.wconst * x;
-          z[u * pts + (size_t)a0 * n + e] = c1 * lv[q] - a.dt * g;
+          double gx;  // g(x) / x
+          if (a.zmode == 0) gx = x * x;
+          else if (a.zmode == 1) gx = 1.0;
+          else if (a.zmode == 2) gx = wv[q] * wv[q];
+          else gx = a.wconst;
+          z[u * pts + (size_t)a0 * n + e] = fma(x, fma(-dts, gx, m4c1s), c1s * sv[q]);
         }
       }
     }
@@ -1260,7 +1273,8 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
         const int e = e0 + q * kThreads;
         if (e < cnt) {
           const int i = a0 + e / n, j = e - (e / n) * n;
-          lz[q] = lap5r<n>(zu, i, j);
+          double zc;
+          lz[q] = nsum4r<n>(zu, i, j, zc) - 4.0 * zc;  // h^2 lap(z) of the scaled z: h^-2 folded in
           yv[q] = __ldcg(Y + base + e);
           hv[q] = __ldcg(yhat + base + e);
           w64[q] = (a.zmode == 2) ? __ldcg(W64 + base + e) : 0.0;
@@ -1270,7 +1284,7 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
       for (int q = 0; q < U; ++q) {
         const int e = e0 + q * kThreads;
         if (e < cnt) {
-          const float hq = float((yv[q] - hv[q]) + a.ih2 * lz[q]);
+          const float hq = float((yv[q] - hv[q]) + lz[q]);
           bad |= !isfinite(hq);
           rhs[base + e] = hq;
           float wq;
@@ -1523,7 +1537,21 @@ __device__ __forceinline__ void cg_update_item(const PArgs& a, int item, int j) 
   __syncthreads();
 }
 
-// N7: Newton stop test per unit (tolerance, or the FP64 floor rule)
+// Newton stop test (the tolerance of Section 4.4, read as a bound on the error of the step). The
+// increment |d| is below tol; or, from the second increment on, the iteration contracts
+// (rho = |d| / |d_prev| < 1/2: the inexact Newton of the CG solves converges linearly at about
+// the CG tolerance) and its estimated remaining error rho / (1 - rho) |d| is below tol; or the
+// FP64 rounding floor of the residual has been reached (an increment below sqrt(tol) that fails
+// to halve the previous one). The error estimate saves the iteration that would only confirm a
+// converged step.
+__device__ __forceinline__ bool newton_done(double dm, double prev, int m, double tol, double floor_) {
+  if (dm <= tol) return true;
+  if (m < 2) return false;
+  if (dm < 0.5 * prev && dm * dm <= tol * (prev - dm)) return true;
+  return dm <= floor_ && dm > 0.5 * prev;
+}
+
+// N7: Newton stop test per unit (newton_done)
 template <int N>
 __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
   const int last = (it_n >= a.newton_max - 1);
@@ -1532,7 +1560,7 @@ __device__ __forceinline__ void ph_newton_end(const PArgs& a, int it_n) {
     const double dm = unit_max_thread<N>(a.pd, u);
     const int mm = ++a.cnt[u];
     const double prev = a.scal[u * 8 + 6];
-    bool done = dm <= a.tol || (mm >= 2 && dm <= a.floor_ && dm > 0.5 * prev);
+    bool done = newton_done(dm, prev, mm, a.tol, a.floor_);
     a.scal[u * 8 + 6] = dm;
     if (!done && last) {
       atomicOr(a.status, ST_NEWTON);
@@ -1751,7 +1779,7 @@ __global__ void __launch_bounds__(kThreads, 2) k2_cluster(PArgs args) {
       cluster_sync();
       const double dm = unit_reduce<N, 1>(a.pd, u);
       ++m;
-      bool done = dm <= a.tol || (m >= 2 && dm <= a.floor_ && dm > 0.5 * prev_dm);
+      bool done = newton_done(dm, prev_dm, m, a.tol, a.floor_);
       prev_dm = dm;
       if (!done && it_n == a.newton_max - 1) {
         st |= ST_NEWTON;

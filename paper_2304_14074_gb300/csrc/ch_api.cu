@@ -280,7 +280,9 @@ ch_status run2d(ch_parareal* h) {
   auto restart_plain = [&](const std::vector<int>& R, int s0) -> ch_status {
     if (R.empty() || s0 >= N) return CH_OK;
     for (int b : R) {
-      CH_CUDA(h, cudaMemsetAsync(h->acc + 4 * b, 0, 4 * sizeof(double), h->st));
+      // the iteration's increment (acc[0]) is kept: it measured the learned sweep that is being
+      // replaced; the error norms and the state range are recomputed for the restarted slices
+      CH_CUDA(h, cudaMemsetAsync(h->acc + 4 * b + 1, 0, 3 * sizeof(double), h->st));
       // slice s0 is the fine result F(U_{s0-1}) (exact), whatever the learned step produced
       if (s0 > 0)
         CH_CUDA(h, cudaMemcpyAsync(h->U + b * us + s0 * pts, h->F + b * fs + (s0 - 1) * pts, pts * sizeof(double),
@@ -305,19 +307,19 @@ ch_status run2d(ch_parareal* h) {
   // problem leaves G_theta before the fine solver is asked to step from it.
   constexpr double kGuard = 2.0;
   // The plain coarse steps of a sweep run on every row, including rows whose learned prediction
-  // has run away; their solves may then report a non-finite value. When every problem with a
-  // non-finite coarse state is one the guard sends back to the plain step (R), that report is
-  // the guard's business, not a failure: it is cleared, unless it was already set before the
-  // coarse sweep (`before`).
+  // has run away; their solves may then report a non-finite value or a refinement that does not
+  // converge. When every problem with a non-finite or out-of-range coarse state is one the guard
+  // sends back to the plain step (R), that report is the guard's business, not a failure: it is
+  // cleared, unless it was already set before the coarse sweep (`before`).
   auto forgive_guarded = [&](const std::vector<int>& R, unsigned before) -> ch_status {
     if (R.empty()) return CH_OK;
+    const unsigned bits = (chg2::ST_NONFINITE | chg2::ST_NEWTON) & ~before;
     const unsigned now = h->p2->read_status(h->st);
-    if (!(now & chg2::ST_NONFINITE) || (before & chg2::ST_NONFINITE)) return CH_OK;
+    if (!(now & bits)) return CH_OK;
     for (int b = 0; b < B; ++b)
-      if (active[b] && !learned[b] && !std::isfinite(acc[4 * b + 3]) &&
-          std::find(R.begin(), R.end(), b) == R.end())
+      if (active[b] && !(acc[4 * b + 3] <= kGuard) && std::find(R.begin(), R.end(), b) == R.end())
         return CH_OK;  // a plain problem failed too: keep the report
-    CH_CUDA(h, h->p2->clear_status(chg2::ST_NONFINITE, h->st));
+    CH_CUDA(h, h->p2->clear_status(now & bits, h->st));
     return CH_OK;
   };
   CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
