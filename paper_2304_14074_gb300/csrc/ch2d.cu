@@ -2048,8 +2048,12 @@ __global__ void __launch_bounds__(kThreads, (N >= 512 ? 2 : 4)) k2_phase(PArgs a
 // which = 0: Newton (active slots 2, 3), 1: CG (slots 0, 1).
 // End of a CG iteration of the graph execution: the scalars of every unit (cg_scalars_all), then
 // continue while units go on and the cap is not reached.
+// One block of kScalarThreads: a warp per unit forms its sums and scalars (FP64 shuffles and
+// divisions on the narrow FP64 pipe), so more warps shorten the chain of units per warp.
+constexpr int kScalarThreads = 1024;
+
 template <int N>
-__global__ void __launch_bounds__(kThreads) k2_cg_cond(PArgs a, cudaGraphConditionalHandle hnd, int lim) {
+__global__ void __launch_bounds__(kScalarThreads) k2_cg_cond(PArgs a, cudaGraphConditionalHandle hnd, int lim) {
   const int it = a.ctr[1];
   const int going = cg_scalars_all<N>(a, it);
   if (threadIdx.x == 0) {
@@ -2060,7 +2064,7 @@ __global__ void __launch_bounds__(kThreads) k2_cg_cond(PArgs a, cudaGraphConditi
 
 // The same for the host-driven execution: the count goes to active[it & 1] for the host.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k2_cg_host(PArgs a) {
+__global__ void __launch_bounds__(kScalarThreads) k2_cg_host(PArgs a) {
   const int it = a.ctr[1];
   const int going = cg_scalars_all<N>(a, it);
   if (threadIdx.x == 0) a.active[it & 1] = going;
@@ -2146,7 +2150,7 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
   if (e == cudaSuccess) {
-    k2_cg_cond<N><<<1, kThreads, 0, bs2>>>(a, hC, cg_max);
+    k2_cg_cond<N><<<1, kScalarThreads, 0, bs2>>>(a, hC, cg_max);
     e = cudaGetLastError();
   }
   {
@@ -2231,7 +2235,7 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
       CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
-      k2_cg_host<N><<<1, kThreads, 0, st>>>(a);
+      k2_cg_host<N><<<1, kScalarThreads, 0, st>>>(a);
       CH_TRY(cudaGetLastError());
       CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CH_TRY(cudaStreamSynchronize(st));

