@@ -579,6 +579,74 @@ ch_status tune_fine_sweep(ch_parareal* h) {
   return CH_OK;
 }
 
+// 2D: the execution of the implicit steps — one CUDA graph per step (conditional loops, a kernel
+// per phase) or one persistent cooperative kernel per propagation (the same phases separated by
+// grid barriers) — is chosen once per handle, before its first reference or run, by timing one
+// fine step of the handle's fine-sweep batch (every slice of every problem, started from u^0)
+// with each (the second of two runs, so graph construction is not timed). The reference and
+// every Parareal iteration then use the same execution, so the iterate at k = N still equals the
+// reference bit for bit. Cached per process by grid, fine scheme and step (not by batch size:
+// handles of the same configuration then share one execution, and a problem's results do not
+// depend on the batch it is solved in). CH_2D_STEP forces an execution; CH_AUTOTUNE=0 keeps the
+// graphs.
+std::map<std::string, int> g_tune2d;
+
+ch_status ensure_tuned2d(ch_parareal* h) {
+  if (h->tuned) return CH_OK;
+  h->tuned = true;
+  if (std::getenv("CH_2D_STEP")) return CH_OK;
+  const char* off = std::getenv("CH_AUTOTUNE");
+  if (off && std::strcmp(off, "0") == 0) return CH_OK;
+  const int units = h->B * h->p.N;
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "2d n=%d scheme=%d dt=%.17g", h->p.n, fine2(h), h->p.dt);
+  const std::string key(buf);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune2d.find(key);
+    if (it != g_tune2d.end()) {
+      h->p2->set_path(static_cast<chg2::StepPath>(it->second));
+      return CH_OK;
+    }
+  }
+  const size_t pts = h->pts, us = (size_t)(h->p.N + 1) * pts;
+  std::vector<long long> offs((size_t)units);
+  for (int b = 0; b < h->B; ++b)
+    for (int sl = 0; sl < h->p.N; ++sl) offs[(size_t)b * h->p.N + sl] = (long long)(b * us);
+  const chg2::StepPath paths[2] = {chg2::PATH_GRAPH, chg2::PATH_PERSISTENT};
+  cudaEvent_t a = nullptr, e2 = nullptr;
+  CH_CUDA(h, cudaEventCreate(&a));
+  CH_CUDA(h, cudaEventCreate(&e2));
+  chg2::StepPath best = chg2::PATH_GRAPH;
+  float best_ms = 1e30f;
+  ch_status s = CH_OK;
+  for (chg2::StepPath pth : paths) {
+    h->p2->set_path(pth);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && s == CH_OK; ++rep) {
+      s = gather_units(h, h->U, offs, true);
+      if (s == CH_OK && cudaEventRecord(a, h->st) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning event");
+      if (s == CH_OK) s = prop2(h, units, fine2(h), h->p.dt, 1);
+      if (s == CH_OK && cudaEventRecord(e2, h->st) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning event");
+      if (s == CH_OK && cudaEventSynchronize(e2) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning sync");
+      if (s == CH_OK && cudaEventElapsedTime(&ms, a, e2) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning time");
+    }
+    if (s != CH_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = pth;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(e2);
+  if (s != CH_OK) return s;
+  h->p2->set_path(best);
+  CH_CUDA(h, h->p2->reset_counters(h->st));  // the trial steps' counts and status bits
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune2d[key] = (int)best;
+  return CH_OK;
+}
+
 // Tunes once per handle, before its first reference or run, so that both use the same fine-sweep
 // configuration (the sequential reference then equals the Parareal iterate at k = N bit for bit).
 // The trial sweeps run on a coarse initial guess written into U (overwritten by run).
@@ -770,7 +838,10 @@ ch_status ch_parareal_compute_reference(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "compute_reference before set_initial");
-  if (h->dim == 2) return reference2d(h);
+  if (h->dim == 2) {
+    ch_status s = ensure_tuned2d(h);
+    return s != CH_OK ? s : reference2d(h);
+  }
   {
     ch_status s = ensure_tuned(h);
     if (s != CH_OK) return s;
@@ -823,7 +894,10 @@ ch_status ch_parareal_run(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "run before set_initial");
-  if (h->dim == 2) return run2d(h);
+  if (h->dim == 2) {
+    ch_status s = ensure_tuned2d(h);
+    return s != CH_OK ? s : run2d(h);
+  }
   const int B = h->B, maxit = h->p.maxit;
   std::vector<int> ones(B, 1);
   {

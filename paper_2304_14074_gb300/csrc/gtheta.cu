@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cstdint>
+#include <cstdio>
 #include <map>
 #include <mutex>
 #include <set>
