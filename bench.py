@@ -103,6 +103,12 @@ FINE_SWEEP_1D_TRAFFIC = {(1024, 256, 64): 219.1e6}
 BYTES_CG_2D = 8 + 12 + 8 + 16 + 44
 BYTES_NEWTON_2D = 16 + 32 + 8 + 16 + 8 + 20
 BYTES_STEP_2D = 16 + 32
+# DRAM traffic of the 2D fine sweep on the 512 x 512 grid, from a one-pass ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum over the kernels of a batched propagation of 64
+# slices (current kernels): a full CG iteration of all 64 units moves 1098-1232 MB of DRAM traffic
+# against 1471 MB of algorithmic bytes (the L2 keeps part of each phase's output for the next).
+# The fine sweep's traffic per launch is reported as that ratio times its algorithmic bytes.
+TRAFFIC_2D_OVER_ALGORITHMIC = {511: 0.79}
 
 
 def max_over_ranks(value, dist, device):
@@ -386,11 +392,14 @@ def bench_ours(args, w, rank, world, local_rank):
         else:
             alg_flops = fine_pts_per_step * FP64_FLOPS_LINEAR_STEP
         achieved = alg_flops / (fine_ms_per_launch / 1e3) / 1e9
+        dgemm = fp64_dgemm_tflops() * 1e3 if rank == 0 else None
         roofline = {"bound": "alu", "kernel": ("k_nn_fine_sweep" if w.get("nn") else "k_fine_sweep") + " (FP64 pipe)",
                     "achieved": round(achieved, 2),
                     "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s",
                     "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
                     "peak_source": "nominal FP64: 152 SMs x 4 flop/clk x 2.07 GHz (no FP64 entry in MEASURED_PEAKS.json)",
+                    "fp64_measured_dgemm_gflops": round(dgemm, 1) if dgemm else None,
+                    "frac_of_measured_dgemm": round(achieved / dgemm, 4) if dgemm else None,
                     "traffic": FINE_SWEEP_1D_TRAFFIC.get((n, B, N)),
                     "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
                     "fine_sweep_share_of_step": round(fine_ms / total_ms, 4) if world == 1 else None,
@@ -456,7 +465,11 @@ def roofline_2d(w, B, fine_ms_per_launch, newton_total, cg_total, share):
             "frac": round(achieved / peak, 4),
             "peak_source": ("MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks
                             else "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"),
-            "traffic": None,
+            "traffic": (round(TRAFFIC_2D_OVER_ALGORITHMIC[n] * alg_bytes) if n in TRAFFIC_2D_OVER_ALGORITHMIC
+                        else None),
+            "traffic_source": ("ncu DRAM bytes of full CG iterations (all units active) over their algorithmic "
+                               f"bytes, {TRAFFIC_2D_OVER_ALGORITHMIC[n]}, times this launch's algorithmic bytes"
+                               if n in TRAFFIC_2D_OVER_ALGORITHMIC else None),
             "fine_sweep_ms_per_launch": round(fine_ms_per_launch, 3),
             "fine_sweep_share_of_step": round(share, 4) if share is not None else None,
             "newton_iterations_per_unit_step": round(newton_total / (units * J), 3),
@@ -584,6 +597,25 @@ def ensemble_c5(args):
             "iterations": int(st[0]["iterations"])}
 
 
+def fp64_dgemm_tflops(size=6144, reps=3):
+    """FP64 rate measured on this GPU: a cuBLAS DGEMM (torch.matmul on float64), timed with CUDA
+    events after a warm-up. A library measurement beside the nominal FP64 peak, as the BF16 peak is
+    a cuBLAS GEMM."""
+    import torch
+    a = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    b = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        c = a @ b
+    e1.record()
+    torch.cuda.synchronize()
+    del a, b, c
+    return 2.0 * size ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -664,7 +696,7 @@ GTHETA_FLOPS_PER_PIXEL = 4 * 2 * 32 * 288 + 2 * 32 * 9 + 2 * 288
 
 def gtheta_forward_roofline(ch, net, batch=8, n=511):
     """Tensor-core roofline of the G_theta forward pass on `batch` fields of the 512^2 grid, timed
-    with CUDA events (the four 32 -> 32 layers are BF16 mma on the tensor cores)."""
+    with CUDA events (the four 32 -> 32 layers are BF16 tcgen05.mma on the tensor cores)."""
     import torch
     x = (0.5 * torch.randn(batch, n, n, dtype=torch.float64, device="cuda")).contiguous()
     for _ in range(3):
@@ -833,7 +865,7 @@ def main():
         torch.cuda.set_device(0)
         net = ch.GTheta(seed=1)
         r = gtheta_forward_roofline(ch, net)
-        r["conv"] = os.environ.get("CH_GTHETA_CONV", "mma")
+        r["conv"] = os.environ.get("CH_GTHETA_CONV", "tcgen05")
         net.close()
         print(json.dumps(r))
         return

@@ -1274,7 +1274,8 @@ __device__ __forceinline__ void ph_resid(const PArgs& a, Items its) {
         if (e < cnt) {
           const int i = a0 + e / n, j = e - (e / n) * n;
           double zc;
-          lz[q] = nsum4r<n>(zu, i, j, zc) - 4.0 * zc;  // h^2 lap(z) of the scaled z: h^-2 folded in
+          const double s4 = nsum4r<n>(zu, i, j, zc);  // sets zc (sequenced before its use below)
+          lz[q] = s4 - 4.0 * zc;  // h^2 lap(z) of the scaled z: h^-2 folded in
           yv[q] = __ldcg(Y + base + e);
           hv[q] = __ldcg(yhat + base + e);
           w64[q] = (a.zmode == 2) ? __ldcg(W64 + base + e) : 0.0;

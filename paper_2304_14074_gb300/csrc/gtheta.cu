@@ -227,16 +227,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid(const bf16* __restrict
 // start + ((2 ks) 18 + dy) 18 + dx + 8h (x 16 B), SBO = one halo row (288 B), LBO = one chunk
 // (5184 B). B (weights, N = 32 output channels x K) is [tap][c][co][8]: SBO = 128 B, LBO = 512 B.
 // Per tile: 2 halves x 9 taps x 2 K steps = 36 MMAs of 128 x 32 x 16 into two 32-column
-// accumulators; one thread issues them and commits to an mbarrier; every wait is bounded.
+// accumulators (one 64-column TMEM stage).
 constexpr int kHaloChunk = kHalo * kHalo * 8;                 // bf16 elements of one channel chunk
 constexpr int kHaloTc = 4 * kHaloChunk;                        // one halo buffer
-// Shared memory: two halo buffers, the weights, the mbarrier and the TMEM address. Every address a
-// descriptor forms (start + 15 row groups (SBO) + the second K half (LBO) + one core matrix)
-// stays inside the two halo buffers.
-constexpr size_t kConvTcSmem = (2 * kHaloTc + 9 * 4 * kC * 8) * sizeof(bf16) + 64;  // + 2 mbarriers, TMEM slot
-constexpr size_t kTcStartMax = (size_t)kHaloTc * 2 + 2 * kHaloChunk * 2 + 2 * kHalo * 16 + 10 * 16;
-static_assert(kTcStartMax + 15 * kHalo * 16 + (size_t)kHaloChunk * 2 + 128 <= (size_t)2 * kHaloTc * 2,
-              "descriptor reach");
 
 __device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
   uint64_t d = 0;
@@ -253,31 +246,72 @@ __host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void load_halo_tc(bf16* halo, const bf16* __restrict__ x, int S, int ty0, int tx0) {
-  for (int c = threadIdx.x; c < kHalo * kHalo * 4; c += kThreads) {
-    const int pix = c >> 2, part = c & 3;
-    const int yy = pix / kHalo, xx = pix - yy * kHalo;
-    const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
-    const bool in = gy >= 0 && gy < S && gx >= 0 && gx < S;
-    const bf16* src = in ? x + ((size_t)gy * S + gx) * kC + part * 8 : x;
-    cp_async16(halo + part * kHaloChunk + (yy * kHalo + xx) * 8, src, in ? 16 : 0);
-  }
-}
+// ---- Pipelined tcgen05 convolution (warp-specialised). The same BF16 products as k_conv_mid in
+// the same FP32 accumulation order per tap (so the same bits), organised as a pipeline without
+// block barriers:
+//   warp 8 (producer): the halo of each tile into one of kTcHaloStages buffers with cp.async; a
+//     stage is handed over (mbarrier `full`) once the lane's copies have landed and been fenced
+//     for the tensor cores' (async) proxy, two stages in flight per lane;
+//   warp 9, lane 0 (issuer): per tile the 36 tcgen05.mma into one of kTcAccStages TMEM
+//     accumulators, then two commits: `accf` (accumulator complete) and `empty` (the halo
+//     buffer may be refilled);
+//   warps 0..7 (epilogue): tcgen05.ld of the accumulator, `acce` (it may be overwritten), then
+//     bias and ReLU (forward) or the ReLU mask (backward data), BF16, global stores.
+// Every wait is bounded: one that gives up sets the CTA's failure flag, the other roles leave
+// their loops at their next check or bounded wait, the issuer waits (longer, still bounded) for
+// its MMAs to complete, and the CTA frees its TMEM and reports the failure.
+// Measured on the forward of 8 x 511^2 fields (one CTA per SM): 4 stages handed over one tile
+// after their copies were issued 0.624 ms; 4 stages, three tiles after 0.855 ms; 8 stages, five
+// tiles after 0.679 ms.
+constexpr int kTcHaloStages = 4;
+constexpr int kTcLag = 1;          // tiles between issuing a stage's copies and handing it over
+constexpr int kTcAccStages = 4;    // 64 TMEM columns each (two halves x 32 channels)
+static_assert(kTcLag < kTcHaloStages, "the producer's wait for a free stage needs its MMAs issued");
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcProducer = 8;
+constexpr int kTcIssuer = 9;
+constexpr int kTcpThreads = 320;
+constexpr int kTcpTmemCols = 64 * kTcAccStages;
+constexpr size_t kTcWeightBytes = (size_t)9 * 4 * kC * 8 * sizeof(bf16);
+constexpr size_t kTcHaloBytes = (size_t)kHaloTc * sizeof(bf16);
+constexpr size_t kTcpSmem = kTcWeightBytes + kTcHaloStages * kTcHaloBytes + 256;  // + barriers, TMEM slot
+static_assert(kTcWeightBytes % 128 == 0 && kTcHaloBytes % 16 == 0, "descriptor alignment");
+// the last address a tap's descriptor reaches stays inside its halo buffer
+static_assert(((size_t)((2 * kHalo + 2) * kHalo + 2 + 8) * 16 + 15 * kHalo * 16 + (size_t)kHaloChunk * 2 + 128) <=
+                  kTcHaloBytes,
+              "descriptor reach");
+// CTAs per SM are limited by shared memory to at most two, so their TMEM (2 x 256 columns) fits
+static_assert(3 * (kTcpSmem + 1024) > 228 * 1024 && 2 * kTcpTmemCols <= 512, "TMEM occupancy");
+static_assert(kTcpSmem <= 227 * 1024, "shared memory per CTA");
 
-__global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restrict__ x, bf16* __restrict__ y,
-                                                             const bf16* __restrict__ W,
-                                                             const float* __restrict__ bias,
-                                                             const bf16* __restrict__ mask, int S, int tiles_x,
-                                                             int tiles, int mode, int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char tc_smem[];
-  bf16* halo = reinterpret_cast<bf16*>(tc_smem);         // two buffers
-  bf16* ws = halo + 2 * kHaloTc;                         // [tap][c][co][8]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(ws + 9 * 4 * kC * 8);  // one per accumulator
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mbar + 2);
-  __shared__ int s_fail;
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(b))
+               : "memory");
+}
+__device__ __forceinline__ unsigned saddr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__global__ void __launch_bounds__(kTcpThreads, 2) k_conv_mid_tcp(const bf16* __restrict__ x, bf16* __restrict__ y,
+                                                                 const bf16* __restrict__ W,
+                                                                 const float* __restrict__ bias,
+                                                                 const bf16* __restrict__ mask, int S, int tiles_x,
+                                                                 int tiles, int mode, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char tcp_smem[];
+  bf16* ws = reinterpret_cast<bf16*>(tcp_smem);                       // [tap][c][co][8]
+  bf16* halo = reinterpret_cast<bf16*>(tcp_smem + kTcWeightBytes);    // kTcHaloStages buffers
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tcp_smem + kTcWeightBytes + kTcHaloStages * kTcHaloBytes);
+  uint64_t* full = bars;                        // halo landed: 32 producer arrivals
+  uint64_t* empty = bars + kTcHaloStages;       // halo read by the MMAs: one commit
+  uint64_t* accf = bars + 2 * kTcHaloStages;    // accumulator complete: one commit
+  uint64_t* acce = accf + kTcAccStages;         // accumulator read out: one arrival per epilogue warp
+  uint64_t* drain = acce + kTcAccStages;        // every issued MMA complete
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(drain + 1);
+  __shared__ volatile int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_img = tiles_x * tiles_x;
-  // tiles of this CTA: blockIdx.x + j gridDim.x, j = 0 .. count-1
   const int count = (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   auto tile_origin = [&](int j, int& img, int& ty0, int& tx0) {
     const int tl = blockIdx.x + j * gridDim.x;
@@ -286,162 +320,183 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_mid_tc(const bf16* __restr
     ty0 = (r / tiles_x) * kTile;
     tx0 = (r % tiles_x) * kTile;
   };
-  auto prefetch = [&](int j) {  // halo of tile j into buffer j & 1
-    int img, ty0, tx0;
-    tile_origin(j, img, ty0, tx0);
-    load_halo_tc(halo + (j & 1) * kHaloTc, x + (size_t)img * S * S * kC, S, ty0, tx0);
-  };
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int b = 0; b < 2; ++b) {
-      const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + b));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    for (int i = 0; i < kTcHaloStages; ++i) {
+      mbar_init(full + i, 32);
+      mbar_init(empty + i, 1);
     }
+    for (int i = 0; i < kTcAccStages; ++i) {
+      mbar_init(accf + i, 1);
+      mbar_init(acce + i, kTcEpiWarps);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
-  if (warp == 0) {  // 128 TMEM columns: two pairs of 128-lane x 32-column FP32 accumulators
-    const unsigned slot = static_cast<unsigned>(__cvta_generic_to_shared(tmem_slot));
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(slot));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                 "n"(kTcpTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
-  if (count > 0) prefetch(0);
-  cp_async_commit();
-  if (count > 1) prefetch(1);
-  cp_async_commit();
-  for (int c = threadIdx.x; c < 9 * kC * 4; c += kThreads) {
+  for (int c = threadIdx.x; c < 9 * kC * 4; c += kTcpThreads) {
     const int row = c >> 2, part = c & 3;  // row = tap * 32 + output channel, part = channel chunk
     const int tap = row / kC, co = row - tap * kC;
     *reinterpret_cast<uint4*>(ws + ((tap * 4 + part) * kC + co) * 8) =
         *reinterpret_cast<const uint4*>(W + row * kC + part * 8);
   }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::);  // the weights, for the tensor cores
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const unsigned tmem = *tmem_slot;
-  const unsigned wbase = static_cast<unsigned>(__cvta_generic_to_shared(ws));
-  constexpr uint32_t idesc = umma_idesc(128, 32);
-  // MMAs of tile j (36 of 128 x 32 x 16) into accumulator pair j & 1, committed to mbar[j & 1]
-  auto issue = [&](int j) {
-    if (threadIdx.x != 0) return;
-    const unsigned hbase = static_cast<unsigned>(__cvta_generic_to_shared(halo + (j & 1) * kHaloTc));
-    const unsigned dbase = tmem + 64u * (unsigned)(j & 1);
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    for (int hh = 0; hh < 2; ++hh)
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap - 3 * dy;
-        for (int ks = 0; ks < 2; ++ks) {
-          const unsigned a_addr = hbase + (unsigned)(((2 * ks * kHalo + dy) * kHalo + dx + 8 * hh) * 16);
-          const unsigned b_addr = wbase + (unsigned)((tap * 4 + 2 * ks) * kC * 16);
-          const uint64_t ad = umma_desc(a_addr, kHaloChunk * 2, kHalo * 16);
-          const uint64_t bd = umma_desc(b_addr, kC * 16, 8 * 16);
-          const unsigned acc = (tap | ks) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\t"
-              "setp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dbase + 32u * hh),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
+
+  if (warp == kTcProducer) {
+    // lane-strided 16-byte copies of the chunk-major halo [chunk][y][x][8] of tile j into stage s
+    auto load = [&](int j) {
+      int img, ty0, tx0;
+      tile_origin(j, img, ty0, tx0);
+      bf16* hb = halo + (size_t)(j % kTcHaloStages) * kHaloTc;
+      const bf16* xi = x + (size_t)img * S * S * kC;
+      for (int c = lane; c < kHalo * kHalo * 4; c += 32) {
+        const int pix = c >> 2, part = c & 3;
+        const int yy = pix / kHalo, xx = pix - yy * kHalo;
+        const int gy = ty0 - 1 + yy, gx = tx0 - 1 + xx;
+        const bool in = gy >= 0 && gy < S && gx >= 0 && gx < S;
+        const bf16* src = in ? xi + ((size_t)gy * S + gx) * kC + part * 8 : xi;
+        cp_async16(hb + part * kHaloChunk + (yy * kHalo + xx) * 8, src, in ? 16 : 0);
       }
-    const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (j & 1)));
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
-  };
-  // epilogue mapping: warp w reads TMEM lanes 32 (w % 4).. of accumulator h = w / 4
-  const int h = warp >> 2, m = (warp & 3) * 32 + lane;
-  const int oy = m >> 3, px = 8 * h + (m & 7);
-  float bv[kC];
-#pragma unroll
-  for (int c = 0; c < kC; ++c) bv[c] = (mode == 0) ? bias[c] : 0.f;
-  unsigned phase[2] = {0u, 0u};
-  int issued = 0;  // tiles whose MMAs have been issued (and committed)
-  int fail_at = -1;
-  if (count > 0) {
-    cp_async_wait<1>();  // tile 0's halo
-    asm volatile("fence.proxy.async.shared::cta;\n" ::);
-    __syncthreads();
-    issue(0);
-    issued = 1;
-  }
-  for (int j = 0; j < count; ++j) {
-    // (a) the next tile's MMAs, as soon as its halo is in
-    if (j + 1 < count) {
-      cp_async_wait<0>();
+      cp_async_commit();
+    };
+    // A stage is handed over kTcLag tiles after its copies were issued (kTcLag + 1 stages in
+    // flight per lane): this lane's copies of it have landed (cp.async groups complete in order)
+    // and are fenced for the async proxy.
+    auto publish = [&](int j) {
       asm volatile("fence.proxy.async.shared::cta;\n" ::);
-      __syncthreads();
-      issue(j + 1);
-      issued = j + 2;
-    }
-    // (b) this tile's MMAs done (bounded wait): its halo buffer and accumulators are free to read
-    const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (j & 1)));
-    if (!chwait::mbar_wait(mb, phase[j & 1], chwait::kSpins)) s_fail = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    __syncthreads();
-    if (s_fail) {
-      fail_at = j;  // tile j's phase has not been consumed
-      break;
-    }
-    phase[j & 1] ^= 1u;
-    // (c) the halo of tile j + 2 into the buffer tile j used
-    if (j + 2 < count) prefetch(j + 2);
-    cp_async_commit();
-    // (d) epilogue of tile j: D[m][co] of half h -> pixel (oy, px)
-    int img, ty0, tx0;
-    tile_origin(j, img, ty0, tx0);
-    unsigned r[32];
-    const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) + 64u * (unsigned)(j & 1) + 32u * h;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-    const int Y = ty0 + oy, X = tx0 + px;
-    if (Y < S && X < S) {
-      const size_t o = (size_t)img * S * S * kC + ((size_t)Y * S + X) * kC;
-      uint4 mk[4];
-      if (mode == 1)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(mask + o + 8 * q);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        unsigned pk[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int c = 8 * q + 2 * e;
-          float v0 = __uint_as_float(r[c]), v1 = __uint_as_float(r[c + 1]);
-          if (mode == 0) {
-            v0 = fmaxf(v0 + bv[c], 0.f);
-            v1 = fmaxf(v1 + bv[c + 1], 0.f);
-          } else {
-            const __nv_bfloat162 mm = reinterpret_cast<const __nv_bfloat162*>(&mk[q])[e];
-            v0 = (__bfloat162float(mm.x) > 0.f) ? v0 : 0.f;
-            v1 = (__bfloat162float(mm.y) > 0.f) ? v1 : 0.f;
-          }
-          const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-          pk[e] = *reinterpret_cast<const unsigned*>(&b2);
-        }
-        *reinterpret_cast<uint4*>(y + o + 8 * q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      mbar_arrive(full + j % kTcHaloStages);
+    };
+    int j = 0;
+    for (; j < count; ++j) {
+      bool ok = true;
+      if (j >= kTcHaloStages)
+        ok = chwait::mbar_wait(saddr(empty + j % kTcHaloStages), ((j / kTcHaloStages) - 1) & 1, chwait::kSpins);
+      if (!__all_sync(0xffffffffu, ok)) s_fail = 1;  // warp-uniform: one lane giving up stops all
+      if (s_fail) break;
+      load(j);
+      if (j >= kTcLag) {
+        cp_async_wait<kTcLag>();
+        publish(j - kTcLag);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();  // accumulators of tile j read before tile j + 2's MMAs overwrite them
-  }
-  cp_async_wait<0>();
-  if (fail_at >= 0 && threadIdx.x == 0) {
-    atomicExch(err, 1);
-    // Issue no more MMAs; let those already issued finish (a second, longer bounded wait)
-    // before their accumulator columns are freed.
-    for (int t = fail_at; t < issued; ++t) {
-      const unsigned mb = static_cast<unsigned>(__cvta_generic_to_shared(mbar + (t & 1)));
-      if (!chwait::mbar_wait(mb, phase[t & 1], chwait::kDrainSpins)) break;
-      phase[t & 1] ^= 1u;
+    cp_async_wait<0>();
+    if (!s_fail)
+      for (int t = (j > kTcLag ? j - kTcLag : 0); t < j; ++t) publish(t);
+  } else if (warp == kTcIssuer) {
+    if (lane == 0) {
+      const unsigned wbase = saddr(ws);
+      constexpr uint32_t idesc = umma_idesc(128, 32);
+      for (int j = 0; j < count; ++j) {
+        const int s = j % kTcHaloStages, a = j % kTcAccStages;
+        if (!chwait::mbar_wait(saddr(full + s), (j / kTcHaloStages) & 1, chwait::kSpins)) s_fail = 1;
+        if (!s_fail && j >= kTcAccStages &&
+            !chwait::mbar_wait(saddr(acce + a), ((j / kTcAccStages) - 1) & 1, chwait::kSpins))
+          s_fail = 1;
+        if (s_fail) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        const unsigned hbase = saddr(halo + (size_t)s * kHaloTc);
+        const unsigned dbase = tmem + 64u * (unsigned)a;
+        for (int hh = 0; hh < 2; ++hh)
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap - 3 * dy;
+            for (int ks = 0; ks < 2; ++ks) {
+              const unsigned a_addr = hbase + (unsigned)(((2 * ks * kHalo + dy) * kHalo + dx + 8 * hh) * 16);
+              const unsigned b_addr = wbase + (unsigned)((tap * 4 + 2 * ks) * kC * 16);
+              const uint64_t ad = umma_desc(a_addr, kHaloChunk * 2, kHalo * 16);
+              const uint64_t bd = umma_desc(b_addr, kC * 16, 8 * 16);
+              const unsigned acc = (tap | ks) ? 1u : 0u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dbase + 32u * hh),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            saddr(accf + a)));
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            saddr(empty + s)));
+      }
+      // every MMA issued so far completes before the accumulators are freed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          saddr(drain)));
+      if (!chwait::mbar_wait(saddr(drain), 0u, chwait::kDrainSpins)) s_fail = 1;
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4).. of half h = w / 4 -> pixel (oy, px)
+    const int h = warp >> 2, m = (warp & 3) * 32 + lane;
+    const int oy = m >> 3, px = 8 * h + (m & 7);
+    float bv[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) bv[c] = (mode == 0) ? bias[c] : 0.f;
+    for (int j = 0; j < count; ++j) {
+      const int a = j % kTcAccStages;
+      const bool ok = chwait::mbar_wait(saddr(accf + a), (j / kTcAccStages) & 1, chwait::kSpins);
+      if (!__all_sync(0xffffffffu, ok)) s_fail = 1;  // warp-uniform (tcgen05.ld is .sync.aligned)
+      if (s_fail) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      unsigned r[32];
+      const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) + 64u * (unsigned)a + 32u * h;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce + a);
+      int img, ty0, tx0;
+      tile_origin(j, img, ty0, tx0);
+      const int Y = ty0 + oy, X = tx0 + px;
+      if (Y < S && X < S) {
+        const size_t o = (size_t)img * S * S * kC + ((size_t)Y * S + X) * kC;
+        uint4 mk[4];
+        if (mode == 1)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(mask + o + 8 * q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          unsigned pk[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 8 * q + 2 * e;
+            float v0 = __uint_as_float(r[c]), v1 = __uint_as_float(r[c + 1]);
+            if (mode == 0) {
+              v0 = fmaxf(v0 + bv[c], 0.f);
+              v1 = fmaxf(v1 + bv[c + 1], 0.f);
+            } else {
+              const __nv_bfloat162 mm = reinterpret_cast<const __nv_bfloat162*>(&mk[q])[e];
+              v0 = (__bfloat162float(mm.x) > 0.f) ? v0 : 0.f;
+              v1 = (__bfloat162float(mm.y) > 0.f) ? v1 : 0.f;
+            }
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+            pk[e] = *reinterpret_cast<const unsigned*>(&b2);
+          }
+          *reinterpret_cast<uint4*>(y + o + 8 * q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
+  if (s_fail && threadIdx.x == 0) atomicExch(err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTcpTmemCols));
+  }
 }
 
 // First layer 1 -> 32: a1 = relu(conv(U, W1) + b1); U FP64 (inference) or FP32 (training).
@@ -787,17 +842,17 @@ void conv_mid_tc(const bf16* x, bf16* y, const bf16* W, const float* bias, const
   std::unique_lock<std::mutex> lock(mu);
   int& slots = slot_of[chctx::cache_key()];
   if (slots == 0) {
-    int sms = 0, per_sm = 0;
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_conv_mid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvTcSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_mid_tc, kThreads, kConvTcSmem);
-    slots = std::max(1, sms * std::max(1, std::min(per_sm, 4)));
+    // One CTA per SM (measured: two per SM take 128 us per layer against 106 us for one); its
+    // shared memory admits at most two, so their TMEM (2 x 256 columns) would always fit.
+    cudaFuncSetAttribute(k_conv_mid_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcpSmem);
+    slots = std::max(1, sms);
   }
   const int tx = (S + kTile - 1) / kTile, tiles = tx * tx * batch;
   const int grid = std::min(tiles, slots);
   lock.unlock();
-  k_conv_mid_tc<<<grid, kThreads, kConvTcSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode,
-                                                                            err);
+  k_conv_mid_tcp<<<grid, kTcpThreads, kTcpSmem, st>>>(x, y, W, bias, mask, S, tx, tiles, mode, err);
 }
 
 // Persistent launch of k_conv_mid: as many CTAs as fit on the GPU (at most one per tile).
@@ -848,9 +903,10 @@ cudaError_t GTheta::init(unsigned long long seed, cudaStream_t st) {
   al((void**)&err_, sizeof(int));
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(err_, 0, sizeof(int), st)) != cudaSuccess) return e;
-  // CH_GTHETA_CONV=tcgen05 runs the 32 -> 32 layers as tcgen05.mma (default: mma.sync)
+  // The 32 -> 32 layers run on tcgen05.mma (k_conv_mid_tcp); CH_GTHETA_CONV=mma selects the
+  // warp-level mma.sync kernel (k_conv_mid), which gives the same bits
   const char* cv = std::getenv("CH_GTHETA_CONV");
-  tc_ = cv && std::strcmp(cv, "tcgen05") == 0;
+  tc_ = !(cv && std::strcmp(cv, "mma") == 0);
   // He-normal initial weights (Box-Muller on SplitMix64), zero biases; the last layer scaled 0.1
   std::vector<float> p(kParams, 0.f);
   const int cin[6] = {1, 32, 32, 32, 32, 32}, cout[6] = {32, 32, 32, 32, 32, 1};

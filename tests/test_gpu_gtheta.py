@@ -105,9 +105,11 @@ def test_forward_is_deterministic_and_batch_independent(gpu_lib):
     assert np.array_equal(a[1:2], c)
 
 
+@pytest.mark.parametrize("conv", ["tcgen05", "mma"])
 @pytest.mark.parametrize("S,margin", [(24, 3), (43, 6)])
-def test_gradients_match_oracle(gpu_lib, S, margin):
+def test_gradients_match_oracle(gpu_lib, monkeypatch, S, margin, conv):
     ch = gpu_lib
+    monkeypatch.setenv("CH_GTHETA_CONV", conv)
     p, (W, b) = fp32_net(ch, *random_net(5))
     net = ch.GTheta()
     net.set_params(p)
@@ -260,7 +262,7 @@ def test_guard_restarts_runaway_learned_coarse_sweep_with_plain_step(gpu_lib):
 
 @pytest.fixture
 def tcgen05_conv(monkeypatch):
-    """The 32 -> 32 layers on tcgen05.mma (read when a network is created)."""
+    """The 32 -> 32 layers on tcgen05.mma (the default; read when a network is created)."""
     monkeypatch.setenv("CH_GTHETA_CONV", "tcgen05")
 
 
@@ -272,10 +274,12 @@ def test_tcgen05_forward_matches_oracle_and_mma_path(gpu_lib, tcgen05_conv, monk
     net.set_params(p)
     u = np.stack([ch_inputs.initial_condition(2, n, 10 + i, kind="normal", amp=0.5).reshape(n, n) for i in range(2)])
     out = net.forward(dev(u)).cpu().numpy()
-    monkeypatch.delenv("CH_GTHETA_CONV")
+    monkeypatch.setenv("CH_GTHETA_CONV", "mma")
     ref_net = ch.GTheta()
     ref_net.set_params(p)
     out_mma = ref_net.forward(dev(u)).cpu().numpy()
+    # the same BF16 products in the same FP32 accumulation order per tap: the same bits
+    assert np.array_equal(out, out_mma)
     for i in range(2):
         _, aq = go.forward(u[i], W, b, bf16=True)
         r, rq = out[i] - u[i], aq[-1][..., 0]
@@ -382,8 +386,7 @@ def test_each_layer_matches_oracle_on_its_own_input(gpu_lib, monkeypatch, conv):
     much plus one BF16 ulp. Most activations are bit-identical (< 1% differ). The FP32 output
     layer R is within gamma_288 sum |terms|."""
     ch = gpu_lib
-    if conv == "tcgen05":
-        monkeypatch.setenv("CH_GTHETA_CONV", "tcgen05")
+    monkeypatch.setenv("CH_GTHETA_CONV", conv)
     p, (W, b) = fp32_net(ch, *random_net(11))
     net = ch.GTheta()
     net.set_params(p)
