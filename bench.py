@@ -528,7 +528,8 @@ def sweep2d(w, args):
     dt = w["T"] / N / J
     u0 = np.stack([ch_inputs.initial_condition(2, n, w.get("seed0", 0) + s, kind="normal", amp=w["amp"])
                    for s in range(N)])
-    cfg = ch.Config(dim=2, n=n, eps=w["eps"], T=w["T"], n_slices=N, fine_steps=J, newton_tol=w["newton_tol"])
+    cfg = ch.Config(dim=2, n=n, eps=w["eps"], T=w["T"], n_slices=N, fine_steps=J, newton_tol=w["newton_tol"],
+                    lin_tol=args.lin_tol)
     X0 = torch.as_tensor(u0, device="cuda")
     # start from states past the initial transient (a few fine steps), as the slices of a sweep
     X0 = ch.propagate(cfg, "nl", dt, 8, X0)
@@ -548,6 +549,7 @@ def sweep2d(w, args):
         tot_newton += int(newton.sum().item())
     t = sum(ms) / len(ms)
     return {"experiment": "sweep2d", "workload": w["name"], "units": N, "fine_steps": args.fine,
+            "lin_tol": args.lin_tol or 1e-4,
             "ms_per_propagation": round(t, 3), "grid_pt_steps_per_s": N * args.fine * n * n / (t / 1e3),
             "newton_per_unit_step": tot_newton / (args.steps * N * args.fine)}
 
@@ -857,6 +859,7 @@ def main():
                          "workload (all its slices batched), `--steps` times `--fine` steps, timed alone. One JSON "
                          "line each.")
     ap.add_argument("--fine", type=int, default=2, help="sweep2d: fine steps per timed propagation")
+    ap.add_argument("--lin-tol", type=float, default=0.0, help="sweep2d: inner CG tolerance (0: the default)")
     args = ap.parse_args()
     if args.experiment == "gtheta-fwd":
         import torch
