@@ -114,6 +114,56 @@ static void add_forcing(int n, double dt, double t, const orc_forcing* f, double
 
 /* ----------------------------------------------------------------- time steps */
 
+/* The linear step M Y = b of Eq. 2.4 / 2.5, M = I + e2dt D_h^2 - cdt D_h diag(w) (w = 1 when
+ * NULL; `a` holds M in band form), taken from its residual instead of one elimination: Y_0 = u^n,
+ * Y_{m+1} = Y_m - M^{-1} H(Y_m) with H(Y) = Y + e2dt D_h (D_h Y) - cdt D_h (w Y) - b, stopped by
+ * the Newton rule of the nonlinear step. The same step with other rounding: the FP64 residual
+ * fixes the attainable accuracy, as in a solver that refines a low-precision solve. */
+static int linear_by_residual(const orc_params* p, int n, double e2dt, double cdt, const double* w,
+                              const double* a, const double* b, const double* u, double* out,
+                              orc_stats* st) {
+  const int wdt = 7;
+  double* lu = (double*)malloc(sizeof(double) * (size_t)n * wdt);
+  double* y = (double*)malloc(sizeof(double) * n);
+  double* hh = (double*)malloc(sizeof(double) * n);
+  double* dy = (double*)malloc(sizeof(double) * n);
+  double* d2y = (double*)malloc(sizeof(double) * n);
+  double* wy = (double*)malloc(sizeof(double) * n);
+  double* dwy = (double*)malloc(sizeof(double) * n);
+  int rc = 0, m = 0, ok = 0;
+  double prev = 0.0;
+  if (!lu || !y || !hh || !dy || !d2y || !wy || !dwy) { rc = 1; goto done; }
+  memcpy(y, u, sizeof(double) * n);
+  while (m < p->newton_max) {
+    orc1d_dh_apply(n, y, dy);
+    orc1d_dh_apply(n, dy, d2y);
+    for (int j = 0; j < n; ++j) wy[j] = (w ? w[j] : 1.0) * y[j];
+    orc1d_dh_apply(n, wy, dwy);
+    for (int j = 0; j < n; ++j) hh[j] = y[j] + e2dt * d2y[j] - cdt * dwy[j] - b[j];
+    memcpy(lu, a, sizeof(double) * (size_t)n * wdt); /* orc_band_solve factors in place */
+    rc = orc_band_solve(n, 2, 2, lu, hh);
+    if (rc) break;
+    double diff = 0.0;
+    for (int j = 0; j < n; ++j) {
+      y[j] -= hh[j];
+      if (fabs(hh[j]) > diff) diff = fabs(hh[j]);
+    }
+    ++m;
+    if (diff <= p->newton_tol) { ok = 1; break; }
+    if (m >= 2 && diff <= sqrt(p->newton_tol) && diff > 0.5 * prev) { ok = 1; break; }
+    prev = diff;
+  }
+  if (st) {
+    st->newton_total += m;
+    if (m > st->newton_max_seen) st->newton_max_seen = m;
+  }
+  if (!rc && !ok) rc = 3;
+  if (!rc) memcpy(out, y, sizeof(double) * n);
+done:
+  free(lu); free(y); free(hh); free(dy); free(d2y); free(wy); free(dwy);
+  return rc;
+}
+
 int orc1d_step(const orc_params* p, int scheme, double dt, double t_next, const double* u,
                double* out, const orc_forcing* f, orc_stats* st) {
   if (!p || !u || !out || p->n < 1 || dt <= 0.0) return 1;
@@ -134,8 +184,12 @@ int orc1d_step(const orc_params* p, int scheme, double dt, double t_next, const 
     for (int j = 0; j < n; ++j) { rhs[j] = u[j] - dt * tmp[j]; w[j] = u[j] * u[j]; }
     add_forcing(n, dt, t_next, f, rhs);
     assemble(n, dt, e2 * dt, p->frozen ? NULL : w, a);
-    rc = orc_band_solve(n, 2, 2, a, rhs);
-    if (!rc) memcpy(out, rhs, sizeof(double) * n);
+    if (p->newton_form == 1) {
+      rc = linear_by_residual(p, n, e2 * dt, dt, p->frozen ? NULL : w, a, rhs, u, out, st);
+    } else {
+      rc = orc_band_solve(n, 2, 2, a, rhs);
+      if (!rc) memcpy(out, rhs, sizeof(double) * n);
+    }
   } else if (scheme == ORC_LIN2) {
     /* Eq. 2.5 (D_h on the implicit 2 dt term) */
     for (int j = 0; j < n; ++j) w[j] = p->frozen ? u[j] : u[j] * u[j] * u[j];
@@ -144,8 +198,12 @@ int orc1d_step(const orc_params* p, int scheme, double dt, double t_next, const 
     for (int j = 0; j < n; ++j) rhs[j] = u[j] + dt * tmp[j] - 3.0 * dt * y[j];
     add_forcing(n, dt, t_next, f, rhs);
     assemble(n, 2.0 * dt, e2 * dt, NULL, a);
-    rc = orc_band_solve(n, 2, 2, a, rhs);
-    if (!rc) memcpy(out, rhs, sizeof(double) * n);
+    if (p->newton_form == 1) {
+      rc = linear_by_residual(p, n, e2 * dt, 2.0 * dt, NULL, a, rhs, u, out, st);
+    } else {
+      rc = orc_band_solve(n, 2, 2, a, rhs);
+      if (!rc) memcpy(out, rhs, sizeof(double) * n);
+    }
   } else if (scheme == ORC_NL) {
     /* Eq. 3.17: Yhat = (I - dt D_h) u^n; Newton of Eq. 3.18 from Y_0 = u^n. */
     double* yhat = (double*)malloc(sizeof(double) * n);

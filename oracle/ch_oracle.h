@@ -51,9 +51,11 @@ typedef struct {
   double tol;         /* stop when max_n ||U_n^k - U_n^{k-1}||_inf < tol (tol <= 0: never) */
   int max_iters;      /* at most this many Parareal iterations (<= N) */
   int newton_form;    /* 0: Eq. 3.18 as printed, Y_{m+1} = J^{-1}(Yhat - 2 dt D_h Y_m^3);
-                         1: the unsimplified Newton step Y_{m+1} = Y_m - J^{-1} H(Y_m). The two are
-                         the same iteration; they differ only in rounding, which measures how far
-                         two correct FP64 implementations can drift apart (parity floor). */
+                         1: the unsimplified Newton step Y_{m+1} = Y_m - J^{-1} H(Y_m), and the
+                         linear steps (Eq. 2.4 / 2.5) taken from their residual the same way
+                         from Y_0 = u^n. The two forms are the same steps; they differ only in
+                         rounding, which measures how far two correct FP64 implementations can
+                         drift apart (parity floor). */
 } orc_params;
 
 /* Manufactured forcing g(x,t) = sum_i a_i exp(b_i t) sin(m_i pi x), added as dt*g(t_{n+1}). */

@@ -94,7 +94,7 @@ class Params:
     frozen: bool = False
     tol: float = 0.0
     max_iters: int = -1
-    newton_form: int = 0  # 0: Eq. 3.18 as printed; 1: Y - J^{-1} H(Y) (same iteration, other rounding)
+    newton_form: int = 0  # 0: Eq. 3.18 as printed, direct linear steps; 1: Y - J^{-1} H(Y) for all (other rounding)
 
     def c(self) -> _Params:
         mi = self.N if self.max_iters < 0 else self.max_iters

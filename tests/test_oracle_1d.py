@@ -121,6 +121,29 @@ def test_newton_forms_reach_the_same_root():
     assert np.max(np.abs(a - b)) < 1e-13
 
 
+@pytest.mark.parametrize("scheme", ["lin1", "lin2"])
+@pytest.mark.parametrize("frozen", [False, True])
+def test_linear_steps_from_their_residual_match_dense_brute_force(scheme, frozen):
+    """The residual form of the linear steps (Eq. 2.4 / 2.5 reached by Y <- Y - M^{-1} H(Y) from
+    u^n) is the same step as the direct solve: both against a dense solve, to rounding; the
+    iteration stops after a few refinements."""
+    n, eps, dt = 14, 0.1, 1e-3
+    u = ch_inputs.initial_condition(1, n, 5, amp=0.8)
+    p = o.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=1e-13, newton_form=1, frozen=frozen)
+    out, iters = o.step(p, scheme, dt, u)
+    if frozen:
+        D, I = dense_dh(n), np.eye(n)
+        c = 1.0 if scheme == "lin1" else 2.0
+        rhs = u - dt * D @ u if scheme == "lin1" else u + dt * D @ u - 3 * dt * D @ u
+        ref = np.linalg.solve(I - c * dt * D + eps ** 2 * dt * D @ D, rhs)
+    else:
+        ref = dense_step(scheme, u, dt, eps)
+    assert np.max(np.abs(out - ref)) < 1e-12
+    direct, _ = o.step(o.Params(n=n, eps=eps, T=1, N=1, J=1, frozen=frozen), scheme, dt, u)
+    assert np.max(np.abs(out - direct)) < 1e-13
+    assert 1 <= iters <= 4
+
+
 @pytest.mark.parametrize("scheme,i", [("lin1", 1), ("lin2", 2), ("nl", 1)])
 def test_frozen_step_matches_lemma_3_1_factor(scheme, i):
     """Frozen model (diag(u^2) = I): each sine mode is scaled by g_i(mu_p) of Lemma 3.1."""
