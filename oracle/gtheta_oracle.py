@@ -112,14 +112,19 @@ def backward(acts, W, grad_r: np.ndarray, bf16: bool = False):
     return gW, gb
 
 
-def mse_crop_loss(r: np.ndarray, target: np.ndarray, margin: int):
+def mse_crop_loss(r: np.ndarray, target: np.ndarray, margin: int, relative: bool = False):
     """Mean of (r - target)^2 over the window [margin, H - margin) x [margin, W - margin); the
-    gradient with respect to r is zero outside it."""
+    gradient with respect to r is zero outside it. relative: the sum of (r - target)^2 over the
+    window divided by E = sum of target^2 there + 1e-12 per window pixel (one crop's relative
+    squared error; a batch's loss is the mean of its crops')."""
     H, Wd = r.shape
     m = np.zeros_like(r)
     m[margin:H - margin, margin:Wd - margin] = 1.0
     cnt = m.sum()
     d = (r - target) * m
+    if relative:
+        e = float((target * target * m).sum()) + 1e-12 * cnt
+        return float((d * d).sum() / e), 2.0 * d / e
     return float((d * d).sum() / cnt), 2.0 * d / cnt
 
 

@@ -38,8 +38,9 @@ def test_zero_padding_matches_embedded_field():
     assert np.allclose(y, yb[2:8, 2:7])
 
 
+@pytest.mark.parametrize("relative", [False, True])
 @pytest.mark.parametrize("layer", [0, 2, 5])
-def test_gradients_match_central_differences(layer):
+def test_gradients_match_central_differences(layer, relative):
     rng = np.random.default_rng(7)
     H = 9
     u = 0.7 * rng.standard_normal((H, H))
@@ -48,10 +49,10 @@ def test_gradients_match_central_differences(layer):
 
     def loss_of(W_, b_):
         gu, acts = g.forward(u, W_, b_)
-        return g.mse_crop_loss(acts[-1][..., 0], target, 1)[0]
+        return g.mse_crop_loss(acts[-1][..., 0], target, 1, relative)[0]
 
     gu, acts = g.forward(u, W, b)
-    _, dr = g.mse_crop_loss(acts[-1][..., 0], target, 1)
+    _, dr = g.mse_crop_loss(acts[-1][..., 0], target, 1, relative)
     gW, gb = g.backward(acts, W, dr)
     hstep = 1e-6
     for idx in [(0, 1, 0, 0), (1, 2, 0, 0), (2, 0, 0, 0)]:
@@ -133,3 +134,21 @@ def test_bf16_backward_matches_fp64_backward_to_bf16_accuracy():
     for l in range(6):
         rel = np.linalg.norm(gWq[l] - gW[l]) / np.linalg.norm(gW[l])
         assert rel < 5e-2, (l, rel)
+
+
+def test_relative_crop_loss_is_the_relative_squared_error():
+    """Relative loss of one crop: r = (1 + c) t on the window gives c^2 (up to the 1e-12 floor),
+    whatever the scale of t; outside the window nothing counts."""
+    rng = np.random.default_rng(3)
+    for scale in (1e-3, 1.0, 50.0):
+        t = scale * rng.standard_normal((10, 10))
+        r = 1.25 * t
+        r[0, :] += 7.0  # outside the window (margin 2)
+        loss, dr = g.mse_crop_loss(r, t, 2, relative=True)
+        et = float((t[2:8, 2:8] ** 2).sum())
+        assert abs(loss - 0.0625 * et / (et + 1e-12 * 36)) <= 1e-12
+        assert np.all(dr[:2] == 0) and np.all(dr[:, :2] == 0)
+        # the gradient of the relative loss is the absolute one scaled by count / E
+        _, dra = g.mse_crop_loss(r, t, 2)
+        e = float((t[2:8, 2:8] ** 2).sum()) + 1e-12 * 36
+        assert np.allclose(dr, dra * 36 / e, rtol=1e-12, atol=0)
