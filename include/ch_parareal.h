@@ -94,7 +94,7 @@ typedef struct {
   double lin_tol;      /* 2D inner linear solves (the Jacobian system of each Newton iteration
                           of Eq. 3.17, and the refinement sweeps of Eq. 2.4 / 2.5): CG stops once
                           the preconditioned residual norm has dropped by this factor; in (0, 1),
-                          <= 0 selects 1e-4. Newton's FP64 residual is unchanged, so the step
+                          <= 0 selects 1e-3. Newton's FP64 residual is unchanged, so the step
                           converges to the same FP64 root; a looser value trades more Newton
                           iterations for fewer CG iterations. Ignored in 1D (direct solves).   */
   int lin_max;         /* 2D: CG iterations per inner solve at most; <= 0 selects 60.         */
@@ -260,8 +260,17 @@ ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, const double* ba
  * [batch][n][n]; len must be batch n^2 (5 * 32 + 1). Synchronises. */
 ch_status ch_gtheta_activations(ch_gtheta* g, const double* in_dev, int batch, int n, float* acts_dev, size_t len);
 
-/* Loss and gradients for one minibatch: in_dev, target_dev FP32 [batch][S][S] (device); loss =
- * mean over the batch and the window [margin, S - margin)^2 of (R(in) - target)^2.
+/* The loss of ch_gtheta_gradients and ch_gtheta_train. relative = 0 (the default): the mean
+ * over the batch and the window [margin, S - margin)^2 of (R(in) - target)^2. relative = 1: the
+ * mean over the batch of each crop's sum over the window of (R(in) - target)^2 divided by
+ * E = sum of target^2 there + 1e-12 (window pixels): every crop counts by its relative error,
+ * as the coarse step is judged (slices late in time, whose changes are small, weigh as much as
+ * early ones). CH_ERR_INVALID for other values. */
+ch_status ch_gtheta_set_loss(ch_gtheta* g, int relative);
+
+/* Loss and gradients for one minibatch: in_dev, target_dev FP32 [batch][S][S] (device); loss as
+ * set by ch_gtheta_set_loss (by default the mean over the batch and the window
+ * [margin, S - margin)^2 of (R(in) - target)^2).
  * grad_host: CH_GTHETA_PARAMS FP32 values in the parameter layout (len must match);
  * loss_host: NULL or one float. Synchronises. */
 ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* target_dev, int batch, int S,

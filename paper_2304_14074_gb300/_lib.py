@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "ch_gtheta_train", "ch_ensemble_create", "ch_ensemble_set_initial", "ch_ensemble_compute_reference",
     "ch_ensemble_run", "ch_ensemble_get_slices", "ch_ensemble_get_reference", "ch_ensemble_get_stats",
     "ch_ensemble_groups", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_parareal_theory_bound",
-    "ch_parareal_set_fine_nn", "ch_wait_selftest", "ch_gtheta_activations",
+    "ch_parareal_set_fine_nn", "ch_wait_selftest", "ch_gtheta_activations", "ch_gtheta_set_loss",
 ]
 _NO_STATUS = ("ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_gtheta_destroy",
               "ch_gtheta_last_error", "ch_ensemble_destroy", "ch_ensemble_last_error", "ch_ensemble_groups")
@@ -87,7 +87,7 @@ class Config:
     frozen: bool = False
     err_tol: float = 0.0
     dim: int = 1
-    lin_tol: float = 0.0  # 2D inner CG reduction factor (<= 0: 1e-4)
+    lin_tol: float = 0.0  # 2D inner CG reduction factor (<= 0: 1e-3)
     lin_max: int = 0      # 2D inner CG iterations at most (<= 0: 60)
 
     def c(self) -> _Config:
@@ -149,6 +149,7 @@ def load(build_if_missing: bool = True):
     lib.ch_gtheta_get_params.argtypes = [vp, f, sz]
     lib.ch_gtheta_forward.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int]
     lib.ch_gtheta_gradients.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, f, sz, f]
+    lib.ch_gtheta_set_loss.argtypes = [vp, C.c_int]
     lib.ch_gtheta_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                     C.c_ulonglong, f]
     ip = C.POINTER(C.c_int)
@@ -390,6 +391,11 @@ class GTheta:
         p = np.ascontiguousarray(params, dtype=np.float32)
         self._check(self.lib.ch_gtheta_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
                     "ch_gtheta_set_params")
+
+    def set_loss(self, relative: bool) -> None:
+        """Training loss: mean squared error on the crop windows (False, the default), or each
+        crop's squared error relative to its target's energy (True)."""
+        self._check(self.lib.ch_gtheta_set_loss(self._h, 1 if relative else 0), "ch_gtheta_set_loss")
 
     def get_params(self) -> np.ndarray:
         p = np.empty(CH_GTHETA_PARAMS, dtype=np.float32)

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libchparareal.so")
-SOURCES = ["ch1d.cu", "ch2d.cu", "ch_api.cu", "ch_noalloc.cu", "gtheta.cu", "ch_gtheta_api.cu", "ch_ensemble.cu",
+SOURCES = ["ch1d.cu", "ch1d_lin.cu", "ch2d.cu", "ch_api.cu", "ch_noalloc.cu", "gtheta.cu", "ch_gtheta_api.cu", "ch_ensemble.cu",
            "ch_theory.cu", "ch_nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

@@ -1,610 +1,11 @@
-// One-dimensional Parareal for the Cahn-Hilliard equation on sm_103a.
-//
-// One CTA owns one state vector (a problem's slice) for the whole propagation: the state
-// lives in registers (thread t holds 2P consecutive rows), so HBM sees only the slice state
-// coming in and F(U) going out. Per time step:
-//   - the nonlinear scheme Eq. 2.3 is solved by Newton (Eq. 3.17/3.18) written as
-//     Y <- Y - J(Y)^{-1} H(Y): the residual H is formed in FP64 (its rounding floor is what
-//     limits attainable accuracy), the Jacobian solve runs in FP32 (precision 1) or FP64;
-//     GB300's FP64 pipe is about 1/58 of its FP32 rate, so FP64 is spent only on H and the
-//     update;
-//   - the linear schemes Eq. 2.4 / Eq. 2.5 are one FP64 pentadiagonal solve.
-// The Jacobian and step matrices are I + eps^2 dt D_h^2 + c dt (-D_h) diag(w) with D_h of
-// Eq. 3.2 (zero boundary values), solved by the partition method of ch_block_solver.cuh.
-#include <cmath>
-#include <mutex>
-#include <set>
-#include <utility>
+// One-dimensional Parareal: host dispatch of the kernels of ch1d_steps.cuh (the FP64 paths and
+// the nonlinear scheme with FP32 inner solves; the linear schemes with FP32 inner solves are
+// launched from ch1d_lin.cu).
+#include <algorithm>
 
-#include "ch_ctx.cuh"
-#include "ch1d.cuh"
-#include "ch_block_solver.cuh"
+#include "ch1d_steps.cuh"
 
 namespace chg {
-
-template <int T>
-union SolverUnion {
-  SolverSmem<float, T> f;
-  SolverSmem<double, T> d;
-};
-
-template <int T>
-struct Smem1D {
-  double fst[T];
-  double lst[T];
-  SolverUnion<T> s;
-  ReduceSmem<T> red;
-  int unit;
-};
-
-template <typename S, int T>
-__device__ __forceinline__ SolverSmem<S, T>& solver_smem(Smem1D<T>& sm);
-template <>
-__device__ __forceinline__ SolverSmem<float, 32>& solver_smem<float, 32>(Smem1D<32>& sm) { return sm.s.f; }
-template <>
-__device__ __forceinline__ SolverSmem<float, 64>& solver_smem<float, 64>(Smem1D<64>& sm) { return sm.s.f; }
-template <>
-__device__ __forceinline__ SolverSmem<float, 128>& solver_smem<float, 128>(Smem1D<128>& sm) { return sm.s.f; }
-template <>
-__device__ __forceinline__ SolverSmem<float, 256>& solver_smem<float, 256>(Smem1D<256>& sm) { return sm.s.f; }
-template <>
-__device__ __forceinline__ SolverSmem<double, 32>& solver_smem<double, 32>(Smem1D<32>& sm) { return sm.s.d; }
-template <>
-__device__ __forceinline__ SolverSmem<double, 64>& solver_smem<double, 64>(Smem1D<64>& sm) { return sm.s.d; }
-template <>
-__device__ __forceinline__ SolverSmem<double, 128>& solver_smem<double, 128>(Smem1D<128>& sm) { return sm.s.d; }
-template <>
-__device__ __forceinline__ SolverSmem<double, 256>& solver_smem<double, 256>(Smem1D<256>& sm) { return sm.s.d; }
-
-// Exchange of chunk-edge values: left = value of row r0-1, right = value of row r0+2P.
-template <int T>
-__device__ __forceinline__ void exchange(Smem1D<T>& sm, double first, double last, double& left,
-                                         double& right) {
-  const int t = threadIdx.x;
-  sm.fst[t] = first;
-  sm.lst[t] = last;
-  __syncthreads();
-  left = (t > 0) ? sm.lst[t - 1] : 0.0;
-  right = (t < T - 1) ? sm.fst[t + 1] : 0.0;
-  __syncthreads();
-}
-
-struct StepCtx {
-  int n;
-  int frozen;
-  int newton_max;
-  double ih2;  // 1/h^2
-  double eps2;
-  double newton_tol;
-  double newton_floor;  // sqrt(newton_tol)
-};
-
-// Blocks of  I + alpha S4 + beta A diag(w)  for the 2P rows r0.. of this thread, where
-// S4 = h^4 D_h^2 rows [1 -4 6 -4 1] (first/last rows [5 -4 1]) and A = -h^2 D_h rows
-// [-1 2 -1]; rows >= n are identity rows with no coupling. w has the neighbours wl (row r0-1)
-// and wr (row r0+2P).
-template <typename S, int P>
-__device__ __forceinline__ void assemble(int r0, int n, S alpha, S beta, const S (&w)[2 * P], S wl,
-                                         S wr, M2<S> (&A)[P], M2<S> (&B)[P], M2<S> (&C)[P]) {
-  constexpr int R = 2 * P;
-  S e[R], a[R], b[R], c[R], f[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int r = r0 + q;
-    const S wm = (q > 0) ? w[q - 1] : wl;
-    const S wp = (q < R - 1) ? w[q + 1] : wr;
-    const bool in = r < n;
-    e[q] = (in && r >= 2) ? alpha : S(0);
-    a[q] = (in && r >= 1) ? (S(-4) * alpha - beta * wm) : S(0);
-    const S diag4 = S(6) - S(r == 0 ? 1 : 0) - S(r == n - 1 ? 1 : 0);
-    b[q] = in ? (S(1) + diag4 * alpha + S(2) * beta * w[q]) : S(1);
-    c[q] = (r + 1 < n) ? (S(-4) * alpha - beta * wp) : S(0);
-    f[q] = (r + 2 < n) ? alpha : S(0);
-  }
-#pragma unroll
-  for (int l = 0; l < P; ++l) {
-    const int q0 = 2 * l, q1 = 2 * l + 1;
-    A[l] = {e[q0], a[q0], S(0), e[q1]};
-    B[l] = {b[q0], c[q0], a[q1], b[q1]};
-    C[l] = {f[q0], S(0), c[q1], f[q1]};
-  }
-}
-
-// One step of the nonlinear scheme Eq. 2.3 by Newton from Y_0 = u^n (Eq. 3.17/3.18), with
-// the Jacobian solve in precision S. y holds u^n on entry and u^{n+1} on return.
-// Returns the Newton iterations (negative if newton_max was reached); sets `bad` on a
-// non-finite value.
-template <int T, int P, typename S>
-__device__ int nl_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
-  constexpr int R = 2 * P;
-  const int r0 = threadIdx.x * R;
-  double L, Rt;
-  double yh[R];
-  exchange(sm, y[0], y[R - 1], L, Rt);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const double um = (q > 0) ? y[q - 1] : L;
-    const double up = (q < R - 1) ? y[q + 1] : Rt;
-    yh[q] = (r0 + q < c.n) ? y[q] - dt * c.ih2 * (um - 2.0 * y[q] + up) : 0.0;  // (I - dt D_h) u^n
-  }
-  const double c1 = c.eps2 * dt * c.ih2;
-  const S alpha = S(c.eps2 * dt * c.ih2 * c.ih2);
-  const S beta = S((c.frozen ? 1.0 : 3.0) * dt * c.ih2);
-  double prev = 0.0;
-  int m = 0;
-  bool ok = false;
-  while (m < c.newton_max) {
-    exchange(sm, y[0], y[R - 1], L, Rt);
-    // H(Y) = Y - Yhat + D_h z,  z = eps^2 dt D_h Y - dt Y^3   (Eq. 3.17)
-    double z[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const double um = (q > 0) ? y[q - 1] : L;
-      const double up = (q < R - 1) ? y[q + 1] : Rt;
-      const double cube = c.frozen ? y[q] : y[q] * y[q] * y[q];
-      z[q] = (r0 + q < c.n) ? c1 * (um - 2.0 * y[q] + up) - dt * cube : 0.0;
-    }
-    double zl, zr;
-    exchange(sm, z[0], z[R - 1], zl, zr);
-    S w[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) w[q] = c.frozen ? S(1) : S(y[q]) * S(y[q]);
-    const S wl = c.frozen ? S(1) : S(L) * S(L);
-    const S wr = c.frozen ? S(1) : S(Rt) * S(Rt);
-    M2<S> A[P], B[P], C[P];
-    assemble<S, P>(r0, c.n, alpha, beta, w, wl, wr, A, B, C);
-    V2<S> d[P], x[P];
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
-      double hh[2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int q = 2 * l + i;
-        const double zm = (q > 0) ? z[q - 1] : zl;
-        const double zp = (q < R - 1) ? z[q + 1] : zr;
-        hh[i] = (r0 + q < c.n) ? (y[q] - yh[q]) + c.ih2 * (zm - 2.0 * z[q] + zp) : 0.0;
-      }
-      d[l] = {S(hh[0]), S(hh[1])};
-    }
-    block_tridiag_solve<S, T, P>(A, B, C, d, x, solver_smem<S, T>(sm));
-    double dm = 0.0;
-    bool nf = false;
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
-      const double dx = double(x[l].x), dy = double(x[l].y);
-      nf |= !isfinite(dx) || !isfinite(dy);
-      y[2 * l] = (r0 + 2 * l < c.n) ? y[2 * l] - dx : 0.0;
-      y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? y[2 * l + 1] - dy : 0.0;
-      dm = fmax(dm, fmax(fabs(dx), fabs(dy)));
-    }
-    if (__syncthreads_or(nf)) {
-      bad = true;
-      return -(m + 1);
-    }
-    dm = cta_max<T>(dm, sm.red);
-    ++m;
-    if (dm <= c.newton_tol) { ok = true; break; }
-    // FP64 rounding floor of the residual reached (see the header comment of ch_parareal.h)
-    if (m >= 2 && dm <= c.newton_floor && dm > 0.5 * prev) { ok = true; break; }
-    prev = dm;
-  }
-  return ok ? m : -m;
-}
-
-// One step of the nonlinear scheme Eq. 2.3 by Newton (Eq. 3.17/3.18) with the Jacobian solve in
-// FP32 through a balanced mixed form. The correction d of J d = H, J = I + eps^2 dt A^2 + c dt A W
-// (A = -D_h, W = diag(w), c = 3, w = Y^2), is found from the pair (d, v) with
-//     d + s A v = H,      v - (eps^2 dt A d + c dt W d) / s = 0,      s = eps sqrt(dt),
-// which eliminates to J d = H. With this s both couplings have size sigma = eps sqrt(dt) / h^2,
-// about the square root of the 16 eps^2 dt / h^4 of the pentadiagonal form, so the FP32 solve is
-// accurate to ~3e-6 instead of ~3e-3 and Newton keeps its quadratic rate down to the FP64
-// rounding floor. Unknowns (d_i, v_i) form the 2x2 blocks
-//     B_i = [[1, 2 sigma], [-2 sigma - c dt w_i / s, 1]],  A_i = C_i = [[0, -sigma], [sigma, 0]].
-// FP64 is spent on the residual H and the update only; w comes from a float shadow of Y, and the
-// stop test uses the float correction. The iteration starts from the cubic extrapolation
-// 4 u^n - 6 u^{n-1} + 4 u^{n-2} - u^{n-3} when three earlier states of the same propagation are
-// known, the quadratic or linear one when two or one are (u^n otherwise);
-// the root it converges to is the same (the step is the unique minimiser of a strictly convex
-// functional), only the number of iterations changes.
-template <int T, int P>
-__device__ int nl_step_mixed(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double (&yp)[2 * P],
-                             double (&ypp)[2 * P], double (&yppp)[2 * P], int have_prev, float (&y32)[2 * P],
-                             double dt, bool& bad) {
-  constexpr int R = 2 * P;
-  const int r0 = threadIdx.x * R;
-  double L, Rt;
-  double yh[R];
-  exchange(sm, y[0], y[R - 1], L, Rt);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const double um = (q > 0) ? y[q - 1] : L;
-    const double up = (q < R - 1) ? y[q + 1] : Rt;
-    yh[q] = (r0 + q < c.n) ? y[q] - dt * c.ih2 * (um - 2.0 * y[q] + up) : 0.0;  // (I - dt D_h) u^n
-  }
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const double g = (have_prev >= 3)   ? 4.0 * y[q] - 6.0 * yp[q] + 4.0 * ypp[q] - yppp[q]
-                     : (have_prev == 2) ? 3.0 * (y[q] - yp[q]) + ypp[q]
-                     : (have_prev == 1) ? 2.0 * y[q] - yp[q]
-                                        : y[q];
-    yppp[q] = ypp[q];
-    ypp[q] = yp[q];
-    yp[q] = y[q];
-    y[q] = (r0 + q < c.n) ? g : 0.0;
-    y32[q] = float(y[q]);
-  }
-  const double c1 = c.eps2 * dt * c.ih2;
-  const float sigma = float(sqrt(c.eps2 * dt) * c.ih2);
-  const float cs = float((c.frozen ? 1.0 : 3.0) * sqrt(dt / c.eps2));  // c dt / s
-  const float tol = float(c.newton_tol), floor_ = float(c.newton_floor);
-  float prev = 0.f;
-  int m = 0;
-  bool ok = false;
-  while (m < c.newton_max) {
-    exchange(sm, y[0], y[R - 1], L, Rt);
-    // z = eps^2 dt D_h Y - dt Y^3 = c1 (Y_{i-1} + Y_{i+1}) + Y (-2 c1 - dt Y^2)
-    double z[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const double um = (q > 0) ? y[q - 1] : L;
-      const double up = (q < R - 1) ? y[q + 1] : Rt;
-      const double y2 = c.frozen ? 1.0 : y[q] * y[q];
-      z[q] = (r0 + q < c.n) ? fma(y[q], fma(-dt, y2, -2.0 * c1), c1 * (um + up)) : 0.0;
-    }
-    double zl, zr;
-    exchange(sm, z[0], z[R - 1], zl, zr);
-    M2<float> A[R], B[R], C[R];
-    V2<float> d[R], x[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int i = r0 + q;
-      const double zm = (q > 0) ? z[q - 1] : zl;
-      const double zp = (q < R - 1) ? z[q + 1] : zr;
-      const float hq = (i < c.n) ? float((y[q] - yh[q]) + c.ih2 * (zm - 2.0 * z[q] + zp)) : 0.f;
-      const float w = c.frozen ? 1.f : y32[q] * y32[q];
-      A[q] = (i >= 1 && i < c.n) ? M2<float>{0.f, -sigma, sigma, 0.f} : mzero<float>();
-      C[q] = (i + 1 < c.n) ? M2<float>{0.f, -sigma, sigma, 0.f} : mzero<float>();
-      B[q] = (i < c.n) ? M2<float>{1.f, 2.f * sigma, -2.f * sigma - cs * w, 1.f} : M2<float>{1.f, 0.f, 0.f, 1.f};
-      d[q] = {hq, 0.f};
-    }
-    block_tridiag_solve<float, T, R>(A, B, C, d, x, solver_smem<float, T>(sm));
-    float dm = 0.f;
-    bool nf = false;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const float dx = (r0 + q < c.n) ? x[q].x : 0.f;
-      nf |= !isfinite(dx);
-      y[q] -= double(dx);
-      y32[q] -= dx;
-      dm = fmaxf(dm, fabsf(dx));
-    }
-    if (__syncthreads_or(nf)) {
-      bad = true;
-      return -(m + 1);
-    }
-    dm = cta_max_f<T>(dm, sm.red);
-    ++m;
-    if (dm <= tol) { ok = true; break; }
-    // FP64 rounding floor of the residual reached (an increment below sqrt(tol) not halving)
-    if (m >= 2 && dm <= floor_ && dm > 0.5f * prev) { ok = true; break; }
-    prev = dm;
-  }
-  return ok ? m : -m;
-}
-
-// One step of the linear scheme Eq. 2.4 (LIN1), FP64 solve.
-template <int T, int P>
-__device__ void lin1_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
-  constexpr int R = 2 * P;
-  const int r0 = threadIdx.x * R;
-  double L, Rt;
-  exchange(sm, y[0], y[R - 1], L, Rt);
-  double w[R];
-  V2<double> d[P], x[P];
-#pragma unroll
-  for (int q = 0; q < R; ++q) w[q] = c.frozen ? 1.0 : y[q] * y[q];
-  const double wl = c.frozen ? 1.0 : L * L, wr = c.frozen ? 1.0 : Rt * Rt;
-#pragma unroll
-  for (int l = 0; l < P; ++l) {
-    double rr[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int q = 2 * l + i;
-      const double um = (q > 0) ? y[q - 1] : L;
-      const double up = (q < R - 1) ? y[q + 1] : Rt;
-      rr[i] = (r0 + q < c.n) ? y[q] - dt * c.ih2 * (um - 2.0 * y[q] + up) : 0.0;  // (I - dt D_h) u^n
-    }
-    d[l] = {rr[0], rr[1]};
-  }
-  M2<double> A[P], B[P], C[P];
-  assemble<double, P>(r0, c.n, c.eps2 * dt * c.ih2 * c.ih2, dt * c.ih2, w, wl, wr, A, B, C);
-  block_tridiag_solve<double, T, P>(A, B, C, d, x, solver_smem<double, T>(sm));
-  bool nf = false;
-#pragma unroll
-  for (int l = 0; l < P; ++l) {
-    nf |= !isfinite(x[l].x) || !isfinite(x[l].y);
-    y[2 * l] = (r0 + 2 * l < c.n) ? x[l].x : 0.0;
-    y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? x[l].y : 0.0;
-  }
-  if (__syncthreads_or(nf)) bad = true;
-}
-
-// One step of the linear scheme Eq. 2.5 (LIN2, Laplacian on the implicit 2 dt term), FP64 solve.
-template <int T, int P>
-__device__ void lin2_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, bool& bad) {
-  constexpr int R = 2 * P;
-  const int r0 = threadIdx.x * R;
-  double L, Rt;
-  exchange(sm, y[0], y[R - 1], L, Rt);
-  // rhs = u + dt D_h (u^3 - 3u)   (frozen: u + dt D_h (-2u))
-  auto vfun = [&](double u) { return c.frozen ? -2.0 * u : u * u * u - 3.0 * u; };
-  double v[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) v[q] = vfun(y[q]);
-  const double vl = vfun(L), vr = vfun(Rt);
-  double w[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) w[q] = 1.0;
-  V2<double> d[P], x[P];
-#pragma unroll
-  for (int l = 0; l < P; ++l) {
-    double rr[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int q = 2 * l + i;
-      const double vm = (q > 0) ? v[q - 1] : vl;
-      const double vp = (q < R - 1) ? v[q + 1] : vr;
-      rr[i] = (r0 + q < c.n) ? y[q] + dt * c.ih2 * (vm - 2.0 * v[q] + vp) : 0.0;
-    }
-    d[l] = {rr[0], rr[1]};
-  }
-  M2<double> A[P], B[P], C[P];
-  assemble<double, P>(r0, c.n, c.eps2 * dt * c.ih2 * c.ih2, 2.0 * dt * c.ih2, w, 1.0, 1.0, A, B, C);
-  block_tridiag_solve<double, T, P>(A, B, C, d, x, solver_smem<double, T>(sm));
-  bool nf = false;
-#pragma unroll
-  for (int l = 0; l < P; ++l) {
-    nf |= !isfinite(x[l].x) || !isfinite(x[l].y);
-    y[2 * l] = (r0 + 2 * l < c.n) ? x[l].x : 0.0;
-    y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? x[l].y : 0.0;
-  }
-  if (__syncthreads_or(nf)) bad = true;
-}
-
-// Dispatch one step. Returns Newton iterations (0 for the linear schemes; negative on failure).
-template <int T, int P>
-__device__ __forceinline__ int do_step(Smem1D<T>& sm, const StepCtx& c, int scheme, int fp32_newton,
-                                       double (&y)[2 * P], double dt, bool& bad) {
-  if (scheme == SCHEME_NL) {
-    return fp32_newton ? nl_step<T, P, float>(sm, c, y, dt, bad) : nl_step<T, P, double>(sm, c, y, dt, bad);
-  }
-  if (scheme == SCHEME_LIN2) {
-    lin2_step<T, P>(sm, c, y, dt, bad);
-  } else {
-    lin1_step<T, P>(sm, c, y, dt, bad);
-  }
-  return 0;
-}
-
-__device__ __forceinline__ StepCtx make_ctx(const Params1D& p) {
-  StepCtx c;
-  c.n = p.n;
-  c.frozen = p.frozen;
-  c.newton_max = p.newton_max;
-  c.ih2 = 1.0 / (p.h * p.h);
-  c.eps2 = p.eps2;
-  c.newton_tol = p.newton_tol;
-  c.newton_floor = sqrt(p.newton_tol);
-  return c;
-}
-
-template <int P>
-__device__ __forceinline__ void load_state(const double* __restrict__ src, int n, double (&y)[2 * P]) {
-  const int r0 = threadIdx.x * 2 * P;
-#pragma unroll
-  for (int q = 0; q < 2 * P; ++q) y[q] = (r0 + q < n) ? src[r0 + q] : 0.0;
-}
-template <int P>
-__device__ __forceinline__ void store_state(double* __restrict__ dst, int n, const double (&y)[2 * P]) {
-  const int r0 = threadIdx.x * 2 * P;
-#pragma unroll
-  for (int q = 0; q < 2 * P; ++q)
-    if (r0 + q < n) dst[r0 + q] = y[q];
-}
-
-// Runs `nsteps` steps; accumulates Newton statistics; returns false on failure.
-template <int T, int P>
-__device__ bool run_steps(Smem1D<T>& sm, const StepCtx& c, int scheme, int fp32_newton, double (&y)[2 * P],
-                          double dt, int nsteps, unsigned long long& newton_sum, int& newton_peak,
-                          unsigned& status) {
-  bool bad = false;
-  for (int j = 0; j < nsteps; ++j) {
-    const int m = do_step<T, P>(sm, c, scheme, fp32_newton, y, dt, bad);
-    if (m < 0) {
-      status |= ST_NEWTON;
-      newton_sum += (unsigned long long)(-m);
-      newton_peak = max(newton_peak, -m);
-    } else {
-      newton_sum += (unsigned long long)m;
-      newton_peak = max(newton_peak, m);
-    }
-    if (bad) {
-      status |= ST_NONFINITE;
-      return false;
-    }
-  }
-  return status == 0;
-}
-
-// `nsteps` nonlinear steps with FP32 mixed-form Jacobian solves (nl_step_mixed); keeps the
-// previous state for the Newton predictor and the float shadow of Y across steps.
-template <int T, int P>
-__device__ bool run_steps_nl32(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], double dt, int nsteps,
-                               unsigned long long& newton_sum, int& newton_peak, unsigned& status) {
-  double yp[2 * P], ypp[2 * P], yppp[2 * P];
-  float y32[2 * P];
-  bool bad = false;
-  for (int j = 0; j < nsteps; ++j) {
-    const int m = nl_step_mixed<T, P>(sm, c, y, yp, ypp, yppp, j < 3 ? j : 3, y32, dt, bad);
-    const int a = (m < 0) ? -m : m;
-    if (m < 0) status |= ST_NEWTON;
-    newton_sum += (unsigned long long)a;
-    newton_peak = max(newton_peak, a);
-    if (bad) {
-      status |= ST_NONFINITE;
-      return false;
-    }
-  }
-  return status == 0;
-}
-
-// Dispatch of a propagation: FAST = nonlinear scheme with FP32 mixed-form Jacobian solves.
-template <int T, int P, bool FAST>
-__device__ __forceinline__ bool propagate_state(Smem1D<T>& sm, const StepCtx& c, int scheme, int precision,
-                                                double (&y)[2 * P], double dt, int nsteps,
-                                                unsigned long long& nsum, int& npeak, unsigned& status) {
-  if constexpr (FAST) {
-    return run_steps_nl32<T, P>(sm, c, y, dt, nsteps, nsum, npeak, status);
-  } else {
-    return run_steps<T, P>(sm, c, scheme, precision, y, dt, nsteps, nsum, npeak, status);
-  }
-}
-
-// ----------------------------------------------------------------------------- kernels
-
-// Fine sweep of one Parareal iteration: F(U_s^k) for every active problem b and slice s >= k,
-// as one persistent launch; CTAs take (problem, slice) units from a device counter.
-template <int T, int P, bool FAST>
-__global__ void __launch_bounds__(T) k_fine_sweep(Params1D p, const double* __restrict__ U,
-                                                  double* __restrict__ F, Ctrl* ctrl, ProblemState ps) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
-  const int k = ctrl->k;
-  const int per = p.N - k;
-  if (per <= 0) return;
-  const int total = p.B * per;
-  const StepCtx c = make_ctx(p);
-  for (;;) {
-    if (threadIdx.x == 0) sm.unit = atomicAdd(&ctrl->next_unit, 1);
-    __syncthreads();
-    const int u = sm.unit;
-    __syncthreads();
-    if (u >= total) break;
-    const int b = u / per;
-    const int s = k + u % per;
-    if (!ps.active[b]) continue;
-    double y[2 * P];
-    load_state<P>(U + ((size_t)b * (p.N + 1) + s) * p.n, p.n, y);
-    unsigned long long nsum = 0;
-    int npeak = 0;
-    unsigned status = 0;
-    propagate_state<T, P, FAST>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
-    store_state<P>(F + ((size_t)b * p.N + s) * p.n, p.n, y);
-    if (threadIdx.x == 0) {
-      atomicAdd(&ps.newton_total[b], nsum);
-      atomicMax(&ps.newton_max[b], npeak);
-      if (status) atomicOr(&ctrl->status, status);
-    }
-  }
-}
-
-// L2_h and max-abs error of one slice against the reference (Section 4 norm).
-template <int T, int P>
-__device__ __forceinline__ void slice_error(Smem1D<T>& sm, const double (&y)[2 * P], const double* ref,
-                                            int n, double h, double& el2, double& emx) {
-  const int r0 = threadIdx.x * 2 * P;
-  double s = 0.0, m = 0.0;
-#pragma unroll
-  for (int q = 0; q < 2 * P; ++q) {
-    if (r0 + q < n) {
-      const double e = y[q] - ref[r0 + q];
-      s += e * e;
-      m = fmax(m, fabs(e));
-    }
-  }
-  cta_sum_max<T>(s, m, sm.red);
-  el2 = fmax(el2, sqrt(h * s));
-  emx = fmax(emx, m);
-}
-
-// Coarse sweep, sequential over slices, one CTA per problem.
-// init = 1: U_{s+1}^0 = G(U_s^0), Gold_s = U_{s+1}^0 (Section 4 initial guess).
-// init = 0: U_{s+1}^{k+1} = F_s + (G(U_s^{k+1}) - Gold_s), Gold_s = G(U_s^{k+1}) (Eq. 2.2), for
-//           s >= k, with the increment max_s |U^{k+1} - U^k| and the error against Uref.
-template <int T, int P>
-__global__ void __launch_bounds__(T) k_coarse_sweep(Params1D p, double* __restrict__ U,
-                                                    const double* __restrict__ F, double* __restrict__ Gold,
-                                                    const double* __restrict__ Uref, Ctrl* ctrl,
-                                                    ProblemState ps, int init) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
-  const int b = blockIdx.x;
-  if (!init && !ps.active[b]) return;
-  const int k = init ? 0 : ctrl->k;
-  const int n = p.n;
-  const StepCtx c = make_ctx(p);
-  double* Ub = U + (size_t)b * (p.N + 1) * n;
-  const double* Rb = Uref ? Uref + (size_t)b * (p.N + 1) * n : nullptr;
-  const int r0 = threadIdx.x * 2 * P;
-  double cur[2 * P];
-  load_state<P>(Ub + (size_t)k * n, n, cur);
-  double el2 = 0.0, emx = 0.0, inc = 0.0;
-  if (Rb) {
-    for (int s = 0; s <= k; ++s) {
-      double y[2 * P];
-      load_state<P>(Ub + (size_t)s * n, n, y);
-      slice_error<T, P>(sm, y, Rb + (size_t)s * n, n, p.h, el2, emx);
-    }
-  }
-  unsigned long long nsum = 0;
-  int npeak = 0;
-  unsigned status = 0;
-  for (int s = k; s < p.N; ++s) {
-    double g[2 * P];
-#pragma unroll
-    for (int q = 0; q < 2 * P; ++q) g[q] = cur[q];
-    run_steps<T, P>(sm, c, p.coarse_scheme, 0, g, p.dtc, p.coarse_steps, nsum, npeak, status);
-    double* Gs = Gold + ((size_t)b * p.N + s) * n;
-    double* Un = Ub + (size_t)(s + 1) * n;
-    if (init) {
-#pragma unroll
-      for (int q = 0; q < 2 * P; ++q) cur[q] = g[q];
-    } else {
-      const double* Fs = F + ((size_t)b * p.N + s) * n;
-#pragma unroll
-      for (int q = 0; q < 2 * P; ++q) {
-        if (r0 + q < n) {
-          const double nw = Fs[r0 + q] + (g[q] - Gs[r0 + q]);
-          inc = fmax(inc, fabs(nw - Un[r0 + q]));
-          cur[q] = nw;
-        } else {
-          cur[q] = 0.0;
-        }
-      }
-    }
-    store_state<P>(Un, n, cur);
-    store_state<P>(Gs, n, g);
-    if (Rb) slice_error<T, P>(sm, cur, Rb + (size_t)(s + 1) * n, n, p.h, el2, emx);
-  }
-  inc = cta_max<T>(inc, sm.red);
-  if (threadIdx.x == 0) {
-    const size_t eo = (size_t)b * (p.maxit + 1);
-    if (init) {
-      ps.err_l2[eo] = Rb ? el2 : -1.0;
-      ps.err_max[eo] = Rb ? emx : -1.0;
-    } else {
-      ps.inc[(size_t)b * p.maxit + k] = inc;
-      ps.err_l2[eo + k + 1] = Rb ? el2 : -1.0;
-      ps.err_max[eo + k + 1] = Rb ? emx : -1.0;
-      ps.iterations[b] = k + 1;
-      if ((p.tol > 0.0 && inc < p.tol) || (Rb && p.err_tol > 0.0 && el2 <= p.err_tol)) {
-        ps.converged[b] = 1;
-        ps.active[b] = 0;
-      }
-    }
-    if (status) atomicOr(&ctrl->status, status);
-  }
-}
 
 // End of an iteration: count active problems, advance k, reset the work counter.
 __global__ void k_tally(int B, Ctrl* ctrl, ProblemState ps, int* host_active) {
@@ -623,110 +24,12 @@ __global__ void k_tally(int B, Ctrl* ctrl, ProblemState ps, int* host_active) {
   }
 }
 
-// Sequential fine solution U^fine_{s+1} = F(U^fine_s), one CTA per problem (serial in time).
-template <int T, int P, bool FAST>
-__global__ void __launch_bounds__(T) k_reference(Params1D p, double* __restrict__ Uref, Ctrl* ctrl) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
-  const int b = blockIdx.x;
-  const StepCtx c = make_ctx(p);
-  double* Rb = Uref + (size_t)b * (p.N + 1) * p.n;
-  double y[2 * P];
-  load_state<P>(Rb, p.n, y);
-  unsigned long long nsum = 0;
-  int npeak = 0;
-  unsigned status = 0;
-  for (int s = 0; s < p.N; ++s) {
-    propagate_state<T, P, FAST>(sm, c, p.fine_scheme, p.precision, y, p.dt, p.J, nsum, npeak, status);
-    store_state<P>(Rb + (size_t)(s + 1) * p.n, p.n, y);
-  }
-  if (threadIdx.x == 0 && status) atomicOr(&ctrl->status, status);
-}
-
-// Stateless propagation: nsteps steps of `scheme` for each problem (one CTA each).
-template <int T, int P, bool FAST>
-__global__ void __launch_bounds__(T) k_propagate(Params1D p, int scheme, double dt, int nsteps,
-                                                 const double* uin, double* uout, int* newton, Ctrl* ctrl) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem1D<T>& sm = *reinterpret_cast<Smem1D<T>*>(smem_raw);
-  const int b = blockIdx.x;
-  const StepCtx c = make_ctx(p);
-  double y[2 * P];
-  load_state<P>(uin + (size_t)b * p.n, p.n, y);
-  __syncthreads();  // uin and uout may alias: every thread has read its rows before any write
-  unsigned long long nsum = 0;
-  int npeak = 0;
-  unsigned status = 0;
-  propagate_state<T, P, FAST>(sm, c, scheme, p.precision, y, dt, nsteps, nsum, npeak, status);
-  store_state<P>(uout + (size_t)b * p.n, p.n, y);
-  if (threadIdx.x == 0) {
-    if (newton) newton[b] = (int)nsum;
-    if (status) atomicOr(&ctrl->status, status);
-  }
-}
-
 // ------------------------------------------------------------------------- host dispatch
 
-// (T, P) by problem size: T threads, 2P rows per thread, n <= 2 T P.
-#define CH_DISPATCH_TP(n, ...)            \
-  do {                                    \
-    if ((n) <= 128) {                     \
-      constexpr int T_ = 32, P_ = 2;      \
-      __VA_ARGS__;                        \
-    } else if ((n) <= 256) {              \
-      constexpr int T_ = 64, P_ = 2;      \
-      __VA_ARGS__;                        \
-    } else if ((n) <= 512) {              \
-      constexpr int T_ = 128, P_ = 2;     \
-      __VA_ARGS__;                        \
-    } else if ((n) <= 1024) {             \
-      constexpr int T_ = 128, P_ = 4;     \
-      __VA_ARGS__;                        \
-    } else {                              \
-      constexpr int T_ = 256, P_ = 4;     \
-      __VA_ARGS__;                        \
-    }                                     \
-  } while (0)
-
-// Opt a kernel into its dynamic shared memory once per device (not during graph capture).
-// (T, P) for the nonlinear FP32-Newton path: at most 4 rows per thread up to n = 1024, which
-// halves the registers per thread and doubles the resident warps of the FP64-bound sweep.
-#define CH_DISPATCH_TP_FAST(n, ...)       \
-  do {                                    \
-    if ((n) <= 128) {                     \
-      constexpr int T_ = 32, P_ = 2;      \
-      __VA_ARGS__;                        \
-    } else if ((n) <= 256) {              \
-      constexpr int T_ = 64, P_ = 2;      \
-      __VA_ARGS__;                        \
-    } else if ((n) <= 512) {              \
-      constexpr int T_ = 128, P_ = 2;     \
-      __VA_ARGS__;                        \
-    } else if ((n) <= 1024) {             \
-      constexpr int T_ = 256, P_ = 2;     \
-      __VA_ARGS__;                        \
-    } else {                              \
-      constexpr int T_ = 256, P_ = 4;     \
-      __VA_ARGS__;                        \
-    }                                     \
-  } while (0)
-
-template <typename K>
-static cudaError_t prep(K kernel, size_t smem) {
-  static std::mutex mu;
-  static std::set<std::pair<const void*, unsigned long long>> done;  // (kernel, context)
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), chctx::cache_key());
-  if (done.count(key)) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) done.insert(key);
-  return e;
-}
-
-// The fine propagator is the nonlinear scheme with FP32 Jacobian solves: use the mixed-form path.
+// The fine propagator is the nonlinear scheme with FP32 inner solves: the mixed-form kernels of
+// this file. With a linear fine scheme and FP32 inner solves, ch1d_lin.cu launches them.
 static bool fast_fine(const Params1D& p) { return p.fine_scheme == SCHEME_NL && p.precision == 1; }
+static bool mixed_linear(int scheme, int precision) { return scheme != SCHEME_NL && precision == 1; }
 
 // Fine-sweep mapping of the mixed-form path with the autotuned alternative: alt = 1 halves the
 // threads per CTA and doubles the block rows per thread (more CTAs resident per SM, longer
@@ -754,6 +57,13 @@ bool fine_sweep_has_alt(const Params1D& p) { return fast_fine(p) && p.n > 128; }
 
 cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   if (p.nn_sub > 0) return nn_max_grid(p, grid);
+  if (mixed_linear(p.fine_scheme, p.precision)) {
+    cudaError_t e = lin_fine_sweep_max_grid(p, grid);
+    CH_DISPATCH_TP(p.n, {
+      if (e == cudaSuccess) e = prep(k_coarse_sweep<T_, P_>, sizeof(Smem1D<T_>));
+    });
+    return e;
+  }
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -761,41 +71,45 @@ cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid) {
   if (fast_fine(p)) {
     CH_DISPATCH_TP_FINE(p.n, p.alt, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_fine_sweep<T_, P_, true>, smem);
+      e = prep(k_fine_sweep<T_, P_, MODE_MIXED_NL>, smem);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, true>, T_, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, MODE_MIXED_NL>, T_, smem);
     });
   } else {
     CH_DISPATCH_TP(p.n, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_fine_sweep<T_, P_, false>, smem);
+      e = prep(k_fine_sweep<T_, P_, MODE_FP64>, smem);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, false>, T_, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine_sweep<T_, P_, MODE_FP64>, T_, smem);
     });
   }
   CH_DISPATCH_TP(p.n, {
     if (e == cudaSuccess) e = prep(k_coarse_sweep<T_, P_>, sizeof(Smem1D<T_>));
   });
   if (per_sm < 1) per_sm = 1;
-  *grid = sms * per_sm;
+  // No more CTAs than units: a small batch then has its units spread over distinct SMs instead of
+  // going to whichever resident CTAs take them first (several per SM share its FP64 pipe).
+  const long long units = (long long)p.B * p.N;
+  *grid = (int)std::min<long long>((long long)sms * per_sm, std::max<long long>(units, 1));
   return e;
 }
 
 cudaError_t launch_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps,
                               int grid, cudaStream_t st) {
   if (p.nn_sub > 0) return launch_nn_fine_sweep(p, U, F, ctrl, ps, grid, st);
+  if (mixed_linear(p.fine_scheme, p.precision)) return launch_lin_fine_sweep(p, U, F, ctrl, ps, grid, st);
   cudaError_t e = cudaSuccess;
   if (fast_fine(p)) {
     CH_DISPATCH_TP_FINE(p.n, p.alt, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_fine_sweep<T_, P_, true>, smem);
-      if (e == cudaSuccess) k_fine_sweep<T_, P_, true><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
+      e = prep(k_fine_sweep<T_, P_, MODE_MIXED_NL>, smem);
+      if (e == cudaSuccess) k_fine_sweep<T_, P_, MODE_MIXED_NL><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
     });
   } else {
     CH_DISPATCH_TP(p.n, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_fine_sweep<T_, P_, false>, smem);
-      if (e == cudaSuccess) k_fine_sweep<T_, P_, false><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
+      e = prep(k_fine_sweep<T_, P_, MODE_FP64>, smem);
+      if (e == cudaSuccess) k_fine_sweep<T_, P_, MODE_FP64><<<grid, T_, smem, st>>>(p, U, F, ctrl, ps);
     });
   }
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -823,18 +137,19 @@ cudaError_t launch_tally(const Params1D& p, Ctrl* ctrl, ProblemState ps, int* ho
 
 cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st) {
   if (p.nn_sub > 0) return launch_nn_reference(p, Uref, ctrl, st);
+  if (mixed_linear(p.fine_scheme, p.precision)) return launch_lin_reference(p, Uref, ctrl, st);
   cudaError_t e = cudaSuccess;
   if (fast_fine(p)) {
     CH_DISPATCH_TP_FINE(p.n, p.alt, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_reference<T_, P_, true>, smem);
-      if (e == cudaSuccess) k_reference<T_, P_, true><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
+      e = prep(k_reference<T_, P_, MODE_MIXED_NL>, smem);
+      if (e == cudaSuccess) k_reference<T_, P_, MODE_MIXED_NL><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
     });
   } else {
     CH_DISPATCH_TP(p.n, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_reference<T_, P_, false>, smem);
-      if (e == cudaSuccess) k_reference<T_, P_, false><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
+      e = prep(k_reference<T_, P_, MODE_FP64>, smem);
+      if (e == cudaSuccess) k_reference<T_, P_, MODE_FP64><<<p.B, T_, smem, st>>>(p, Uref, ctrl);
     });
   }
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -843,20 +158,21 @@ cudaError_t launch_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaSt
 
 cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nsteps, const double* uin,
                              double* uout, int* newton, Ctrl* ctrl, cudaStream_t st) {
+  if (mixed_linear(scheme, p.precision)) return launch_lin_propagate(p, scheme, dt, nsteps, uin, uout, newton, ctrl, st);
   cudaError_t e = cudaSuccess;
   if (scheme == SCHEME_NL && p.precision == 1) {
     CH_DISPATCH_TP_FAST(p.n, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_propagate<T_, P_, true>, smem);
+      e = prep(k_propagate<T_, P_, MODE_MIXED_NL>, smem);
       if (e == cudaSuccess)
-        k_propagate<T_, P_, true><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
+        k_propagate<T_, P_, MODE_MIXED_NL><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
     });
   } else {
     CH_DISPATCH_TP(p.n, {
       const size_t smem = sizeof(Smem1D<T_>);
-      e = prep(k_propagate<T_, P_, false>, smem);
+      e = prep(k_propagate<T_, P_, MODE_FP64>, smem);
       if (e == cudaSuccess)
-        k_propagate<T_, P_, false><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
+        k_propagate<T_, P_, MODE_FP64><<<p.B, T_, smem, st>>>(p, scheme, dt, nsteps, uin, uout, newton, ctrl);
     });
   }
   if (e == cudaSuccess) e = cudaGetLastError();

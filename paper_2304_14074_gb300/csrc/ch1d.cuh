@@ -40,7 +40,7 @@ struct Params1D {
   int coarse_steps;  // coarse steps per slice
   int fine_scheme;   // Scheme
   int coarse_scheme; // Scheme
-  int precision;     // 0: FP64 Newton solves, 1: FP32 Newton solves
+  int precision;     // 0: FP64 solves; 1: FP32 inner solves of the fine steps, refined in FP64
   int frozen;
   int newton_max;
   int maxit;         // history stride
@@ -76,6 +76,14 @@ cudaError_t launch_propagate(const Params1D& p, int scheme, double dt, int nstep
                              double* uout, int* newton, Ctrl* ctrl, cudaStream_t st);
 // CTAs of the fine sweep that fit on the device at once (for the persistent grid).
 cudaError_t fine_sweep_max_grid(const Params1D& p, int* grid);
+// The linear schemes (Eq. 2.4 / 2.5) as fine steps with FP32 inner solves refined against FP64
+// residuals (precision 1; implemented in ch1d_lin.cu): the same contracts as the launches above.
+cudaError_t lin_fine_sweep_max_grid(const Params1D& p, int* grid);
+cudaError_t launch_lin_fine_sweep(const Params1D& p, const double* U, double* F, Ctrl* ctrl, ProblemState ps,
+                                  int grid, cudaStream_t st);
+cudaError_t launch_lin_reference(const Params1D& p, double* Uref, Ctrl* ctrl, cudaStream_t st);
+cudaError_t launch_lin_propagate(const Params1D& p, int scheme, double dt, int nsteps, const double* uin,
+                                 double* uout, int* newton, Ctrl* ctrl, cudaStream_t st);
 // Neumann-Neumann fine solver (implemented in ch_nn.cu): whether p's sizes are supported, the
 // persistent grid of its fine sweep, and the launches that replace the fine sweep and the
 // sequential fine solution when p.nn_sub > 0.

@@ -112,6 +112,18 @@ __device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const fl
   return make_float2(sa, sb);
 }
 
+// The odd extension of a row pair held in shared memory as (x0[k], x1[k]) pairs at s[k], k < n.
+template <int N>
+__device__ __forceinline__ float2 odd_ext_s(const float2* s, bool v0, bool v1, int m) {
+  constexpr int L = 2 * N;
+  const bool zero = (m == 0 || m == N), neg = m > N;
+  const int q = zero ? 0 : (neg ? L - m - 1 : m - 1);
+  const float2 c = s[q];
+  const float sa = (zero || !v0) ? 0.f : (neg ? -c.x : c.x);
+  const float sb = (zero || !v1) ? 0.f : (neg ? -c.y : c.y);
+  return make_float2(sa, sb);
+}
+
 // Shared-memory index with one padding element every 8 complex values: the radix-8 stores of
 // the early stages write with strides of 8 and 64 elements, which would otherwise hit the same
 // banks (16-way conflicts at stride 8).
@@ -237,12 +249,15 @@ __device__ __forceinline__ float2 twmul32(float2 a, int j) {
   return cmul(a, w32(j));
 }
 
-// 32-point FFT in registers, radix-2 decimation in frequency: on return v[i] = X[bitrev5(i)].
-__device__ __forceinline__ void fft32_dif(float2 (&v)[32]) {
+// L-point FFT in registers (L = 16 or 32), radix-2 decimation in frequency: on return
+// v[i] = X[bit-reversed i]. The stage twiddle W_L^(j L / (2 span)) is W_32^(j 16 / span).
+template <int L>
+__device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
+  static_assert(L == 16 || L == 32, "register FFT length");
 #pragma unroll
-  for (int span = 16; span >= 1; span >>= 1) {
+  for (int span = L / 2; span >= 1; span >>= 1) {
 #pragma unroll
-    for (int start = 0; start < 32; start += 2 * span) {
+    for (int start = 0; start < L; start += 2 * span) {
 #pragma unroll
       for (int j = 0; j < span; ++j) {
         const float2 a = v[start + j], b = v[start + j + span];
@@ -253,23 +268,35 @@ __device__ __forceinline__ void fft32_dif(float2 (&v)[32]) {
   }
 }
 
+__device__ __forceinline__ void fft32_dif(float2 (&v)[32]) { fft_dif<32>(v); }
+
 __host__ __device__ constexpr int bitrev5(int i) {
   return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
 }
+__host__ __device__ constexpr int bitrev4(int i) {
+  return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
+}
 
-template <int N>
+// SM: the input rows are the warp's own row of `buf` as (x0, x1) pairs (odd_ext_s), not `src`.
+template <int N, bool SM = false>
 __device__ __forceinline__ void fft_rows_warp(float2* buf, const float2* tw2, const float* src, int a0) {
   static_assert(N == 512 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 1024");
   constexpr int n = N - 1;
   const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int ra = a0 + 2 * f, rb = ra + 1;
-  const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
-  const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
-  float2 v[32];
-#pragma unroll
-  for (int m1 = 0; m1 < 32; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
-  fft32_dif(v);
   float2* s = buf + f * buf_row<N>();
+  float2 v[32];
+  if constexpr (SM) {
+#pragma unroll
+    for (int m1 = 0; m1 < 32; ++m1) v[m1] = odd_ext_s<N>(s, ra < n, rb < n, 32 * m1 + t);
+    __syncwarp();  // every lane has read the row before any lane overwrites it
+  } else {
+    const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
+    const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
+#pragma unroll
+    for (int m1 = 0; m1 < 32; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
+  }
+  fft32_dif(v);
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const int k1 = bitrev5(i);
@@ -284,16 +311,96 @@ __device__ __forceinline__ void fft_rows_warp(float2* buf, const float2* tw2, co
   for (int i = 0; i < 32; ++i) s[pad8(t + 32 * bitrev5(i))] = v[i];
 }
 
-// The row FFTs of a transform pass (four-step warp version at L = 1024); ends with a block
-// barrier, after which `buf` holds the transforms for the epilogue.
+// The 256 x 256 grid (L = 512 = 32 x 16), one warp per row-pair FFT with 16 values per lane:
+// lane t holds y[32 m1 + t], m1 < 16; a 16-point FFT over m1 in registers; the twiddles
+// W_512^(t k1) (table tw2[k1][t]); a transpose through the FFT's buffer row (rows padded to 34
+// entries: the lane pairs below then read distinct banks); then each 32-point FFT over t, for one
+// k1, is split across the lane pair (2 k1, 2 k1 + 1): each lane a 16-point FFT of the even / odd
+// samples (E, O), and one shuffle combines them, X[k1 + 16 k2] = E[k2] + W_32^k2 O[k2] (even lane,
+// k2 < 16) and X[k1 + 16 (k2 + 16)] = E[k2] - W_32^k2 O[k2] (odd lane).
+template <int N, bool SM = false>
+__device__ __forceinline__ void fft_rows_warp512(float2* buf, const float2* tw2, const float* src, int a0) {
+  static_assert(N == 256 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 512");
+  static_assert(16 * 34 <= buf_row<N>(), "transpose rows fit the buffer row");
+  constexpr int n = N - 1;
+  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int ra = a0 + 2 * f, rb = ra + 1;
+  float2* s = buf + f * buf_row<N>();
+  float2 v[16];
+  if constexpr (SM) {
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext_s<N>(s, ra < n, rb < n, 32 * m1 + t);
+    __syncwarp();  // every lane has read the row before any lane overwrites it
+  } else {
+    const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
+    const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
+  }
+  fft_dif<16>(v);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int k1 = bitrev4(i);
+    s[k1 * 34 + t] = cmul(v[i], tw2[k1 * 32 + t]);
+  }
+  __syncwarp();
+  const int k1 = t >> 1, odd = t & 1;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = s[k1 * 34 + 2 * m + odd];
+  __syncwarp();
+  fft_dif<16>(v);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int k2 = bitrev4(i);
+    const float2 w = odd ? twmul32(v[i], k2) : v[i];  // odd lane: W_32^k2 O
+    const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, w.x, 1), __shfl_xor_sync(0xffffffffu, w.y, 1));
+    const float2 X = odd ? make_float2(o.x - w.x, o.y - w.y) : make_float2(w.x + o.x, w.y + o.y);
+    s[pad8(k1 + 16 * (k2 + 16 * odd))] = X;
+  }
+}
+
+// The row FFTs of a transform pass (four-step warp versions at L = 1024 and 512); ends with a
+// block barrier, after which `buf` holds the transforms for the epilogue.
 template <int N, int F>
 __device__ __forceinline__ void fft_rows_any(float2* buf, const float2* twd, const float* src, int a0) {
   if constexpr (N == 512) {
     fft_rows_warp<N>(buf, twd, src, a0);
     __syncthreads();
+  } else if constexpr (N == 256) {
+    fft_rows_warp512<N>(buf, twd, src, a0);
+    __syncthreads();
   } else {
     fft_rows<N, F>(buf, twd, src, a0);
   }
+}
+
+// Grids whose row FFTs are the warp four-step ones: each warp owns its row pair's buffer row, so
+// a pass can transform rows it has just written there (fft_rows_own).
+template <int N>
+__host__ __device__ constexpr bool warp_fft() {
+  return N == 512 || N == 256;
+}
+
+// Grids whose CG iterations use the fused middle pass and the untransposed last pass. Measured
+// (fine-sweep batches, graph execution): 256 x 256, 32 units: 6.81 -> 6.74 ms; 512 x 512, 64
+// units: 126.3 -> 132.8 ms (slower: at two blocks per SM the fused pass's shared-memory-only
+// second transform leaves fewer loads in flight), so only the smaller grid takes them.
+template <int N>
+__host__ __device__ constexpr bool fuse_cg() {
+  return N == 256;
+}
+
+// The row FFTs of rows held in the buffer itself: row pair f as (x0[k], x1[k]) at
+// buf[f * buf_row + k], k < n (warp_fft grids only); ends with a block barrier.
+template <int N>
+__device__ __forceinline__ void fft_rows_own(float2* buf, const float2* twd, int a0) {
+  static_assert(warp_fft<N>(), "rows held in the buffer need the warp FFT");
+  if constexpr (N == 512) {
+    fft_rows_warp<N, true>(buf, twd, nullptr, a0);
+  } else {
+    fft_rows_warp512<N, true>(buf, twd, nullptr, a0);
+  }
+  __syncthreads();
 }
 
 // One transform pass: rows of `in` ([units][n][n]) -> orthonormal DST-I -> written transposed.
@@ -531,12 +638,12 @@ size_t correct_partials(int count) { return (size_t)count * 4 * kBlk; }
 // Twiddles of the stages after the first of fft_rows<N> (radix 8 with Ns = 8, 64, ..., then the
 // radix-2 or radix-4 stage), stage after stage: entry (r - 1) Ns + k = exp(-2 pi i m / L) with
 // m = r k L / (R Ns), r = 1..R-1, k < Ns (host libm, rounded to FP32). At most L entries. For
-// N = 512 the four-step table of fft_rows_warp instead.
+// N = 512 and 256 the four-step tables of fft_rows_warp / fft_rows_warp512 instead.
 static std::vector<float2> twiddle_table(int N) {
   const int L = 2 * N;
-  if (N == 512) {  // four-step warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / 1024), k1, t < 32
+  if (N == 512 || N == 256) {  // four-step warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / L), t < 32
     std::vector<float2> tw(L);
-    for (int k1 = 0; k1 < 32; ++k1)
+    for (int k1 = 0; k1 < L / 32; ++k1)
       for (int t = 0; t < 32; ++t) {
         const double a = -2.0 * M_PI * k1 * t / L;
         tw[k1 * 32 + t] = make_float2(float(std::cos(a)), float(std::sin(a)));
@@ -1078,6 +1185,127 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   }
 }
 
+// The two middle transform passes of a CG iteration in one (warp_fft grids). In: the rows
+// [a0, a0 + kDstRows) of S p^T (the output of the first inverse pass). Their DST gives the
+// columns a0.. of p (physical space), each multiplied by dt (wc - wbar): the rows a0.. of q^T,
+// kept in the transform buffer; their DST gives the rows of q^T S, written transposed: S q.
+// The last pass then transforms rows of S q into S q S without transposing (dst_item_wn).
+// (Separately: rows of S p^T -> p, written out; rows of q -> S q^T; rows of that -> S q S.)
+template <int N>
+__device__ __forceinline__ void dst_item_wprod2(const PArgs& a, float2* buf, const float2* twd, const float* in,
+                                                float* out, int item) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int KS = kThreads / kDstRows;  // output rows apart of one thread's elements
+  constexpr int J = (n + KS - 1) / KS;     // epilogue elements per thread
+  const size_t pts = (size_t)n * n;
+  const float sc = 0.5f * sqrtf(2.0f / N);
+  const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+  if (a.flag[2 * u] || a.flag[2 * u + 1]) return;  // Newton- or CG-done unit (block-uniform)
+  fft_rows_any<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
+  const float cwb = float(__ldcg(a.scal + u * 8 + 4));
+  const int r = threadIdx.x % kDstRows, k0 = threadIdx.x / kDstRows, c = a0 + r;
+  const bool cok = c < n;
+  const size_t ob = u * pts + c;
+  float qv[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int k = k0 + j * KS;
+    qv[j] = 0.f;
+    if (cok && k < n) {
+      const float wv = __ldcg(a.w + ob + (size_t)k * n);
+      const float2 cv = buf[(r >> 1) * buf_row<N>() + pad8(k + 1)];
+      const float v = (r & 1) ? cv.x * sc : -cv.y * sc;  // p[k][c]
+      qv[j] = a.fdt * (wv - cwb) * v;
+    }
+  }
+  __syncthreads();  // every transform value has been read
+  float* sq = reinterpret_cast<float*>(buf + (r >> 1) * buf_row<N>()) + (r & 1);
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int k = k0 + j * KS;
+    if (cok && k < n) sq[2 * k] = qv[j];
+  }
+  __syncthreads();
+  fft_rows_own<N>(buf, twd, a0);
+#pragma unroll 4
+  for (int j = 0; j < J; ++j) {
+    const int k = k0 + j * KS;
+    if (cok && k < n) {
+      const float2 cv = buf[(r >> 1) * buf_row<N>() + pad8(k + 1)];
+      out[ob + (size_t)k * n] = (r & 1) ? cv.x * sc : -cv.y * sc;
+    }
+  }
+}
+
+// The last transform pass of a CG iteration after dst_item_wprod2: rows c = a0.. of S q -> rows
+// of S q S, not transposed; w = m u + S q S (= S u) and the partial sums (w, u), (r, u) of the
+// item. Each warp finishes its own row pair, lanes over consecutive columns.
+template <int N>
+__device__ __forceinline__ void dst_item_wn(const PArgs& a, float2* buf, const float2* twd, const float* in,
+                                            int item) {
+  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
+  constexpr int JW = (n + 31) / 32;  // columns per lane
+  const size_t pts = (size_t)n * n;
+  const float sc = 0.5f * sqrtf(2.0f / N);
+  const float* __restrict__ mu1 = a.mu1;
+  const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
+  if (a.flag[2 * u] || a.flag[2 * u + 1]) return;  // Newton- or CG-done unit (block-uniform)
+  fft_rows_any<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
+  const float cwb = float(__ldcg(a.scal + u * 8 + 4));
+  const float fcwb = a.fdt * cwb;
+  const float fe2dt = unit_fe2dt(a, u);
+  const int f = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const float2* s = buf + f * buf_row<N>();
+  float acc = 0.f, acc2 = 0.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = a0 + 2 * f + h;
+    if (c >= n) break;  // warp-uniform
+    const float mc = mu1[c];
+    const size_t ob = u * pts + (size_t)c * n;
+    float uv[JW], rv[JW];  // all of the row's loads in flight together
+#pragma unroll
+    for (int j = 0; j < JW; ++j) {
+      const int k = l + 32 * j;
+      uv[j] = k < n ? __ldcg(a.uh + ob + k) : 0.f;
+      rv[j] = k < n ? __ldcg(a.rh + ob + k) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < JW; ++j) {
+      const int k = l + 32 * j;
+      if (k < n) {
+        const float2 cv = s[pad8(k + 1)];
+        const float v = h ? cv.x * sc : -cv.y * sc;
+        const float w = mdiag(mu1[k] + mc, fe2dt, fcwb) * uv[j] + v;
+        a.qh[ob + k] = w;
+        acc = fmaf(w, uv[j], acc);
+        acc2 = fmaf(rv[j], uv[j], acc2);
+      }
+    }
+  }
+  // FP32 shuffle tree within each warp, the warps' sums added in FP64 in a fixed order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  }
+  __shared__ float ws[2][kThreads / 32];
+  if (l == 0) {
+    ws[0][f] = acc;
+    ws[1][f] = acc2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double wu = 0.0, ru = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) {
+      wu += (double)ws[0][i];
+      ru += (double)ws[1][i];
+    }
+    a.pdel[(size_t)u * nb + b] = wu;
+    a.pgam[(size_t)u * nb + b] = ru;
+  }
+}
+
 // A transform phase of the persistent kernel: its blocks walk the items (one call per item keeps
 // the transform's register allocation that of a single item).
 template <int N, int EPI>
@@ -1087,6 +1315,21 @@ __device__ __forceinline__ void dst_phase(const PArgs& a, float2* buf, const flo
   for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
     __syncthreads();  // the previous item's epilogue has finished reading buf
     noinl([&] { dst_item<N, EPI>(a, buf, twd, in, out, act, part, item); });
+  }
+}
+
+// The fused middle pass (LAST = false) or the untransposed last pass (LAST = true) of a CG
+// iteration as a phase of the persistent kernel (fuse_cg grids).
+template <int N, bool LAST>
+__device__ __forceinline__ void dst_phase_fused(const PArgs& a, float2* buf, const float2* twd) {
+  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
+  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
+    __syncthreads();  // the previous item's epilogue has finished reading buf
+    if constexpr (LAST) {
+      noinl([&] { dst_item_wn<N>(a, buf, twd, a.t2, item); });
+    } else {
+      noinl([&] { dst_item_wprod2<N>(a, buf, twd, a.tmp, a.t2, item); });
+    }
   }
 }
 
@@ -1614,11 +1857,17 @@ __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
       for (int it = 0; it < a.cg_max; ++it) {
         noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.uh, a.tmp, 1, nullptr); });  // u to physical space
         CH_BAR();
-        noinl([&] { dst_phase<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr); });  // dt (wc - wbar) p
-        CH_BAR();
-        noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr); });  // back to sine space
-        CH_BAR();
-        noinl([&] { dst_phase<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr); });  // w = S u, (w,u), (r,u)
+        if constexpr (fuse_cg<N>()) {
+          noinl([&] { dst_phase_fused<N, false>(a, buf, twd); });  // dt (wc - wbar) p, back to sine space
+          CH_BAR();
+          noinl([&] { dst_phase_fused<N, true>(a, buf, twd); });  // w = S u, (w,u), (r,u)
+        } else {
+          noinl([&] { dst_phase<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr); });  // dt (wc - wbar) p
+          CH_BAR();
+          noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr); });  // back to sine space
+          CH_BAR();
+          noinl([&] { dst_phase<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr); });  // w = S u, (w,u), (r,u)
+        }
         CH_BAR();
         noinl([&] { ph_cg_update<N>(a, it); });
         CH_BAR();
@@ -1994,14 +2243,15 @@ namespace {
 
 // PH_P1U: the CG update of the previous iteration on the item's rows, then P1 on them;
 // PH_X1U: the update of the last iteration for units that left the CG loop at cg_max, then X1.
+// PH_P23 / PH_P4N: P2 and P3 as one pass, then P4 without the transpose (fuse_cg grids).
 enum Phase {
   PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_UPDATE,
-  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U
+  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U, PH_P23, PH_P4N
 };
 
 __host__ __device__ constexpr bool is_dst_phase(int ph) {
   return ph == PH_H1 || ph == PH_H2 || ph == PH_P1 || ph == PH_P2 || ph == PH_P3 || ph == PH_P4 || ph == PH_X1 ||
-         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U;
+         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U || ph == PH_P23 || ph == PH_P4N;
 }
 
 // Four blocks per SM (a batch's items all resident at n = 255), two for the length-1024
@@ -2031,6 +2281,12 @@ __global__ void __launch_bounds__(kThreads, (N >= 512 ? 2 : 4)) k2_phase(PArgs a
   if constexpr (PH == PH_P2) dst_item<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P3) dst_item<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P4) dst_item<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P23) {
+    if constexpr (fuse_cg<N>()) dst_item_wprod2<N>(a, buf, twd, a.tmp, a.t2, blockIdx.x);
+  }
+  if constexpr (PH == PH_P4N) {
+    if constexpr (fuse_cg<N>()) dst_item_wn<N>(a, buf, twd, a.t2, blockIdx.x);
+  }
   if constexpr (PH == PH_UPDATE) ph_cg_update<N>(a, it);
   if constexpr (PH == PH_X1) dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
   if constexpr (PH == PH_P1U) {
@@ -2102,7 +2358,18 @@ cudaError_t phase_prepare() {
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X2>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_P1U>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X1U>, smem);
+  if constexpr (fuse_cg<N>()) {
+    if (e == cudaSuccess) e = prep(k2_phase<N, PH_P23>, smem);
+    if (e == cudaSuccess) e = prep(k2_phase<N, PH_P4N>, smem);
+  }
   return e;
+}
+
+// The CG's fused middle pass and untransposed last pass (fuse_cg grids) in the graph and host
+// executions; CH_2D_FUSED=0 selects the three separate passes instead.
+static bool fused_cg_passes() {
+  const char* v = std::getenv("CH_2D_FUSED");
+  return !(v && v[0] == '0');
 }
 
 // The step graph of one grid size.
@@ -2147,9 +2414,14 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   // ---- CG body
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs2, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = phase_launch<N, PH_P1U>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
+  if (fuse_cg<N>() && fused_cg_passes()) {
+    if (e == cudaSuccess) e = phase_launch<N, PH_P23>(a, have_prev, bs2);
+    if (e == cudaSuccess) e = phase_launch<N, PH_P4N>(a, have_prev, bs2);
+  } else {
+    if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
+    if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
+    if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
+  }
   if (e == cudaSuccess) {
     k2_cg_cond<N><<<1, kScalarThreads, 0, bs2>>>(a, hC, cg_max);
     e = cudaGetLastError();
@@ -2233,9 +2505,14 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
       hc[1] = it;
       CH_TRY(cudaMemcpyAsync(ctr, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
       CH_TRY((phase_launch<N, PH_P1U>(a, have_prev, st)));
-      CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
-      CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
-      CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
+      if (fuse_cg<N>() && fused_cg_passes()) {
+        CH_TRY((phase_launch<N, PH_P23>(a, have_prev, st)));
+        CH_TRY((phase_launch<N, PH_P4N>(a, have_prev, st)));
+      } else {
+        CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
+        CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
+        CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
+      }
       k2_cg_host<N><<<1, kScalarThreads, 0, st>>>(a);
       CH_TRY(cudaGetLastError());
       CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -146,7 +146,7 @@ chg2::Params2D params2d(const ch_config* c) {
   q.n = c->n;
   q.frozen = c->frozen ? 1 : 0;
   q.newton_max = c->newton_max;
-  // Inexact Newton: each CG solve reduces the preconditioned residual by lin_tol (default 1e-4);
+  // Inexact Newton: each CG solve reduces the preconditioned residual by lin_tol (default 1e-3);
   // the Newton error then contracts by about that factor per iteration down to the FP64
   // residual floor.
   q.cg_max = chcfg::lin_max_of(c);

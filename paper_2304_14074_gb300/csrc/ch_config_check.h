@@ -37,7 +37,7 @@ inline bool valid_run(const ch_config* c, bool (*supported_2d)(int), std::string
 }
 
 // Inner CG controls of the 2D solver (defaults for values <= 0).
-inline double lin_tol_of(const ch_config* c) { return c->lin_tol > 0.0 ? c->lin_tol : 1e-4; }
+inline double lin_tol_of(const ch_config* c) { return c->lin_tol > 0.0 ? c->lin_tol : 1e-3; }
 inline int lin_max_of(const ch_config* c) { return c->lin_max > 0 ? c->lin_max : 60; }
 
 }  // namespace chcfg

@@ -135,6 +135,14 @@ ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* ta
   return s;
 }
 
+ch_status ch_gtheta_set_loss(ch_gtheta* g, int relative) {
+  if (!g) return CH_ERR_INVALID;
+  if (g->sticky != CH_OK) return g->sticky;
+  if (relative != 0 && relative != 1) return gfail(g, CH_ERR_INVALID, "set_loss: relative must be 0 or 1");
+  g->net.set_relative_loss(relative == 1);
+  return CH_OK;
+}
+
 ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, const double* base_dev, int ntraj, int nsnap,
                           int n, int stride, int steps, int batch, double lr, unsigned long long seed,
                           float* losses_host) {

@@ -562,21 +562,45 @@ __global__ void __launch_bounds__(kThreads) k_conv_last(const bf16* __restrict__
   if (out) out[o] = base[o] + (double)s;
 }
 
-// Loss on the window [margin, S - margin)^2: dr = 2 (r - t) / count there, 0 elsewhere;
-// per-block partial sums of (r - t)^2.
+// Energy of each crop's target on the window, E_b = sum t^2 + 1e-12 count (one block per crop;
+// the floor keeps an all-zero target finite), for the relative loss.
+__global__ void k_target_energy(const float* __restrict__ t, int S, int margin, double* __restrict__ eng) {
+  __shared__ double sh[kThreads / 32];
+  const int inner = S - 2 * margin;
+  const float* tb = t + (size_t)blockIdx.x * S * S;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < inner * inner; k += kThreads) {
+    const float v = tb[(size_t)(margin + k / inner) * S + margin + k % inner];
+    acc += (double)v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) s += sh[i];
+    eng[blockIdx.x] = s + 1e-12 * inner * inner;
+  }
+}
+
+// Loss on the window [margin, S - margin)^2, dr = dLoss/dr there and 0 elsewhere; per-block
+// partial sums of the loss. eng = null: mean of (r - t)^2 over the batch's windows; otherwise
+// the mean over the batch of sum (r - t)^2 / E_b (the relative squared error of each crop).
 __global__ void k_loss(const float* __restrict__ r, const float* __restrict__ t, float* __restrict__ dr, int B, int S,
-                       int margin, double* __restrict__ part) {
+                       int margin, const double* __restrict__ eng, double* __restrict__ part) {
   __shared__ double sh[kThreads / 32];
   const size_t total = (size_t)B * S * S;
   const int inner = S - 2 * margin;
-  const double inv = 1.0 / ((double)B * inner * inner);
+  const double inv = eng ? 1.0 / B : 1.0 / ((double)B * inner * inner);
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)kThreads + threadIdx.x; k < total; k += (size_t)gridDim.x * kThreads) {
     const int X = (int)(k % S), Y = (int)((k / S) % S);
     const bool in = Y >= margin && Y < S - margin && X >= margin && X < S - margin;
     const float d = in ? r[k] - t[k] : 0.f;
-    dr[k] = (float)(2.0 * d * inv);
-    acc += (double)d * d;
+    const double w = eng ? 1.0 / eng[k / ((size_t)S * S)] : 1.0;
+    dr[k] = (float)(2.0 * d * inv * w);
+    acc += (double)d * d * w;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -924,7 +948,7 @@ cudaError_t GTheta::init(unsigned long long seed, cudaStream_t st) {
 
 void GTheta::release() {
   void* ptrs[] = {master_, grad_, m_, v_, wmid_, wbwd_, loss_dev_, a0_, r_, dr_, part_, tgt_, crops_, lpart_,
-                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part2_, err_};
+                  act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part2_, err_, eng_};
   for (void* q : ptrs) cudaFree(q);
   master_ = grad_ = m_ = v_ = nullptr;
   wmid_ = wbwd_ = nullptr;
@@ -933,6 +957,7 @@ void GTheta::release() {
   err_ = nullptr;
   crops_ = nullptr;
   lpart_ = nullptr;
+  eng_ = nullptr;
   for (auto& a : act_) a = nullptr;
   for (auto& gg : g_) gg = nullptr;
   cap_batch_ = cap_S_ = 0;
@@ -962,7 +987,8 @@ cudaError_t GTheta::get_params(float* host, cudaStream_t st) {
 cudaError_t GTheta::ensure(int batch, int S) {
   if (batch <= cap_batch_ && S <= cap_S_) return cudaSuccess;
   const int B = std::max(batch, cap_batch_), SS = std::max(S, cap_S_);
-  void* old[] = {a0_, r_, dr_, tgt_, act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part_, crops_, part2_};
+  void* old[] = {a0_, r_, dr_, tgt_, act_[0], act_[1], act_[2], act_[3], act_[4], g_[0], g_[1], part_, crops_, part2_,
+                 eng_};
   for (void* q : old) cudaFree(q);
   const size_t f = (size_t)B * SS * SS;
   const size_t tiles = (size_t)B * ((SS + kTile - 1) / kTile) * ((SS + kTile - 1) / kTile);
@@ -980,6 +1006,7 @@ cudaError_t GTheta::ensure(int batch, int S) {
   al((void**)&part_, part_cap_ * sizeof(float));
   al((void**)&part2_, ((tiles + kChunk - 1) / kChunk) * (size_t)(9 * kC * kC + kC) * sizeof(double));
   al((void**)&crops_, (size_t)B * sizeof(int4));
+  al((void**)&eng_, (size_t)B * sizeof(double));
   if (e == cudaSuccess) {
     cap_batch_ = B;
     cap_S_ = SS;
@@ -1066,7 +1093,8 @@ cudaError_t GTheta::grad_step(const float* in, const float* target, int batch, i
   if (e != cudaSuccess) return e;
   k_conv_last<<<grid, kThreads, 0, st>>>(act_[4], r_, master_, S, nullptr, nullptr);
   const int lb = 256;
-  k_loss<<<lb, kThreads, 0, st>>>(r_, target, dr_, batch, S, margin, lpart_);
+  if (rel_loss_) k_target_energy<<<batch, kThreads, 0, st>>>(target, S, margin, eng_);
+  k_loss<<<lb, kThreads, 0, st>>>(r_, target, dr_, batch, S, margin, rel_loss_ ? eng_ : nullptr, lpart_);
   k_loss_sum<<<1, 32, 0, st>>>(lpart_, lb, loss_dev_ + slot);
   // last layer: weights from (dr, a5), gradient into a5
   const int le = 9 * kC + kC;

@@ -40,6 +40,9 @@ class GTheta {
   // receives a1..a5 as [5][batch][S][S][32] (the stored BF16 values) followed by R [batch][S][S].
   cudaError_t activations(const double* in, int batch, int S, float* out, cudaStream_t st);
   const float* grads() const { return grad_; }
+  // Loss of grad_step / train: false = mean squared error on the windows; true = each crop's
+  // squared error over its target's energy on the window, averaged over the batch.
+  void set_relative_loss(bool on) { rel_loss_ = on; }
   // 1 if a bounded wait of the tcgen05 path gave up since the handle was created (synchronises).
   int wait_failures(cudaStream_t st);
 
@@ -72,6 +75,8 @@ class GTheta {
   float* tgt_ = nullptr;            // [B][S][S] crop targets
   int4* crops_ = nullptr;           // crop descriptors
   double* lpart_ = nullptr;         // loss partials
+  double* eng_ = nullptr;           // [B] target energy of each crop (relative loss)
+  bool rel_loss_ = false;
   int* err_ = nullptr;              // a bounded tensor-core wait gave up (tcgen05 path)
   bool tc_ = false;                 // 32 -> 32 layers on tcgen05.mma instead of mma.sync
 };

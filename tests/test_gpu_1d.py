@@ -38,10 +38,12 @@ def step_bound(n, eps, dt, c=3.0, wmax=1.0):
     return U_ROUND * (1 + 16 * alpha + 4 * beta * wmax)
 
 
-def oracle_and_floor(p, u0, Ufine=None):
-    """Oracle Parareal and its rounding floor (Eq. 3.18 form vs the unsimplified Newton form)."""
+def oracle_and_floor(p, u0, Ufine=None, residual_linear=False):
+    """Oracle Parareal and its rounding floor (Eq. 3.18 form vs the unsimplified Newton form; with
+    residual_linear, also the linear steps taken from their FP64 residual, as the GPU's FP32 solves
+    refined in FP64 take them)."""
     r = o.parareal(p, u0, Ufine)
-    if FINE_OF_SCHEME_NL(p):
+    if FINE_OF_SCHEME_NL(p) or residual_linear:
         q = o.Params(**{**p.__dict__, "newton_form": 1})
         floor = float(np.max(np.abs(o.parareal(q, u0).U - r.U)))
     else:
@@ -85,7 +87,7 @@ def test_propagate_matches_oracle(gpu_lib, n, scheme):
             ref = o.propagate(p, scheme, dt, nsteps, u0[b])
             err = np.max(np.abs(out[b] - ref))
             assert err <= tol, (precision, b, err, tol)
-        if scheme == "nl":
+        if scheme == "nl" or precision == 1:  # Newton, or refinement of the FP32 linear solves
             assert torch.all(newton >= nsteps).item() and torch.all(newton <= 12 * nsteps).item()
         else:
             assert torch.all(newton == 0).item()
@@ -135,11 +137,14 @@ def run_gpu(ch, cfg, u0s, reference=True):
     return pr, status
 
 
-def test_c1_linear_parareal_full_size_matches_oracle(gpu_lib):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c1_linear_parareal_full_size_matches_oracle(gpu_lib, precision):
     """1D PA-I, M=128, eps=0.05, T=0.1, N=16, dt=1e-5, one coarse step, u0 = 0.1 U(-1,1) seed 0,
-    stop at ||U^k - U^{k-1}||_inf < 1e-10."""
+    stop at ||U^k - U^{k-1}||_inf < 1e-10; the fine steps as FP64 solves (precision 0) and as FP32
+    solves refined against the FP64 residual (precision 1), both within the FP64 bound."""
     ch = gpu_lib
-    cfg = ch.Config(n=128, eps=0.05, T=0.1, n_slices=16, fine_steps=625, variant="PA-I", tol=1e-10, precision=0)
+    cfg = ch.Config(n=128, eps=0.05, T=0.1, n_slices=16, fine_steps=625, variant="PA-I", tol=1e-10,
+                    precision=precision)
     u0 = ch_inputs.initial_condition(1, 128, 0, amp=0.1)
     pr, status = run_gpu(ch, cfg, [u0])
     U = pr.get_slices(0)
@@ -147,13 +152,23 @@ def test_c1_linear_parareal_full_size_matches_oracle(gpu_lib):
     p = oracle_params(cfg)
     Uf = o.fine_solution(p, u0)
     r = o.parareal(p, u0, Uf)
-    assert np.max(np.abs(U - r.U)) <= 1e-11
-    assert np.max(np.abs(pr.get_reference(0) - Uf)) <= 1e-11
+    tol = 1e-11
+    if precision == 1:
+        # Each fine step is taken from its FP64 residual. The oracle's residual form of the same
+        # steps differs from its direct solves by rounding only, amplified by the growth of the
+        # unstable modes (about e^10 over T = 0.1 at eps = 0.05): that distance is the floor.
+        Uf1 = o.fine_solution(oracle_params(cfg, newton_form=1), u0)
+        floor = float(np.max(np.abs(Uf1 - Uf)))
+        assert floor < 1e-10
+        tol = max(tol, 4 * floor)
+        assert np.max(np.abs(pr.get_reference(0) - Uf1)) <= tol
+    assert np.max(np.abs(U - r.U)) <= tol
+    assert np.max(np.abs(pr.get_reference(0) - Uf)) <= tol
     assert st["iterations"] == r.iterations
     assert st["converged"] == r.converged
     k = min(len(st["inc"]), len(r.inc))
-    assert np.allclose(st["inc"][:k], r.inc[:k], rtol=1e-6, atol=1e-11)
-    assert np.allclose(st["err_l2"], r.err_l2, rtol=1e-6, atol=1e-11)
+    assert np.allclose(st["inc"][:k], r.inc[:k], rtol=1e-6, atol=tol)
+    assert np.allclose(st["err_l2"], r.err_l2, rtol=1e-6, atol=tol)
     pr.close()
 
 
@@ -171,8 +186,8 @@ def test_all_variants_match_oracle_and_finite_step_exactness(gpu_lib, variant, p
         Uref = pr.get_reference(b)
         # Theorem 3.2 / remark closing Section 3: after N iterations the iterate is the fine solution
         assert np.array_equal(U, Uref)
-        r = o.parareal(oracle_params(cfg), u0)
-        assert np.max(np.abs(U - r.U)) <= 1e-11, variant
+        r, tol = oracle_and_floor(oracle_params(cfg), u0, residual_linear=precision == 1)
+        assert np.max(np.abs(U - r.U)) <= tol, variant
         st = pr.stats(b)
         assert st["iterations"] == N
         assert st["err_max"][-1] == 0.0

@@ -106,13 +106,14 @@ def test_forward_is_deterministic_and_batch_independent(gpu_lib):
 
 
 @pytest.mark.parametrize("conv", ["tcgen05", "mma"])
-@pytest.mark.parametrize("S,margin", [(24, 3), (43, 6)])
-def test_gradients_match_oracle(gpu_lib, monkeypatch, S, margin, conv):
+@pytest.mark.parametrize("S,margin,relative", [(24, 3, False), (43, 6, False), (43, 6, True)])
+def test_gradients_match_oracle(gpu_lib, monkeypatch, S, margin, relative, conv):
     ch = gpu_lib
     monkeypatch.setenv("CH_GTHETA_CONV", conv)
     p, (W, b) = fp32_net(ch, *random_net(5))
     net = ch.GTheta()
     net.set_params(p)
+    net.set_loss(relative)
     B = 2
     rng = np.random.default_rng(S)
     x = (0.6 * rng.standard_normal((B, S, S))).astype(np.float32)
@@ -123,7 +124,7 @@ def test_gradients_match_oracle(gpu_lib, monkeypatch, S, margin, conv):
     want_loss = 0.0
     for i in range(B):
         _, aq = go.forward(x[i].astype(np.float64), W, b, bf16=True)
-        li, dr = go.mse_crop_loss(aq[-1][..., 0], t[i].astype(np.float64), margin)
+        li, dr = go.mse_crop_loss(aq[-1][..., 0], t[i].astype(np.float64), margin, relative)
         want_loss += li / B
         gWi, gbi = go.backward(aq, W, dr / B, bf16=True)
         for l in range(6):
@@ -328,7 +329,8 @@ def test_trained_network_beats_the_plain_coarse_step_on_held_out_data(gpu_lib):
     relative to the change F(U) - U, than the plain coarse step G(U) (one step of Eq. 2.4 over
     the slice) alone. Training pairs (the fine solver's snapshot pairs, and pairs from perturbed
     slice states, whose response is what the Parareal correction differences) and evaluation
-    pairs all come from the library's own solvers."""
+    pairs all come from the library's own solvers. Measured spread over initial weights with the
+    relative loss: learned / plain median 0.52-0.80 (0.87 with the plain mean squared error)."""
     ch = gpu_lib
     n, eps, T, N, J, stride = 63, 0.05, 0.3, 16, 8, 4
     dT = T / N
@@ -349,13 +351,25 @@ def test_trained_network_beats_the_plain_coarse_step_on_held_out_data(gpu_lib):
         pairs.append(torch.stack([Sp, ch.propagate(one, "nl", dT / J, J, Sp)], 1))
     pert = torch.cat(pairs).contiguous()
     pbase = ch.propagate(one, "lin1", dT, 1, pert.reshape(-1, n * n)).reshape(pert.shape)
-    net = ch.GTheta(seed=1)
-    for lr, steps in ((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)):
-        for rep in range(4):
-            la = net.train(X, stride=stride, steps=steps // 8, batch=32, lr=lr, seed=rep + int(lr * 1e6), base=base)
-            lb = net.train(pert, stride=1, steps=steps // 8, batch=32, lr=lr, seed=50 + rep + int(lr * 1e6),
-                           base=pbase)
-            assert np.all(np.isfinite(la)) and np.all(np.isfinite(lb))
+    # Three restarts (initial weights from seeds 1..3), the relative loss (every slice by its
+    # relative error, as the metric below counts it); kept: the lowest final training loss.
+    best = None
+    for init in (1, 2, 3):
+        net = ch.GTheta(seed=init)
+        net.set_loss(True)
+        for lr, steps in ((1e-3, 8000), (3e-4, 6000), (1e-4, 4000)):
+            for rep in range(4):
+                la = net.train(X, stride=stride, steps=steps // 8, batch=32, lr=lr, seed=rep + int(lr * 1e6),
+                               base=base)
+                lb = net.train(pert, stride=1, steps=steps // 8, batch=32, lr=lr, seed=50 + rep + int(lr * 1e6),
+                               base=pbase)
+                assert np.all(np.isfinite(la)) and np.all(np.isfinite(lb))
+        final = float(np.mean(la[-200:]) + np.mean(lb[-200:]))
+        if best is None or final < best[0]:
+            best = (final, net.get_params())
+        net.close()
+    net = ch.GTheta()
+    net.set_params(best[1])
     H = _trajectories(ch, n, eps, T, N, J, stride, range(5000, 5004))[:, ::stride]  # held out, slice ends
     U = H[:, :N].reshape(-1, n * n).contiguous()
     F = H[:, 1:].reshape(-1, n * n)
