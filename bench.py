@@ -357,6 +357,7 @@ def bench_ours(args, w, rank, world, local_rank):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
+    execution = pr.execution()
     fine_pts_per_step = B * N * J * pts
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     fine_ms, newton_total, launches, cg_per_step = 0.0, 0, 0, 0
@@ -449,7 +450,7 @@ def bench_ours(args, w, rank, world, local_rank):
     if dim == 1 and not args.no_2d and rank == 0:
         r2d = c4_step_roofline(ch, stream)
     return dict(value=value, total_ms=total_ms, step_ms=step_ms, roofline=roofline, e2e=e2e,
-                clocks=clk.summary(), launches=launches, ttol=ttol, roofline_2d=r2d)
+                clocks=clk.summary(), launches=launches, ttol=ttol, roofline_2d=r2d, execution=execution)
 
 
 def roofline_2d(w, B, fine_ms_per_launch, newton_total, cg_total, share):
@@ -512,8 +513,10 @@ def c4_step_roofline(ch, stream, warmup=1, steps=1):
     b.record(stream)
     torch.cuda.synchronize()
     step_ms = a.elapsed_time(b) / steps
+    execution = pr.execution()
     pr.close()
     r = roofline_2d(w, 1, fine_ms / steps, newton / steps, cg / steps, fine_ms / steps / step_ms)
+    r["execution"] = execution
     r["step_ms"] = round(step_ms, 2)
     r["grid_pt_steps_per_s"] = w["N"] * w["J"] * w["n"] ** 2 / (step_ms / 1e3)
     return r
@@ -954,6 +957,7 @@ def main():
         dist.destroy_process_group()
     if rank != 0:
         return
+    config["execution"] = r["execution"]
     line = {"metric": METRIC, "value": r["value"], "unit": "grid-pt-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,

@@ -179,6 +179,13 @@ ch_status ch_parareal_get_reference(ch_parareal* h, int problem, double* out_hos
 /* Statistics of the last run for one problem. */
 ch_status ch_parareal_get_stats(ch_parareal* h, int problem, ch_stats* out);
 
+/* The execution of a 2D handle's steps, fixed by its first reference or run (chosen by timing,
+ * or by the environment): 0 CUDA graphs, 1 persistent cooperative kernel, 2 host-driven
+ * launches, 3 one thread-block cluster per unit; -1 before that choice. 1D handles: the fine
+ * sweep's CTA mapping, 0 the default or 1 the alternative (T/2 threads, twice the rows each).
+ * CH_ERR_INVALID for a NULL argument. */
+ch_status ch_parareal_get_execution(ch_parareal* h, int* out);
+
 /* Releases the handle and its device memory; NULL is accepted. */
 void ch_parareal_destroy(ch_parareal* h);
 
@@ -191,7 +198,10 @@ const char* ch_status_string(ch_status s);
 /* Orthonormal 2D sine transform (DST-I in x and y, its own inverse) of `batch` FP32 n x n
  * fields: out = S X S, S_jk = sqrt(2/(n+1)) sin(pi j k / (n+1)). The diagonalising transform of
  * D_h (eigenvalues below Eq. 3.2) used by the 2D solver. in_dev != out_dev, device arrays
- * [batch][n][n]; n + 1 a power of two in 16..512. Synchronises the stream. */
+ * [batch][n][n]; n + 1 a power of two in 16..512. FP32 arithmetic: about 1e-7 of the largest
+ * output for n <= 255 (FFTs of the odd extension, length 2(n + 1)), about 1e-6 for n = 511
+ * (FFTs of length n + 1 whose odd coefficients are running sums of FFT outputs). Synchronises
+ * the stream. */
 ch_status ch_sine_transform_2d(const float* in_dev, float* out_dev, int batch, int n, void* cuda_stream);
 
 /* Stateless propagation (the fine or coarse propagator as a batched kernel): applies `nsteps`

@@ -27,6 +27,7 @@ EXPORTED_SYMBOLS = [
     "ch_parareal_set_initial_device", "ch_parareal_get_slices_batch",
     "ch_parareal_compute_reference", "ch_parareal_run", "ch_parareal_get_slices",
     "ch_parareal_get_slices_device", "ch_parareal_get_reference", "ch_parareal_get_stats",
+    "ch_parareal_get_execution",
     "ch_parareal_destroy", "ch_parareal_last_error", "ch_status_string", "ch_propagate",
     "ch_parareal_solve_noalloc", "ch_sine_transform_2d", "ch_parareal_set_coarse_model",
     "ch_parareal_get_reference_device", "ch_parareal_set_eps", "ch_gtheta_create", "ch_gtheta_destroy", "ch_gtheta_last_error",
@@ -123,6 +124,7 @@ def load(build_if_missing: bool = True):
     lib.ch_parareal_get_slices_device.argtypes = [vp, vp, sz]
     lib.ch_parareal_get_reference.argtypes = [vp, C.c_int, d, sz]
     lib.ch_parareal_get_stats.argtypes = [vp, C.c_int, C.POINTER(_Stats)]
+    lib.ch_parareal_get_execution.argtypes = [vp, C.POINTER(C.c_int)]
     lib.ch_parareal_destroy.argtypes = [vp]
     lib.ch_parareal_destroy.restype = None
     lib.ch_parareal_last_error.argtypes = [vp]
@@ -266,6 +268,17 @@ class Parareal:
                                                        out.ctypes.data_as(C.POINTER(C.c_double)), out.size),
                     "ch_parareal_get_reference")
         return out
+
+    def execution(self) -> str:
+        """The execution its first reference or run chose: 2D "graphs", "persistent", "host" or
+        "cluster"; 1D "default" or "alt" (the fine sweep's CTA mapping); "" before that."""
+        v = C.c_int()
+        self._check(self.lib.ch_parareal_get_execution(self._h, C.byref(v)), "ch_parareal_get_execution")
+        if v.value < 0:
+            return ""
+        if self.cfg.dim == 2:
+            return ("graphs", "persistent", "host", "cluster")[v.value]
+        return ("default", "alt")[v.value]
 
     def stats(self, problem: int) -> dict:
         st = _Stats()

@@ -127,14 +127,21 @@ __device__ __forceinline__ float2 odd_ext_s(const float2* s, bool v0, bool v1, i
 // Shared-memory index with one padding element every 8 complex values: the radix-8 stores of
 // the early stages write with strides of 8 and 64 elements, which would otherwise hit the same
 // banks (16-way conflicts at stride 8).
-__device__ __forceinline__ int pad8(int x) { return x + (x >> 3); }
+__host__ __device__ constexpr int pad8(int x) { return x + (x >> 3); }
 
 // Row stride (complex values) of the transform buffer: a padded row of L = 2N plus one value,
 // so that the eight row pairs an epilogue half-warp reads start in eight different banks (a
 // stride of 9L/8 complex values is a multiple of 32 words: all eight in one bank).
+// Length of the complex FFT behind a DST-I of length N - 1: 2N (odd extension, two rows packed)
+// except on the 512 x 512 grid, whose rows are transformed through an FFT of length N (dst_half).
+template <int N>
+__host__ __device__ constexpr int fft_len() {
+  return N == 512 ? N : 2 * N;
+}
+
 template <int N>
 __host__ __device__ constexpr int buf_row() {
-  return 2 * N + (2 * N) / 8 + 1;
+  return fft_len<N>() + fft_len<N>() / 8 + 1;
 }
 template <int N>
 __host__ __device__ constexpr int buf_elems() {
@@ -249,11 +256,11 @@ __device__ __forceinline__ float2 twmul32(float2 a, int j) {
   return cmul(a, w32(j));
 }
 
-// L-point FFT in registers (L = 16 or 32), radix-2 decimation in frequency: on return
-// v[i] = X[bit-reversed i]. The stage twiddle W_L^(j L / (2 span)) is W_32^(j 16 / span).
+// 16-point FFT in registers, radix-2 decimation in frequency: on return v[i] = X[bitrev4(i)].
+// The stage twiddle W_16^(j 8 / span) is W_32^(j 16 / span).
 template <int L>
 __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
-  static_assert(L == 16 || L == 32, "register FFT length");
+  static_assert(L == 16, "register FFT length");
 #pragma unroll
   for (int span = L / 2; span >= 1; span >>= 1) {
 #pragma unroll
@@ -268,75 +275,19 @@ __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
   }
 }
 
-__device__ __forceinline__ void fft32_dif(float2 (&v)[32]) { fft_dif<32>(v); }
-
-__host__ __device__ constexpr int bitrev5(int i) {
-  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
-}
 __host__ __device__ constexpr int bitrev4(int i) {
   return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
 }
 
-// SM: the input rows are the warp's own row of `buf` as (x0, x1) pairs (odd_ext_s), not `src`.
-template <int N, bool SM = false>
-__device__ __forceinline__ void fft_rows_warp(float2* buf, const float2* tw2, const float* src, int a0) {
-  static_assert(N == 512 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 1024");
-  constexpr int n = N - 1;
-  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const int ra = a0 + 2 * f, rb = ra + 1;
-  float2* s = buf + f * buf_row<N>();
-  float2 v[32];
-  if constexpr (SM) {
-#pragma unroll
-    for (int m1 = 0; m1 < 32; ++m1) v[m1] = odd_ext_s<N>(s, ra < n, rb < n, 32 * m1 + t);
-    __syncwarp();  // every lane has read the row before any lane overwrites it
-  } else {
-    const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
-    const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
-#pragma unroll
-    for (int m1 = 0; m1 < 32; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
-  }
-  fft32_dif(v);
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int k1 = bitrev5(i);
-    s[k1 * 33 + t] = cmul(v[i], tw2[k1 * 32 + t]);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int m2 = 0; m2 < 32; ++m2) v[m2] = s[t * 33 + m2];
-  __syncwarp();
-  fft32_dif(v);
-#pragma unroll
-  for (int i = 0; i < 32; ++i) s[pad8(t + 32 * bitrev5(i))] = v[i];
-}
-
-// The 256 x 256 grid (L = 512 = 32 x 16), one warp per row-pair FFT with 16 values per lane:
-// lane t holds y[32 m1 + t], m1 < 16; a 16-point FFT over m1 in registers; the twiddles
-// W_512^(t k1) (table tw2[k1][t]); a transpose through the FFT's buffer row (rows padded to 34
-// entries: the lane pairs below then read distinct banks); then each 32-point FFT over t, for one
-// k1, is split across the lane pair (2 k1, 2 k1 + 1): each lane a 16-point FFT of the even / odd
-// samples (E, O), and one shuffle combines them, X[k1 + 16 k2] = E[k2] + W_32^k2 O[k2] (even lane,
-// k2 < 16) and X[k1 + 16 (k2 + 16)] = E[k2] - W_32^k2 O[k2] (odd lane).
-template <int N, bool SM = false>
-__device__ __forceinline__ void fft_rows_warp512(float2* buf, const float2* tw2, const float* src, int a0) {
-  static_assert(N == 256 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 512");
-  static_assert(16 * 34 <= buf_row<N>(), "transpose rows fit the buffer row");
-  constexpr int n = N - 1;
-  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const int ra = a0 + 2 * f, rb = ra + 1;
-  float2* s = buf + f * buf_row<N>();
-  float2 v[16];
-  if constexpr (SM) {
-#pragma unroll
-    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext_s<N>(s, ra < n, rb < n, 32 * m1 + t);
-    __syncwarp();  // every lane has read the row before any lane overwrites it
-  } else {
-    const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
-    const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
-#pragma unroll
-    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
-  }
+// A 512-point FFT of one row pair by one warp, 16 values per lane (four-step, 512 = 32 x 16): on
+// entry lane t holds v[m1] = y[32 m1 + t], m1 < 16; a 16-point FFT over m1 in registers; the
+// twiddles W_512^(t k1) (table tw2[k1][t]); a transpose through the warp's buffer row s (rows
+// padded to 34 entries: the lane pairs below then read distinct banks); then each 32-point FFT
+// over t, for one k1, is split across the lane pair (2 k1, 2 k1 + 1): each lane a 16-point FFT of
+// the even / odd samples (E, O), and one shuffle combines them, X[k1 + 16 k2] = E[k2] +
+// W_32^k2 O[k2] (even lane, k2 < 16) and X[k1 + 16 (k2 + 16)] = E[k2] - W_32^k2 O[k2] (odd lane).
+// On return X[k] is at s[pad8(k)], k < 512.
+__device__ __forceinline__ void fft512_warp(float2 (&v)[16], float2* s, const float2* tw2, int t) {
   fft_dif<16>(v);
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
@@ -359,12 +310,110 @@ __device__ __forceinline__ void fft_rows_warp512(float2* buf, const float2* tw2,
   }
 }
 
-// The row FFTs of a transform pass (four-step warp versions at L = 1024 and 512); ends with a
+// The 256 x 256 grid: the odd extension of each row pair (length 512) through fft512_warp.
+// SM: the input rows are the warp's own row of `buf` as (x0, x1) pairs (odd_ext_s), not `src`.
+template <int N, bool SM = false>
+__device__ __forceinline__ void fft_rows_warp512(float2* buf, const float2* tw2, const float* src, int a0) {
+  static_assert(N == 256 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 512");
+  static_assert(16 * 34 <= buf_row<N>(), "transpose rows fit the buffer row");
+  constexpr int n = N - 1;
+  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int ra = a0 + 2 * f, rb = ra + 1;
+  float2* s = buf + f * buf_row<N>();
+  float2 v[16];
+  if constexpr (SM) {
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext_s<N>(s, ra < n, rb < n, 32 * m1 + t);
+    __syncwarp();  // every lane has read the row before any lane overwrites it
+  } else {
+    const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
+    const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
+  }
+  fft512_warp(v, s, tw2, t);
+}
+
+// The 512 x 512 grid: the DST-I of length N - 1 = 511 of each row from an FFT of length N = 512
+// (half the odd extension's), one warp per row pair. With y_0 = y_N = 0 and s_j = sin(pi j / N),
+//   w_j = s_j (y_j + y_{N-j}) + (y_j - y_{N-j}) / 2,   j < N,
+// and W = FFT(w) (W_k = sum_j w_j e^{-2 pi i j k / N}), the sine coefficients
+// F_m = sum_j y_j sin(pi j m / N) are F_{2k} = -Im W_k and F_{2k+1} = F_{2k-1} + Re W_k
+// (F_1 = Re W_0 / 2): the symmetric part of w carries the odd coefficients as differences, the
+// antisymmetric part the even ones (Numerical Recipes' sine transform, written here from that
+// identity). The two rows are packed as z = w_a + i w_b; W_a, W_b are split from Z_k and
+// conj(Z_{N-k}), and the odd coefficients summed by a warp scan (each lane eight consecutive k).
+// The buffer row then holds what the odd-extension FFT of length 2N would have produced,
+// (2 F_m(b), -2 F_m(a)) at pad8(m), so the pass epilogues are the same for every grid.
+// twd: tw2[16][32] for fft512_warp, then s_j, j < 512, as floats.
+template <int N>
+__device__ __forceinline__ void fft_rows_half512(float2* buf, const float2* twd, const float* src, int a0) {
+  static_assert(N == 512 && kDstRows == 16 && kThreads == 256, "one warp per row pair, FFT length N");
+  static_assert(16 * 34 <= buf_row<N>() && pad8(N - 1) < buf_row<N>(), "the FFT fits the buffer row");
+  constexpr int n = N - 1;
+  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const int ra = a0 + 2 * f, rb = ra + 1;
+  const bool va = ra < n, vb = rb < n;
+  const float* r0 = src + (size_t)(va ? ra : 0) * n;
+  const float* r1 = src + (size_t)(vb ? rb : 0) * n;
+  const float* sj = reinterpret_cast<const float*>(twd + 512);
+  float2* s = buf + f * buf_row<N>();
+  float2 v[16];
+#pragma unroll
+  for (int m1 = 0; m1 < 16; ++m1) {
+    const int j = 32 * m1 + t;
+    const bool in = j > 0;  // y_0 = y_N = 0
+    const int q = in ? j - 1 : 0, qr = in ? N - j - 1 : 0;
+    const float a = __ldcg(r0 + q), ar = __ldcg(r0 + qr), b = __ldcg(r1 + q), br = __ldcg(r1 + qr);
+    const float sn = sj[j];
+    const float wa = fmaf(sn, a + ar, 0.5f * (a - ar)), wb = fmaf(sn, b + br, 0.5f * (b - br));
+    v[m1] = make_float2((in && va) ? wa : 0.f, (in && vb) ? wb : 0.f);
+  }
+  fft512_warp(v, s, twd, t);
+  __syncwarp();
+  // Lane t: k = 8 t + i, i < 8. W_a = (Z_k + conj Z_{N-k}) / 2, W_b = (Z_k - conj Z_{N-k}) / (2i).
+  float ea[8], eb[8], oa[8], ob[8];
+  float sa = 0.f, sb = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = 8 * t + i;
+    const float2 z = s[pad8(k)], zr = s[pad8((N - k) & (N - 1))];
+    const float war = 0.5f * (z.x + zr.x), wai = 0.5f * (z.y - zr.y);
+    const float wbr = 0.5f * (z.y + zr.y), wbi = -0.5f * (z.x - zr.x);
+    ea[i] = -wai;  // F_{2k} (row a); unused at k = 0
+    eb[i] = -wbi;
+    sa += (k == 0) ? 0.5f * war : war;  // running sums: F_{2k+1} of this lane's part
+    sb += (k == 0) ? 0.5f * wbr : wbr;
+    oa[i] = sa;
+    ob[i] = sb;
+  }
+  // exclusive warp scan of the lanes' totals
+  float pa = sa, pb = sb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float qa = __shfl_up_sync(0xffffffffu, pa, o), qb = __shfl_up_sync(0xffffffffu, pb, o);
+    if (t >= o) {
+      pa += qa;
+      pb += qb;
+    }
+  }
+  pa -= sa;
+  pb -= sb;
+  __syncwarp();  // every lane has read Z before any lane overwrites it
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = 8 * t + i;
+    if (k > 0) s[pad8(2 * k)] = make_float2(2.f * eb[i], -2.f * ea[i]);
+    s[pad8(2 * k + 1)] = make_float2(2.f * (pb + ob[i]), -2.f * (pa + oa[i]));
+  }
+}
+
+// The row FFTs of a transform pass (the warp versions at 512 x 512 and 256 x 256); ends with a
 // block barrier, after which `buf` holds the transforms for the epilogue.
 template <int N, int F>
 __device__ __forceinline__ void fft_rows_any(float2* buf, const float2* twd, const float* src, int a0) {
   if constexpr (N == 512) {
-    fft_rows_warp<N>(buf, twd, src, a0);
+    fft_rows_half512<N>(buf, twd, src, a0);
     __syncthreads();
   } else if constexpr (N == 256) {
     fft_rows_warp512<N>(buf, twd, src, a0);
@@ -394,12 +443,8 @@ __host__ __device__ constexpr bool fuse_cg() {
 // buf[f * buf_row + k], k < n (warp_fft grids only); ends with a block barrier.
 template <int N>
 __device__ __forceinline__ void fft_rows_own(float2* buf, const float2* twd, int a0) {
-  static_assert(warp_fft<N>(), "rows held in the buffer need the warp FFT");
-  if constexpr (N == 512) {
-    fft_rows_warp<N, true>(buf, twd, nullptr, a0);
-  } else {
-    fft_rows_warp512<N, true>(buf, twd, nullptr, a0);
-  }
+  static_assert(N == 256, "rows held in the buffer: the 256 x 256 warp FFT");
+  fft_rows_warp512<N, true>(buf, twd, nullptr, a0);
   __syncthreads();
 }
 
@@ -638,16 +683,20 @@ size_t correct_partials(int count) { return (size_t)count * 4 * kBlk; }
 // Twiddles of the stages after the first of fft_rows<N> (radix 8 with Ns = 8, 64, ..., then the
 // radix-2 or radix-4 stage), stage after stage: entry (r - 1) Ns + k = exp(-2 pi i m / L) with
 // m = r k L / (R Ns), r = 1..R-1, k < Ns (host libm, rounded to FP32). At most L entries. For
-// N = 512 and 256 the four-step tables of fft_rows_warp / fft_rows_warp512 instead.
+// N = 512 and 256 the table of fft512_warp instead (and at 512 the sines of fft_rows_half512).
 static std::vector<float2> twiddle_table(int N) {
   const int L = 2 * N;
-  if (N == 512 || N == 256) {  // four-step warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / L), t < 32
-    std::vector<float2> tw(L);
-    for (int k1 = 0; k1 < L / 32; ++k1)
+  if (N == 512 || N == 256) {  // 512-point warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / 512), t < 32
+    std::vector<float2> tw(L, make_float2(0.f, 0.f));
+    for (int k1 = 0; k1 < 16; ++k1)
       for (int t = 0; t < 32; ++t) {
-        const double a = -2.0 * M_PI * k1 * t / L;
+        const double a = -2.0 * M_PI * k1 * t / 512;
         tw[k1 * 32 + t] = make_float2(float(std::cos(a)), float(std::sin(a)));
       }
+    if (N == 512) {  // then sin(pi j / N), j < N, as floats (fft_rows_half512)
+      float* sj = reinterpret_cast<float*>(tw.data() + 512);
+      for (int j = 0; j < N; ++j) sj[j] = float(std::sin(M_PI * j / N));
+    }
     return tw;
   }
   int lg = 0;
@@ -1078,7 +1127,8 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   static_assert(kThreads % kDstRows == 0, "epilogue thread layout");
   constexpr int KS = kThreads / kDstRows;  // output rows apart of one thread's elements
   constexpr int J = (n + KS - 1) / KS;     // epilogue elements per thread
-  constexpr int UB = J < 16 ? J : 16;      // elements whose loads are issued together
+  constexpr int UBM = (EPI == E_W || EPI == E_UPDATE) ? 8 : 16;  // two operands, or an FP64 one
+  constexpr int UB = J < UBM ? J : UBM;       // elements whose loads are issued together
   static_assert(J % UB == 0, "epilogue batches");
   __shared__ double sh[kThreads / 32];
   const size_t pts = (size_t)n * n;
@@ -2254,10 +2304,10 @@ __host__ __device__ constexpr bool is_dst_phase(int ph) {
          ph == PH_X2 || ph == PH_P1U || ph == PH_X1U || ph == PH_P23 || ph == PH_P4N;
 }
 
-// Four blocks per SM (a batch's items all resident at n = 255), two for the length-1024
-// transforms of n = 511, whose butterflies need the registers.
+// Four blocks per SM: 64 registers hold the 16 complex values a lane carries through the warp
+// FFTs of 256 x 256 and 512 x 512 (at 256 x 256 a batch's items are then all resident).
 template <int N, int PH>
-__global__ void __launch_bounds__(kThreads, (N >= 512 ? 2 : 4)) k2_phase(PArgs a, int have_prev) {
+__global__ void __launch_bounds__(kThreads, 4) k2_phase(PArgs a, int have_prev) {
   constexpr int L = 2 * N, nb = (N - 1 + kDstRows - 1) / kDstRows;
   extern __shared__ float2 smem2[];
   float2* buf = smem2;

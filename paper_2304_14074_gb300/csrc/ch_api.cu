@@ -626,7 +626,7 @@ ch_status ensure_tuned2d(ch_parareal* h) {
     for (int rep = 0; rep < 2 && s == CH_OK; ++rep) {
       s = gather_units(h, h->U, offs, true);
       if (s == CH_OK && cudaEventRecord(a, h->st) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning event");
-      if (s == CH_OK) s = prop2(h, units, fine2(h), h->p.dt, 1);
+      if (s == CH_OK) s = prop2(h, units, fine2(h), h->p.dt, rep == 0 ? 1 : 2);
       if (s == CH_OK && cudaEventRecord(e2, h->st) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning event");
       if (s == CH_OK && cudaEventSynchronize(e2) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning sync");
       if (s == CH_OK && cudaEventElapsedTime(&ms, a, e2) != cudaSuccess) s = fail(h, CH_ERR_CUDA, "tuning time");
@@ -1001,6 +1001,17 @@ ch_status ch_parareal_get_reference(ch_parareal* h, int problem, double* out_hos
     return fail(h, CH_ERR_INVALID, "get_reference: bad problem index, pointer or length");
   CH_CUDA(h, cudaMemcpyAsync(out_host, h->Uref + (size_t)problem * want, want * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CH_CUDA(h, cudaStreamSynchronize(h->st));
+  return CH_OK;
+}
+
+ch_status ch_parareal_get_execution(ch_parareal* h, int* out) {
+  if (!h) return CH_ERR_INVALID;
+  if (!out) return fail(h, CH_ERR_INVALID, "get_execution: null pointer");
+  if (h->dim == 2) {
+    *out = h->tuned ? (int)h->p2->path() : -1;
+  } else {
+    *out = h->tuned ? h->p.alt : -1;
+  }
   return CH_OK;
 }
 
