@@ -94,7 +94,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # all slices iterating), from a one-launch ncu capture of dram__bytes_read.sum +
 # dram__bytes_write.sum on the current kernel; independent of the fine steps per slice (the slice
 # state stays in registers). None when the kernel has changed since the capture.
-FINE_SWEEP_1D_TRAFFIC = {(1024, 256, 64): 219.1e6}
+FINE_SWEEP_1D_TRAFFIC = {(1024, 256, 64): 218.5e6}
 
 
 # 2D fine sweep, algorithmic DRAM/L2 bytes per grid point and unit, each array read or written
@@ -111,10 +111,11 @@ BYTES_NEWTON_2D = 16 + 32 + 8 + 16 + 8 + 20
 BYTES_STEP_2D = 16 + 32
 # DRAM traffic of the 2D fine sweep on the 512 x 512 grid, from a one-pass ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum over the kernels of a batched propagation of 64
-# slices (current kernels): a full CG iteration of all 64 units moves 1098-1232 MB of DRAM traffic
-# against 1471 MB of algorithmic bytes (the L2 keeps part of each phase's output for the next).
-# The fine sweep's traffic per launch is reported as that ratio times its algorithmic bytes.
-TRAFFIC_2D_OVER_ALGORITHMIC = {511: 0.79}
+# slices (current kernels): the first two CG iterations of all 64 units move 565 + 1099 MB of DRAM
+# traffic against 735 + 1471 MB of algorithmic bytes (the L2 keeps part of each phase's output for
+# the next). The fine sweep's traffic per launch is reported as that ratio times its algorithmic
+# bytes.
+TRAFFIC_2D_OVER_ALGORITHMIC = {511: 0.754}
 
 
 def max_over_ranks(value, dist, device):
