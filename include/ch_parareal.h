@@ -199,9 +199,9 @@ const char* ch_status_string(ch_status s);
  * fields: out = S X S, S_jk = sqrt(2/(n+1)) sin(pi j k / (n+1)). The diagonalising transform of
  * D_h (eigenvalues below Eq. 3.2) used by the 2D solver. in_dev != out_dev, device arrays
  * [batch][n][n]; n + 1 a power of two in 16..512. FP32 arithmetic: about 1e-7 of the largest
- * output for n <= 255 (FFTs of the odd extension, length 2(n + 1)), about 1e-6 for n = 511
- * (FFTs of length n + 1 whose odd coefficients are running sums of FFT outputs). Synchronises
- * the stream. */
+ * output for n <= 127 (FFTs of the odd extension, length 2(n + 1)), about 1e-6 for n = 255 and
+ * 511 (FFTs of length n + 1 whose odd coefficients are running sums of FFT outputs).
+ * Synchronises the stream. */
 ch_status ch_sine_transform_2d(const float* in_dev, float* out_dev, int batch, int n, void* cuda_stream);
 
 /* Stateless propagation (the fine or coarse propagator as a batched kernel): applies `nsteps`

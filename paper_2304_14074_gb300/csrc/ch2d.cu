@@ -112,18 +112,6 @@ __device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const fl
   return make_float2(sa, sb);
 }
 
-// The odd extension of a row pair held in shared memory as (x0[k], x1[k]) pairs at s[k], k < n.
-template <int N>
-__device__ __forceinline__ float2 odd_ext_s(const float2* s, bool v0, bool v1, int m) {
-  constexpr int L = 2 * N;
-  const bool zero = (m == 0 || m == N), neg = m > N;
-  const int q = zero ? 0 : (neg ? L - m - 1 : m - 1);
-  const float2 c = s[q];
-  const float sa = (zero || !v0) ? 0.f : (neg ? -c.x : c.x);
-  const float sb = (zero || !v1) ? 0.f : (neg ? -c.y : c.y);
-  return make_float2(sa, sb);
-}
-
 // Shared-memory index with one padding element every 8 complex values: the radix-8 stores of
 // the early stages write with strides of 8 and 64 elements, which would otherwise hit the same
 // banks (16-way conflicts at stride 8).
@@ -133,10 +121,11 @@ __host__ __device__ constexpr int pad8(int x) { return x + (x >> 3); }
 // so that the eight row pairs an epilogue half-warp reads start in eight different banks (a
 // stride of 9L/8 complex values is a multiple of 32 words: all eight in one bank).
 // Length of the complex FFT behind a DST-I of length N - 1: 2N (odd extension, two rows packed)
-// except on the 512 x 512 grid, whose rows are transformed through an FFT of length N (dst_half).
+// except on the 256 x 256 and 512 x 512 grids, whose rows are transformed through an FFT of
+// length N (fft_rows_half).
 template <int N>
 __host__ __device__ constexpr int fft_len() {
-  return N == 512 ? N : 2 * N;
+  return (N == 512 || N == 256) ? N : 2 * N;
 }
 
 template <int N>
@@ -256,11 +245,11 @@ __device__ __forceinline__ float2 twmul32(float2 a, int j) {
   return cmul(a, w32(j));
 }
 
-// 16-point FFT in registers, radix-2 decimation in frequency: on return v[i] = X[bitrev4(i)].
-// The stage twiddle W_16^(j 8 / span) is W_32^(j 16 / span).
+// 8- or 16-point FFT in registers, radix-2 decimation in frequency: on return v[i] =
+// X[bitrev3(i)] or X[bitrev4(i)]. The stage twiddle W_(2 span)^j is W_32^(j 16 / span).
 template <int L>
 __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
-  static_assert(L == 16, "register FFT length");
+  static_assert(L == 8 || L == 16, "register FFT length");
 #pragma unroll
   for (int span = L / 2; span >= 1; span >>= 1) {
 #pragma unroll
@@ -275,6 +264,7 @@ __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
   }
 }
 
+__host__ __device__ constexpr int bitrev3(int i) { return ((i & 1) << 2) | (i & 2) | ((i & 4) >> 2); }
 __host__ __device__ constexpr int bitrev4(int i) {
   return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
 }
@@ -310,57 +300,74 @@ __device__ __forceinline__ void fft512_warp(float2 (&v)[16], float2* s, const fl
   }
 }
 
-// The 256 x 256 grid: the odd extension of each row pair (length 512) through fft512_warp.
-// SM: the input rows are the warp's own row of `buf` as (x0, x1) pairs (odd_ext_s), not `src`.
-template <int N, bool SM = false>
-__device__ __forceinline__ void fft_rows_warp512(float2* buf, const float2* tw2, const float* src, int a0) {
-  static_assert(N == 256 && kDstRows == 16 && kThreads == 256, "one warp per row pair, L = 512");
-  static_assert(16 * 34 <= buf_row<N>(), "transpose rows fit the buffer row");
-  constexpr int n = N - 1;
-  const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
-  const int ra = a0 + 2 * f, rb = ra + 1;
-  float2* s = buf + f * buf_row<N>();
-  float2 v[16];
-  if constexpr (SM) {
+// A 256-point FFT of one row pair by one warp, 8 values per lane (four-step, 256 = 8 x 32): on
+// entry lane t holds v[m1] = y[32 m1 + t], m1 < 8; an 8-point FFT over m1 in registers; the
+// twiddles W_256^(t k1) (table tw2[k1][t]); a transpose through the warp's buffer row s (rows
+// padded to 36 entries: a half-warp's reads below then fall in distinct banks); then the 32-point
+// FFT over t for one k1 is split across the lane quad 4 k1 + q: lane q takes the samples
+// t = 4 m + q, an 8-point FFT E_q over m, and two shuffle steps combine the quad: with
+// q = q0 + 2 q1, G_q0[k' + 8 q1] = E_q0[k'] +- W_16^k' E_(q0+2)[k'] (partners 2 apart), then
+// X[k'' + 16 q0] = G_0[k''] +- W_32^k'' G_1[k''] (partners 1 apart), k'' = k' + 8 q1. On return
+// X[k] is at s[pad8(k)], k < 256.
+__device__ __forceinline__ void fft256_warp(float2 (&v)[8], float2* s, const float2* tw2, int t) {
+  constexpr int R = 36;
+  fft_dif<8>(v);
 #pragma unroll
-    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext_s<N>(s, ra < n, rb < n, 32 * m1 + t);
-    __syncwarp();  // every lane has read the row before any lane overwrites it
-  } else {
-    const float* r0 = src + (size_t)(ra < n ? ra : 0) * n;
-    const float* r1 = src + (size_t)(rb < n ? rb : 0) * n;
-#pragma unroll
-    for (int m1 = 0; m1 < 16; ++m1) v[m1] = odd_ext<N>(r0, r1, ra < n, rb < n, 32 * m1 + t);
+  for (int i = 0; i < 8; ++i) {
+    const int k1 = bitrev3(i);
+    s[k1 * R + t] = cmul(v[i], tw2[k1 * 32 + t]);
   }
-  fft512_warp(v, s, tw2, t);
+  __syncwarp();
+  const int k1 = t >> 2, q0 = t & 1, q1 = (t >> 1) & 1;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = s[k1 * R + 4 * m + (t & 3)];
+  __syncwarp();
+  fft_dif<8>(v);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int kp = bitrev3(i);
+    // partners 2 apart: the q1 = 1 lane holds E_(q0+2), scaled by W_16^kp = W_32^(2 kp)
+    float2 w = q1 ? twmul32(v[i], 2 * kp) : v[i];
+    float2 o = make_float2(__shfl_xor_sync(0xffffffffu, w.x, 2), __shfl_xor_sync(0xffffffffu, w.y, 2));
+    const float2 g = q1 ? make_float2(o.x - w.x, o.y - w.y) : make_float2(w.x + o.x, w.y + o.y);
+    // partners 1 apart: the q0 = 1 lane holds G_1[k''], scaled by W_32^k'' = W_32^kp (-i)^q1
+    float2 gt = twmul32(g, kp);
+    if (q1) gt = make_float2(gt.y, -gt.x);
+    w = q0 ? gt : g;
+    o = make_float2(__shfl_xor_sync(0xffffffffu, w.x, 1), __shfl_xor_sync(0xffffffffu, w.y, 1));
+    const float2 X = q0 ? make_float2(o.x - w.x, o.y - w.y) : make_float2(w.x + o.x, w.y + o.y);
+    s[pad8(k1 + 8 * (kp + 8 * q1 + 16 * q0))] = X;
+  }
 }
 
-// The 512 x 512 grid: the DST-I of length N - 1 = 511 of each row from an FFT of length N = 512
-// (half the odd extension's), one warp per row pair. With y_0 = y_N = 0 and s_j = sin(pi j / N),
+// The 256 x 256 and 512 x 512 grids: the DST-I of length N - 1 of each row from an FFT of length
+// N (half the odd extension's), one warp per row pair. With y_0 = y_N = 0 and s_j = sin(pi j / N),
 //   w_j = s_j (y_j + y_{N-j}) + (y_j - y_{N-j}) / 2,   j < N,
 // and W = FFT(w) (W_k = sum_j w_j e^{-2 pi i j k / N}), the sine coefficients
 // F_m = sum_j y_j sin(pi j m / N) are F_{2k} = -Im W_k and F_{2k+1} = F_{2k-1} + Re W_k
 // (F_1 = Re W_0 / 2): the symmetric part of w carries the odd coefficients as differences, the
 // antisymmetric part the even ones (Numerical Recipes' sine transform, written here from that
 // identity). The two rows are packed as z = w_a + i w_b; W_a, W_b are split from Z_k and
-// conj(Z_{N-k}), and the odd coefficients summed by a warp scan (each lane eight consecutive k).
+// conj(Z_{N-k}), and the odd coefficients summed by a warp scan (each lane N / 64 consecutive k).
 // The buffer row then holds what the odd-extension FFT of length 2N would have produced,
 // (2 F_m(b), -2 F_m(a)) at pad8(m), so the pass epilogues are the same for every grid.
-// twd: tw2[16][32] for fft512_warp, then s_j, j < 512, as floats.
+// twd: tw2[N / 32][32] of the warp FFT, then s_j, j < N, as floats.
 template <int N>
-__device__ __forceinline__ void fft_rows_half512(float2* buf, const float2* twd, const float* src, int a0) {
-  static_assert(N == 512 && kDstRows == 16 && kThreads == 256, "one warp per row pair, FFT length N");
-  static_assert(16 * 34 <= buf_row<N>() && pad8(N - 1) < buf_row<N>(), "the FFT fits the buffer row");
-  constexpr int n = N - 1;
+__device__ __forceinline__ void fft_rows_half(float2* buf, const float2* twd, const float* src, int a0) {
+  static_assert((N == 512 || N == 256) && kDstRows == 16 && kThreads == 256, "one warp per row pair");
+  constexpr int n = N - 1, VPL = N / 32, KPL = N / 64;
+  static_assert(pad8(N - 1) < buf_row<N>() && (N == 512 ? 16 * 34 : 7 * 36 + 32) <= buf_row<N>(),
+                "the FFT fits the buffer row");
   const int f = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int ra = a0 + 2 * f, rb = ra + 1;
   const bool va = ra < n, vb = rb < n;
   const float* r0 = src + (size_t)(va ? ra : 0) * n;
   const float* r1 = src + (size_t)(vb ? rb : 0) * n;
-  const float* sj = reinterpret_cast<const float*>(twd + 512);
+  const float* sj = reinterpret_cast<const float*>(twd + N);
   float2* s = buf + f * buf_row<N>();
-  float2 v[16];
+  float2 v[VPL];
 #pragma unroll
-  for (int m1 = 0; m1 < 16; ++m1) {
+  for (int m1 = 0; m1 < VPL; ++m1) {
     const int j = 32 * m1 + t;
     const bool in = j > 0;  // y_0 = y_N = 0
     const int q = in ? j - 1 : 0, qr = in ? N - j - 1 : 0;
@@ -369,14 +376,18 @@ __device__ __forceinline__ void fft_rows_half512(float2* buf, const float2* twd,
     const float wa = fmaf(sn, a + ar, 0.5f * (a - ar)), wb = fmaf(sn, b + br, 0.5f * (b - br));
     v[m1] = make_float2((in && va) ? wa : 0.f, (in && vb) ? wb : 0.f);
   }
-  fft512_warp(v, s, twd, t);
+  if constexpr (N == 512) {
+    fft512_warp(v, s, twd, t);
+  } else {
+    fft256_warp(v, s, twd, t);
+  }
   __syncwarp();
-  // Lane t: k = 8 t + i, i < 8. W_a = (Z_k + conj Z_{N-k}) / 2, W_b = (Z_k - conj Z_{N-k}) / (2i).
-  float ea[8], eb[8], oa[8], ob[8];
+  // Lane t: k = KPL t + i. W_a = (Z_k + conj Z_{N-k}) / 2, W_b = (Z_k - conj Z_{N-k}) / (2i).
+  float ea[KPL], eb[KPL], oa[KPL], ob[KPL];
   float sa = 0.f, sb = 0.f;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int k = 8 * t + i;
+  for (int i = 0; i < KPL; ++i) {
+    const int k = KPL * t + i;
     const float2 z = s[pad8(k)], zr = s[pad8((N - k) & (N - 1))];
     const float war = 0.5f * (z.x + zr.x), wai = 0.5f * (z.y - zr.y);
     const float wbr = 0.5f * (z.y + zr.y), wbi = -0.5f * (z.x - zr.x);
@@ -401,8 +412,8 @@ __device__ __forceinline__ void fft_rows_half512(float2* buf, const float2* twd,
   pb -= sb;
   __syncwarp();  // every lane has read Z before any lane overwrites it
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int k = 8 * t + i;
+  for (int i = 0; i < KPL; ++i) {
+    const int k = KPL * t + i;
     if (k > 0) s[pad8(2 * k)] = make_float2(2.f * eb[i], -2.f * ea[i]);
     s[pad8(2 * k + 1)] = make_float2(2.f * (pb + ob[i]), -2.f * (pa + oa[i]));
   }
@@ -412,40 +423,12 @@ __device__ __forceinline__ void fft_rows_half512(float2* buf, const float2* twd,
 // block barrier, after which `buf` holds the transforms for the epilogue.
 template <int N, int F>
 __device__ __forceinline__ void fft_rows_any(float2* buf, const float2* twd, const float* src, int a0) {
-  if constexpr (N == 512) {
-    fft_rows_half512<N>(buf, twd, src, a0);
-    __syncthreads();
-  } else if constexpr (N == 256) {
-    fft_rows_warp512<N>(buf, twd, src, a0);
+  if constexpr (N == 512 || N == 256) {
+    fft_rows_half<N>(buf, twd, src, a0);
     __syncthreads();
   } else {
     fft_rows<N, F>(buf, twd, src, a0);
   }
-}
-
-// Grids whose row FFTs are the warp four-step ones: each warp owns its row pair's buffer row, so
-// a pass can transform rows it has just written there (fft_rows_own).
-template <int N>
-__host__ __device__ constexpr bool warp_fft() {
-  return N == 512 || N == 256;
-}
-
-// Grids whose CG iterations use the fused middle pass and the untransposed last pass. Measured
-// (fine-sweep batches, graph execution): 256 x 256, 32 units: 6.81 -> 6.74 ms; 512 x 512, 64
-// units: 126.3 -> 132.8 ms (slower: at two blocks per SM the fused pass's shared-memory-only
-// second transform leaves fewer loads in flight), so only the smaller grid takes them.
-template <int N>
-__host__ __device__ constexpr bool fuse_cg() {
-  return N == 256;
-}
-
-// The row FFTs of rows held in the buffer itself: row pair f as (x0[k], x1[k]) at
-// buf[f * buf_row + k], k < n (warp_fft grids only); ends with a block barrier.
-template <int N>
-__device__ __forceinline__ void fft_rows_own(float2* buf, const float2* twd, int a0) {
-  static_assert(N == 256, "rows held in the buffer: the 256 x 256 warp FFT");
-  fft_rows_warp512<N, true>(buf, twd, nullptr, a0);
-  __syncthreads();
 }
 
 // One transform pass: rows of `in` ([units][n][n]) -> orthonormal DST-I -> written transposed.
@@ -683,20 +666,18 @@ size_t correct_partials(int count) { return (size_t)count * 4 * kBlk; }
 // Twiddles of the stages after the first of fft_rows<N> (radix 8 with Ns = 8, 64, ..., then the
 // radix-2 or radix-4 stage), stage after stage: entry (r - 1) Ns + k = exp(-2 pi i m / L) with
 // m = r k L / (R Ns), r = 1..R-1, k < Ns (host libm, rounded to FP32). At most L entries. For
-// N = 512 and 256 the table of fft512_warp instead (and at 512 the sines of fft_rows_half512).
+// N = 512 and 256 the tables of fft512_warp / fft256_warp and the sines of fft_rows_half.
 static std::vector<float2> twiddle_table(int N) {
   const int L = 2 * N;
-  if (N == 512 || N == 256) {  // 512-point warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / 512), t < 32
+  if (N == 512 || N == 256) {  // N-point warp FFT: tw2[k1][t] = exp(-2 pi i k1 t / N), t < 32
     std::vector<float2> tw(L, make_float2(0.f, 0.f));
-    for (int k1 = 0; k1 < 16; ++k1)
+    for (int k1 = 0; k1 < N / 32; ++k1)
       for (int t = 0; t < 32; ++t) {
-        const double a = -2.0 * M_PI * k1 * t / 512;
+        const double a = -2.0 * M_PI * k1 * t / N;
         tw[k1 * 32 + t] = make_float2(float(std::cos(a)), float(std::sin(a)));
       }
-    if (N == 512) {  // then sin(pi j / N), j < N, as floats (fft_rows_half512)
-      float* sj = reinterpret_cast<float*>(tw.data() + 512);
-      for (int j = 0; j < N; ++j) sj[j] = float(std::sin(M_PI * j / N));
-    }
+    float* sj = reinterpret_cast<float*>(tw.data() + N);  // then sin(pi j / N), j < N (fft_rows_half)
+    for (int j = 0; j < N; ++j) sj[j] = float(std::sin(M_PI * j / N));
     return tw;
   }
   int lg = 0;
@@ -1235,127 +1216,6 @@ __device__ __forceinline__ void dst_item(const PArgs& a, float2* buf, const floa
   }
 }
 
-// The two middle transform passes of a CG iteration in one (warp_fft grids). In: the rows
-// [a0, a0 + kDstRows) of S p^T (the output of the first inverse pass). Their DST gives the
-// columns a0.. of p (physical space), each multiplied by dt (wc - wbar): the rows a0.. of q^T,
-// kept in the transform buffer; their DST gives the rows of q^T S, written transposed: S q.
-// The last pass then transforms rows of S q into S q S without transposing (dst_item_wn).
-// (Separately: rows of S p^T -> p, written out; rows of q -> S q^T; rows of that -> S q S.)
-template <int N>
-__device__ __forceinline__ void dst_item_wprod2(const PArgs& a, float2* buf, const float2* twd, const float* in,
-                                                float* out, int item) {
-  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
-  constexpr int KS = kThreads / kDstRows;  // output rows apart of one thread's elements
-  constexpr int J = (n + KS - 1) / KS;     // epilogue elements per thread
-  const size_t pts = (size_t)n * n;
-  const float sc = 0.5f * sqrtf(2.0f / N);
-  const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
-  if (a.flag[2 * u] || a.flag[2 * u + 1]) return;  // Newton- or CG-done unit (block-uniform)
-  fft_rows_any<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
-  const float cwb = float(__ldcg(a.scal + u * 8 + 4));
-  const int r = threadIdx.x % kDstRows, k0 = threadIdx.x / kDstRows, c = a0 + r;
-  const bool cok = c < n;
-  const size_t ob = u * pts + c;
-  float qv[J];
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int k = k0 + j * KS;
-    qv[j] = 0.f;
-    if (cok && k < n) {
-      const float wv = __ldcg(a.w + ob + (size_t)k * n);
-      const float2 cv = buf[(r >> 1) * buf_row<N>() + pad8(k + 1)];
-      const float v = (r & 1) ? cv.x * sc : -cv.y * sc;  // p[k][c]
-      qv[j] = a.fdt * (wv - cwb) * v;
-    }
-  }
-  __syncthreads();  // every transform value has been read
-  float* sq = reinterpret_cast<float*>(buf + (r >> 1) * buf_row<N>()) + (r & 1);
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int k = k0 + j * KS;
-    if (cok && k < n) sq[2 * k] = qv[j];
-  }
-  __syncthreads();
-  fft_rows_own<N>(buf, twd, a0);
-#pragma unroll 4
-  for (int j = 0; j < J; ++j) {
-    const int k = k0 + j * KS;
-    if (cok && k < n) {
-      const float2 cv = buf[(r >> 1) * buf_row<N>() + pad8(k + 1)];
-      out[ob + (size_t)k * n] = (r & 1) ? cv.x * sc : -cv.y * sc;
-    }
-  }
-}
-
-// The last transform pass of a CG iteration after dst_item_wprod2: rows c = a0.. of S q -> rows
-// of S q S, not transposed; w = m u + S q S (= S u) and the partial sums (w, u), (r, u) of the
-// item. Each warp finishes its own row pair, lanes over consecutive columns.
-template <int N>
-__device__ __forceinline__ void dst_item_wn(const PArgs& a, float2* buf, const float2* twd, const float* in,
-                                            int item) {
-  constexpr int n = N - 1, nb = (n + kDstRows - 1) / kDstRows;
-  constexpr int JW = (n + 31) / 32;  // columns per lane
-  const size_t pts = (size_t)n * n;
-  const float sc = 0.5f * sqrtf(2.0f / N);
-  const float* __restrict__ mu1 = a.mu1;
-  const int u = item / nb, b = item - u * nb, a0 = b * kDstRows;
-  if (a.flag[2 * u] || a.flag[2 * u + 1]) return;  // Newton- or CG-done unit (block-uniform)
-  fft_rows_any<N, kDstRows / 2>(buf, twd, in + u * pts, a0);
-  const float cwb = float(__ldcg(a.scal + u * 8 + 4));
-  const float fcwb = a.fdt * cwb;
-  const float fe2dt = unit_fe2dt(a, u);
-  const int f = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const float2* s = buf + f * buf_row<N>();
-  float acc = 0.f, acc2 = 0.f;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int c = a0 + 2 * f + h;
-    if (c >= n) break;  // warp-uniform
-    const float mc = mu1[c];
-    const size_t ob = u * pts + (size_t)c * n;
-    float uv[JW], rv[JW];  // all of the row's loads in flight together
-#pragma unroll
-    for (int j = 0; j < JW; ++j) {
-      const int k = l + 32 * j;
-      uv[j] = k < n ? __ldcg(a.uh + ob + k) : 0.f;
-      rv[j] = k < n ? __ldcg(a.rh + ob + k) : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < JW; ++j) {
-      const int k = l + 32 * j;
-      if (k < n) {
-        const float2 cv = s[pad8(k + 1)];
-        const float v = h ? cv.x * sc : -cv.y * sc;
-        const float w = mdiag(mu1[k] + mc, fe2dt, fcwb) * uv[j] + v;
-        a.qh[ob + k] = w;
-        acc = fmaf(w, uv[j], acc);
-        acc2 = fmaf(rv[j], uv[j], acc2);
-      }
-    }
-  }
-  // FP32 shuffle tree within each warp, the warps' sums added in FP64 in a fixed order
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
-  }
-  __shared__ float ws[2][kThreads / 32];
-  if (l == 0) {
-    ws[0][f] = acc;
-    ws[1][f] = acc2;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double wu = 0.0, ru = 0.0;
-    for (int i = 0; i < kThreads / 32; ++i) {
-      wu += (double)ws[0][i];
-      ru += (double)ws[1][i];
-    }
-    a.pdel[(size_t)u * nb + b] = wu;
-    a.pgam[(size_t)u * nb + b] = ru;
-  }
-}
-
 // A transform phase of the persistent kernel: its blocks walk the items (one call per item keeps
 // the transform's register allocation that of a single item).
 template <int N, int EPI>
@@ -1365,21 +1225,6 @@ __device__ __forceinline__ void dst_phase(const PArgs& a, float2* buf, const flo
   for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
     __syncthreads();  // the previous item's epilogue has finished reading buf
     noinl([&] { dst_item<N, EPI>(a, buf, twd, in, out, act, part, item); });
-  }
-}
-
-// The fused middle pass (LAST = false) or the untransposed last pass (LAST = true) of a CG
-// iteration as a phase of the persistent kernel (fuse_cg grids).
-template <int N, bool LAST>
-__device__ __forceinline__ void dst_phase_fused(const PArgs& a, float2* buf, const float2* twd) {
-  constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
-  for (int item = blockIdx.x; item < a.units * nb; item += gridDim.x) {
-    __syncthreads();  // the previous item's epilogue has finished reading buf
-    if constexpr (LAST) {
-      noinl([&] { dst_item_wn<N>(a, buf, twd, a.t2, item); });
-    } else {
-      noinl([&] { dst_item_wprod2<N>(a, buf, twd, a.tmp, a.t2, item); });
-    }
   }
 }
 
@@ -1907,17 +1752,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k2_persist(PArgs args) {
       for (int it = 0; it < a.cg_max; ++it) {
         noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.uh, a.tmp, 1, nullptr); });  // u to physical space
         CH_BAR();
-        if constexpr (fuse_cg<N>()) {
-          noinl([&] { dst_phase_fused<N, false>(a, buf, twd); });  // dt (wc - wbar) p, back to sine space
-          CH_BAR();
-          noinl([&] { dst_phase_fused<N, true>(a, buf, twd); });  // w = S u, (w,u), (r,u)
-        } else {
-          noinl([&] { dst_phase<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr); });  // dt (wc - wbar) p
-          CH_BAR();
-          noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr); });  // back to sine space
-          CH_BAR();
-          noinl([&] { dst_phase<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr); });  // w = S u, (w,u), (r,u)
-        }
+        noinl([&] { dst_phase<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr); });  // dt (wc - wbar) p
+        CH_BAR();
+        noinl([&] { dst_phase<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr); });  // back to sine space
+        CH_BAR();
+        noinl([&] { dst_phase<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr); });  // w = S u, (w,u), (r,u)
         CH_BAR();
         noinl([&] { ph_cg_update<N>(a, it); });
         CH_BAR();
@@ -2293,15 +2132,14 @@ namespace {
 
 // PH_P1U: the CG update of the previous iteration on the item's rows, then P1 on them;
 // PH_X1U: the update of the last iteration for units that left the CG loop at cg_max, then X1.
-// PH_P23 / PH_P4N: P2 and P3 as one pass, then P4 without the transpose (fuse_cg grids).
 enum Phase {
   PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_UPDATE,
-  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U, PH_P23, PH_P4N
+  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U
 };
 
 __host__ __device__ constexpr bool is_dst_phase(int ph) {
   return ph == PH_H1 || ph == PH_H2 || ph == PH_P1 || ph == PH_P2 || ph == PH_P3 || ph == PH_P4 || ph == PH_X1 ||
-         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U || ph == PH_P23 || ph == PH_P4N;
+         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U;
 }
 
 // Four blocks per SM: 64 registers hold the 16 complex values a lane carries through the warp
@@ -2331,12 +2169,7 @@ __global__ void __launch_bounds__(kThreads, 4) k2_phase(PArgs a, int have_prev) 
   if constexpr (PH == PH_P2) dst_item<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P3) dst_item<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P4) dst_item<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr, blockIdx.x);
-  if constexpr (PH == PH_P23) {
-    if constexpr (fuse_cg<N>()) dst_item_wprod2<N>(a, buf, twd, a.tmp, a.t2, blockIdx.x);
-  }
-  if constexpr (PH == PH_P4N) {
-    if constexpr (fuse_cg<N>()) dst_item_wn<N>(a, buf, twd, a.t2, blockIdx.x);
-  }
+
   if constexpr (PH == PH_UPDATE) ph_cg_update<N>(a, it);
   if constexpr (PH == PH_X1) dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
   if constexpr (PH == PH_P1U) {
@@ -2408,18 +2241,7 @@ cudaError_t phase_prepare() {
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X2>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_P1U>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X1U>, smem);
-  if constexpr (fuse_cg<N>()) {
-    if (e == cudaSuccess) e = prep(k2_phase<N, PH_P23>, smem);
-    if (e == cudaSuccess) e = prep(k2_phase<N, PH_P4N>, smem);
-  }
   return e;
-}
-
-// The CG's fused middle pass and untransposed last pass (fuse_cg grids) in the graph and host
-// executions; CH_2D_FUSED=0 selects the three separate passes instead.
-static bool fused_cg_passes() {
-  const char* v = std::getenv("CH_2D_FUSED");
-  return !(v && v[0] == '0');
 }
 
 // The step graph of one grid size.
@@ -2464,14 +2286,9 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   // ---- CG body
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs2, bodyC, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = phase_launch<N, PH_P1U>(a, have_prev, bs2);
-  if (fuse_cg<N>() && fused_cg_passes()) {
-    if (e == cudaSuccess) e = phase_launch<N, PH_P23>(a, have_prev, bs2);
-    if (e == cudaSuccess) e = phase_launch<N, PH_P4N>(a, have_prev, bs2);
-  } else {
-    if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
-    if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
-    if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
-  }
+  if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
+  if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
   if (e == cudaSuccess) {
     k2_cg_cond<N><<<1, kScalarThreads, 0, bs2>>>(a, hC, cg_max);
     e = cudaGetLastError();
@@ -2555,14 +2372,9 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
       hc[1] = it;
       CH_TRY(cudaMemcpyAsync(ctr, hc, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
       CH_TRY((phase_launch<N, PH_P1U>(a, have_prev, st)));
-      if (fuse_cg<N>() && fused_cg_passes()) {
-        CH_TRY((phase_launch<N, PH_P23>(a, have_prev, st)));
-        CH_TRY((phase_launch<N, PH_P4N>(a, have_prev, st)));
-      } else {
-        CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
-        CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
-        CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
-      }
+      CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
+      CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
       k2_cg_host<N><<<1, kScalarThreads, 0, st>>>(a);
       CH_TRY(cudaGetLastError());
       CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));

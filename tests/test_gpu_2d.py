@@ -37,13 +37,13 @@ def mode2(n, p, q):
 
 @pytest.mark.parametrize("n", [15, 31, 63, 127, 255, 511])
 def test_sine_transform_matches_oracle(gpu_lib, n):
-    """FP32 2D DST-I against the oracle's FP64 one, and its own inverse. At n = 511 each row's DST
-    comes from an FFT of length n + 1 whose odd coefficients are running sums of FFT outputs: their
-    rounding accumulates along the sum (FP32 emulation: 7.8e-7 of the maximum per 2D transform,
-    3.1e-6 after two), hence the looser bound there; the odd-extension FFT of the other sizes
-    stays near 1e-7."""
+    """FP32 2D DST-I against the oracle's FP64 one, and its own inverse. At n = 255 and 511 each
+    row's DST comes from an FFT of length n + 1 whose odd coefficients are running sums of FFT
+    outputs: their rounding accumulates along the sum (FP32 emulation at n = 511: 7.8e-7 of the
+    maximum per 2D transform, 3.1e-6 after two; at 255: 6.6e-7 and 1.5e-6), hence the looser
+    bound there; the odd-extension FFT of the other sizes stays near 1e-7."""
     ch = gpu_lib
-    tol = 3e-5 if n == 511 else 1e-5
+    tol = 3e-5 if n >= 255 else 1e-5
     x = np.stack([ch_inputs.initial_condition(2, n, 50 + b, kind="normal", amp=1.0).reshape(n, n)
                   for b in range(3)]).astype(np.float32)
     X = ch.sine_transform_2d(dev(x, torch.float32)).cpu().numpy()
