@@ -764,6 +764,7 @@ cudaError_t Prop2D::init(const Params2D& p, int cap, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(tw_, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status_, 0, 4 * sizeof(unsigned) + sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(cg_dev_, 0, 4 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctr_, 0, 4 * kMaxGroups * sizeof(int), st);  // [2], [3]: scalar kernels
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
@@ -1610,11 +1611,14 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
   }
 }
 
-// The CG scalars of iteration `it` for every unit still in both loops, in one block (the graph
-// execution's loop condition): gamma and delta from the unit's item partials (one warp per
-// unit, the shuffle tree of unit_reduce), the stop test (a unit whose gamma has fallen to
-// cg_tol^2 gamma_0 is done: flag set, x kept), and alpha, beta into cgs. Returns, in every
-// thread, the number of units that go on.
+// The CG scalars of iteration `it` for every unit still in both loops (the graph execution's loop
+// condition): gamma and delta from the unit's item partials (one warp per unit, the shuffle tree
+// of unit_reduce), the stop test (a unit whose gamma has fallen to cg_tol^2 gamma_0 is done: flag
+// set, x kept), and alpha, beta into cgs. The units are spread over the grid's blocks, a warp per
+// unit, so that their FP64 shuffles and divisions run on many SMs' FP64 pipes (in one block they
+// queued on one SM's: 14 us per call at 32 units). Each block adds its count of units that go on
+// to ctr[2]; the last block to finish (ctr[3]) reads the total, resets both and returns it (-1 in
+// every other thread and block).
 template <int N>
 __device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
@@ -1627,8 +1631,8 @@ __device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
     evaluated = 0ull;
   }
   __syncthreads();
-  const int l = threadIdx.x & 31;
-  for (int u = threadIdx.x >> 5; u < a.units; u += blockDim.x >> 5) {
+  const int l = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < a.units; u += gridDim.x * wpb) {
     if (__ldcg(a.flag + 2 * u) || __ldcg(a.flag + 2 * u + 1)) continue;  // warp-uniform
     double g = (l < nb) ? __ldcg(a.pgam + (size_t)u * nb + l) : 0.0;
     double d = (l < nb) ? __ldcg(a.pdel + (size_t)u * nb + l) : 0.0;
@@ -1655,11 +1659,19 @@ __device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
     }
   }
   __syncthreads();
+  int total = -1;
   if (threadIdx.x == 0) {
     atomicAdd(a.totals + 2, evaluated);
-    atomicAdd(a.totals, 1ull);
+    atomicAdd(a.ctr + 2, going);
+    __threadfence();  // this block's scalars, flags and count before its arrival
+    if (atomicAdd(a.ctr + 3, 1) == (int)gridDim.x - 1) {
+      __threadfence();
+      total = atomicExch(a.ctr + 2, 0);
+      a.ctr[3] = 0;
+      atomicAdd(a.totals, 1ull);
+    }
   }
-  return going;
+  return total;
 }
 
 // The vector updates of CG iteration j, with the scalars cg_scalars_all stored, on the rows of
@@ -2187,16 +2199,19 @@ __global__ void __launch_bounds__(kThreads, 4) k2_phase(PArgs a, int have_prev) 
 // End of a loop iteration: continue while units remain active and the cap is not reached.
 // which = 0: Newton (active slots 2, 3), 1: CG (slots 0, 1).
 // End of a CG iteration of the graph execution: the scalars of every unit (cg_scalars_all), then
-// continue while units go on and the cap is not reached.
-// One block of kScalarThreads: a warp per unit forms its sums and scalars (FP64 shuffles and
-// divisions on the narrow FP64 pipe), so more warps shorten the chain of units per warp.
-constexpr int kScalarThreads = 1024;
+// (in the last block to finish) continue while units go on and the cap is not reached. Blocks of
+// kScalarThreads, a warp per unit: scalar_blocks(units) of them.
+constexpr int kScalarThreads = 64;
+inline int scalar_blocks(int units) {
+  const int b = (units + kScalarThreads / 32 - 1) / (kScalarThreads / 32);
+  return b < 1 ? 1 : (b > 1024 ? 1024 : b);
+}
 
 template <int N>
 __global__ void __launch_bounds__(kScalarThreads) k2_cg_cond(PArgs a, cudaGraphConditionalHandle hnd, int lim) {
   const int it = a.ctr[1];
   const int going = cg_scalars_all<N>(a, it);
-  if (threadIdx.x == 0) {
+  if (going >= 0) {  // the last block's thread 0: every block has read ctr[1]
     a.ctr[1] = it + 1;
     cudaGraphSetConditional(hnd, (going > 0 && it + 1 < lim) ? 1u : 0u);
   }
@@ -2207,7 +2222,7 @@ template <int N>
 __global__ void __launch_bounds__(kScalarThreads) k2_cg_host(PArgs a) {
   const int it = a.ctr[1];
   const int going = cg_scalars_all<N>(a, it);
-  if (threadIdx.x == 0) a.active[it & 1] = going;
+  if (going >= 0) a.active[it & 1] = going;
 }
 
 __global__ void k2_cond(cudaGraphConditionalHandle hnd, int* __restrict__ ctr, const int* __restrict__ active,
@@ -2290,7 +2305,7 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
   if (e == cudaSuccess) {
-    k2_cg_cond<N><<<1, kScalarThreads, 0, bs2>>>(a, hC, cg_max);
+    k2_cg_cond<N><<<scalar_blocks(a.units), kScalarThreads, 0, bs2>>>(a, hC, cg_max);
     e = cudaGetLastError();
   }
   {
@@ -2375,7 +2390,7 @@ cudaError_t host_step_n(const PArgs& a, int have_prev, int newton_max, int cg_ma
       CH_TRY((phase_launch<N, PH_P2>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P3>(a, have_prev, st)));
       CH_TRY((phase_launch<N, PH_P4>(a, have_prev, st)));
-      k2_cg_host<N><<<1, kScalarThreads, 0, st>>>(a);
+      k2_cg_host<N><<<scalar_blocks(a.units), kScalarThreads, 0, st>>>(a);
       CH_TRY(cudaGetLastError());
       CH_TRY(cudaMemcpyAsync(act, active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CH_TRY(cudaStreamSynchronize(st));

@@ -138,7 +138,7 @@ class Prop2D {
   int* flag_ = nullptr;      // [units][2]: newton done, cg done
   int* newton_cnt_ = nullptr;  // [units] Newton iterations of the current step
   unsigned* status_ = nullptr;
-  int* ctr_ = nullptr;         // device loop counters: [0] Newton, [1] CG
+  int* ctr_ = nullptr;         // per group: [0] Newton, [1] CG iteration; [2], [3] the CG scalar kernel's sum and arrivals
   unsigned long long* cg_dev_ = nullptr;  // CG iterations (batched) since the last reset
   int* host_cnt_ = nullptr;    // pinned
   unsigned long long newton_total_ = 0;
