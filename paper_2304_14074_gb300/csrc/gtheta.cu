@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kTcpThreads, 2) k_conv_mid_tcp(const bf16* __r
 
 // First layer 1 -> 32: a1 = relu(conv(U, W1) + b1); U FP64 (inference) or FP32 (training).
 template <typename TIn>
-__global__ void __launch_bounds__(kThreads) k_conv_first(const TIn* __restrict__ u, bf16* __restrict__ y,
+__global__ void __launch_bounds__(kThreads, 4) k_conv_first(const TIn* __restrict__ u, bf16* __restrict__ y,
                                                          const float* __restrict__ P, int S, float* __restrict__ a0) {
   __shared__ float tile[kHalo * kHalo];
   __shared__ float w[9 * kC + kC];
@@ -522,15 +522,25 @@ __global__ void __launch_bounds__(kThreads) k_conv_first(const TIn* __restrict__
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap) nb[tap] = tile[(oy + tap / 3) * kHalo + ox + tap % 3];
   bf16* yo = y + (((size_t)img * S + Y) * S + X) * kC;
+  float acc[kC];
 #pragma unroll
-  for (int co = 0; co < kC; co += 2) {
-    float s0 = w[9 * kC + co], s1 = w[9 * kC + co + 1];
+  for (int co = 0; co < kC; ++co) acc[co] = w[9 * kC + co];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      s0 += w[tap * kC + co] * nb[tap];
-      s1 += w[tap * kC + co + 1] * nb[tap];
+  for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+    for (int co = 0; co < kC; ++co) acc[co] += w[tap * kC + co] * nb[tap];
+  }
+  // eight channels per 16-byte store (a pixel's 64 bytes in four stores, not sixteen)
+#pragma unroll
+  for (int c8 = 0; c8 < kC; c8 += 8) {
+    unsigned h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float lo = fmaxf(acc[c8 + 2 * q], 0.f), hi = fmaxf(acc[c8 + 2 * q + 1], 0.f);
+      h[q] = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+             ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
     }
-    *reinterpret_cast<__nv_bfloat162*>(yo + co) = __floats2bfloat162_rn(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+    *reinterpret_cast<uint4*>(yo + c8) = make_uint4(h[0], h[1], h[2], h[3]);
   }
 }
 
@@ -552,9 +562,16 @@ __global__ void __launch_bounds__(kThreads) k_conv_last(const bf16* __restrict__
   for (int tap = 0; tap < 9; ++tap) {
     const bf16* p = tile + ((oy + tap / 3) * kHalo + ox + tap % 3) * kPix;
 #pragma unroll
-    for (int ci = 0; ci < kC; ci += 2) {
-      const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + ci));
-      s += w[tap * kC + ci] * v.x + w[tap * kC + ci + 1] * v.y;
+    for (int c8 = 0; c8 < kC; c8 += 8) {
+      // eight channels per 16-byte shared load (80-byte pixel stride: conflict-free per quarter warp)
+      const uint4 raw = *reinterpret_cast<const uint4*>(p + c8);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int ci = c8 + 2 * q;
+        const float2 v = __bfloat1622float2(h[q]);
+        s += w[tap * kC + ci] * v.x + w[tap * kC + ci + 1] * v.y;
+      }
     }
   }
   const size_t o = ((size_t)img * S + Y) * S + X;
