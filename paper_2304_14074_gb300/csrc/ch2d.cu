@@ -852,7 +852,8 @@ cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int n
   // Independent units are split into up to kMaxGroups groups whose step graphs run concurrently
   // on streams of their own: each phase is a chain of dependent latencies over few blocks, so
   // concurrent groups fill the GPU that one group leaves idle.
-  const int groups = std::max(1, std::min(kMaxGroups, units / kMinGroupUnits));
+  int groups = std::max(1, std::min(kMaxGroups, units / kMinGroupUnits));
+  if (const char* ge = std::getenv("CH_2D_GROUPS")) groups = std::max(1, std::min(groups, std::atoi(ge)));
   cudaError_t e = cudaSuccess;
   if (groups > 1) {
     if (!gs_[0]) {
@@ -865,11 +866,13 @@ cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int n
     }
     if ((e = cudaEventRecord(gfork_, st)) != cudaSuccess) return e;
   }
-  for (int g = 0; g < groups; ++g) {
-    const int u0 = (int)((long long)units * g / groups), u1 = (int)((long long)units * (g + 1) / groups);
-    cudaStream_t gst = (groups > 1) ? gs_[g] : st;
-    if (groups > 1 && (e = cudaStreamWaitEvent(gst, gfork_, 0)) != cudaSuccess) return e;
-    for (int j = 0; j < nsteps; ++j) {
+  for (int g = 0; g < groups && groups > 1; ++g)
+    if ((e = cudaStreamWaitEvent(gs_[g], gfork_, 0)) != cudaSuccess) return e;
+  // step j of every group, then step j + 1: the groups' graphs are enqueued side by side
+  for (int j = 0; j < nsteps; ++j) {
+    for (int g = 0; g < groups; ++g) {
+      const int u0 = (int)((long long)units * g / groups), u1 = (int)((long long)units * (g + 1) / groups);
+      cudaStream_t gst = (groups > 1) ? gs_[g] : st;
       StepKey k{Y + (size_t)u0 * pts_, u1 - u0, scheme, dt, (scheme == SCHEME_NL && j > 0) ? 1 : 0, u0, g};
       cudaGraphExec_t ex = nullptr;
       for (auto& c : graphs_)
@@ -881,10 +884,10 @@ cudaError_t Prop2D::propagate(double* Y, int units, int scheme, double dt, int n
       if ((e = cudaGraphLaunch(ex, gst)) != cudaSuccess) return e;
       step_kernels_ += (scheme == SCHEME_NL) ? kStepKernelsNL : kStepKernelsLin;
     }
-    if (groups > 1) {
-      if ((e = cudaEventRecord(gev_[g], gst)) != cudaSuccess) return e;
-      if ((e = cudaStreamWaitEvent(st, gev_[g], 0)) != cudaSuccess) return e;
-    }
+  }
+  for (int g = 0; g < groups && groups > 1; ++g) {
+    if ((e = cudaEventRecord(gev_[g], gs_[g])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, gev_[g], 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
