@@ -19,11 +19,12 @@
 // on the diagonal, so FP32 CG reaches ~1e-6 relative accuracy; the FP64 residual sets the
 // attainable accuracy of each step.
 //
-// DST-I: the sine transform of length n is computed from the complex FFT of length L = 2(n+1)
-// of the odd extension of a row (mixed radix-8 Stockham, butterflies in registers, one shared
-// memory buffer; the first stage reads the row from global memory), two real rows packed as
-// the real and imaginary parts of one complex FFT; each pass transforms rows and writes them
-// transposed, so two passes give S X S (S the orthonormal DST-I matrix, S^2 = I).
+// DST-I: the sine transform of length n is computed from a complex FFT, two real rows packed as
+// the real and imaginary parts of one complex FFT: up to n = 127 of length L = 2(n+1), the odd
+// extension of the rows (mixed radix-8 Stockham, butterflies in registers, one shared memory
+// buffer; the first stage reads the rows from global memory); at n = 255 and 511 of length n + 1
+// (fft_rows_half: warp four-step FFTs and a running sum). Each pass transforms rows and writes
+// them transposed, so two passes give S X S (S the orthonormal DST-I matrix, S^2 = I).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -117,9 +118,6 @@ __device__ __forceinline__ float2 odd_ext(const float* __restrict__ r0, const fl
 // banks (16-way conflicts at stride 8).
 __host__ __device__ constexpr int pad8(int x) { return x + (x >> 3); }
 
-// Row stride (complex values) of the transform buffer: a padded row of L = 2N plus one value,
-// so that the eight row pairs an epilogue half-warp reads start in eight different banks (a
-// stride of 9L/8 complex values is a multiple of 32 words: all eight in one bank).
 // Length of the complex FFT behind a DST-I of length N - 1: 2N (odd extension, two rows packed)
 // except on the 256 x 256 and 512 x 512 grids, whose rows are transformed through an FFT of
 // length N (fft_rows_half).
@@ -128,6 +126,9 @@ __host__ __device__ constexpr int fft_len() {
   return (N == 512 || N == 256) ? N : 2 * N;
 }
 
+// Row stride (complex values) of the transform buffer: a padded row of the FFT length L plus one
+// value, so that the eight row pairs an epilogue half-warp reads start in eight different banks
+// (a stride of 9L/8 complex values is a multiple of 32 words: all eight in one bank).
 template <int N>
 __host__ __device__ constexpr int buf_row() {
   return fft_len<N>() + fft_len<N>() / 8 + 1;
@@ -206,16 +207,12 @@ __device__ __forceinline__ void fft_rows(float2* buf, const float2* twd, const f
   if constexpr (rem == 2) fft_stage<N, 4, F, false>(buf, twd + off, Ns, nullptr, 0);
 }
 
-// ---- Four-step FFT of length 1024, one warp per FFT (the 512 x 512 grid: L = 2(n + 1) = 1024).
-// The Stockham version above makes four passes through shared memory with a block barrier
-// after each; here each 1024-point FFT (a row pair of the odd extension) is done by one warp
-// as 1024 = 32 x 32 (Cooley-Tukey four-step): lane t holds y[32 m1 + t] for m1 < 32,
-//   (1) a 32-point FFT over m1 in registers,            Z[k1][t] = sum_m1 y[32 m1 + t] W_32^(m1 k1)
-//   (2) the twiddle W_1024^(t k1) (table tw2[k1][t]),
-//   (3) a transpose through the FFT's own row of the block buffer (rows padded to 33 entries),
-//   (4) a 32-point FFT over t in registers,             Y[k1 + 32 k2] = sum_t A[k1][t] W_32^(t k2),
-// and the result is stored where the Stockham version leaves it, so the pass epilogues read it
-// unchanged. One shared-memory round trip and warp barriers only.
+// ---- Warp FFTs (the 256 x 256 and 512 x 512 grids). The Stockham version above makes a pass
+// through shared memory with a block barrier per stage; here each row pair's FFT is done by one
+// warp as a Cooley-Tukey four-step FFT (an FFT over m1 in registers, the twiddles, a transpose
+// through the warp's own buffer row, FFTs over t split across lane groups), with one shared-
+// memory round trip and warp barriers only; the result is stored where the Stockham version
+// leaves it, so the pass epilogues read it unchanged.
 
 // exp(-2 pi i j / 32), j < 16: cos and sin of the angle, rounded to FP32 (host libm values).
 __device__ __forceinline__ float2 w32(int j) {
@@ -1810,7 +1807,7 @@ cudaError_t launch_persist(const PArgs& a, int* grid_out, cudaStream_t st) {
 }
 
 // Compiled for two blocks per SM (128 registers per thread): measured fastest at n = 255 among
-// 2, 3 and 4, and it keeps the length-1024 transform of n = 511 out of local memory.
+// 2, 3 and 4.
 template <int N>
 cudaError_t launch_persist_sel(const PArgs& a, int minb, int* grid_out, cudaStream_t st) {
   (void)minb;

@@ -19,7 +19,8 @@ enum : unsigned { ST_NEWTON = 1u, ST_NONFINITE = 2u, ST_LINSOLVE = 4u, ST_TIMEOU
 // thread-block cluster per unit running that unit's whole propagation in one launch.
 enum StepPath { PATH_GRAPH = 0, PATH_PERSISTENT = 1, PATH_HOST = 2, PATH_CLUSTER = 3 };
 
-// Grid sizes the sine transform supports: n + 1 a power of two (radix-2 FFT of length 2(n+1)).
+// Grid sizes the sine transform supports: n + 1 a power of two in 16..512 (FFTs of length
+// 2(n+1), or n + 1 at n = 255 and 511).
 bool supported_n(int n);
 
 struct Params2D {

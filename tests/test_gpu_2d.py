@@ -373,3 +373,17 @@ def test_execution_is_reported(gpu_lib, monkeypatch, env):
         pr.run()
         got = pr.execution()
     assert got == env if env else got in ("graphs", "persistent")
+
+
+def test_unit_groups_do_not_change_results(gpu_lib, monkeypatch):
+    """A batch of 16 or more units runs as up to four groups of step graphs on their own streams;
+    the units are independent, so one group or four give the same bits."""
+    ch = gpu_lib
+    n, B = 31, 32
+    u0 = np.stack([ch_inputs.initial_condition(2, n, 300 + b, amp=0.5) for b in range(B)])
+    cfg = ch.Config(dim=2, n=n, eps=0.05, T=1.0, n_slices=1, fine_steps=1, newton_tol=1e-12)
+    out = {}
+    for groups in ("1", "4"):
+        monkeypatch.setenv("CH_2D_GROUPS", groups)
+        out[groups] = ch.propagate(cfg, "nl", 2e-4, 3, dev(u0)).cpu().numpy()
+    assert np.array_equal(out["1"], out["4"])
