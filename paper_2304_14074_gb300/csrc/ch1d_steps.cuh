@@ -13,6 +13,9 @@
 //     scheme's FP64 residual to the FP64 rounding level (the same iteration as Newton's).
 // The Jacobian and step matrices are I + eps^2 dt D_h^2 + c dt (-D_h) diag(w) with D_h of
 // Eq. 3.2 (zero boundary values), solved by the partition method of ch_block_solver.cuh.
+// This header holds the steps, the kernels and the launch shapes; ch1d.cu instantiates and
+// launches the FP64 and nonlinear-scheme kernels, ch1d_lin.cu the linear fine steps with FP32
+// solves (kept apart to keep the build's longest translation unit short).
 #pragma once
 #include <cmath>
 #include <mutex>
