@@ -970,6 +970,7 @@ struct PArgs {
   double eps2;           // eps^2 of every unit, unless eps2u is set
   const double* eps2u;   // per-unit eps^2 [units] (device) or null
   int units, nsteps, scheme, zmode, newton_max, cg_max, have_prev0, frozen;
+  cudaGraphConditionalHandle hcg;  // graph path, small batches: the CG loop's condition (PH_P4S)
 };
 
 namespace {
@@ -1619,20 +1620,16 @@ __device__ __forceinline__ void ph_cg_update(const PArgs& a, int it) {
 // queued on one SM's: 14 us per call at 32 units). Each block adds its count of units that go on
 // to ctr[2]; the last block to finish (ctr[3]) reads the total, resets both and returns it (-1 in
 // every other thread and block).
+// The per-unit part of cg_scalars_all for units first, first + step, ... (a warp per unit); adds
+// the block's count of units that go on to `going` and of units evaluated to `evaluated`.
 template <int N>
-__device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
+__device__ __forceinline__ void cg_scalars_units(const PArgs& a, int it, int first, int step, int& going,
+                                                 unsigned long long& evaluated) {
   constexpr int nb = (N - 1 + kDstRows - 1) / kDstRows;
   static_assert(nb <= 32, "one partial per lane");
   const int cur = (it & 1) * 2, prev = ((it + 1) & 1) * 2;
-  __shared__ int going;
-  __shared__ unsigned long long evaluated;
-  if (threadIdx.x == 0) {
-    going = 0;
-    evaluated = 0ull;
-  }
-  __syncthreads();
-  const int l = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < a.units; u += gridDim.x * wpb) {
+  const int l = threadIdx.x & 31;
+  for (int u = first; u < a.units; u += step) {
     if (__ldcg(a.flag + 2 * u) || __ldcg(a.flag + 2 * u + 1)) continue;  // warp-uniform
     double g = (l < nb) ? __ldcg(a.pgam + (size_t)u * nb + l) : 0.0;
     double d = (l < nb) ? __ldcg(a.pdel + (size_t)u * nb + l) : 0.0;
@@ -1658,6 +1655,19 @@ __device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
       }
     }
   }
+}
+
+template <int N>
+__device__ __forceinline__ int cg_scalars_all(const PArgs& a, int it) {
+  __shared__ int going;
+  __shared__ unsigned long long evaluated;
+  if (threadIdx.x == 0) {
+    going = 0;
+    evaluated = 0ull;
+  }
+  __syncthreads();
+  const int wpb = blockDim.x >> 5;
+  cg_scalars_units<N>(a, it, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb, going, evaluated);
   __syncthreads();
   int total = -1;
   if (threadIdx.x == 0) {
@@ -2144,15 +2154,21 @@ namespace {
 
 // PH_P1U: the CG update of the previous iteration on the item's rows, then P1 on them;
 // PH_X1U: the update of the last iteration for units that left the CG loop at cg_max, then X1.
+// PH_P4S: P4, then the last block to finish forms the CG scalars of every unit and sets the CG
+// loop's condition (small batches: no separate scalar kernel).
 enum Phase {
   PH_PROLOGUE = 0, PH_PREDICT, PH_Z, PH_RESID, PH_H1, PH_H2, PH_P1, PH_P2, PH_P3, PH_P4, PH_UPDATE,
-  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U
+  PH_X1, PH_X2, PH_NEWTON_END, PH_P1U, PH_X1U, PH_P4S
 };
 
 __host__ __device__ constexpr bool is_dst_phase(int ph) {
   return ph == PH_H1 || ph == PH_H2 || ph == PH_P1 || ph == PH_P2 || ph == PH_P3 || ph == PH_P4 || ph == PH_X1 ||
-         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U;
+         ph == PH_X2 || ph == PH_P1U || ph == PH_X1U || ph == PH_P4S;
 }
+
+// Batches of at most this many units end a CG iteration with PH_P4S instead of P4 and the scalar
+// kernel: one launch fewer per CG iteration where the scalar work is a few warps' worth.
+constexpr int kFuseScalarUnits = 4;
 
 // Four blocks per SM: 64 registers hold the 16 complex values a lane carries through the warp
 // FFTs of 256 x 256 and 512 x 512 (at 256 x 256 a batch's items are then all resident).
@@ -2181,6 +2197,31 @@ __global__ void __launch_bounds__(kThreads, 4) k2_phase(PArgs a, int have_prev) 
   if constexpr (PH == PH_P2) dst_item<N, E_WPROD>(a, buf, twd, a.tmp, a.t2, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P3) dst_item<N, E_PLAIN>(a, buf, twd, a.t2, a.tmp, 1, nullptr, blockIdx.x);
   if constexpr (PH == PH_P4) dst_item<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr, blockIdx.x);
+  if constexpr (PH == PH_P4S) {
+    dst_item<N, E_W>(a, buf, twd, a.tmp, nullptr, 1, nullptr, blockIdx.x);
+    __shared__ int last, going;
+    __shared__ unsigned long long evaluated;
+    __syncthreads();  // the block's partials are written (or its unit is done)
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = (atomicAdd(a.ctr + 3, 1) == (int)gridDim.x - 1);
+      going = 0;
+      evaluated = 0ull;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();  // every block's partials before they are summed
+      cg_scalars_units<N>(a, it, threadIdx.x >> 5, kThreads >> 5, going, evaluated);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        a.ctr[3] = 0;
+        atomicAdd(a.totals + 2, evaluated);
+        atomicAdd(a.totals, 1ull);
+        a.ctr[1] = it + 1;
+        cudaGraphSetConditional(a.hcg, (going > 0 && it + 1 < a.cg_max) ? 1u : 0u);
+      }
+    }
+  }
 
   if constexpr (PH == PH_UPDATE) ph_cg_update<N>(a, it);
   if constexpr (PH == PH_X1) dst_item<N, E_PLAIN>(a, buf, twd, a.xh, a.tmp, 0, nullptr, blockIdx.x);
@@ -2256,6 +2297,7 @@ cudaError_t phase_prepare() {
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X2>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_P1U>, smem);
   if (e == cudaSuccess) e = prep(k2_phase<N, PH_X1U>, smem);
+  if (e == cudaSuccess) e = prep(k2_phase<N, PH_P4S>, smem);
   return e;
 }
 
@@ -2303,10 +2345,17 @@ cudaError_t build_step_n(const PArgs& a, int have_prev, int newton_max, int cg_m
   if (e == cudaSuccess) e = phase_launch<N, PH_P1U>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P2>(a, have_prev, bs2);
   if (e == cudaSuccess) e = phase_launch<N, PH_P3>(a, have_prev, bs2);
-  if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
-  if (e == cudaSuccess) {
-    k2_cg_cond<N><<<scalar_blocks(a.units), kScalarThreads, 0, bs2>>>(a, hC, cg_max);
-    e = cudaGetLastError();
+  if (a.units <= kFuseScalarUnits) {
+    PArgs a4 = a;
+    a4.hcg = hC;
+    a4.cg_max = cg_max;
+    if (e == cudaSuccess) e = phase_launch<N, PH_P4S>(a4, have_prev, bs2);
+  } else {
+    if (e == cudaSuccess) e = phase_launch<N, PH_P4>(a, have_prev, bs2);
+    if (e == cudaSuccess) {
+      k2_cg_cond<N><<<scalar_blocks(a.units), kScalarThreads, 0, bs2>>>(a, hC, cg_max);
+      e = cudaGetLastError();
+    }
   }
   {
     cudaGraph_t dummy = nullptr;
