@@ -67,12 +67,27 @@ template <int T>
 __device__ __forceinline__ void exchange(Smem1D<T>& sm, double first, double last, double& left,
                                          double& right) {
   const int t = threadIdx.x;
-  sm.fst[t] = first;
-  sm.lst[t] = last;
-  __syncthreads();
-  left = (t > 0) ? sm.lst[t - 1] : 0.0;
-  right = (t < T - 1) ? sm.fst[t + 1] : 0.0;
-  __syncthreads();
+  if constexpr (T == 32) {
+    // one warp: neighbours by shuffle
+    const double l = __shfl_up_sync(0xffffffffu, last, 1);
+    const double r = __shfl_down_sync(0xffffffffu, first, 1);
+    left = (t > 0) ? l : 0.0;
+    right = (t < T - 1) ? r : 0.0;
+  } else {
+    sm.fst[t] = first;
+    sm.lst[t] = last;
+    __syncthreads();
+    left = (t > 0) ? sm.lst[t - 1] : 0.0;
+    right = (t < T - 1) ? sm.fst[t + 1] : 0.0;
+    __syncthreads();
+  }
+}
+
+// Whether any thread of the CTA has the flag set (a vote when the CTA is one warp).
+template <int T>
+__device__ __forceinline__ bool cta_any(bool f) {
+  if constexpr (T == 32) return __any_sync(0xffffffffu, f);
+  else return __syncthreads_or(f) != 0;
 }
 
 struct StepCtx {
@@ -183,7 +198,7 @@ __device__ int nl_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], doub
       y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? y[2 * l + 1] - dy : 0.0;
       dm = fmax(dm, fmax(fabs(dx), fabs(dy)));
     }
-    if (__syncthreads_or(nf)) {
+    if (cta_any<T>(nf)) {
       bad = true;
       return -(m + 1);
     }
@@ -320,7 +335,7 @@ __device__ int step_mixed(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], d
       y32[q] -= dx;
       dm = fmaxf(dm, fabsf(dx));
     }
-    if (__syncthreads_or(nf)) {
+    if (cta_any<T>(nf)) {
       bad = true;
       return -(m + 1);
     }
@@ -368,7 +383,7 @@ __device__ void lin1_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], d
     y[2 * l] = (r0 + 2 * l < c.n) ? x[l].x : 0.0;
     y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? x[l].y : 0.0;
   }
-  if (__syncthreads_or(nf)) bad = true;
+  if (cta_any<T>(nf)) bad = true;
 }
 
 // One step of the linear scheme Eq. 2.5 (LIN2, Laplacian on the implicit 2 dt term), FP64 solve.
@@ -410,7 +425,7 @@ __device__ void lin2_step(Smem1D<T>& sm, const StepCtx& c, double (&y)[2 * P], d
     y[2 * l] = (r0 + 2 * l < c.n) ? x[l].x : 0.0;
     y[2 * l + 1] = (r0 + 2 * l + 1 < c.n) ? x[l].y : 0.0;
   }
-  if (__syncthreads_or(nf)) bad = true;
+  if (cta_any<T>(nf)) bad = true;
 }
 
 // Dispatch one step. Returns Newton iterations (0 for the linear schemes; negative on failure).

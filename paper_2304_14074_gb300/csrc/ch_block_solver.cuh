@@ -88,6 +88,28 @@ __device__ __forceinline__ M2<S> get_m(S (*arr)[T], int base, int t) {
   return {arr[base + 0][t], arr[base + 1][t], arr[base + 2][t], arr[base + 3][t]};
 }
 
+// Warp shuffles of the 2x2 blocks and 2-vectors: a CTA of one warp exchanges through these
+// instead of shared memory and block barriers (out-of-range lanes get their own values back,
+// which the callers do not use).
+template <typename S>
+__device__ __forceinline__ V2<S> shfl_up_v(const V2<S>& v, int s) {
+  return {__shfl_up_sync(0xffffffffu, v.x, s), __shfl_up_sync(0xffffffffu, v.y, s)};
+}
+template <typename S>
+__device__ __forceinline__ V2<S> shfl_down_v(const V2<S>& v, int s) {
+  return {__shfl_down_sync(0xffffffffu, v.x, s), __shfl_down_sync(0xffffffffu, v.y, s)};
+}
+template <typename S>
+__device__ __forceinline__ M2<S> shfl_up_m(const M2<S>& m, int s) {
+  return {__shfl_up_sync(0xffffffffu, m.a, s), __shfl_up_sync(0xffffffffu, m.b, s),
+          __shfl_up_sync(0xffffffffu, m.c, s), __shfl_up_sync(0xffffffffu, m.d, s)};
+}
+template <typename S>
+__device__ __forceinline__ M2<S> shfl_down_m(const M2<S>& m, int s) {
+  return {__shfl_down_sync(0xffffffffu, m.a, s), __shfl_down_sync(0xffffffffu, m.b, s),
+          __shfl_down_sync(0xffffffffu, m.c, s), __shfl_down_sync(0xffffffffu, m.d, s)};
+}
+
 // Solve the block-tridiagonal system held as (A[l], B[l], C[l], d[l]), l = 0..P-1 of thread t
 // (block row t*P + l). Block rows beyond the system are identity rows with zero couplings.
 // On return x[l] holds the solution. All threads of the CTA must call this.
@@ -118,27 +140,37 @@ __device__ void block_tridiag_solve(const M2<S> (&A)[P], const M2<S> (&B)[P], co
     V2<S> g = mvec(Binv[P - 1], dd[P - 1]);
     M2<S> G = mneg(mmul(Binv[P - 1], Et[P - 1]));
     M2<S> H = mneg(mmul(Binv[P - 1], C[P - 1]));
-    // publish the last-interior representation for thread t+1
-    sm.nbr[0][t] = g.x;
-    sm.nbr[1][t] = g.y;
-    put_m<S, T>(sm.nbr, 2, t, G);
-    put_m<S, T>(sm.nbr, 6, t, H);
+    // publish the last-interior representation for thread t+1 (one warp: shuffles)
+    V2<S> gL;
+    M2<S> GL, HL;
+    if constexpr (T == 32) {
+      gL = shfl_up_v(g, 1);
+      GL = shfl_up_m(G, 1);
+      HL = shfl_up_m(H, 1);
+    } else {
+      sm.nbr[0][t] = g.x;
+      sm.nbr[1][t] = g.y;
+      put_m<S, T>(sm.nbr, 2, t, G);
+      put_m<S, T>(sm.nbr, 6, t, H);
+    }
 #pragma unroll
     for (int l = P - 2; l >= 1; --l) {
       g = mvec(Binv[l], vsub(dd[l], mvec(C[l], g)));
       G = mneg(mmul(Binv[l], madd(Et[l], mmul(C[l], G))));
       H = mneg(mmul(Binv[l], mmul(C[l], H)));
     }
-    __syncthreads();
+    if constexpr (T != 32) __syncthreads();
     // reduced row of separator t: A0 x_{i0-1} + B0 S_t + C0 x_{i0+1} = d0
     RB = madd(B[0], mmul(C[0], G));
     Rd = vsub(d[0], mvec(C[0], g));
     RC = mmul(C[0], H);
     RA = mzero<S>();
     if (t > 0) {
-      const V2<S> gL = {sm.nbr[0][t - 1], sm.nbr[1][t - 1]};
-      const M2<S> GL = get_m<S, T>(sm.nbr, 2, t - 1);
-      const M2<S> HL = get_m<S, T>(sm.nbr, 6, t - 1);
+      if constexpr (T != 32) {
+        gL = {sm.nbr[0][t - 1], sm.nbr[1][t - 1]};
+        GL = get_m<S, T>(sm.nbr, 2, t - 1);
+        HL = get_m<S, T>(sm.nbr, 6, t - 1);
+      }
       RA = mmul(A[0], GL);
       RB = madd(RB, mmul(A[0], HL));
       Rd = vsub(Rd, mvec(A[0], gL));
@@ -152,47 +184,72 @@ __device__ void block_tridiag_solve(const M2<S> (&A)[P], const M2<S> (&B)[P], co
   // ---- 2. block parallel cyclic reduction on the T separators
 #pragma unroll 1
   for (int s = 1; s < T; s <<= 1) {
-    put_m<S, T>(sm.red, 0, t, RA);
-    put_m<S, T>(sm.red, 4, t, RB);
-    put_m<S, T>(sm.red, 8, t, RC);
-    sm.red[12][t] = Rd.x;
-    sm.red[13][t] = Rd.y;
-    __syncthreads();
     M2<S> nA = mzero<S>(), nC = mzero<S>();
     M2<S> nB = RB;
     V2<S> nd = Rd;
-    if (t - s >= 0) {
-      const M2<S> al = mneg(mmul(RA, minv(get_m<S, T>(sm.red, 4, t - s))));
-      nA = mmul(al, get_m<S, T>(sm.red, 0, t - s));
-      nB = madd(nB, mmul(al, get_m<S, T>(sm.red, 8, t - s)));
-      nd = vadd(nd, mvec(al, V2<S>{sm.red[12][t - s], sm.red[13][t - s]}));
-    }
-    if (t + s < T) {
-      const M2<S> ga = mneg(mmul(RC, minv(get_m<S, T>(sm.red, 4, t + s))));
-      nC = mmul(ga, get_m<S, T>(sm.red, 8, t + s));
-      nB = madd(nB, mmul(ga, get_m<S, T>(sm.red, 0, t + s)));
-      nd = vadd(nd, mvec(ga, V2<S>{sm.red[12][t + s], sm.red[13][t + s]}));
+    if constexpr (T == 32) {
+      // the rows of separators t - s and t + s by shuffles (one warp)
+      const M2<S> Am = shfl_up_m(RA, s), Bm = shfl_up_m(RB, s), Cm = shfl_up_m(RC, s);
+      const V2<S> dm = shfl_up_v(Rd, s);
+      const M2<S> Ap = shfl_down_m(RA, s), Bp = shfl_down_m(RB, s), Cp = shfl_down_m(RC, s);
+      const V2<S> dp = shfl_down_v(Rd, s);
+      if (t - s >= 0) {
+        const M2<S> al = mneg(mmul(RA, minv(Bm)));
+        nA = mmul(al, Am);
+        nB = madd(nB, mmul(al, Cm));
+        nd = vadd(nd, mvec(al, dm));
+      }
+      if (t + s < T) {
+        const M2<S> ga = mneg(mmul(RC, minv(Bp)));
+        nC = mmul(ga, Cp);
+        nB = madd(nB, mmul(ga, Ap));
+        nd = vadd(nd, mvec(ga, dp));
+      }
+    } else {
+      put_m<S, T>(sm.red, 0, t, RA);
+      put_m<S, T>(sm.red, 4, t, RB);
+      put_m<S, T>(sm.red, 8, t, RC);
+      sm.red[12][t] = Rd.x;
+      sm.red[13][t] = Rd.y;
+      __syncthreads();
+      if (t - s >= 0) {
+        const M2<S> al = mneg(mmul(RA, minv(get_m<S, T>(sm.red, 4, t - s))));
+        nA = mmul(al, get_m<S, T>(sm.red, 0, t - s));
+        nB = madd(nB, mmul(al, get_m<S, T>(sm.red, 8, t - s)));
+        nd = vadd(nd, mvec(al, V2<S>{sm.red[12][t - s], sm.red[13][t - s]}));
+      }
+      if (t + s < T) {
+        const M2<S> ga = mneg(mmul(RC, minv(get_m<S, T>(sm.red, 4, t + s))));
+        nC = mmul(ga, get_m<S, T>(sm.red, 8, t + s));
+        nB = madd(nB, mmul(ga, get_m<S, T>(sm.red, 0, t + s)));
+        nd = vadd(nd, mvec(ga, V2<S>{sm.red[12][t + s], sm.red[13][t + s]}));
+      }
     }
     RA = nA;
     RB = nB;
     RC = nC;
     Rd = nd;
-    __syncthreads();
+    if constexpr (T != 32) __syncthreads();
   }
   const V2<S> St = mvec(minv(RB), Rd);
   x[0] = St;
   if constexpr (P >= 2) {
     // ---- 3. back-substitution with S_t and S_{t+1}
-    sm.sep[0][t] = St.x;
-    sm.sep[1][t] = St.y;
-    __syncthreads();
     V2<S> Sn = {S(0), S(0)};
-    if (t + 1 < T) Sn = {sm.sep[0][t + 1], sm.sep[1][t + 1]};
+    if constexpr (T == 32) {
+      const V2<S> sd = shfl_down_v(St, 1);
+      if (t + 1 < T) Sn = sd;
+    } else {
+      sm.sep[0][t] = St.x;
+      sm.sep[1][t] = St.y;
+      __syncthreads();
+      if (t + 1 < T) Sn = {sm.sep[0][t + 1], sm.sep[1][t + 1]};
+    }
     x[P - 1] = mvec(Binv[P - 1], vsub(vsub(dd[P - 1], mvec(Et[P - 1], St)), mvec(C[P - 1], Sn)));
 #pragma unroll
     for (int l = P - 2; l >= 1; --l)
       x[l] = mvec(Binv[l], vsub(vsub(dd[l], mvec(Et[l], St)), mvec(C[l], x[l + 1])));
-    __syncthreads();
+    if constexpr (T != 32) __syncthreads();
   }
 }
 
@@ -208,6 +265,7 @@ template <int T>
 __device__ __forceinline__ double cta_max(double v, ReduceSmem<T>& sm) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if constexpr (T == 32) return v;
   if ((threadIdx.x & 31) == 0) sm.v[threadIdx.x >> 5] = v;
   __syncthreads();
   double r = sm.v[0];
@@ -221,6 +279,7 @@ template <int T>
 __device__ __forceinline__ float cta_max_f(float v, ReduceSmem<T>& sm) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if constexpr (T == 32) return v;
   if ((threadIdx.x & 31) == 0) sm.v[threadIdx.x >> 5] = v;
   __syncthreads();
   float r = float(sm.v[0]);
@@ -238,6 +297,7 @@ __device__ __forceinline__ void cta_sum_max(double& s, double& m, ReduceSmem<T>&
     s += __shfl_xor_sync(0xffffffffu, s, o);
     m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   }
+  if constexpr (T == 32) return;
   if ((threadIdx.x & 31) == 0) {
     sm.v[threadIdx.x >> 5] = s;
     sm.w[threadIdx.x >> 5] = m;
