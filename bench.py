@@ -443,7 +443,7 @@ def bench_ours(args, w, rank, world, local_rank):
 
     ttol = None
     if w.get("ttol") and not args.no_ttol and rank == 0:
-        ttol = time_to_tolerance(ch, w, u0, stream)
+        ttol = time_to_tolerance(ch, w, u0, stream, metrics_jsonl=args.metrics_jsonl)
         if w["variant"].startswith("PA"):
             ttol["theory_bound"] = theory_vs_measured(ch, w, u0, stream, ttol.pop("err_ratio"))
         else:
@@ -640,9 +640,10 @@ def measured_peaks():
         return {}
 
 
-def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
+def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8, metrics_jsonl=None):
     """Plain-G Parareal until every problem is within err_tol (max_n L2_h) of the sequential fine
-    solution; reports the device time of the Parareal run and of the serial fine solve."""
+    solution; reports the device time of the Parareal run and of the serial fine solve. With
+    metrics_jsonl, every problem's per-iteration history is appended to that file."""
     import torch
     B, N = w["batch"], w["N"]
     cfg = ch.Config(dim=w.get("dim", 1), n=w["n"], eps=w["eps"], T=w["T"], n_slices=N, fine_steps=w["J"],
@@ -660,6 +661,10 @@ def time_to_tolerance(ch, w, u0, stream, err_tol=1e-8):
     serial_ms = a.elapsed_time(b)
     status = pr.run()
     stats = [pr.stats(i) for i in range(B)]
+    if metrics_jsonl:
+        for i, st in enumerate(stats):
+            ch.append_jsonl(metrics_jsonl, ch.stats_records(st, workload=w["name"], run="time_to_1e-8", problem=i,
+                                                            status=int(status)))
     iters = max(s["iterations"] for s in stats)
     t_ms = stats[0]["t_iter_ms"][iters]
     worst = max(s["err_l2"][s["iterations"]] for s in stats)
@@ -872,6 +877,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain coarse propagator run")
     ap.add_argument("--no-2d", action="store_true", help="skip the 512 x 512 2D step (roofline_2d)")
+    ap.add_argument("--metrics-jsonl", default=None,
+                    help="append the time-to-1e-8 run's per-iteration history of every problem to this file")
     ap.add_argument("--experiment", choices=["learned-c4", "sweep2d", "c5", "gtheta-fwd"], default=None,
                     help="learned-c4: learned vs plain coarse propagator to 1e-8 on the 512 x 512 configuration "
                          "(training included); sweep2d: the 2D fine propagation of one Parareal fine sweep of a 2D "

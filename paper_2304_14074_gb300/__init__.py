@@ -8,9 +8,11 @@ package is the thin Python binding of that ABI.
 from ._lib import (CH_GTHETA_PARAMS, CH_MAX_ITERS, EXPORTED_SYMBOLS, SCHEMES, STATUS, VARIANTS, ChError, Config,
                    Ensemble, GTheta, Parareal, gtheta_flatten, gtheta_unflatten, load, propagate, sine_transform_2d,
                    theory_bound, wait_selftest)
+from .metrics import append_jsonl, stats_records
 from .build import LIB as LIBRARY_PATH
 from .build import build
 
 __all__ = ["CH_GTHETA_PARAMS", "CH_MAX_ITERS", "EXPORTED_SYMBOLS", "SCHEMES", "STATUS", "VARIANTS", "ChError",
            "Config", "Ensemble", "GTheta", "Parareal", "gtheta_flatten", "gtheta_unflatten", "load", "propagate",
-           "sine_transform_2d", "theory_bound", "wait_selftest", "build", "LIBRARY_PATH"]
+           "sine_transform_2d", "theory_bound", "wait_selftest", "build", "LIBRARY_PATH", "stats_records",
+           "append_jsonl"]

@@ -16,6 +16,7 @@
 #include "ch1d.cuh"
 #include "ch2d.cuh"
 #include "ch_parareal.h"
+#include "ch_trace.cuh"
 #include "ch_config_check.h"
 #include "gtheta.cuh"
 
@@ -331,13 +332,16 @@ ch_status run2d(ch_parareal* h) {
   std::vector<long long> off(L.size());
   for (size_t i = 0; i < L.size(); ++i) off[i] = (long long)(L[i] * us);
   ch_status s = gather_units(h, h->U, off, true);
-  for (int k = 0; k < N && s == CH_OK; ++k) {
-    s = coarse_rows(h, (int)L.size(), nl);
-    if (s != CH_OK) break;
-    CH_CUDA(h, chg2::launch_correct(h->U + (k + 1) * pts, h->F + k * pts, h->W, h->Gold + k * pts,
-                                    ref ? ref + (k + 1) * pts : nullptr, h->dlist, (int)L.size(), pts, us, fs, 1,
-                                    h->cpart, h->acc, h2, h->st));
-    h->aux_launches += 2;
+  {
+    chtrace::Range range("coarse initial sweep");
+    for (int k = 0; k < N && s == CH_OK; ++k) {
+      s = coarse_rows(h, (int)L.size(), nl);
+      if (s != CH_OK) break;
+      CH_CUDA(h, chg2::launch_correct(h->U + (k + 1) * pts, h->F + k * pts, h->W, h->Gold + k * pts,
+                                      ref ? ref + (k + 1) * pts : nullptr, h->dlist, (int)L.size(), pts, us, fs, 1,
+                                      h->cpart, h->acc, h2, h->st));
+      h->aux_launches += 2;
+    }
   }
   if (s != CH_OK) return s;
   if ((s = pull_acc()) != CH_OK) return s;
@@ -376,9 +380,12 @@ ch_status run2d(ch_parareal* h) {
     const unsigned long long n0 = h->p2->newton_iterations();
     const long long c0 = h->p2->cg_unit_iterations();
     CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
-    if ((s = gather_units(h, h->U, uoff, true)) != CH_OK) return s;
-    if ((s = prop2(h, (int)uoff.size(), fine2(h), h->p.dt, h->p.J)) != CH_OK) return s;
-    if ((s = gather_units(h, h->F, foff, false)) != CH_OK) return s;
+    {
+      chtrace::Range range("fine sweep");
+      if ((s = gather_units(h, h->U, uoff, true)) != CH_OK) return s;
+      if ((s = prop2(h, (int)uoff.size(), fine2(h), h->p.dt, h->p.J)) != CH_OK) return s;
+      if ((s = gather_units(h, h->F, foff, false)) != CH_OK) return s;
+    }
     CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
     const unsigned st_fine = h->p2->read_status(h->st);
     h->fine_newton += h->p2->newton_iterations() - n0;
@@ -388,13 +395,16 @@ ch_status run2d(ch_parareal* h) {
     CH_CUDA(h, cudaMemsetAsync(h->acc, 0, 4 * B * sizeof(double), h->st));
     off.resize(nb);
     for (int i = 0; i < nb; ++i) off[i] = (long long)(L[i] * us + k * pts);
-    if ((s = gather_units(h, h->U, off, true)) != CH_OK) return s;
-    for (int sl = k; sl < N; ++sl) {
-      if ((s = coarse_rows(h, nb, nl)) != CH_OK) return s;
-      CH_CUDA(h, chg2::launch_correct(h->U + (sl + 1) * pts, h->F + sl * pts, h->W, h->Gold + sl * pts,
-                                      ref ? ref + (sl + 1) * pts : nullptr, h->dlist, nb, pts, us, fs, 0, h->cpart,
-                                      h->acc, h2, h->st));
-      h->aux_launches += 2;
+    {
+      chtrace::Range range("coarse sweep");
+      if ((s = gather_units(h, h->U, off, true)) != CH_OK) return s;
+      for (int sl = k; sl < N; ++sl) {
+        if ((s = coarse_rows(h, nb, nl)) != CH_OK) return s;
+        CH_CUDA(h, chg2::launch_correct(h->U + (sl + 1) * pts, h->F + sl * pts, h->W, h->Gold + sl * pts,
+                                        ref ? ref + (sl + 1) * pts : nullptr, h->dlist, nb, pts, us, fs, 0,
+                                        h->cpart, h->acc, h2, h->st));
+        h->aux_launches += 2;
+      }
     }
     CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
     CH_CUDA(h, cudaEventRecord(h->ev[k + 2], h->st));
@@ -512,6 +522,7 @@ void tune_save_locked() {
 ch_status tune_fine_sweep(ch_parareal* h) {
   const char* off = std::getenv("CH_AUTOTUNE");
   if (off && std::strcmp(off, "0") == 0) return CH_OK;
+  chtrace::Range range("autotune");
   const std::string key = tune_key(h->p);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -595,6 +606,7 @@ ch_status ensure_tuned2d(ch_parareal* h) {
   if (h->tuned) return CH_OK;
   h->tuned = true;
   if (std::getenv("CH_2D_STEP")) return CH_OK;
+  chtrace::Range range("autotune");
   const char* off = std::getenv("CH_AUTOTUNE");
   if (off && std::strcmp(off, "0") == 0) return CH_OK;
   const int units = h->B * h->p.N;
@@ -836,6 +848,7 @@ static bool all_initial(const ch_parareal* h) {
 
 ch_status ch_parareal_compute_reference(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
+  chtrace::Range range("ch_parareal_compute_reference");
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "compute_reference before set_initial");
   if (h->dim == 2) {
@@ -892,6 +905,7 @@ extern "C" {
 
 ch_status ch_parareal_run(ch_parareal* h) {
   if (!h) return CH_ERR_INVALID;
+  chtrace::Range range("ch_parareal_run");
   if (h->sticky != CH_OK) return h->sticky;
   if (!all_initial(h)) return fail(h, CH_ERR_STATE, "run before set_initial");
   if (h->dim == 2) {
@@ -913,7 +927,10 @@ ch_status ch_parareal_run(ch_parareal* h) {
   CH_CUDA(h, cudaMemcpyAsync(h->ps.active, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice, h->st));
   const double* ref = h->ref_valid ? h->Uref : nullptr;
   CH_CUDA(h, cudaEventRecord(h->ev[0], h->st));
-  CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 1, h->st));
+  {
+    chtrace::Range r_init("coarse initial sweep");
+    CH_CUDA(h, chg::launch_coarse_sweep(h->p, h->U, h->F, h->Gold, ref, h->ctrl, h->ps, 1, h->st));
+  }
   CH_CUDA(h, cudaEventRecord(h->ev[1], h->st));
   // The iteration graphs read k and the active set from device memory, so one capture
   // serves every iteration.
@@ -941,9 +958,15 @@ ch_status ch_parareal_run(ch_parareal* h) {
   for (; k < maxit && active > 0; ++k) {
     h->active_before.push_back(active);
     CH_CUDA(h, cudaEventRecord(h->ph[0], h->st));
-    CH_CUDA(h, cudaGraphLaunch(h->gfine, h->st));
+    {
+      chtrace::Range r_fine("fine sweep");
+      CH_CUDA(h, cudaGraphLaunch(h->gfine, h->st));
+    }
     CH_CUDA(h, cudaEventRecord(h->ph[1], h->st));
-    CH_CUDA(h, cudaGraphLaunch(h->gcoarse, h->st));
+    {
+      chtrace::Range r_coarse("coarse sweep");
+      CH_CUDA(h, cudaGraphLaunch(h->gcoarse, h->st));
+    }
     CH_CUDA(h, cudaEventRecord(h->ph[2], h->st));
     CH_CUDA(h, cudaEventRecord(h->ev[k + 2], h->st));
     CH_CUDA(h, cudaStreamSynchronize(h->st));
@@ -1183,6 +1206,7 @@ ch_status ch_sine_transform_2d(const float* in_dev, float* out_dev, int batch, i
 
 ch_status ch_propagate(const ch_config* cfg, int batch, int scheme, double dt, int nsteps, const double* u_in_dev,
                        double* u_out_dev, int* newton_dev, void* cuda_stream) {
+  chtrace::Range range("ch_propagate");
   std::string why;
   if (!valid_common(cfg, why) || batch < 1 || nsteps < 0 || !(dt > 0.0) || !u_in_dev || !u_out_dev ||
       scheme < CH_SCHEME_LIN1 || scheme > CH_SCHEME_LIN2)

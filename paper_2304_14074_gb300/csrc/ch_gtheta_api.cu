@@ -5,6 +5,7 @@
 #include <string>
 
 #include "ch_parareal.h"
+#include "ch_trace.cuh"
 #include "ch_wait.cuh"
 #include "gtheta.cuh"
 
@@ -98,6 +99,7 @@ ch_status ch_gtheta_get_params(ch_gtheta* g, float* params_host, size_t len) {
 ch_status ch_gtheta_forward(ch_gtheta* g, const double* in_dev, const double* base_dev, double* out_dev, int batch,
                             int n) {
   if (!g) return CH_ERR_INVALID;
+  chtrace::Range range("G_theta forward");
   if (g->sticky != CH_OK) return g->sticky;
   if (!in_dev || !out_dev || batch < 1 || batch > 65535 || n < 1 || n > 65535)
     return gfail(g, CH_ERR_INVALID, "forward: bad arguments");
@@ -119,6 +121,7 @@ ch_status ch_gtheta_activations(ch_gtheta* g, const double* in_dev, int batch, i
 ch_status ch_gtheta_gradients(ch_gtheta* g, const float* in_dev, const float* target_dev, int batch, int S,
                               int margin, float* grad_host, size_t len, float* loss_host) {
   if (!g) return CH_ERR_INVALID;
+  chtrace::Range range("G_theta gradients");
   if (g->sticky != CH_OK) return g->sticky;
   if (!in_dev || !target_dev || !grad_host || len != (size_t)CH_GTHETA_PARAMS || batch < 1 || S < 1 || S > 4096 ||
       margin < 0 || 2 * margin >= S)
@@ -147,6 +150,7 @@ ch_status ch_gtheta_train(ch_gtheta* g, const double* states_dev, const double* 
                           int n, int stride, int steps, int batch, double lr, unsigned long long seed,
                           float* losses_host) {
   if (!g) return CH_ERR_INVALID;
+  chtrace::Range range("G_theta training");
   if (g->sticky != CH_OK) return g->sticky;
   if (!states_dev || ntraj < 1 || stride < 1 || nsnap <= stride || n < 1 || n > 65535 || steps < 1 || batch < 1 ||
       batch > 65535 || !(lr > 0.0))

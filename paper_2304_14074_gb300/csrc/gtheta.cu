@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "ch_ctx.cuh"
+#include "ch_trace.cuh"
 #include "ch_wait.cuh"
 #include "gtheta.cuh"
 
@@ -1150,6 +1151,7 @@ cudaError_t GTheta::train(const double* states, const double* base, int ntraj, i
   uint64_t s = seed;
   const int span = n + 2 * margin - S + 1;  // crop origins in [-margin, n + margin - S]
   for (int it = 0; it < steps && e == cudaSuccess; ++it) {
+    chtrace::Range range("training step");
     for (int b = 0; b < batch; ++b) {
       crops[b].x = (int)(splitmix(s) % (uint64_t)ntraj);
       crops[b].y = (int)(splitmix(s) % (uint64_t)(nsnap - stride));
