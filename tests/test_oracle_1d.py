@@ -112,6 +112,39 @@ def test_newton_step_solves_nonlinear_system():
     assert 2 <= iters <= 8
 
 
+def _dh_extended(v, n):
+    """D_h (Eq. 3.2, zero Dirichlet values) in numpy's extended precision."""
+    w = np.zeros(n + 2, dtype=np.longdouble)
+    w[1:-1] = v
+    return (w[:-2] - 2 * w[1:-1] + w[2:]) * np.longdouble((n + 1) ** 2)
+
+
+@pytest.mark.parametrize("n,eps,dt,amp,tol", [
+    (1024, 0.02, 1.0 / (64 * 200), 0.1, 1e-12),  # the 1D nonlinear workload's grid and fine step
+    (1024, 0.02, 1.0 / (64 * 200), 0.9, 1e-12),  # same, states near the wells: the floor exit decides
+    (255, 0.02, 1e-4, 0.9, 1e-10),
+    (63, 0.1, 1e-3, 0.9, 1e-12),
+])
+def test_newton_stops_at_the_root_within_the_rounding_floor(n, eps, dt, amp, tol):
+    """Where Newton stops, by the increment test or by the rounding-floor exit (an increment
+    below sqrt(tol) that fails to halve), the step is the root of Eq. 3.17 to within
+    max(tol, u * 16 eps^2 dt / h^4 * max|Y|): one Newton correction with the residual evaluated
+    in extended precision moves it by no more. An exit that accepted a slowly converging
+    iterate (up to sqrt(tol) = 1e-6 here) would fail this."""
+    if np.finfo(np.longdouble).eps >= np.finfo(np.float64).eps:
+        pytest.skip("no extended precision on this platform")
+    u = ch_inputs.initial_condition(1, n, 3, amp=amp)
+    y, _ = o.step(o.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=tol), "nl", dt, u)
+    Y, U, dtl = y.astype(np.longdouble), u.astype(np.longdouble), np.longdouble(dt)
+    H = (Y + np.longdouble(eps) ** 2 * dtl * _dh_extended(_dh_extended(Y, n), n) - dtl * _dh_extended(Y ** 3, n)
+         - (U - dtl * _dh_extended(U, n)))
+    D = dense_dh(n)
+    Jac = np.eye(n) + eps ** 2 * dt * D @ D - 3 * dt * D @ np.diag(y ** 2)
+    dist = np.max(np.abs(np.linalg.solve(Jac, H.astype(np.float64))))
+    floor = np.finfo(np.float64).eps * 16 * eps ** 2 * dt * (n + 1) ** 4 * np.max(np.abs(y))
+    assert dist <= max(tol, floor), (dist, tol, floor)
+
+
 def test_newton_forms_reach_the_same_root():
     """Eq. 3.18 as printed and the unsimplified Newton step give the same step to rounding."""
     n, eps, dt = 40, 0.1, 2e-3
