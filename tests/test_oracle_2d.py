@@ -66,6 +66,39 @@ def test_newton_step_is_root_of_eq_3_17():
     assert 2 <= m <= 8
 
 
+def _dh2_extended(v, n):
+    """2D D_h (five-point, zero Dirichlet values, row-major) in numpy's extended precision."""
+    w = np.zeros((n + 2, n + 2), dtype=np.longdouble)
+    w[1:-1, 1:-1] = v.reshape(n, n)
+    out = w[:-2, 1:-1] + w[2:, 1:-1] + w[1:-1, :-2] + w[1:-1, 2:] - 4 * w[1:-1, 1:-1]
+    return (out * np.longdouble((n + 1) ** 2)).reshape(-1)
+
+
+@pytest.mark.parametrize("n,eps,dt,tol", [
+    (63, 0.01, 2.0 / (64 * 100), 1e-12),   # the 512 x 512 workload's eps and fine step, coarser grid
+    (127, 0.01, 2.0 / (64 * 100), 1e-12),
+    (63, 0.05, 1e-3, 1e-10),
+])
+def test_newton_stops_at_the_root_within_the_rounding_floor_2d(n, eps, dt, tol):
+    """2D counterpart of the 1D pin: wherever Newton stops, one correction with the residual of
+    Eq. 3.17 evaluated in extended precision moves the step by at most
+    max(tol, u * 64 eps^2 dt / h^4 * max|Y|)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    if np.finfo(np.longdouble).eps >= np.finfo(np.float64).eps:
+        pytest.skip("no extended precision on this platform")
+    u = ch_inputs.initial_condition(2, n, 5, amp=0.9)
+    y, _ = o2.step(o2.Params(n=n, eps=eps, T=1, N=1, J=1, newton_tol=tol), "nl", dt, u)
+    Y, U, dtl = y.astype(np.longdouble), u.astype(np.longdouble), np.longdouble(dt)
+    H = (Y + np.longdouble(eps) ** 2 * dtl * _dh2_extended(_dh2_extended(Y, n), n) - dtl * _dh2_extended(Y ** 3, n)
+         - (U - dtl * _dh2_extended(U, n)))
+    D = o2.dh_matrix(n)
+    Jac = sp.identity(n * n, format="csc") + eps ** 2 * dt * (D @ D) - 3 * dt * (D @ sp.diags(y ** 2))
+    dist = np.max(np.abs(spl.spsolve(Jac.tocsc(), H.astype(np.float64))))
+    floor = np.finfo(np.float64).eps * 64 * eps ** 2 * dt * (n + 1) ** 4 * np.max(np.abs(y))
+    assert dist <= max(tol, floor), (dist, tol, floor)
+
+
 @pytest.mark.parametrize("scheme,i", [("lin1", 1), ("lin2", 2), ("nl", 1)])
 def test_frozen_step_factor_lemma_3_1(scheme, i):
     n, eps, dt = 15, 0.07, 2e-3
